@@ -1,0 +1,190 @@
+/*
+ * dgwedge -- nodal discontinuous Galerkin for the first-order acoustic wave
+ * equation on hybrid meshes of vertically mapped wedges and tetrahedra,
+ * following Chan, Wang, Hewett & Warburton, "Reduced storage nodal
+ * discontinuous Galerkin methods on semi-structured prismatic meshes".
+ *
+ * C ABI.  Plain pointers and sizes only.  Every call returns a dg_status
+ * (0 = success); no exception, abort or device trap ever crosses this
+ * boundary.  dg_last_error() gives a one-line description of the last failure
+ * on a context.
+ *
+ * Problem (Section 2, eq. (1)):
+ *   (1/kappa) dp/dt + div u = 0,   rho du/dt + grad p = 0,   kappa = rho c^2,
+ * with rho and c constant per element, strong DG form with penalty fluxes
+ *   F_p = 1/2 (tau_p [p] - n.[u]),  F_u = 1/2 (tau_u [u].n - [p]),
+ *   tau_p = 1/{rho c}, tau_u = {rho c} (upwind) or tau = 0 (central),
+ * where [x] = x_neighbour - x_own and {rho c} is the two-sided average.
+ * Boundary ghosts: Dirichlet (p+ = -p-, u+ = u-, Section 2) or rigid wall
+ * (p+ = p-, u+ = u- - 2 (n.u-) n).
+ *
+ * Discretisation: degree-N nodal bases (Section 3.1).  Wedges use the exact,
+ * Jacobian-weighted mass matrix M^k = M^{tri,k} (x) M^1D (Section 4.2), with all
+ * geometric factors recomputed from the six vertices on every evaluation
+ * (Lemma 3.1); nothing per element is stored but vertex ids, neighbour ids and
+ * material.  Time integration: five-stage fourth-order low-storage
+ * Runge-Kutta (Carpenter & Kennedy 1994), res <- a_s res + dt f(q),
+ * q <- q + b_s res.
+ *
+ * Canonical field layout (used by dg_set_fields, dg_get_fields, dg_rhs and
+ * dg_node_coords): q[4][total_nodes], fields (p, u_x, u_y, u_z); nodes ordered
+ * element by element in input order, each element contiguous:
+ *   wedge: node n = j * Nt + i, j = 0..N the GLL index along the extruded
+ *          (vertex 0 -> vertex 3) direction, i the triangle node;
+ *   triangle node order: for b = 0..N, for a = 0..N-b  (barycentric weights
+ *          (N-a-b, a, b)/N on vertices (0, 1, 2) before warping);
+ *   tet:   for c = 0..N, for b = 0..N-c, for a = 0..N-b-c  (weights
+ *          (N-a-b-c, a, b, c)/N on vertices (0, 1, 2, 3) before warping).
+ * Nodes are Warp & Blend points (tet) and the tet's face points x GLL (wedge).
+ * Element type sizes: wedge Np = (N+1)^2 (N+2)/2, tet Np = (N+1)(N+2)(N+3)/6.
+ *
+ * Memory: the library allocates no device memory.  The caller allocates one
+ * mesh blob and three field buffers (sizes from dg_device_bytes) and passes
+ * them to dg_bind; it keeps ownership.  Host arrays passed in are copied.
+ * Work is issued asynchronously on the stream given to dg_bind.
+ *
+ * Call order: dg_mesh_create -> dg_set_order -> [dg_set_material]
+ *   -> [dg_set_options] -> dg_device_bytes -> dg_bind -> dg_set_fields
+ *   -> dg_step / dg_rhs / dg_energy / dg_get_fields.
+ * Setters after dg_bind return DG_ERR_STATE.  Several contexts may live in one
+ * process; contexts with different (N, precision) must not run concurrently
+ * on one device (operator tables live in device constant memory and are
+ * reloaded, in stream order, when the configuration changes).
+ */
+#ifndef DGWEDGE_H
+#define DGWEDGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_ctx dg_ctx;
+
+typedef enum dg_status {
+  DG_OK = 0,
+  DG_ERR_ARG = -1,       /* null pointer, size or enum out of range              */
+  DG_ERR_MESH = -2,      /* invalid mesh: not vertically mapped, J <= 0, a face
+                            shared by more than two elements, bad vertex id      */
+  DG_ERR_ORDER = -3,     /* N outside 1..4                                       */
+  DG_ERR_CUDA = -4,      /* a CUDA runtime call failed (message has the name)    */
+  DG_ERR_STATE = -5,     /* call out of order                                    */
+  DG_ERR_TIMEOUT = -6,   /* a bounded device-side wait ran out                   */
+  DG_ERR_NONFINITE = -7  /* non-finite value found in the state                  */
+} dg_status;
+
+enum { DG_TET = 4, DG_WEDGE = 6 };
+enum { DG_BC_DIRICHLET = 0, DG_BC_RIGID = 1 };
+enum { DG_FLUX_UPWIND = 0, DG_FLUX_CENTRAL = 1 };
+enum { DG_F32 = 0, DG_F64 = 1 };
+
+/* Create a mesh context from vertices and element-to-vertex lists
+ * (Section 2.1 "triangulation of the domain"; Section 3.2 vertex maps).
+ *   VX    [nverts][3] vertex coordinates (x, y, z).
+ *   EToV  [nelem][6]  vertex ids.  Wedge: (b0, b1, b2, t0, t1, t2), bottom
+ *         triangle counter-clockwise seen from +z, t_a above b_a with equal x
+ *         and y (vertically mapped, Section 3.2) and z(t_a) > z(b_a).  Tet: the
+ *         first four entries with positive orientation, the rest ignored.
+ *   etype [nelem] DG_WEDGE or DG_TET.
+ * Faces are matched by vertex sets; unmatched faces are domain boundary.
+ * Errors: DG_ERR_ARG, DG_ERR_MESH (message names the element). */
+int dg_mesh_create(dg_ctx** out, int64_t nverts, const double* VX, int64_t nelem,
+                   const int64_t* EToV, const uint8_t* etype);
+
+/* Polynomial degree N in 1..4 (Section 3).  Builds the reference operators
+ * (GLL line, Warp & Blend triangle/tet, Section 3.1; Kronecker factors of
+ * Section 4.2) and the face-node orientation maps. */
+int dg_set_order(dg_ctx* ctx, int N);
+
+/* Per-element c^2 and rho (host arrays of length nelem, copied; both > 0).
+ * Default: c^2 = rho = 1. */
+int dg_set_material(dg_ctx* ctx, const double* c2, const double* rho);
+
+/* Boundary condition (DG_BC_*), flux (DG_FLUX_*), arithmetic precision
+ * (DG_F32: fields and arithmetic in float; DG_F64: double).
+ * Default: rigid walls, upwind, DG_F32. */
+int dg_set_options(dg_ctx* ctx, int bc, int flux, int precision);
+
+/* Node counts: total wedge nodes and total tet nodes; the canonical layout
+ * holds wedge_nodes + tet_nodes nodes. */
+int dg_num_nodes(const dg_ctx* ctx, int64_t* wedge_nodes, int64_t* tet_nodes);
+
+/* Physical node coordinates, host array xyz[3][total_nodes] (canonical
+ * order), computed from the vertex maps.  Needs dg_set_order. */
+int dg_node_coords(const dg_ctx* ctx, double* xyz);
+
+/* For every element (input order), face and face node: the canonical index
+ * of the coincident node of the neighbouring element, or -1 on the domain
+ * boundary.  Face order: wedge (bottom t=-1, top t=+1, quads over triangle
+ * edges (0,1), (1,2), (2,0)); tet (vertices (0,1,2), (0,1,3), (1,2,3),
+ * (0,2,3)).  Face nodes in element node order.  `out` holds
+ * sum_k sum_f nfacenodes(k, f) entries; *count receives that number (pass
+ * out = NULL to query it).  Host only. */
+int dg_face_neighbors(const dg_ctx* ctx, int64_t* out, int64_t* count);
+
+/* Reference operator by name, row-major doubles, host only (diagnostics):
+ * "tri.r", "tri.s" (nodes), "tri.Dr", "tri.Ds", "tri.M", "tri.M0", "tri.M1",
+ * "tri.M2" (barycentric-weighted masses int l_i l_j lambda_a), "line.r",
+ * "line.D", "line.M", "line.ell0", "line.ellN", "line.Ma", "line.Mb",
+ * "tet.r", "tet.s", "tet.t", "tet.Dr", "tet.Ds", "tet.Dt", "tet.M", "tet.LIFT".
+ * *rows, *cols receive the shape; pass out = NULL to query it. */
+int dg_reference_operator(const dg_ctx* ctx, const char* name, double* out,
+                          int64_t* rows, int64_t* cols);
+
+/* Device sizes for the current mesh, order and precision: the mesh blob
+ * (connectivity, vertices, material, operator scratch) and one field buffer
+ * (packed state of all elements, padded to 32-element blocks). */
+int dg_device_bytes(const dg_ctx* ctx, size_t* mesh_bytes, size_t* field_bytes);
+
+/* Bind caller-owned device memory (256-byte aligned) and a cudaStream_t
+ * (NULL = legacy default stream), upload the mesh blob and operator tables,
+ * and zero the state.  q0/q1 are the two state buffers the Runge-Kutta stages
+ * alternate between, res the low-storage residual.  The current device must be
+ * the one that owns the buffers. */
+int dg_bind(dg_ctx* ctx, void* d_mesh, void* d_q0, void* d_q1, void* d_res, void* stream);
+
+/* Set / read the state in the canonical layout ([4][total_nodes] of float or
+ * double per precision).  on_device != 0: a device pointer, else host.  Host
+ * transfers synchronise the stream; device ones are asynchronous.
+ * dg_set_fields resets the simulation time to 0 and the residual to 0. */
+int dg_set_fields(dg_ctx* ctx, const void* q, int on_device);
+int dg_get_fields(dg_ctx* ctx, void* q, int on_device);
+
+/* Semi-discrete right-hand side dq/dt = rhs(q) (Section 2.1), canonical
+ * layout, device pointers (d_q may equal d_rhs).  Uses the inactive state
+ * buffer and the residual buffer as scratch: call between steps only.  The
+ * current state is not modified.  Asynchronous. */
+int dg_rhs(dg_ctx* ctx, const void* d_q, void* d_rhs);
+
+/* Advance the bound state by nsteps LSRK45 steps of size dt (dt > 0,
+ * nsteps >= 0).  One fused kernel per element type per stage, replayed from
+ * a CUDA graph.  Asynchronous; launch errors are returned, device-side errors
+ * (bounded waits) surface at the next synchronising call. */
+int dg_step(dg_ctx* ctx, double dt, int64_t nsteps);
+
+/* Discrete energy E = 1/2 sum_k (p^T M^k p / kappa_k + rho_k sum_c u_c^T M^k u_c)
+ * with the scheme's exact mass matrices (Section 4.1), accumulated in double.
+ * Synchronises the stream.  Returns DG_ERR_NONFINITE if E is not finite and
+ * DG_ERR_TIMEOUT if a device-side wait had run out since the last check. */
+int dg_energy(dg_ctx* ctx, double* E);
+
+/* Synchronise the bound stream and report pending device-side errors. */
+int dg_sync(dg_ctx* ctx);
+
+/* Simulation time of the bound state (sum of dt over completed steps). */
+int dg_time(const dg_ctx* ctx, double* t);
+
+/* Stable time step dt = cfl * min_k 1 / (c_k (N+1)^2 max_f(area_f / vol_k)).
+ * The paper bounds dt by trace and Markov constants without printing them
+ * (Section 6); this is the library's explicit form of that bound. */
+int dg_stable_dt(const dg_ctx* ctx, double cfl, double* dt);
+
+const char* dg_last_error(const dg_ctx* ctx);
+void dg_destroy(dg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGWEDGE_H */

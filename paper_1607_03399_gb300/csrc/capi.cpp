@@ -1,0 +1,1009 @@
+// C ABI of the DG library (see include/dgwedge.h).
+//
+// Host side: mesh validation (vertically mapped wedges, Section 3.2;
+// positive Jacobians), face matching by vertex sets, face-node orientation
+// codes, reference operators (refel.cpp), packing into the device blob, and
+// the stage/step driver (LSRK45 stages replayed from a captured CUDA graph).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/dgwedge.h"
+#include "dg_internal.hpp"
+#include "refel.hpp"
+
+using namespace dgw;
+
+namespace {
+// dispatch to the (precision, order) translation units
+#define DGW_SWITCH_N(N, P, CALL)  \
+  switch (N) {                    \
+    case 1: return P##n1 CALL;    \
+    case 2: return P##n2 CALL;    \
+    case 3: return P##n3 CALL;    \
+    case 4: return P##n4 CALL;    \
+  }                               \
+  return int(cudaErrorInvalidValue);
+
+int upload_ops(int N, bool dbl, const void* p, size_t n, void* s) {
+  if (dbl) {
+    DGW_SWITCH_N(N, upload_ops_f64, (p, n, s))
+  } else {
+    DGW_SWITCH_N(N, upload_ops_f32, (p, n, s))
+  }
+}
+int stage_f32(int N, const StageArgs<float>& a, bool rk, void* s) { DGW_SWITCH_N(N, launch_stage_f32, (a, rk, s)) }
+int stage_f64(int N, const StageArgs<double>& a, bool rk, void* s) { DGW_SWITCH_N(N, launch_stage_f64, (a, rk, s)) }
+int pack_f32(int N, const DevMesh<float>& m, const float* c, float* p, bool u, void* s) {
+  DGW_SWITCH_N(N, launch_pack_f32, (m, c, p, u, s))
+}
+int pack_f64(int N, const DevMesh<double>& m, const double* c, double* p, bool u, void* s) {
+  DGW_SWITCH_N(N, launch_pack_f64, (m, c, p, u, s))
+}
+int energy_f32(int N, const DevMesh<float>& m, const float* q, void* s) { DGW_SWITCH_N(N, launch_energy_f32, (m, q, s)) }
+int energy_f64(int N, const DevMesh<double>& m, const double* q, void* s) { DGW_SWITCH_N(N, launch_energy_f64, (m, q, s)) }
+}  // namespace
+
+namespace {
+
+const int kWedgeFaceVerts[5][4] = {{0, 1, 2, -1}, {3, 4, 5, -1}, {0, 1, 4, 3}, {1, 2, 5, 4}, {2, 0, 3, 5}};
+const int kTetFaceVerts[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
+
+struct FaceKey {
+  int64_t v[4];
+  bool operator==(const FaceKey& o) const { return v[0] == o.v[0] && v[1] == o.v[1] && v[2] == o.v[2] && v[3] == o.v[3]; }
+};
+struct FaceKeyHash {
+  size_t operator()(const FaceKey& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int i = 0; i < 4; ++i) {
+      h ^= uint64_t(k.v[i]) + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+      h *= 1099511628211ull;
+    }
+    return size_t(h);
+  }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// devices (bit mask) whose constant banks hold the operators of (order, precision)
+uint64_t g_loaded[2 * (kMaxOrder + 1)] = {0};
+
+}  // namespace
+
+struct dg_ctx {
+  mutable std::string err;
+  // mesh (input order)
+  int64_t nverts = 0, K = 0;
+  std::vector<double> VX;
+  std::vector<int64_t> EToV;
+  std::vector<uint8_t> etype;
+  // per element: type-local index and type-local lists
+  std::vector<int64_t> local;  // index within its type
+  std::vector<int64_t> wedges, tets;
+  // connectivity (input order): neighbour element and its face per face (-1 boundary)
+  std::vector<std::array<int64_t, 5>> nbr;
+  std::vector<std::array<int, 5>> nface;
+  std::vector<std::array<int, 5>> code;  // orientation code (see dg_internal.hpp)
+  // order
+  int N = 0;
+  std::unique_ptr<RefElems> ref;
+  std::vector<int64_t> node_off;  // canonical node offset per element
+  int64_t wedge_nodes = 0, tet_nodes = 0;
+  // material
+  std::vector<double> c2, rho;
+  // options
+  int bc = DG_BC_RIGID, flux = DG_FLUX_UPWIND, prec = DG_F32;
+  // binding
+  bool bound = false;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  void* d_mesh = nullptr;
+  void* d_q[2] = {nullptr, nullptr};
+  void* d_res = nullptr;
+  int cur = 0;
+  double t = 0.0;
+  DevMesh<float> m32;
+  DevMesh<double> m64;
+  size_t mesh_bytes = 0, field_bytes = 0;
+  std::vector<unsigned char> ops_host;
+  // graphs: one LSRK step starting from buffer 0 / 1 for a given dt
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  double gdt[2] = {0.0, 0.0};
+
+  int fail(int code_, const std::string& msg) const {
+    err = msg;
+    return code_;
+  }
+};
+
+namespace {
+
+int cuda_fail(dg_ctx* c, cudaError_t e, const char* what) {
+  return c->fail(DG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int64_t nblk(int64_t K) { return (K + kB - 1) / kB; }
+
+// ----------------------------------------------------------------- operators
+template <int NN, typename real>
+void fill_ops(const RefElems& R, std::vector<unsigned char>& out) {
+  AllOps<NN, real> o;
+  std::memset(&o, 0, sizeof(o));
+  const int Nt = R.Nt, Nq = R.Nq, Npt = R.Npt;
+  for (int i = 0; i < Nt; ++i)
+    for (int l = 0; l < Nt; ++l) {
+      o.w.Dr[i * Nt + l] = real(R.Dr(i, l));
+      o.w.Ds[i * Nt + l] = real(R.Ds(i, l));
+      o.w.M[i * Nt + l] = real(R.Mt(i, l));
+      for (int a = 0; a < 3; ++a) o.w.Ma[a][i * Nt + l] = real(R.Ma[a](i, l));
+    }
+  for (int m = 0; m < Nq; ++m) {
+    for (int n = 0; n < Nq; ++n) {
+      o.w.Dt[m * Nq + n] = real(R.D1(m, n));
+      o.w.Mea[m * Nq + n] = real(R.Mea(m, n));
+      o.w.Meb[m * Nq + n] = real(R.Meb(m, n));
+      o.w.M1[m * Nq + n] = real(R.M1(m, n));
+    }
+    o.w.ell0[m] = real(R.ell0[m]);
+    o.w.ellN[m] = real(R.ellN[m]);
+    o.w.gll[m] = real(R.gll[m]);
+  }
+  for (int i = 0; i < Npt; ++i) {
+    for (int l = 0; l < Npt; ++l) {
+      o.t.Dr[i * Npt + l] = real(R.tDr(i, l));
+      o.t.Ds[i * Npt + l] = real(R.tDs(i, l));
+      o.t.Dt[i * Npt + l] = real(R.tDt(i, l));
+    }
+    for (int k = 0; k < 4 * Nt; ++k) o.t.LIFT[i * 4 * Nt + k] = real(R.tLIFT(i, k));
+  }
+  for (int c = 0; c < 9; ++c)
+    for (int k = 0; k < Nt; ++k) o.tab.tri_perm[c][k] = R.tri_perm[c].empty() ? 0 : int8_t(R.tri_perm[c][k]);
+  for (int e = 0; e < 3; ++e)
+    for (int m = 0; m < Nq; ++m) o.tab.edge[e][m] = int8_t(R.edge_nodes[e][m]);
+  for (int f = 0; f < 4; ++f)
+    for (int k = 0; k < Nt; ++k) o.tab.tet_face[f][k] = int8_t(R.tet_face_nodes[f][k]);
+  out.resize(sizeof(o));
+  std::memcpy(out.data(), &o, sizeof(o));
+}
+
+void build_ops(dg_ctx* c) {
+  const bool dbl = c->prec == DG_F64;
+  const RefElems& R = *c->ref;
+  switch (c->N) {
+    case 1: dbl ? fill_ops<1, double>(R, c->ops_host) : fill_ops<1, float>(R, c->ops_host); break;
+    case 2: dbl ? fill_ops<2, double>(R, c->ops_host) : fill_ops<2, float>(R, c->ops_host); break;
+    case 3: dbl ? fill_ops<3, double>(R, c->ops_host) : fill_ops<3, float>(R, c->ops_host); break;
+    case 4: dbl ? fill_ops<4, double>(R, c->ops_host) : fill_ops<4, float>(R, c->ops_host); break;
+  }
+}
+
+// Operator tables depend only on (order, precision); each lives in the
+// constant bank of its own translation unit, uploaded once per device.
+int ensure_ops(dg_ctx* c) {
+  const int key = c->N * 2 + (c->prec == DG_F64 ? 1 : 0);
+  const uint64_t bit = uint64_t(1) << (c->device & 63);
+  if (g_loaded[key] & bit) return DG_OK;
+  const int rc = upload_ops(c->N, c->prec == DG_F64, c->ops_host.data(), c->ops_host.size(), c->stream);
+  if (rc) return cuda_fail(c, cudaError_t(rc), "operator upload");
+  const cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "operator upload synchronize");
+  g_loaded[key] |= bit;
+  return DG_OK;
+}
+
+// ----------------------------------------------------------------- geometry helpers
+void wedge_face_vertex_list(const dg_ctx* c, int64_t k, int f, int64_t* out) {
+  for (int i = 0; i < (f < 2 ? 3 : 4); ++i) out[i] = c->EToV[k * 6 + kWedgeFaceVerts[f][i]];
+}
+
+int nfaces_of(uint8_t t) { return t == DG_WEDGE ? 5 : 4; }
+
+// vertex list (3 ids) of a triangle face in that element's face vertex order
+void tri_face_vertices(const dg_ctx* c, int64_t k, int f, int64_t* out) {
+  if (c->etype[k] == DG_WEDGE) {
+    for (int i = 0; i < 3; ++i) out[i] = c->EToV[k * 6 + kWedgeFaceVerts[f][i]];
+  } else {
+    for (int i = 0; i < 3; ++i) out[i] = c->EToV[k * 6 + kTetFaceVerts[f][i]];
+  }
+}
+
+double wedge_stable_ratio(const dg_ctx* c, int64_t k) {
+  const double* V = c->VX.data();
+  auto P = [&](int a, int d) { return V[c->EToV[k * 6 + a] * 3 + d]; };
+  const double xr = 0.5 * (P(1, 0) - P(0, 0)), xs = 0.5 * (P(2, 0) - P(0, 0));
+  const double yr = 0.5 * (P(1, 1) - P(0, 1)), ys = 0.5 * (P(2, 1) - P(0, 1));
+  const double A = xr * ys - xs * yr;
+  double h[3], hs = 0;
+  for (int a = 0; a < 3; ++a) {
+    h[a] = P(a + 3, 2) - P(a, 2);
+    hs += h[a];
+  }
+  const double vol = (2.0 / 3.0) * A * hs;
+  double amax = 0.0;
+  for (int top = 0; top < 2; ++top) {
+    const int o = top ? 3 : 0;
+    double ab[3], ac[3];
+    for (int d = 0; d < 3; ++d) {
+      ab[d] = P(o + 1, d) - P(o, d);
+      ac[d] = P(o + 2, d) - P(o, d);
+    }
+    const double cx = ab[1] * ac[2] - ab[2] * ac[1], cy = ab[2] * ac[0] - ab[0] * ac[2], cz = ab[0] * ac[1] - ab[1] * ac[0];
+    amax = std::max(amax, 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz));
+  }
+  for (int e = 0; e < 3; ++e) {
+    const int a = e, b = (e + 1) % 3;
+    const double L = std::hypot(P(b, 0) - P(a, 0), P(b, 1) - P(a, 1));
+    amax = std::max(amax, L * 0.5 * (h[a] + h[b]));
+  }
+  return amax / vol;
+}
+
+double tet_det(const dg_ctx* c, int64_t k) {
+  const double* V = c->VX.data();
+  double G[3][3];
+  for (int m = 0; m < 3; ++m)
+    for (int d = 0; d < 3; ++d) G[d][m] = V[c->EToV[k * 6 + m + 1] * 3 + d] - V[c->EToV[k * 6] * 3 + d];
+  return G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) - G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+         G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+}
+
+double tet_stable_ratio(const dg_ctx* c, int64_t k) {
+  const double* V = c->VX.data();
+  const double vol = tet_det(c, k) / 6.0;
+  double amax = 0.0;
+  for (int f = 0; f < 4; ++f) {
+    const int64_t a = c->EToV[k * 6 + kTetFaceVerts[f][0]], b = c->EToV[k * 6 + kTetFaceVerts[f][1]],
+                  d = c->EToV[k * 6 + kTetFaceVerts[f][2]];
+    double ab[3], ad[3];
+    for (int i = 0; i < 3; ++i) {
+      ab[i] = V[b * 3 + i] - V[a * 3 + i];
+      ad[i] = V[d * 3 + i] - V[a * 3 + i];
+    }
+    const double cx = ab[1] * ad[2] - ab[2] * ad[1], cy = ab[2] * ad[0] - ab[0] * ad[2], cz = ab[0] * ad[1] - ab[1] * ad[0];
+    amax = std::max(amax, 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz));
+  }
+  return amax / vol;
+}
+
+// ----------------------------------------------------------------- blob
+struct BlobLayout {
+  size_t w_vid, w_nbr, w_code, w_mat, w_canon, t_vid, t_nbr, t_code, t_mat, t_canon, vx, vy, vz, err, partials, energy,
+      tmass, total;
+};
+
+BlobLayout blob_layout(const dg_ctx* c) {
+  const size_t rs = c->prec == DG_F64 ? 8 : 4;
+  const int64_t Kwp = nblk(int64_t(c->wedges.size())) * kB, Ktp = nblk(int64_t(c->tets.size())) * kB;
+  const int64_t nparts = (nblk(int64_t(c->wedges.size())) + 3) / 4 + (nblk(int64_t(c->tets.size())) + 3) / 4 + 1;
+  BlobLayout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.w_vid = take(6 * Kwp * 4);
+  L.w_nbr = take(5 * Kwp * 4);
+  L.w_code = take(5 * Kwp * 4);
+  L.w_mat = take(3 * Kwp * rs);
+  L.w_canon = take(Kwp * 8);
+  L.t_vid = take(4 * Ktp * 4);
+  L.t_nbr = take(4 * Ktp * 4);
+  L.t_code = take(4 * Ktp * 4);
+  L.t_mat = take(3 * Ktp * rs);
+  L.t_canon = take(Ktp * 8);
+  L.vx = take(c->nverts * rs);
+  L.vy = take(c->nverts * rs);
+  L.vz = take(c->nverts * rs);
+  L.err = take(16);
+  L.partials = take(nparts * 8);
+  L.energy = take(8);
+  L.tmass = take(size_t(npt_of(c->N)) * npt_of(c->N) * rs);
+  L.total = o;
+  return L;
+}
+
+template <typename real>
+void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>& blob) {
+  blob.assign(L.total, 0);
+  const int64_t Kw = int64_t(c->wedges.size()), Kt = int64_t(c->tets.size());
+  const int64_t Kwp = nblk(Kw) * kB, Ktp = nblk(Kt) * kB;
+  int* w_vid = reinterpret_cast<int*>(blob.data() + L.w_vid);
+  int* w_nbr = reinterpret_cast<int*>(blob.data() + L.w_nbr);
+  int* w_code = reinterpret_cast<int*>(blob.data() + L.w_code);
+  real* w_mat = reinterpret_cast<real*>(blob.data() + L.w_mat);
+  int64_t* w_canon = reinterpret_cast<int64_t*>(blob.data() + L.w_canon);
+  for (int64_t w = 0; w < Kwp; ++w) {
+    const int64_t k = c->wedges[w < Kw ? w : 0];  // padding replicates a valid element
+    for (int v = 0; v < 6; ++v) w_vid[v * Kwp + w] = int(c->EToV[k * 6 + v]);
+    for (int f = 0; f < 5; ++f) {
+      const int64_t n = (w < Kw) ? c->nbr[k][f] : -1;
+      w_nbr[f * Kwp + w] = (n < 0) ? -1 : int(c->local[n]);
+      w_code[f * Kwp + w] = (n < 0) ? 0 : c->code[k][f];
+    }
+    const double cc = std::sqrt(c->c2[k]);
+    w_mat[0 * Kwp + w] = real(c->rho[k] * c->c2[k]);
+    w_mat[1 * Kwp + w] = real(1.0 / c->rho[k]);
+    w_mat[2 * Kwp + w] = real(c->rho[k] * cc);
+    if (w < Kw) w_canon[w] = c->node_off[k];
+  }
+  int* t_vid = reinterpret_cast<int*>(blob.data() + L.t_vid);
+  int* t_nbr = reinterpret_cast<int*>(blob.data() + L.t_nbr);
+  int* t_code = reinterpret_cast<int*>(blob.data() + L.t_code);
+  real* t_mat = reinterpret_cast<real*>(blob.data() + L.t_mat);
+  int64_t* t_canon = reinterpret_cast<int64_t*>(blob.data() + L.t_canon);
+  for (int64_t t = 0; t < Ktp; ++t) {
+    const int64_t k = c->tets[t < Kt ? t : 0];
+    for (int v = 0; v < 4; ++v) t_vid[v * Ktp + t] = int(c->EToV[k * 6 + v]);
+    for (int f = 0; f < 4; ++f) {
+      const int64_t n = (t < Kt) ? c->nbr[k][f] : -1;
+      t_nbr[f * Ktp + t] = (n < 0) ? -1 : int(c->local[n]);
+      t_code[f * Ktp + t] = (n < 0) ? 0 : c->code[k][f];
+    }
+    const double cc = std::sqrt(c->c2[k]);
+    t_mat[0 * Ktp + t] = real(c->rho[k] * c->c2[k]);
+    t_mat[1 * Ktp + t] = real(1.0 / c->rho[k]);
+    t_mat[2 * Ktp + t] = real(c->rho[k] * cc);
+    if (t < Kt) t_canon[t] = c->node_off[k];
+  }
+  real* vx = reinterpret_cast<real*>(blob.data() + L.vx);
+  real* vy = reinterpret_cast<real*>(blob.data() + L.vy);
+  real* vz = reinterpret_cast<real*>(blob.data() + L.vz);
+  real* tm = reinterpret_cast<real*>(blob.data() + L.tmass);
+  for (int i = 0; i < c->ref->Npt * c->ref->Npt; ++i) tm[i] = real(c->ref->tM.a[i]);
+  for (int64_t v = 0; v < c->nverts; ++v) {
+    vx[v] = real(c->VX[v * 3 + 0]);
+    vy[v] = real(c->VX[v * 3 + 1]);
+    vz[v] = real(c->VX[v * 3 + 2]);
+  }
+}
+
+template <typename real>
+void fill_devmesh(const dg_ctx* c, const BlobLayout& L, DevMesh<real>& m) {
+  unsigned char* b = static_cast<unsigned char*>(c->d_mesh);
+  const int64_t Kw = int64_t(c->wedges.size()), Kt = int64_t(c->tets.size());
+  m.Kw = int(Kw);
+  m.Kw_pad = int(nblk(Kw) * kB);
+  m.nblk_w = int(nblk(Kw));
+  m.Kt = int(Kt);
+  m.Kt_pad = int(nblk(Kt) * kB);
+  m.nblk_t = int(nblk(Kt));
+  m.w_vid = reinterpret_cast<const int*>(b + L.w_vid);
+  m.w_nbr = reinterpret_cast<const int*>(b + L.w_nbr);
+  m.w_code = reinterpret_cast<const int*>(b + L.w_code);
+  m.w_mat = reinterpret_cast<const real*>(b + L.w_mat);
+  m.w_canon = reinterpret_cast<const int64_t*>(b + L.w_canon);
+  m.t_vid = reinterpret_cast<const int*>(b + L.t_vid);
+  m.t_nbr = reinterpret_cast<const int*>(b + L.t_nbr);
+  m.t_code = reinterpret_cast<const int*>(b + L.t_code);
+  m.t_mat = reinterpret_cast<const real*>(b + L.t_mat);
+  m.t_canon = reinterpret_cast<const int64_t*>(b + L.t_canon);
+  m.vx = reinterpret_cast<const real*>(b + L.vx);
+  m.vy = reinterpret_cast<const real*>(b + L.vy);
+  m.vz = reinterpret_cast<const real*>(b + L.vz);
+  m.err = reinterpret_cast<int*>(b + L.err);
+  m.partials = reinterpret_cast<double*>(b + L.partials);
+  m.energy = reinterpret_cast<double*>(b + L.energy);
+  m.tet_mass = reinterpret_cast<const real*>(b + L.tmass);
+  m.tet_off = int64_t(m.nblk_w) * 4 * npw_of(c->N) * kB;
+  m.total_nodes = c->wedge_nodes + c->tet_nodes;
+}
+
+size_t field_bytes_of(const dg_ctx* c) {
+  const size_t rs = c->prec == DG_F64 ? 8 : 4;
+  const int64_t nw = nblk(int64_t(c->wedges.size())), nt = nblk(int64_t(c->tets.size()));
+  return align256(size_t(nw * 4 * npw_of(c->N) * kB + nt * 4 * npt_of(c->N) * kB) * rs);
+}
+
+int launch_stage(dg_ctx* c, const void* q_in, void* q_out, void* res, double a, double b, double dt, bool rk,
+                 cudaStream_t s) {
+  int rc;
+  if (c->prec == DG_F64) {
+    StageArgs<double> A;
+    A.m = c->m64;
+    A.q_in = static_cast<const double*>(q_in);
+    A.q_out = static_cast<double*>(q_out);
+    A.res = static_cast<double*>(res);
+    A.rk_a = a;
+    A.rk_b = b;
+    A.dt = dt;
+    A.bc = c->bc;
+    A.flux = c->flux;
+    rc = stage_f64(c->N, A, rk, s);
+  } else {
+    StageArgs<float> A;
+    A.m = c->m32;
+    A.q_in = static_cast<const float*>(q_in);
+    A.q_out = static_cast<float*>(q_out);
+    A.res = static_cast<float*>(res);
+    A.rk_a = float(a);
+    A.rk_b = float(b);
+    A.dt = float(dt);
+    A.bc = c->bc;
+    A.flux = c->flux;
+    rc = stage_f32(c->N, A, rk, s);
+  }
+  if (rc) return cuda_fail(c, cudaError_t(rc), "stage launch");
+  return DG_OK;
+}
+
+int launch_pack(dg_ctx* c, const void* canon, void* packed, bool unpack, cudaStream_t s) {
+  int rc;
+  if (c->prec == DG_F64)
+    rc = pack_f64(c->N, c->m64, static_cast<const double*>(canon), static_cast<double*>(packed), unpack, s);
+  else
+    rc = pack_f32(c->N, c->m32, static_cast<const float*>(canon), static_cast<float*>(packed), unpack, s);
+  if (rc) return cuda_fail(c, cudaError_t(rc), "pack launch");
+  return DG_OK;
+}
+
+int check_device_error(dg_ctx* c) {
+  int h = 0;
+  int* derr = (c->prec == DG_F64) ? c->m64.err : c->m32.err;
+  cudaError_t e = cudaMemcpyAsync(&h, derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device error check");
+  if (h) {
+    cudaMemsetAsync(derr, 0, sizeof(int), c->stream);
+    cudaStreamSynchronize(c->stream);
+    if (h & kErrTimeout) return c->fail(DG_ERR_TIMEOUT, "a bounded device-side wait ran out");
+    if (h & kErrNonfinite) return c->fail(DG_ERR_NONFINITE, "non-finite value in the state");
+  }
+  return DG_OK;
+}
+
+void drop_graphs(dg_ctx* c) {
+  for (int i = 0; i < 2; ++i) {
+    if (c->gexec[i]) cudaGraphExecDestroy(c->gexec[i]);
+    c->gexec[i] = nullptr;
+  }
+}
+
+}  // namespace
+
+// =========================================================================== ABI
+extern "C" {
+
+int dg_mesh_create(dg_ctx** out, int64_t nverts, const double* VX, int64_t nelem, const int64_t* EToV,
+                   const uint8_t* etype) {
+  if (!out || !VX || !EToV || !etype || nverts <= 0 || nelem <= 0) return DG_ERR_ARG;
+  *out = nullptr;
+  std::unique_ptr<dg_ctx> c(new dg_ctx);
+  c->nverts = nverts;
+  c->K = nelem;
+  c->VX.assign(VX, VX + nverts * 3);
+  c->EToV.assign(EToV, EToV + nelem * 6);
+  c->etype.assign(etype, etype + nelem);
+  c->local.assign(nelem, -1);
+  c->nbr.assign(nelem, {-1, -1, -1, -1, -1});
+  c->nface.assign(nelem, {-1, -1, -1, -1, -1});
+  c->code.assign(nelem, {0, 0, 0, 0, 0});
+  for (int64_t k = 0; k < nelem; ++k) {
+    const uint8_t t = etype[k];
+    if (t != DG_WEDGE && t != DG_TET) {
+      *out = c.release();
+      return (*out)->fail(DG_ERR_ARG, "element " + std::to_string(k) + ": unknown element type");
+    }
+    const int nv = (t == DG_WEDGE) ? 6 : 4;
+    for (int v = 0; v < nv; ++v) {
+      const int64_t id = EToV[k * 6 + v];
+      if (id < 0 || id >= nverts) {
+        *out = c.release();
+        return (*out)->fail(DG_ERR_MESH, "element " + std::to_string(k) + ": vertex id out of range");
+      }
+    }
+    if (t == DG_WEDGE) {
+      c->local[k] = int64_t(c->wedges.size());
+      c->wedges.push_back(k);
+    } else {
+      c->local[k] = int64_t(c->tets.size());
+      c->tets.push_back(k);
+    }
+  }
+  if (c->wedges.size() >= (1u << 30) || c->tets.size() >= (1u << 30)) {
+    *out = c.release();
+    return (*out)->fail(DG_ERR_ARG, "too many elements");
+  }
+  // validation: vertically mapped wedges with positive Jacobian, positive tets
+  for (int64_t k = 0; k < nelem; ++k) {
+    const double* V = c->VX.data();
+    if (etype[k] == DG_WEDGE) {
+      auto P = [&](int a, int d) { return V[EToV[k * 6 + a] * 3 + d]; };
+      double scale = 0.0;
+      for (int a = 0; a < 6; ++a)
+        for (int d = 0; d < 3; ++d) scale = std::max(scale, std::fabs(P(a, d) - P(0, d)));
+      for (int a = 0; a < 3; ++a)
+        if (std::fabs(P(a, 0) - P(a + 3, 0)) > 1e-10 * scale || std::fabs(P(a, 1) - P(a + 3, 1)) > 1e-10 * scale) {
+          *out = c.release();
+          return (*out)->fail(DG_ERR_MESH, "wedge " + std::to_string(k) + " is not vertically mapped");
+        }
+      const double A = (P(1, 0) - P(0, 0)) * (P(2, 1) - P(0, 1)) - (P(2, 0) - P(0, 0)) * (P(1, 1) - P(0, 1));
+      bool ok = A > 0;
+      for (int a = 0; a < 3; ++a) ok = ok && (P(a + 3, 2) - P(a, 2) > 0);
+      if (!ok) {
+        *out = c.release();
+        return (*out)->fail(DG_ERR_MESH, "wedge " + std::to_string(k) +
+                                             " has J <= 0 (bottom must be counter-clockwise seen from +z, top above bottom)");
+      }
+    } else {
+      if (!(tet_det(c.get(), k) > 0)) {
+        *out = c.release();
+        return (*out)->fail(DG_ERR_MESH, "tet " + std::to_string(k) + " has J <= 0");
+      }
+    }
+  }
+  // face matching by vertex sets
+  std::unordered_map<FaceKey, std::pair<int64_t, int>, FaceKeyHash> open;
+  open.reserve(size_t(nelem) * 3);
+  for (int64_t k = 0; k < nelem; ++k) {
+    const bool w = etype[k] == DG_WEDGE;
+    for (int f = 0; f < nfaces_of(etype[k]); ++f) {
+      FaceKey key{{-1, -1, -1, -1}};
+      int nv = 3;
+      if (w) {
+        nv = (f < 2) ? 3 : 4;
+        for (int i = 0; i < nv; ++i) key.v[i] = EToV[k * 6 + kWedgeFaceVerts[f][i]];
+      } else {
+        for (int i = 0; i < 3; ++i) key.v[i] = EToV[k * 6 + kTetFaceVerts[f][i]];
+      }
+      std::sort(key.v, key.v + nv);
+      auto it = open.find(key);
+      if (it == open.end()) {
+        open.emplace(key, std::make_pair(k, f));
+      } else {
+        // matched faces stay in the table (marked by f2 < 0) so that a third
+        // element on the same face is detected
+        const int64_t k2 = it->second.first;
+        const int f2 = it->second.second;
+        if (f2 < 0) {
+          *out = c.release();
+          return (*out)->fail(DG_ERR_MESH, "a face of element " + std::to_string(k) + " is shared by more than two elements");
+        }
+        c->nbr[k][f] = k2;
+        c->nface[k][f] = f2;
+        c->nbr[k2][f2] = k;
+        c->nface[k2][f2] = f;
+        it->second.second = -1;
+      }
+    }
+  }
+  // orientation codes
+  for (int64_t k = 0; k < nelem; ++k) {
+    for (int f = 0; f < nfaces_of(etype[k]); ++f) {
+      const int64_t k2 = c->nbr[k][f];
+      if (k2 < 0) continue;
+      const int f2 = c->nface[k][f];
+      const bool quad = etype[k] == DG_WEDGE && f >= 2;
+      if (quad) {
+        const int64_t a = EToV[k * 6 + kWedgeFaceVerts[f][0]], b = EToV[k * 6 + kWedgeFaceVerts[f][1]];
+        const int64_t a2 = EToV[k2 * 6 + kWedgeFaceVerts[f2][0]], b2 = EToV[k2 * 6 + kWedgeFaceVerts[f2][1]];
+        int rev;
+        if (a == a2 && b == b2)
+          rev = 0;
+        else if (a == b2 && b == a2)
+          rev = 1;
+        else {
+          *out = c.release();
+          return (*out)->fail(DG_ERR_MESH, "wedges " + std::to_string(k) + " and " + std::to_string(k2) +
+                                                " meet on a quad face with opposite vertical orientation");
+        }
+        c->code[k][f] = (f2 - 2) * 2 + rev;
+      } else {
+        int64_t own[3], oth[3];
+        tri_face_vertices(c.get(), k, f, own);
+        tri_face_vertices(c.get(), k2, f2, oth);
+        int pos[3];
+        for (int m = 0; m < 3; ++m) {
+          pos[m] = -1;
+          for (int i = 0; i < 3; ++i)
+            if (oth[m] == own[i]) pos[m] = i;
+        }
+        c->code[k][f] = (etype[k2] == DG_TET ? kCodeTet : 0) | (f2 << 4) | (pos[0] * 3 + pos[1]);
+      }
+    }
+  }
+  c->c2.assign(nelem, 1.0);
+  c->rho.assign(nelem, 1.0);
+  *out = c.release();
+  return DG_OK;
+}
+
+int dg_set_order(dg_ctx* c, int N) {
+  if (!c) return DG_ERR_ARG;
+  if (c->bound) return c->fail(DG_ERR_STATE, "dg_set_order after dg_bind");
+  if (N < 1 || N > kMaxOrder) return c->fail(DG_ERR_ORDER, "order must be in 1..4");
+  try {
+    c->ref.reset(new RefElems(build_reference(N)));
+  } catch (const std::exception& ex) {
+    return c->fail(DG_ERR_ORDER, ex.what());
+  }
+  c->N = N;
+  c->node_off.assign(c->K + 1, 0);
+  c->wedge_nodes = c->tet_nodes = 0;
+  for (int64_t k = 0; k < c->K; ++k) {
+    const int np = c->etype[k] == DG_WEDGE ? c->ref->Npw : c->ref->Npt;
+    c->node_off[k + 1] = c->node_off[k] + np;
+    (c->etype[k] == DG_WEDGE ? c->wedge_nodes : c->tet_nodes) += np;
+  }
+  return DG_OK;
+}
+
+int dg_set_material(dg_ctx* c, const double* c2, const double* rho) {
+  if (!c) return DG_ERR_ARG;
+  if (!c2 || !rho) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (c->bound) return c->fail(DG_ERR_STATE, "dg_set_material after dg_bind");
+  for (int64_t k = 0; k < c->K; ++k)
+    if (!(c2[k] > 0) || !(rho[k] > 0) || !std::isfinite(c2[k]) || !std::isfinite(rho[k]))
+      return c->fail(DG_ERR_ARG, "material of element " + std::to_string(k) + " must be positive and finite");
+  c->c2.assign(c2, c2 + c->K);
+  c->rho.assign(rho, rho + c->K);
+  return DG_OK;
+}
+
+int dg_set_options(dg_ctx* c, int bc, int flux, int precision) {
+  if (!c) return DG_ERR_ARG;
+  if (c->bound) return c->fail(DG_ERR_STATE, "dg_set_options after dg_bind");
+  if ((bc != DG_BC_DIRICHLET && bc != DG_BC_RIGID) || (flux != DG_FLUX_UPWIND && flux != DG_FLUX_CENTRAL) ||
+      (precision != DG_F32 && precision != DG_F64))
+    return c->fail(DG_ERR_ARG, "option out of range");
+  c->bc = bc;
+  c->flux = flux;
+  c->prec = precision;
+  return DG_OK;
+}
+
+int dg_num_nodes(const dg_ctx* c, int64_t* wn, int64_t* tn) {
+  if (!c) return DG_ERR_ARG;
+  if (!wn || !tn) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
+  *wn = c->wedge_nodes;
+  *tn = c->tet_nodes;
+  return DG_OK;
+}
+
+int dg_node_coords(const dg_ctx* c, double* xyz) {
+  if (!c) return DG_ERR_ARG;
+  if (!xyz) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
+  const RefElems& R = *c->ref;
+  const int64_t tot = c->wedge_nodes + c->tet_nodes;
+  const double* V = c->VX.data();
+  for (int64_t k = 0; k < c->K; ++k) {
+    const int64_t o = c->node_off[k];
+    if (c->etype[k] == DG_WEDGE) {
+      for (int j = 0; j < R.Nq; ++j)
+        for (int i = 0; i < R.Nt; ++i) {
+          const double r = R.tri_r[i], s = R.tri_s[i], t = R.gll[j];
+          const double lam[3] = {-0.5 * (r + s), 0.5 * (1 + r), 0.5 * (1 + s)};
+          const double lo = 0.5 * (1 - t), hi = 0.5 * (1 + t);
+          for (int d = 0; d < 3; ++d) {
+            double x = 0.0;
+            for (int a = 0; a < 3; ++a)
+              x += lam[a] * (lo * V[c->EToV[k * 6 + a] * 3 + d] + hi * V[c->EToV[k * 6 + a + 3] * 3 + d]);
+            xyz[d * tot + o + j * R.Nt + i] = x;
+          }
+        }
+    } else {
+      for (int n = 0; n < R.Npt; ++n) {
+        const double r = R.tet_r[n], s = R.tet_s[n], t = R.tet_t[n];
+        const double lam[4] = {-0.5 * (1 + r + s + t), 0.5 * (1 + r), 0.5 * (1 + s), 0.5 * (1 + t)};
+        for (int d = 0; d < 3; ++d) {
+          double x = 0.0;
+          for (int v = 0; v < 4; ++v) x += lam[v] * V[c->EToV[k * 6 + v] * 3 + d];
+          xyz[d * tot + o + n] = x;
+        }
+      }
+    }
+  }
+  return DG_OK;
+}
+
+int dg_face_neighbors(const dg_ctx* c, int64_t* out, int64_t* count) {
+  if (!c) return DG_ERR_ARG;
+  if (!count) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
+  const RefElems& R = *c->ref;
+  int64_t n = 0;
+  for (int64_t k = 0; k < c->K; ++k) {
+    const bool w = c->etype[k] == DG_WEDGE;
+    for (int f = 0; f < nfaces_of(c->etype[k]); ++f) {
+      const std::vector<int>& own = w ? R.wedge_face_nodes[f] : R.tet_face_nodes[f];
+      const int64_t k2 = c->nbr[k][f];
+      for (size_t q = 0; q < own.size(); ++q, ++n) {
+        if (!out) continue;
+        if (k2 < 0) {
+          out[n] = -1;
+          continue;
+        }
+        const int code = c->code[k][f];
+        int node;
+        if (w && f >= 2) {
+          const int jj = int(q) / R.Nq, m = int(q) % R.Nq;
+          const int ep = code >> 1, rev = code & 1;
+          node = jj * R.Nt + R.edge_nodes[ep][rev ? R.N - m : m];
+        } else {
+          const int nf = (code >> 4) & 3, perm = code & 15;
+          const int nk = R.tri_perm[perm][q];
+          node = (c->etype[k2] == DG_TET) ? R.tet_face_nodes[nf][nk] : (nf ? R.N * R.Nt : 0) + nk;
+        }
+        out[n] = c->node_off[k2] + node;
+      }
+    }
+  }
+  *count = n;
+  return DG_OK;
+}
+
+int dg_reference_operator(const dg_ctx* c, const char* name, double* out, int64_t* rows, int64_t* cols) {
+  if (!c) return DG_ERR_ARG;
+  if (!name || !rows || !cols) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
+  const RefElems& R = *c->ref;
+  const Mat* M = nullptr;
+  const std::vector<double>* v = nullptr;
+  const std::string s(name);
+  if (s == "tri.Dr") M = &R.Dr;
+  else if (s == "tri.Ds") M = &R.Ds;
+  else if (s == "tri.M") M = &R.Mt;
+  else if (s == "tri.M0") M = &R.Ma[0];
+  else if (s == "tri.M1") M = &R.Ma[1];
+  else if (s == "tri.M2") M = &R.Ma[2];
+  else if (s == "line.D") M = &R.D1;
+  else if (s == "line.M") M = &R.M1;
+  else if (s == "line.Ma") M = &R.Mea;
+  else if (s == "line.Mb") M = &R.Meb;
+  else if (s == "tet.Dr") M = &R.tDr;
+  else if (s == "tet.Ds") M = &R.tDs;
+  else if (s == "tet.Dt") M = &R.tDt;
+  else if (s == "tet.M") M = &R.tM;
+  else if (s == "tet.LIFT") M = &R.tLIFT;
+  else if (s == "tri.r") v = &R.tri_r;
+  else if (s == "tri.s") v = &R.tri_s;
+  else if (s == "line.r") v = &R.gll;
+  else if (s == "line.ell0") v = &R.ell0;
+  else if (s == "line.ellN") v = &R.ellN;
+  else if (s == "tet.r") v = &R.tet_r;
+  else if (s == "tet.s") v = &R.tet_s;
+  else if (s == "tet.t") v = &R.tet_t;
+  else return DG_ERR_ARG;
+  if (M) {
+    *rows = M->r;
+    *cols = M->c;
+    if (out) std::copy(M->a.begin(), M->a.end(), out);
+  } else {
+    *rows = int64_t(v->size());
+    *cols = 1;
+    if (out) std::copy(v->begin(), v->end(), out);
+  }
+  return DG_OK;
+}
+
+int dg_device_bytes(const dg_ctx* c, size_t* mesh_bytes, size_t* field_bytes) {
+  if (!c) return DG_ERR_ARG;
+  if (!mesh_bytes || !field_bytes) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
+  *mesh_bytes = blob_layout(c).total;
+  *field_bytes = field_bytes_of(c);
+  return DG_OK;
+}
+
+int dg_bind(dg_ctx* c, void* d_mesh, void* d_q0, void* d_q1, void* d_res, void* stream) {
+  if (!c) return DG_ERR_ARG;
+  if (!d_mesh || !d_q0 || !d_q1 || !d_res) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!c->N) return c->fail(DG_ERR_STATE, "dg_bind before dg_set_order");
+  if (c->bound) return c->fail(DG_ERR_STATE, "context already bound");
+  for (void* p : {d_mesh, d_q0, d_q1, d_res})
+    if (reinterpret_cast<uintptr_t>(p) % 256) return c->fail(DG_ERR_ARG, "device buffers must be 256-byte aligned");
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->d_mesh = d_mesh;
+  c->d_q[0] = d_q0;
+  c->d_q[1] = d_q1;
+  c->d_res = d_res;
+  const BlobLayout L = blob_layout(c);
+  std::vector<unsigned char> blob;
+  if (c->prec == DG_F64) {
+    fill_blob<double>(c, L, blob);
+    fill_devmesh<double>(c, L, c->m64);
+  } else {
+    fill_blob<float>(c, L, blob);
+    fill_devmesh<float>(c, L, c->m32);
+  }
+  c->mesh_bytes = L.total;
+  c->field_bytes = field_bytes_of(c);
+  e = cudaMemcpyAsync(d_mesh, blob.data(), blob.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "mesh upload");
+  for (void* p : {d_q0, d_q1, d_res}) {
+    e = cudaMemsetAsync(p, 0, c->field_bytes, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "state clear");
+  }
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "bind synchronize");
+  build_ops(c);
+  const int rc = ensure_ops(c);
+  if (rc) return rc;
+  e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(c, e, "capture stream");
+  c->bound = true;
+  c->cur = 0;
+  c->t = 0.0;
+  return DG_OK;
+}
+
+int dg_set_fields(dg_ctx* c, const void* q, int on_device) {
+  if (!c) return DG_ERR_ARG;
+  if (!q) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_set_fields before dg_bind");
+  int rc = ensure_ops(c);
+  if (rc) return rc;
+  const size_t rs = c->prec == DG_F64 ? 8 : 4;
+  const size_t bytes = size_t(4) * (c->wedge_nodes + c->tet_nodes) * rs;
+  const void* src = q;
+  if (!on_device) {
+    cudaError_t e = cudaMemcpyAsync(c->d_q[1 - c->cur], q, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "state upload");
+    src = c->d_q[1 - c->cur];
+    // pack reads the scratch copy into the current buffer
+  }
+  rc = launch_pack(c, src, c->d_q[c->cur], false, c->stream);
+  if (rc) return rc;
+  cudaError_t e = cudaMemsetAsync(c->d_res, 0, c->field_bytes, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "residual clear");
+  if (!on_device) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "state upload synchronize");
+  }
+  c->t = 0.0;
+  return DG_OK;
+}
+
+int dg_get_fields(dg_ctx* c, void* q, int on_device) {
+  if (!c) return DG_ERR_ARG;
+  if (!q) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_get_fields before dg_bind");
+  const size_t rs = c->prec == DG_F64 ? 8 : 4;
+  const size_t bytes = size_t(4) * (c->wedge_nodes + c->tet_nodes) * rs;
+  void* dst = on_device ? q : c->d_q[1 - c->cur];
+  int rc = launch_pack(c, dst, c->d_q[c->cur], true, c->stream);
+  if (rc) return rc;
+  if (!on_device) {
+    cudaError_t e = cudaMemcpyAsync(q, dst, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "state download");
+  }
+  return DG_OK;
+}
+
+int dg_rhs(dg_ctx* c, const void* d_q, void* d_rhs) {
+  if (!c) return DG_ERR_ARG;
+  if (!d_q || !d_rhs) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_rhs before dg_bind");
+  int rc = ensure_ops(c);
+  if (rc) return rc;
+  void* A = c->d_q[1 - c->cur];
+  void* B = c->d_res;
+  rc = launch_pack(c, d_q, A, false, c->stream);
+  if (rc) return rc;
+  rc = launch_stage(c, A, B, nullptr, 0.0, 0.0, 0.0, false, c->stream);
+  if (rc) return rc;
+  rc = launch_pack(c, d_rhs, B, true, c->stream);
+  if (rc) return rc;
+  // the residual buffer was used as scratch; the next step starts from zero
+  cudaError_t e = cudaMemsetAsync(c->d_res, 0, c->field_bytes, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "residual clear");
+  return DG_OK;
+}
+
+int dg_step(dg_ctx* c, double dt, int64_t nsteps) {
+  if (!c) return DG_ERR_ARG;
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_step before dg_bind");
+  if (!(dt > 0) || nsteps < 0) return c->fail(DG_ERR_ARG, "dt must be positive and nsteps >= 0");
+  int rc = ensure_ops(c);
+  if (rc) return rc;
+  for (int64_t n = 0; n < nsteps; ++n) {
+    const int p = c->cur;
+    if (!c->gexec[p] || c->gdt[p] != dt) {
+      if (c->gexec[p]) {
+        cudaGraphExecDestroy(c->gexec[p]);
+        c->gexec[p] = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph capture begin");
+      int src = p;
+      int lrc = DG_OK;
+      for (int s = 0; s < 5 && lrc == DG_OK; ++s) {
+        lrc = launch_stage(c, c->d_q[src], c->d_q[1 - src], c->d_res, kLSRK_A[s], kLSRK_B[s], dt, true, c->cap_stream);
+        src = 1 - src;
+      }
+      e = cudaStreamEndCapture(c->cap_stream, &g);
+      if (lrc) {
+        if (g) cudaGraphDestroy(g);
+        return lrc;
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph capture end");
+      e = cudaGraphInstantiate(&c->gexec[p], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+      c->gdt[p] = dt;
+    }
+    cudaError_t e = cudaGraphLaunch(c->gexec[p], c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    c->cur = 1 - c->cur;  // five stages: odd number of buffer swaps
+    c->t += dt;
+  }
+  return DG_OK;
+}
+
+int dg_energy(dg_ctx* c, double* E) {
+  if (!c) return DG_ERR_ARG;
+  if (!E) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_energy before dg_bind");
+  int rc = ensure_ops(c);
+  if (rc) return rc;
+  int lr;
+  double* dE;
+  if (c->prec == DG_F64) {
+    lr = energy_f64(c->N, c->m64, static_cast<const double*>(c->d_q[c->cur]), c->stream);
+    dE = c->m64.energy;
+  } else {
+    lr = energy_f32(c->N, c->m32, static_cast<const float*>(c->d_q[c->cur]), c->stream);
+    dE = c->m32.energy;
+  }
+  if (lr) return cuda_fail(c, cudaError_t(lr), "energy launch");
+  cudaError_t e = cudaMemcpyAsync(E, dE, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "energy download");
+  return check_device_error(c);
+}
+
+int dg_sync(dg_ctx* c) {
+  if (!c) return DG_ERR_ARG;
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_sync before dg_bind");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  return check_device_error(c);
+}
+
+int dg_time(const dg_ctx* c, double* t) {
+  if (!c) return DG_ERR_ARG;
+  if (!t) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  *t = c->t;
+  return DG_OK;
+}
+
+int dg_stable_dt(const dg_ctx* c, double cfl, double* dt) {
+  if (!c) return DG_ERR_ARG;
+  if (!dt || !(cfl > 0)) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
+  double best = INFINITY;
+  for (int64_t k = 0; k < c->K; ++k) {
+    const double ratio = c->etype[k] == DG_WEDGE ? wedge_stable_ratio(c, k) : tet_stable_ratio(c, k);
+    const double cc = std::sqrt(c->c2[k]);
+    best = std::min(best, 1.0 / (cc * (c->N + 1) * (c->N + 1) * ratio));
+  }
+  *dt = cfl * best;
+  return DG_OK;
+}
+
+const char* dg_last_error(const dg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void dg_destroy(dg_ctx* c) {
+  if (!c) return;
+  drop_graphs(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+}  // extern "C"

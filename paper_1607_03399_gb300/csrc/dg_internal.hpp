@@ -1,0 +1,114 @@
+// Internal types shared by the host library and the CUDA kernels.
+//
+// Device data layout (all element-indexed arrays are structure-of-arrays over
+// 32-element blocks so that one warp reads one 128-byte line per item):
+//   field buffers  wedge region [nblk_w][4 fields][Np_w][32], then
+//                  tet region   [nblk_t][4 fields][Np_t][32]   (packed state)
+//   w_vid   [6][Kw_pad]  vertex ids            t_vid  [4][Kt_pad]
+//   w_nbr   [5][Kw_pad]  neighbour index       t_nbr  [4][Kt_pad]
+//   w_code  [5][Kw_pad]  orientation code      t_code [4][Kt_pad]
+//   w_mat   [3][Kw_pad]  kappa, 1/rho, rho c   t_mat  [3][Kt_pad]
+//   vx, vy, vz [nverts]
+// Neighbour index -1 marks a boundary face.  Orientation codes:
+//   triangle face: bit 6 set = neighbour is a tet; bits 4-5 = neighbour's face;
+//                  bits 0-3 = triangle symmetry p0*3+p1 (see RefElems::tri_perm)
+//   wedge quad face: (neighbour's triangle edge) * 2 + reversed
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace dgw {
+
+constexpr int kB = 32;            // elements per block (one warp lane each)
+constexpr int kMaxOrder = 4;
+constexpr int kCodeTet = 64;
+
+__host__ __device__ constexpr int nt_of(int N) { return (N + 1) * (N + 2) / 2; }
+__host__ __device__ constexpr int npw_of(int N) { return nt_of(N) * (N + 1); }
+__host__ __device__ constexpr int npt_of(int N) { return (N + 1) * (N + 2) * (N + 3) / 6; }
+
+// Operator tables placed in device constant memory, one configuration at a time.
+template <int N, typename real>
+struct WedgeOps {
+  static constexpr int Nt = nt_of(N), Nq = N + 1;
+  real Dr[Nt * Nt], Ds[Nt * Nt], M[Nt * Nt], Ma[3][Nt * Nt];
+  real Dt[Nq * Nq], ell0[Nq], ellN[Nq], Mea[Nq * Nq], Meb[Nq * Nq], M1[Nq * Nq], gll[Nq];
+};
+
+template <int N, typename real>
+struct TetOps {
+  static constexpr int Np = npt_of(N), Nt = nt_of(N);
+  real Dr[Np * Np], Ds[Np * Np], Dt[Np * Np], LIFT[Np * 4 * Nt];
+};
+
+template <int N>
+struct Tables {
+  static constexpr int Nt = nt_of(N), Nq = N + 1;
+  int8_t tri_perm[9][Nt];
+  int8_t edge[3][Nq];
+  int8_t tet_face[4][Nt];
+};
+
+template <int N, typename real>
+struct AllOps {
+  WedgeOps<N, real> w;
+  TetOps<N, real> t;
+  Tables<N> tab;
+};
+
+template <typename real>
+struct DevMesh {
+  int Kw = 0, Kw_pad = 0, nblk_w = 0;
+  const int* w_vid = nullptr;
+  const int* w_nbr = nullptr;
+  const int* w_code = nullptr;
+  const real* w_mat = nullptr;
+  const int64_t* w_canon = nullptr;  // canonical node offset of each wedge
+  int Kt = 0, Kt_pad = 0, nblk_t = 0;
+  const int* t_vid = nullptr;
+  const int* t_nbr = nullptr;
+  const int* t_code = nullptr;
+  const real* t_mat = nullptr;
+  const int64_t* t_canon = nullptr;
+  const real* vx = nullptr;
+  const real* vy = nullptr;
+  const real* vz = nullptr;
+  int64_t tet_off = 0;               // first real of the tet region in a field buffer
+  int64_t total_nodes = 0;           // canonical nodes
+  int* err = nullptr;                // device error word
+  double* partials = nullptr;        // per-block energy partial sums
+  double* energy = nullptr;          // final energy
+  const real* tet_mass = nullptr;    // reference tet mass matrix (energy only)
+};
+
+template <typename real>
+struct StageArgs {
+  DevMesh<real> m;
+  const real* q_in = nullptr;   // packed state read by this stage
+  real* q_out = nullptr;        // RK: packed next state; RHS mode: packed rhs
+  real* res = nullptr;          // RK residual (unused in RHS mode)
+  real rk_a = 0, rk_b = 0, dt = 0;
+  int bc = 1, flux = 0;
+};
+
+enum : int { kErrTimeout = 1, kErrNonfinite = 2 };
+
+// Launchers, one set per (precision, order) translation unit k_<p>_n<N>.cu;
+// all return 0 or a cudaError_t value.
+#define DGW_DECLARE_LAUNCHERS(P, T, N)                                                              \
+  int upload_ops_##P##n##N(const void* host_ops, size_t bytes, void* stream);                      \
+  int launch_stage_##P##n##N(const StageArgs<T>& a, bool rk, void* stream);                        \
+  int launch_pack_##P##n##N(const DevMesh<T>& m, const T* canon, T* packed, bool unpack, void* s); \
+  int launch_energy_##P##n##N(const DevMesh<T>& m, const T* q, void* stream);
+DGW_DECLARE_LAUNCHERS(f32, float, 1)
+DGW_DECLARE_LAUNCHERS(f32, float, 2)
+DGW_DECLARE_LAUNCHERS(f32, float, 3)
+DGW_DECLARE_LAUNCHERS(f32, float, 4)
+DGW_DECLARE_LAUNCHERS(f64, double, 1)
+DGW_DECLARE_LAUNCHERS(f64, double, 2)
+DGW_DECLARE_LAUNCHERS(f64, double, 3)
+DGW_DECLARE_LAUNCHERS(f64, double, 4)
+
+}  // namespace dgw

@@ -1,0 +1,977 @@
+// CUDA kernels of the DG stage (included once per precision; the including
+// translation unit defines REAL and the constant-memory table c_ops).
+//
+// Wedge stage (Sections 3.2, 4.2; one launch per Runge-Kutta stage):
+//   CTA = 32 consecutive wedges x (N+1) warps; warp j owns GLL slice j of all
+//   32 elements, lane = element.  Per element and slice:
+//     geometry from the 6 vertices (Lemma 3.1): r_x, r_y, s_x, s_y, t_zJ = A
+//       constant, t_xJ, t_yJ at t_j, J_a = A h_a / 2 at the three columns;
+//     W_j = M^tri [ T_j + J_fb ell0_j F_bot + J_ft ellN_j F_top ]
+//           + sum_quad M~_e F_e,j                       (lift, weak form)
+//       T_j = - sum_c t_cJ(t_j) (D_t u_c)_j  (p),  - t_cJ(t_j) (D_t p)_j  (u_c)
+//     X_j = (M^{tri,k})^{-1} W_j, M^{tri,k} = sum_a J_a M_a, by a per-element
+//       Cholesky factor computed on the fly (exact inverse of the
+//       Jacobian-weighted wedge mass, Section 4.2);
+//     rhs = kappa (-(D_r (r.u) + D_s (s.u))_j + X_p),
+//     rhs_u_c = (1/rho) (-(r_c D_r p + s_c D_s p)_j + X_u_c);
+//     fused LSRK update res <- a res + dt rhs, q_out <- q_in + b res.
+// Tet stage: affine tets, one thread per element (Section 3.2: physical
+//   operators are scaled reference operators).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dg_internal.hpp"
+
+namespace dgw {
+namespace REALNS {
+
+using real = REAL;
+
+template <int N>
+__device__ __forceinline__ const AllOps<N, real>& OPS() {
+  static_assert(N == NORD, "one order per translation unit");
+  return c_ops;
+}
+
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_r(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+
+// triangle node (a, b) -> index; edge node m of triangle edge ed (from its
+// first to its second vertex)
+__host__ __device__ constexpr int tri_idx(int N, int a, int b) { return b * (N + 1) - (b * (b - 1)) / 2 + a; }
+__host__ __device__ constexpr int edge_node(int N, int ed, int m) {
+  return ed == 0 ? tri_idx(N, m, 0) : (ed == 1 ? tri_idx(N, N - m, m) : tri_idx(N, 0, N - m));
+}
+// k-th node of tet face f in element node order
+__host__ __device__ constexpr int tet_face_node(int N, int f, int k) {
+  int n = 0, cnt = 0;
+  for (int c = 0; c <= N; ++c)
+    for (int b = 0; b <= N - c; ++b)
+      for (int a = 0; a <= N - b - c; ++a) {
+        const bool on = (f == 0) ? (c == 0) : (f == 1) ? (b == 0) : (f == 2) ? (a + b + c == N) : (a == 0);
+        if (on) {
+          if (cnt == k) return n;
+          ++cnt;
+        }
+        ++n;
+      }
+  return -1;
+}
+
+template <int N>
+__device__ __forceinline__ int64_t widx(int blk_e, int f, int node, int lane) {
+  constexpr int Np = npw_of(N);
+  return ((int64_t(blk_e) * 4 + f) * Np + node) * kB + lane;
+}
+template <int N>
+__device__ __forceinline__ int64_t tidx(int64_t off, int blk_e, int f, int node, int lane) {
+  constexpr int Np = npt_of(N);
+  return off + ((int64_t(blk_e) * 4 + f) * Np + node) * kB + lane;
+}
+
+// Penalty fluxes of eq. (1): F_p = 1/2 (tau_p [p] - [u_n]), F_u = 1/2 (tau_u [u_n] - [p]).
+__device__ __forceinline__ void penalty_flux(real dp, real dun, real tau_p, real tau_u, real& Fp, real& Fu) {
+  Fp = real(0.5) * (tau_p * dp - dun);
+  Fu = real(0.5) * (tau_u * dun - dp);
+}
+// Boundary ghosts: Dirichlet p+ = -p-, u+ = u-  -> [p] = -2p, [u_n] = 0;
+// rigid p+ = p-, u+ = u- - 2 u_n n             -> [p] = 0, [u_n] = -2 u_n.
+__device__ __forceinline__ void boundary_jumps(int bc, real pM, real unM, real& dp, real& dun) {
+  if (bc == 0) {
+    dp = real(-2) * pM;
+    dun = real(0);
+  } else {
+    dp = real(0);
+    dun = real(-2) * unM;
+  }
+}
+
+__device__ __forceinline__ void taus(int flux, real zM, real zP, real& tau_p, real& tau_u) {
+  const real zavg = real(0.5) * (zM + zP);
+  if (flux == 0) {
+    tau_p = real(1) / zavg;
+    tau_u = zavg;
+  } else {
+    tau_p = real(0);
+    tau_u = real(0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// wedge stage
+// ---------------------------------------------------------------------------
+// per-element geometric factors kept in shared memory ([item][32])
+enum WGeo : int {
+  G_RX, G_RY, G_SX, G_SY, G_A, G_J0, G_J1, G_J2, G_NB0, G_NB1, G_NB2, G_NT0, G_NT1, G_NT2, G_JFB, G_JFT,
+  G_QNX0, G_QNX1, G_QNX2, G_QNY0, G_QNY1, G_QNY2, G_QCA0, G_QCA1, G_QCA2, G_QCB0, G_QCB1, G_QCB2,
+  G_KAPPA, G_IRHO, G_Z, G_TX0, G_TX1, G_TY0, G_TY1, G_COUNT
+};
+
+template <int N>
+__host__ __device__ constexpr int wedge_smem_reals() {
+  return 4 * npw_of(N) * kB + (nt_of(N) * (nt_of(N) + 1) / 2) * kB + 4 * nt_of(N) * kB + G_COUNT * kB;
+}
+
+// Lemma 3.1 for the wedge of lane e: everything the stage needs, from the six
+// vertices (bi-unit reference, x = sum_a lambda_a(r,s) [(1-t)/2 X_a + (1+t)/2 X_{a+3}]).
+__device__ __forceinline__ void wedge_geometry(const DevMesh<real>& M, int e, real* sG, int lane) {
+  const int Kp = M.Kw_pad;
+  const int vb0 = M.w_vid[0 * Kp + e], vb1 = M.w_vid[1 * Kp + e], vb2 = M.w_vid[2 * Kp + e];
+  const int vt0 = M.w_vid[3 * Kp + e], vt1 = M.w_vid[4 * Kp + e], vt2 = M.w_vid[5 * Kp + e];
+  const real x0 = M.vx[vb0], x1 = M.vx[vb1], x2 = M.vx[vb2];
+  const real y0 = M.vy[vb0], y1 = M.vy[vb1], y2 = M.vy[vb2];
+  const real zb0 = M.vz[vb0], zb1 = M.vz[vb1], zb2 = M.vz[vb2];
+  const real zt0 = M.vz[vt0], zt1 = M.vz[vt1], zt2 = M.vz[vt2];
+  auto put = [&](int item, real v) { sG[item * kB + lane] = v; };
+  const real xr = real(0.5) * (x1 - x0), xs = real(0.5) * (x2 - x0);
+  const real yr = real(0.5) * (y1 - y0), ys = real(0.5) * (y2 - y0);
+  const real A = xr * ys - xs * yr;  // t_z J (constant)
+  const real iA = real(1) / A;
+  put(G_RX, ys * iA);
+  put(G_RY, -xs * iA);
+  put(G_SX, -yr * iA);
+  put(G_SY, xr * iA);
+  put(G_A, A);
+  const real h0 = zt0 - zb0, h1 = zt1 - zb1, h2 = zt2 - zb2;
+  put(G_J0, real(0.5) * A * h0);  // J at the three columns (J linear in r, s)
+  put(G_J1, real(0.5) * A * h1);
+  put(G_J2, real(0.5) * A * h2);
+  // z_r, z_s are linear in t: z_r(t) = zr0 + t zr1 (likewise z_s), so
+  // t_x J = y_r z_s - z_r y_s and t_y J = z_r x_s - x_r z_s are linear in t
+  const real zr0 = real(0.25) * ((zb1 - zb0) + (zt1 - zt0)), zr1 = real(0.25) * ((zt1 - zt0) - (zb1 - zb0));
+  const real zs0 = real(0.25) * ((zb2 - zb0) + (zt2 - zt0)), zs1 = real(0.25) * ((zt2 - zt0) - (zb2 - zb0));
+  put(G_TX0, yr * zs0 - zr0 * ys);
+  put(G_TX1, yr * zs1 - zr1 * ys);
+  put(G_TY0, zr0 * xs - xr * zs0);
+  put(G_TY1, zr1 * xs - xr * zs1);
+  {
+    const real ax = x1 - x0, ay = y1 - y0, bx = x2 - x0, by = y2 - y0;
+    real az = zb1 - zb0, bz = zb2 - zb0;
+    real cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+    real nrm = sqrt_r(cx * cx + cy * cy + cz * cz);
+    put(G_JFB, real(0.25) * nrm);  // J_f = area / 2
+    put(G_NB0, -cx / nrm);
+    put(G_NB1, -cy / nrm);
+    put(G_NB2, -cz / nrm);
+    az = zt1 - zt0;
+    bz = zt2 - zt0;
+    cx = ay * bz - az * by;
+    cy = az * bx - ax * bz;
+    cz = ax * by - ay * bx;
+    nrm = sqrt_r(cx * cx + cy * cy + cz * cz);
+    put(G_JFT, real(0.25) * nrm);
+    put(G_NT0, cx / nrm);
+    put(G_NT1, cy / nrm);
+    put(G_NT2, cz / nrm);
+  }
+  const real xx[3] = {x0, x1, x2}, yy[3] = {y0, y1, y2}, hh[3] = {h0, h1, h2};
+#pragma unroll
+  for (int ed = 0; ed < 3; ++ed) {
+    const int ia = ed, ib = (ed + 1) % 3;
+    const real dx = xx[ib] - xx[ia], dy = yy[ib] - yy[ia];
+    const real Le = sqrt_r(dx * dx + dy * dy);
+    put(G_QNX0 + ed, dy / Le);  // horizontal outward normal of the quad face
+    put(G_QNY0 + ed, -dx / Le);
+    put(G_QCA0 + ed, real(0.25) * Le * hh[ia]);  // M~_e = ca Mea + cb Meb
+    put(G_QCB0 + ed, real(0.25) * Le * hh[ib]);
+  }
+  put(G_KAPPA, M.w_mat[0 * Kp + e]);
+  put(G_IRHO, M.w_mat[1 * Kp + e]);
+  put(G_Z, M.w_mat[2 * Kp + e]);
+}
+
+template <int N>
+__global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 2 : 4) : 1) k_wedge_stage(const StageArgs<real> A, bool rk) {
+  constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
+  constexpr int NL = Nt * (Nt + 1) / 2;
+  const AllOps<N, real>& O = OPS<N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sq = reinterpret_cast<real*>(smem_raw);  // [4][Np][32]  state slab
+  real* sL = sq + 4 * Np * kB;                   // [NL][32]     Cholesky factor
+  real* sF = sL + NL * kB;                       // [4][Nt][32]  bottom/top F_p, F_u
+  real* sG = sF + 4 * Nt * kB;                   // [G_COUNT][32] geometry
+  const DevMesh<real>& M = A.m;
+  const int lane = threadIdx.x & 31;
+  const int j = threadIdx.x >> 5;
+  const int blk = blockIdx.x;
+  const int e = blk * kB + lane;
+  const int Kp = M.Kw_pad;
+#define GEO(item) sG[(item) * kB + lane]
+
+  // 0. state slab of this block -> shared memory (one contiguous range);
+  //    warp 0 also evaluates the geometric factors
+  {
+    constexpr int nvec = 4 * Np * kB * int(sizeof(real)) / 16;
+    const int4* src = reinterpret_cast<const int4*>(A.q_in + int64_t(blk) * 4 * Np * kB);
+    int4* dst = reinterpret_cast<int4*>(sq);
+    for (int v = threadIdx.x; v < nvec; v += blockDim.x) dst[v] = __ldg(src + v);
+  }
+  if (j == 0) wedge_geometry(M, e, sG, lane);
+  __syncthreads();
+
+  // 1. prologue: triangle-face fluxes (warps 0 and N), Cholesky (warp 1, or 0 if N = 1)
+  if (j == 0 || j == N) {
+    const int fb = (j == 0) ? 0 : 1;
+    const real nn0 = fb ? GEO(G_NT0) : GEO(G_NB0), nn1 = fb ? GEO(G_NT1) : GEO(G_NB1), nn2 = fb ? GEO(G_NT2) : GEO(G_NB2);
+    const real zM = GEO(G_Z);
+    const int nbr = M.w_nbr[fb * Kp + e];
+    const int code = M.w_code[fb * Kp + e];
+    const int own0 = fb ? N * Nt : 0;
+    real tau_p, tau_u;
+    if (nbr < 0) {
+      taus(A.flux, zM, zM, tau_p, tau_u);
+#pragma unroll
+      for (int k = 0; k < Nt; ++k) {
+        const real pM = sq[(0 * Np + own0 + k) * kB + lane];
+        const real unM = nn0 * sq[(1 * Np + own0 + k) * kB + lane] + nn1 * sq[(2 * Np + own0 + k) * kB + lane] +
+                         nn2 * sq[(3 * Np + own0 + k) * kB + lane];
+        real dp, dun, Fp, Fu;
+        boundary_jumps(A.bc, pM, unM, dp, dun);
+        penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
+        sF[((2 * fb + 0) * Nt + k) * kB + lane] = Fp;
+        sF[((2 * fb + 1) * Nt + k) * kB + lane] = Fu;
+      }
+    } else {
+      const bool ntet = (code & kCodeTet) != 0;
+      const int nf = (code >> 4) & 3;
+      const int perm = code & 15;
+      const real zP = ntet ? M.t_mat[2 * M.Kt_pad + nbr] : M.w_mat[2 * Kp + nbr];
+      taus(A.flux, zM, zP, tau_p, tau_u);
+      const bool inblk = !ntet && ((nbr >> 5) == blk);
+#pragma unroll
+      for (int k = 0; k < Nt; ++k) {
+        const int nk = O.tab.tri_perm[perm][k];
+        real pP, uxP, uyP, uzP;
+        if (ntet) {
+          const int node = O.tab.tet_face[nf][nk];
+          pP = __ldg(A.q_in + tidx<N>(M.tet_off, nbr >> 5, 0, node, nbr & 31));
+          uxP = __ldg(A.q_in + tidx<N>(M.tet_off, nbr >> 5, 1, node, nbr & 31));
+          uyP = __ldg(A.q_in + tidx<N>(M.tet_off, nbr >> 5, 2, node, nbr & 31));
+          uzP = __ldg(A.q_in + tidx<N>(M.tet_off, nbr >> 5, 3, node, nbr & 31));
+        } else {
+          const int node = (nf ? N * Nt : 0) + nk;
+          if (inblk) {
+            pP = sq[(0 * Np + node) * kB + (nbr & 31)];
+            uxP = sq[(1 * Np + node) * kB + (nbr & 31)];
+            uyP = sq[(2 * Np + node) * kB + (nbr & 31)];
+            uzP = sq[(3 * Np + node) * kB + (nbr & 31)];
+          } else {
+            pP = __ldg(A.q_in + widx<N>(nbr >> 5, 0, node, nbr & 31));
+            uxP = __ldg(A.q_in + widx<N>(nbr >> 5, 1, node, nbr & 31));
+            uyP = __ldg(A.q_in + widx<N>(nbr >> 5, 2, node, nbr & 31));
+            uzP = __ldg(A.q_in + widx<N>(nbr >> 5, 3, node, nbr & 31));
+          }
+        }
+        const real pM = sq[(0 * Np + own0 + k) * kB + lane];
+        const real unM = nn0 * sq[(1 * Np + own0 + k) * kB + lane] + nn1 * sq[(2 * Np + own0 + k) * kB + lane] +
+                         nn2 * sq[(3 * Np + own0 + k) * kB + lane];
+        const real unP = nn0 * uxP + nn1 * uyP + nn2 * uzP;
+        real Fp, Fu;
+        penalty_flux(pP - pM, unP - unM, tau_p, tau_u, Fp, Fu);
+        sF[((2 * fb + 0) * Nt + k) * kB + lane] = Fp;
+        sF[((2 * fb + 1) * Nt + k) * kB + lane] = Fu;
+      }
+    }
+  }
+  if (j == (N >= 2 ? 1 : 0)) {
+    // M^{tri,k} = sum_a J_a M_a; L L^T factor row by row, inverse diagonal
+    // stored in place of the diagonal.
+    const real J0 = GEO(G_J0), J1 = GEO(G_J1), J2 = GEO(G_J2);
+#pragma unroll
+    for (int i = 0; i < Nt; ++i) {
+      real row[Nt];
+#pragma unroll
+      for (int l = 0; l < i; ++l) {
+        real s = J0 * O.w.Ma[0][i * Nt + l] + J1 * O.w.Ma[1][i * Nt + l] + J2 * O.w.Ma[2][i * Nt + l];
+#pragma unroll
+        for (int k = 0; k < l; ++k) s -= row[k] * sL[(l * (l + 1) / 2 + k) * kB + lane];
+        row[l] = s * sL[(l * (l + 1) / 2 + l) * kB + lane];
+      }
+      real d = J0 * O.w.Ma[0][i * Nt + i] + J1 * O.w.Ma[1][i * Nt + i] + J2 * O.w.Ma[2][i * Nt + i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) d -= row[k] * row[k];
+#pragma unroll
+      for (int l = 0; l < i; ++l) sL[(i * (i + 1) / 2 + l) * kB + lane] = row[l];
+      sL[(i * (i + 1) / 2 + i) * kB + lane] = rsqrt_r(d);
+    }
+  }
+  __syncthreads();
+
+  // 2. slice j of every element of the block
+  real Wp[Nt], Wu[3][Nt];
+#pragma unroll
+  for (int i = 0; i < Nt; ++i) Wp[i] = Wu[0][i] = Wu[1][i] = Wu[2][i] = real(0);
+  // (a) quadrilateral faces at slice j: W += M~_e F, M~_e = (L_e/4)(h_a Mea + h_b Meb)
+  {
+    const real zM = GEO(G_Z);
+#pragma unroll
+    for (int ed = 0; ed < 3; ++ed) {
+      const real nx = GEO(G_QNX0 + ed), ny = GEO(G_QNY0 + ed);
+      const int nbr = M.w_nbr[(2 + ed) * Kp + e];
+      const int code = M.w_code[(2 + ed) * Kp + e];
+      real Fp[Nq], Fu[Nq];
+      if (nbr < 0) {
+        real tau_p, tau_u;
+        taus(A.flux, zM, zM, tau_p, tau_u);
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          const int no = j * Nt + edge_node(N, ed, m);
+          const real pM = sq[(0 * Np + no) * kB + lane];
+          const real unM = nx * sq[(1 * Np + no) * kB + lane] + ny * sq[(2 * Np + no) * kB + lane];
+          real dp, dun;
+          boundary_jumps(A.bc, pM, unM, dp, dun);
+          penalty_flux(dp, dun, tau_p, tau_u, Fp[m], Fu[m]);
+        }
+      } else {
+        const real zP = M.w_mat[2 * Kp + nbr];
+        real tau_p, tau_u;
+        taus(A.flux, zM, zP, tau_p, tau_u);
+        const int ep = code >> 1, rev = code & 1;
+        const bool inblk = (nbr >> 5) == blk;
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          const int no = j * Nt + edge_node(N, ed, m);
+          const int nn = j * Nt + O.tab.edge[ep][rev ? N - m : m];
+          real pP, uxP, uyP;
+          if (inblk) {
+            pP = sq[(0 * Np + nn) * kB + (nbr & 31)];
+            uxP = sq[(1 * Np + nn) * kB + (nbr & 31)];
+            uyP = sq[(2 * Np + nn) * kB + (nbr & 31)];
+          } else {
+            pP = __ldg(A.q_in + widx<N>(nbr >> 5, 0, nn, nbr & 31));
+            uxP = __ldg(A.q_in + widx<N>(nbr >> 5, 1, nn, nbr & 31));
+            uyP = __ldg(A.q_in + widx<N>(nbr >> 5, 2, nn, nbr & 31));
+          }
+          const real pM = sq[(0 * Np + no) * kB + lane];
+          const real unM = nx * sq[(1 * Np + no) * kB + lane] + ny * sq[(2 * Np + no) * kB + lane];
+          penalty_flux(pP - pM, nx * uxP + ny * uyP - unM, tau_p, tau_u, Fp[m], Fu[m]);
+        }
+      }
+      const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
+#pragma unroll
+      for (int m = 0; m < Nq; ++m) {
+        real gpa = 0, gpb = 0, gua = 0, gub = 0;
+#pragma unroll
+        for (int n = 0; n < Nq; ++n) {
+          gpa += O.w.Mea[m * Nq + n] * Fp[n];
+          gpb += O.w.Meb[m * Nq + n] * Fp[n];
+          gua += O.w.Mea[m * Nq + n] * Fu[n];
+          gub += O.w.Meb[m * Nq + n] * Fu[n];
+        }
+        const real gp = ca * gpa + cbq * gpb, gu = ca * gua + cbq * gub;
+        const int i = edge_node(N, ed, m);
+        Wp[i] += gp;
+        Wu[0][i] += nx * gu;
+        Wu[1][i] += ny * gu;
+      }
+    }
+  }
+  {
+    real dtr[Nq];
+#pragma unroll
+    for (int m = 0; m < Nq; ++m) dtr[m] = O.w.Dt[j * Nq + m];
+    const real tj = O.w.gll[j];
+    const real txJ = GEO(G_TX0) + tj * GEO(G_TX1);
+    const real tyJ = GEO(G_TY0) + tj * GEO(G_TY1);
+    const real Aj = GEO(G_A);
+    const real cb = GEO(G_JFB) * O.w.ell0[j];
+    const real ct = GEO(G_JFT) * O.w.ellN[j];
+    // (b) pressure: G = -(t_xJ D_t u_x + t_yJ D_t u_y + A D_t u_z) + lifts; W += M^tri G
+    {
+      real G[Nt];
+#pragma unroll
+      for (int i = 0; i < Nt; ++i) {
+        real dux = 0, duy = 0, duz = 0;
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          dux += dtr[m] * sq[(1 * Np + m * Nt + i) * kB + lane];
+          duy += dtr[m] * sq[(2 * Np + m * Nt + i) * kB + lane];
+          duz += dtr[m] * sq[(3 * Np + m * Nt + i) * kB + lane];
+        }
+        G[i] = cb * sF[(0 * Nt + i) * kB + lane] + ct * sF[(2 * Nt + i) * kB + lane] - (txJ * dux + tyJ * duy + Aj * duz);
+      }
+#pragma unroll
+      for (int i = 0; i < Nt; ++i) {
+        real acc = 0;
+#pragma unroll
+        for (int l = 0; l < Nt; ++l) acc += O.w.M[i * Nt + l] * G[l];
+        Wp[i] += acc;
+      }
+    }
+    // (c) velocity: G_c = -t_cJ D_t p + n_c lifts; W += M^tri G
+    {
+      real dp[Nt];
+#pragma unroll
+      for (int i = 0; i < Nt; ++i) {
+        real acc = 0;
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) acc += dtr[m] * sq[(0 * Np + m * Nt + i) * kB + lane];
+        dp[i] = acc;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const real tc = (c == 0) ? txJ : (c == 1 ? tyJ : Aj);
+        const real nbc = GEO(G_NB0 + c) * cb, ntc = GEO(G_NT0 + c) * ct;
+        real G[Nt];
+#pragma unroll
+        for (int i = 0; i < Nt; ++i)
+          G[i] = nbc * sF[(1 * Nt + i) * kB + lane] + ntc * sF[(3 * Nt + i) * kB + lane] - tc * dp[i];
+#pragma unroll
+        for (int i = 0; i < Nt; ++i) {
+          real acc = 0;
+#pragma unroll
+          for (int l = 0; l < Nt; ++l) acc += O.w.M[i * Nt + l] * G[l];
+          Wu[c][i] += acc;
+        }
+      }
+    }
+  }
+  // (d) X = (M^{tri,k})^{-1} W: forward and backward substitution, 4 right-hand sides
+#pragma unroll
+  for (int i = 0; i < Nt; ++i) {
+#pragma unroll
+    for (int k = 0; k < i; ++k) {
+      const real l = sL[(i * (i + 1) / 2 + k) * kB + lane];
+      Wp[i] -= l * Wp[k];
+      Wu[0][i] -= l * Wu[0][k];
+      Wu[1][i] -= l * Wu[1][k];
+      Wu[2][i] -= l * Wu[2][k];
+    }
+    const real d = sL[(i * (i + 1) / 2 + i) * kB + lane];
+    Wp[i] *= d;
+    Wu[0][i] *= d;
+    Wu[1][i] *= d;
+    Wu[2][i] *= d;
+  }
+#pragma unroll
+  for (int i = Nt - 1; i >= 0; --i) {
+#pragma unroll
+    for (int k = i + 1; k < Nt; ++k) {
+      const real l = sL[(k * (k + 1) / 2 + i) * kB + lane];
+      Wp[i] -= l * Wp[k];
+      Wu[0][i] -= l * Wu[0][k];
+      Wu[1][i] -= l * Wu[1][k];
+      Wu[2][i] -= l * Wu[2][k];
+    }
+    const real d = sL[(i * (i + 1) / 2 + i) * kB + lane];
+    Wp[i] *= d;
+    Wu[0][i] *= d;
+    Wu[1][i] *= d;
+    Wu[2][i] *= d;
+  }
+  // (e) strong r, s parts of slice j (constant metric terms, Lemma 3.1)
+  const real rx = GEO(G_RX), ry = GEO(G_RY), sx = GEO(G_SX), sy = GEO(G_SY);
+  {
+    real av[Nt], bv[Nt];
+#pragma unroll
+    for (int l = 0; l < Nt; ++l) {
+      const real ux = sq[(1 * Np + j * Nt + l) * kB + lane];
+      const real uy = sq[(2 * Np + j * Nt + l) * kB + lane];
+      av[l] = rx * ux + ry * uy;
+      bv[l] = sx * ux + sy * uy;
+    }
+#pragma unroll
+    for (int i = 0; i < Nt; ++i) {
+      real dv = 0;
+#pragma unroll
+      for (int l = 0; l < Nt; ++l) {
+        dv += O.w.Dr[i * Nt + l] * av[l];
+        dv += O.w.Ds[i * Nt + l] * bv[l];
+      }
+      Wp[i] -= dv;
+    }
+  }
+  {
+    real pv[Nt];
+#pragma unroll
+    for (int l = 0; l < Nt; ++l) pv[l] = sq[(0 * Np + j * Nt + l) * kB + lane];
+#pragma unroll
+    for (int i = 0; i < Nt; ++i) {
+      real pr = 0, ps = 0;
+#pragma unroll
+      for (int l = 0; l < Nt; ++l) {
+        pr += O.w.Dr[i * Nt + l] * pv[l];
+        ps += O.w.Ds[i * Nt + l] * pv[l];
+      }
+      Wu[0][i] -= rx * pr + sx * ps;
+      Wu[1][i] -= ry * pr + sy * ps;
+    }
+  }
+  // (f) fused low-storage Runge-Kutta update (or plain right-hand side)
+  if (e < M.Kw) {
+    const real kappa = GEO(G_KAPPA), irho = GEO(G_IRHO);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+#pragma unroll
+      for (int i = 0; i < Nt; ++i) {
+        const int n = j * Nt + i;
+        const int64_t g = widx<N>(blk, f, n, lane);
+        const real r = (f == 0) ? kappa * Wp[i] : irho * Wu[f - 1][i];
+        if (rk) {
+          const real rr = A.rk_a * A.res[g] + A.dt * r;
+          A.res[g] = rr;
+          A.q_out[g] = sq[(f * Np + n) * kB + lane] + A.rk_b * rr;
+        } else {
+          A.q_out[g] = r;
+        }
+      }
+    }
+  }
+#undef GEO
+}
+
+// ---------------------------------------------------------------------------
+// tet stage: 32 tets x 4 warps per CTA.  Warp f computes the fluxes of face
+// f for the 32 elements; after a barrier warp w produces output nodes
+// [w C, w C + C) of every element (C = ceil(Np/4)).
+// ---------------------------------------------------------------------------
+template <int N>
+__host__ __device__ constexpr int tet_chunk() {
+  return (npt_of(N) + 3) / 4;
+}
+template <int N>
+__host__ __device__ constexpr int tet_smem_reals() {
+  return 4 * npt_of(N) * kB + 8 * nt_of(N) * kB;
+}
+
+struct TetGeom {
+  real Ri[3][3];   // d r_m / d x_d
+  real n[4][3];    // outward unit normals
+  real sJ[4];      // J_f / J
+  real kappa, irho, zM;
+};
+
+template <int N>
+__device__ __forceinline__ void tet_geometry(const DevMesh<real>& M, int e, TetGeom& g, real X[4][3]) {
+  const int Kp = M.Kt_pad;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int id = M.t_vid[v * Kp + e];
+    X[v][0] = M.vx[id];
+    X[v][1] = M.vy[id];
+    X[v][2] = M.vz[id];
+  }
+  real G[3][3];  // G[d][m] = d x_d / d r_m, affine map x = sum_v lambda_v X_v
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) G[d][m] = real(0.5) * (X[m + 1][d] - X[0][d]);
+  const real J = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) - G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+                 G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+  const real iJ = real(1) / J;
+  g.Ri[0][0] = (G[1][1] * G[2][2] - G[1][2] * G[2][1]) * iJ;
+  g.Ri[0][1] = (G[0][2] * G[2][1] - G[0][1] * G[2][2]) * iJ;
+  g.Ri[0][2] = (G[0][1] * G[1][2] - G[0][2] * G[1][1]) * iJ;
+  g.Ri[1][0] = (G[1][2] * G[2][0] - G[1][0] * G[2][2]) * iJ;
+  g.Ri[1][1] = (G[0][0] * G[2][2] - G[0][2] * G[2][0]) * iJ;
+  g.Ri[1][2] = (G[0][2] * G[1][0] - G[0][0] * G[1][2]) * iJ;
+  g.Ri[2][0] = (G[1][0] * G[2][1] - G[1][1] * G[2][0]) * iJ;
+  g.Ri[2][1] = (G[0][1] * G[2][0] - G[0][0] * G[2][1]) * iJ;
+  g.Ri[2][2] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) * iJ;
+  constexpr int fv[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
+  constexpr int fo[4] = {3, 2, 0, 1};
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const real ax = X[fv[f][1]][0] - X[fv[f][0]][0], ay = X[fv[f][1]][1] - X[fv[f][0]][1],
+               az = X[fv[f][1]][2] - X[fv[f][0]][2];
+    const real bx = X[fv[f][2]][0] - X[fv[f][0]][0], by = X[fv[f][2]][1] - X[fv[f][0]][1],
+               bz = X[fv[f][2]][2] - X[fv[f][0]][2];
+    const real cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+    const real nrm = sqrt_r(cx * cx + cy * cy + cz * cz);
+    const real ox = X[fo[f]][0] - X[fv[f][0]][0], oy = X[fo[f]][1] - X[fv[f][0]][1], oz = X[fo[f]][2] - X[fv[f][0]][2];
+    const real sgn = (cx * ox + cy * oy + cz * oz > 0) ? real(-1) : real(1);  // away from the opposite vertex
+    g.n[f][0] = sgn * cx / nrm;
+    g.n[f][1] = sgn * cy / nrm;
+    g.n[f][2] = sgn * cz / nrm;
+    g.sJ[f] = real(0.25) * nrm * iJ;
+  }
+  g.kappa = M.t_mat[0 * Kp + e];
+  g.irho = M.t_mat[1 * Kp + e];
+  g.zM = M.t_mat[2 * Kp + e];
+}
+
+// fluxes on tet face F of element e -> sF[F][0/1][k][lane]
+template <int N, int F>
+__device__ __forceinline__ void tet_face_flux(const StageArgs<real>& A, const TetGeom& g, const real* sq, real* sF,
+                                              int e, int lane) {
+  constexpr int Np = npt_of(N), Nt = nt_of(N);
+  const AllOps<N, real>& O = OPS<N>();
+  const DevMesh<real>& M = A.m;
+  const int nbr = M.t_nbr[F * M.Kt_pad + e];
+  const int code = M.t_code[F * M.Kt_pad + e];
+  const real nx = g.n[F][0], ny = g.n[F][1], nz = g.n[F][2];
+  real tau_p, tau_u;
+  if (nbr < 0) {
+    taus(A.flux, g.zM, g.zM, tau_p, tau_u);
+#pragma unroll
+    for (int k = 0; k < Nt; ++k) {
+      const int no = tet_face_node(N, F, k);
+      const real pM = sq[(0 * Np + no) * kB + lane];
+      const real unM = nx * sq[(1 * Np + no) * kB + lane] + ny * sq[(2 * Np + no) * kB + lane] + nz * sq[(3 * Np + no) * kB + lane];
+      real dp, dun, Fp, Fu;
+      boundary_jumps(A.bc, pM, unM, dp, dun);
+      penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
+      sF[((F * 2 + 0) * Nt + k) * kB + lane] = Fp;
+      sF[((F * 2 + 1) * Nt + k) * kB + lane] = Fu;
+    }
+  } else {
+    const bool ntet = (code & kCodeTet) != 0;
+    const int nf = (code >> 4) & 3;
+    const int perm = code & 15;
+    const real zP = ntet ? M.t_mat[2 * M.Kt_pad + nbr] : M.w_mat[2 * M.Kw_pad + nbr];
+    taus(A.flux, g.zM, zP, tau_p, tau_u);
+    const bool inblk = ntet && ((nbr >> 5) == int(blockIdx.x));
+#pragma unroll
+    for (int k = 0; k < Nt; ++k) {
+      const int no = tet_face_node(N, F, k);
+      const int nk = O.tab.tri_perm[perm][k];
+      real pP, uP[3];
+      if (!ntet) {
+        const int node = (nf ? N * nt_of(N) : 0) + nk;
+        pP = __ldg(A.q_in + widx<N>(nbr >> 5, 0, node, nbr & 31));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) uP[d] = __ldg(A.q_in + widx<N>(nbr >> 5, 1 + d, node, nbr & 31));
+      } else {
+        const int node = O.tab.tet_face[nf][nk];
+        if (inblk) {
+          pP = sq[(0 * Np + node) * kB + (nbr & 31)];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) uP[d] = sq[((1 + d) * Np + node) * kB + (nbr & 31)];
+        } else {
+          pP = __ldg(A.q_in + tidx<N>(M.tet_off, nbr >> 5, 0, node, nbr & 31));
+#pragma unroll
+          for (int d = 0; d < 3; ++d) uP[d] = __ldg(A.q_in + tidx<N>(M.tet_off, nbr >> 5, 1 + d, node, nbr & 31));
+        }
+      }
+      const real pM = sq[(0 * Np + no) * kB + lane];
+      const real unM = nx * sq[(1 * Np + no) * kB + lane] + ny * sq[(2 * Np + no) * kB + lane] + nz * sq[(3 * Np + no) * kB + lane];
+      real Fp, Fu;
+      penalty_flux(pP - pM, nx * uP[0] + ny * uP[1] + nz * uP[2] - unM, tau_p, tau_u, Fp, Fu);
+      sF[((F * 2 + 0) * Nt + k) * kB + lane] = Fp;
+      sF[((F * 2 + 1) * Nt + k) * kB + lane] = Fu;
+    }
+  }
+}
+
+// output nodes [I0, I0 + C) of element e: volume terms, lift, update
+template <int N, int I0, int C>
+__device__ __forceinline__ void tet_chunk_out(const StageArgs<real>& A, const TetGeom& g, const real* sq,
+                                              const real* sF, int e, int lane, bool rk) {
+  constexpr int Np = npt_of(N), Nt = nt_of(N);
+  const AllOps<N, real>& O = OPS<N>();
+  const DevMesh<real>& M = A.m;
+  real ap[C], au[3][C];
+  {
+    real dr[C], ds[C], dt[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) dr[c] = ds[c] = dt[c] = ap[c] = real(0);
+#pragma unroll
+    for (int l = 0; l < Np; ++l) {
+      const real p = sq[(0 * Np + l) * kB + lane];
+      const real ux = sq[(1 * Np + l) * kB + lane], uy = sq[(2 * Np + l) * kB + lane], uz = sq[(3 * Np + l) * kB + lane];
+      const real wr = g.Ri[0][0] * ux + g.Ri[0][1] * uy + g.Ri[0][2] * uz;
+      const real ws = g.Ri[1][0] * ux + g.Ri[1][1] * uy + g.Ri[1][2] * uz;
+      const real wt = g.Ri[2][0] * ux + g.Ri[2][1] * uy + g.Ri[2][2] * uz;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        if (I0 + c < Np) {
+          const int i = I0 + c;
+          dr[c] += O.t.Dr[i * Np + l] * p;
+          ds[c] += O.t.Ds[i * Np + l] * p;
+          dt[c] += O.t.Dt[i * Np + l] * p;
+          ap[c] -= O.t.Dr[i * Np + l] * wr + O.t.Ds[i * Np + l] * ws + O.t.Dt[i * Np + l] * wt;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) au[d][c] = -(g.Ri[0][d] * dr[c] + g.Ri[1][d] * ds[c] + g.Ri[2][d] * dt[c]);
+  }
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    real lu[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) lu[c] = real(0);
+#pragma unroll
+    for (int k = 0; k < Nt; ++k) {
+      const real Fp = g.sJ[f] * sF[((f * 2 + 0) * Nt + k) * kB + lane];
+      const real Fu = g.sJ[f] * sF[((f * 2 + 1) * Nt + k) * kB + lane];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        if (I0 + c < Np) {
+          const real L = O.t.LIFT[(I0 + c) * 4 * Nt + f * Nt + k];
+          ap[c] += L * Fp;
+          lu[c] += L * Fu;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) au[d][c] += g.n[f][d] * lu[c];
+  }
+  if (e < M.Kt) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      if (I0 + c < Np) {
+        const int i = I0 + c;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const int64_t gi = tidx<N>(M.tet_off, blockIdx.x, f, i, lane);
+          const real r = (f == 0) ? g.kappa * ap[c] : g.irho * au[f - 1][c];
+          if (rk) {
+            const real rr = A.rk_a * A.res[gi] + A.dt * r;
+            A.res[gi] = rr;
+            A.q_out[gi] = sq[(f * Np + i) * kB + lane] + A.rk_b * rr;
+          } else {
+            A.q_out[gi] = r;
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? 4 : 1) k_tet_stage(const StageArgs<real> A, bool rk) {
+  constexpr int Np = npt_of(N), C = tet_chunk<N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sq = reinterpret_cast<real*>(smem_raw);  // [4][Np][32]
+  real* sF = sq + 4 * Np * kB;                   // [4 faces][2][Nt][32]
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int e = blockIdx.x * kB + lane;
+  {
+    constexpr int nvec = 4 * Np * kB * int(sizeof(real)) / 16;
+    const int4* src = reinterpret_cast<const int4*>(A.q_in + A.m.tet_off + int64_t(blockIdx.x) * 4 * Np * kB);
+    int4* dst = reinterpret_cast<int4*>(sq);
+    for (int v = threadIdx.x; v < nvec; v += blockDim.x) dst[v] = __ldg(src + v);
+  }
+  TetGeom g;
+  real X[4][3];
+  tet_geometry<N>(A.m, e, g, X);
+  __syncthreads();
+  switch (w) {
+    case 0: tet_face_flux<N, 0>(A, g, sq, sF, e, lane); break;
+    case 1: tet_face_flux<N, 1>(A, g, sq, sF, e, lane); break;
+    case 2: tet_face_flux<N, 2>(A, g, sq, sF, e, lane); break;
+    default: tet_face_flux<N, 3>(A, g, sq, sF, e, lane); break;
+  }
+  __syncthreads();
+  switch (w) {
+    case 0: tet_chunk_out<N, 0 * C, C>(A, g, sq, sF, e, lane, rk); break;
+    case 1: tet_chunk_out<N, 1 * C, C>(A, g, sq, sF, e, lane, rk); break;
+    case 2: tet_chunk_out<N, 2 * C, C>(A, g, sq, sF, e, lane, rk); break;
+    default: tet_chunk_out<N, 3 * C, C>(A, g, sq, sF, e, lane, rk); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// canonical <-> packed layout
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void k_pack(const DevMesh<real> M, const real* __restrict__ canon, real* __restrict__ packed, bool unpack) {
+  constexpr int Npw = npw_of(N), Npt = npt_of(N);
+  const int64_t nw = int64_t(M.Kw) * Npw, nt = int64_t(M.Kt) * Npt;
+  for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < nw + nt; idx += int64_t(gridDim.x) * blockDim.x) {
+    int64_t c;
+    int64_t pbase;
+    int64_t stride;
+    if (idx < nw) {
+      const int e = int(idx / Npw), n = int(idx % Npw);
+      c = M.w_canon[e] + n;
+      pbase = widx<N>(e >> 5, 0, n, e & 31);
+      stride = int64_t(Npw) * kB;
+    } else {
+      const int64_t t = idx - nw;
+      const int e = int(t / Npt), n = int(t % Npt);
+      c = M.t_canon[e] + n;
+      pbase = tidx<N>(M.tet_off, e >> 5, 0, n, e & 31);
+      stride = int64_t(Npt) * kB;
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      if (unpack)
+        const_cast<real*>(canon)[f * M.total_nodes + c] = packed[pbase + f * stride];
+      else
+        packed[pbase + f * stride] = canon[f * M.total_nodes + c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// discrete energy (Section 4.1), double accumulation, deterministic order
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(128) k_energy(const DevMesh<real> M, const real* __restrict__ q) {
+  constexpr int Nt = nt_of(N), Nq = N + 1, Npw = npw_of(N), Npt = npt_of(N);
+  const AllOps<N, real>& O = OPS<N>();
+  const int nblk_cta_w = (M.nblk_w + 3) / 4;
+  double E = 0.0;
+  const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);  // 32-element block handled by this warp
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x < nblk_cta_w) {
+    const int e = gw * kB + lane;
+    if (gw < M.nblk_w && e < M.Kw) {
+      const int Kp = M.Kw_pad;
+      const int vb0 = M.w_vid[0 * Kp + e], vb1 = M.w_vid[1 * Kp + e], vb2 = M.w_vid[2 * Kp + e];
+      const double x0 = M.vx[vb0], x1 = M.vx[vb1], x2 = M.vx[vb2];
+      const double y0 = M.vy[vb0], y1 = M.vy[vb1], y2 = M.vy[vb2];
+      const double A = 0.25 * ((x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0));
+      double Ja[3];
+      for (int a = 0; a < 3; ++a) Ja[a] = 0.5 * A * (double(M.vz[M.w_vid[(3 + a) * Kp + e]]) - double(M.vz[M.w_vid[a * Kp + e]]));
+      const double wgt[4] = {1.0 / double(M.w_mat[0 * Kp + e]), 1.0 / double(M.w_mat[1 * Kp + e]),
+                             1.0 / double(M.w_mat[1 * Kp + e]), 1.0 / double(M.w_mat[1 * Kp + e])};
+#pragma unroll 1
+      for (int f = 0; f < 4; ++f) {
+        double ef = 0.0;
+#pragma unroll 1
+        for (int jp = 0; jp < Nq; ++jp)
+#pragma unroll 1
+          for (int jj = 0; jj < Nq; ++jj) {
+            const double m1 = double(O.w.M1[jj * Nq + jp]);
+            double d = 0.0;
+#pragma unroll 1
+            for (int i = 0; i < Nt; ++i) {
+              double s = 0.0;
+#pragma unroll 1
+              for (int l = 0; l < Nt; ++l) {
+                const double mt = Ja[0] * double(O.w.Ma[0][i * Nt + l]) + Ja[1] * double(O.w.Ma[1][i * Nt + l]) +
+                                  Ja[2] * double(O.w.Ma[2][i * Nt + l]);
+                s += mt * double(q[widx<N>(gw, f, jp * Nt + l, lane)]);
+              }
+              d += double(q[widx<N>(gw, f, jj * Nt + i, lane)]) * s;
+            }
+            ef += m1 * d;
+          }
+        E += wgt[f] * ef;
+      }
+    }
+  } else {
+    const int gt = gw - nblk_cta_w * 4;
+    const int e = gt * kB + lane;
+    if (gt < M.nblk_t && e < M.Kt) {
+      const int Kp = M.Kt_pad;
+      double X[4][3];
+      for (int v = 0; v < 4; ++v) {
+        const int id = M.t_vid[v * Kp + e];
+        X[v][0] = M.vx[id];
+        X[v][1] = M.vy[id];
+        X[v][2] = M.vz[id];
+      }
+      double G[3][3];
+      for (int d = 0; d < 3; ++d)
+        for (int m = 0; m < 3; ++m) G[d][m] = 0.5 * (X[m + 1][d] - X[0][d]);
+      const double J = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) - G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+                       G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+      const double wgt[4] = {1.0 / double(M.t_mat[0 * Kp + e]), 1.0 / double(M.t_mat[1 * Kp + e]),
+                             1.0 / double(M.t_mat[1 * Kp + e]), 1.0 / double(M.t_mat[1 * Kp + e])};
+#pragma unroll 1
+      for (int f = 0; f < 4; ++f) {
+        double ef = 0.0;
+#pragma unroll 1
+        for (int i = 0; i < Npt; ++i) {
+          double s = 0.0;
+#pragma unroll 1
+          for (int l = 0; l < Npt; ++l) s += double(M.tet_mass[i * Npt + l]) * double(q[tidx<N>(M.tet_off, gt, f, l, lane)]);
+          ef += s * double(q[tidx<N>(M.tet_off, gt, f, i, lane)]);
+        }
+        E += wgt[f] * J * ef;
+      }
+    }
+  }
+  // block reduction in a fixed order
+  __shared__ double red[128];
+  red[threadIdx.x] = E;
+  __syncthreads();
+  for (int s = 64; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) M.partials[blockIdx.x] = 0.5 * red[0];
+  (void)Npw;
+}
+
+__global__ void k_energy_final(const double* __restrict__ partials, int n, double* out, int* err) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += partials[i];
+    *out = s;
+    if (!isfinite(s)) atomicOr(err, kErrNonfinite);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+// one-time per device: opt in to the dynamic shared memory the stages use
+template <int N>
+int prepare_n() {
+  cudaError_t err = cudaFuncSetAttribute(k_wedge_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         wedge_smem_reals<N>() * int(sizeof(real)));
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_tet_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tet_smem_reals<N>() * int(sizeof(real)));
+  return int(err);
+}
+
+template <int N>
+int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s) {
+  if (a.m.nblk_w > 0) {
+    k_wedge_stage<N><<<a.m.nblk_w, 32 * (N + 1), wedge_smem_reals<N>() * int(sizeof(real)), s>>>(a, rk);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return int(err);
+  }
+  if (a.m.nblk_t > 0) {
+    k_tet_stage<N><<<a.m.nblk_t, 128, tet_smem_reals<N>() * int(sizeof(real)), s>>>(a, rk);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return int(err);
+  }
+  return 0;
+}
+
+template <int N>
+int launch_pack_n(const DevMesh<real>& m, const real* canon, real* packed, bool unpack, cudaStream_t s) {
+  const int64_t total = int64_t(m.Kw) * npw_of(N) + int64_t(m.Kt) * npt_of(N);
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks < 1) blocks = 1;
+  k_pack<N><<<int(blocks), 256, 0, s>>>(m, canon, packed, unpack);
+  return int(cudaGetLastError());
+}
+
+template <int N>
+int launch_energy_n(const DevMesh<real>& m, const real* q, cudaStream_t s) {
+  const int nw = (m.nblk_w + 3) / 4, nt = (m.nblk_t + 3) / 4;
+  const int grid = nw + nt;
+  if (grid > 0) k_energy<N><<<grid, 128, 0, s>>>(m, q);
+  k_energy_final<<<1, 32, 0, s>>>(m.partials, grid, m.energy, m.err);
+  return int(cudaGetLastError());
+}
+
+}  // namespace REALNS
+}  // namespace dgw
+
+// extern launchers of this translation unit (order NORD, precision REAL)
+#define DGW_CAT2(a, b) a##b
+#define DGW_CAT(a, b) DGW_CAT2(a, b)
+namespace dgw {
+int DGW_CAT(upload_ops_, REALNS)(const void* host_ops, size_t bytes, void* stream) {
+  if (bytes != sizeof(AllOps<NORD, REAL>)) return int(cudaErrorInvalidValue);
+  const int rc = REALNS::prepare_n<NORD>();
+  if (rc) return rc;
+  return int(cudaMemcpyToSymbolAsync(REALNS::c_ops, host_ops, bytes, 0, cudaMemcpyHostToDevice, cudaStream_t(stream)));
+}
+int DGW_CAT(launch_stage_, REALNS)(const StageArgs<REAL>& a, bool rk, void* stream) {
+  return REALNS::launch_stage_n<NORD>(a, rk, cudaStream_t(stream));
+}
+int DGW_CAT(launch_pack_, REALNS)(const DevMesh<REAL>& m, const REAL* canon, REAL* packed, bool unpack, void* stream) {
+  return REALNS::launch_pack_n<NORD>(m, canon, packed, unpack, cudaStream_t(stream));
+}
+int DGW_CAT(launch_energy_, REALNS)(const DevMesh<REAL>& m, const REAL* q, void* stream) {
+  return REALNS::launch_energy_n<NORD>(m, q, cudaStream_t(stream));
+}
+}  // namespace dgw

@@ -1,0 +1,207 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (relative L2 over all fields and nodes): FP64 1e-12; FP32 1e-5 per
+right-hand side and 1e-4 after 1000 LSRK45 steps.  Meshes span several
+32-element blocks with ragged tails, wedge-only, tet-only and hybrid cases,
+both boundary conditions and both fluxes; the throughput workload (524288
+wedges, N = 3 and 4) is checked on sampled elements against oracle patches."""
+import numpy as np
+import pytest
+
+from oracle.dg import Solver as Oracle
+from paper_1607_03399_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("CUDA not available", allow_module_level=True)
+
+from paper_1607_03399_gb300 import dg  # noqa: E402
+from paper_1607_03399_gb300.dg import Solver  # noqa: E402
+
+from patch_util import face_adjacency, node_index, patch, submesh  # noqa: E402
+
+MESHES = {
+    # 128 wedges (4 blocks), the FP64 test configuration
+    "wavy128": lambda: I.cube_wavy_mesh(4, 4, 0.03),
+    # 150 wedges: ragged last block
+    "bumpy150": lambda: I.layered_wedge_mesh(5, 5, 3, lambda k, x, y: k / 3 + (0.05 * np.sin(3 * x) * np.cos(2 * y) if 0 < k < 3 else 0)),
+    # 2x3x3 tri columns: 18 wedge + 54 tets (hybrid, ragged)
+    "hybrid": lambda: I.hybrid_mesh(3, 2, 1),
+    # tets only
+    "tets": lambda: I.tet_box_mesh(2, 2),
+    # one wedge
+    "single": lambda: I.cube_wavy_mesh(1, 1, 0.0),
+}
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / np.linalg.norm(b))
+
+
+def _pair(mesh, N, precision, bc="rigid", flux="upwind", seed=3):
+    c2, rho = I.random_material(mesh.K, seed, 1.0, 3.0, 0.5, 2.0)
+    S = Solver(mesh.VX, mesh.EToV, mesh.etype, N, c2, rho, bc=bc, flux=flux, precision=precision)
+    O = Oracle(mesh.VX, mesh.EToV, mesh.etype, N, c2, rho, bc=bc, flux=flux)
+    return S, O
+
+
+@pytest.mark.parametrize("meshname", list(MESHES))
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("bc,flux", [("rigid", "upwind"), ("dirichlet", "central")])
+def test_rhs_parity_f64(meshname, N, bc, flux):
+    S, O = _pair(MESHES[meshname](), N, "f64", bc, flux)
+    q = I.random_fields(S.total_nodes, 11)
+    err = _rel(S.rhs(q).cpu().numpy(), O.rhs(q))
+    S.close()
+    assert err <= 1e-12, err
+
+
+@pytest.mark.parametrize("meshname", list(MESHES))
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("bc,flux", [("rigid", "upwind"), ("dirichlet", "upwind"), ("rigid", "central")])
+def test_rhs_parity_f32(meshname, N, bc, flux):
+    S, O = _pair(MESHES[meshname](), N, "f32", bc, flux)
+    q = I.random_fields(S.total_nodes, 12).astype(np.float32)
+    err = _rel(S.rhs(q).cpu().numpy(), O.rhs(q.astype(np.float64)))
+    S.close()
+    assert err <= 1e-5, err
+
+
+def test_config1_fp64_200_steps():
+    """128-wedge wavy unit cube, N=3, rigid walls, upwind, standing mode,
+    200 LSRK45 steps at CFL 0.5: state within 1e-12 of the oracle, energy
+    within 1e-12 and non-increasing, L2 error to the exact solution small."""
+    m = I.cube_wavy_mesh(4, 4, 0.03)
+    S = Solver(m.VX, m.EToV, m.etype, 3, precision="f64")
+    O = Oracle(m.VX, m.EToV, m.etype, 3)
+    q0 = I.standing_mode_unit_cube(O.conn.xyz, 0.0)
+    dt = O.stable_dt(0.5)
+    assert abs(S.stable_dt(0.5) - dt) < 1e-15 * dt
+    S.set_fields(q0)
+    q_ref = q0.copy()
+    E_gpu = [S.energy()]
+    for _ in range(10):
+        S.step(dt, 20)
+        q_ref = O.step(q_ref, dt, 20)
+        E_gpu.append(S.energy())
+    q = S.get_fields()
+    assert _rel(q, q_ref) <= 1e-12
+    assert abs(E_gpu[-1] - O.energy(q_ref)) <= 1e-12 * E_gpu[0]
+    assert np.all(np.diff(E_gpu) <= 1e-14 * E_gpu[0])
+    assert abs(S.time() - 200 * dt) < 1e-12
+    err = O.l2_error(q, I.standing_mode_unit_cube, 200 * dt)
+    assert np.sqrt((err ** 2).sum()) < 1e-3
+    S.close()
+
+
+def test_fp32_1000_steps():
+    """FP32 state after 1000 LSRK45 steps within 1e-4 of the FP64 oracle."""
+    m = I.cube_wavy_mesh(4, 4, 0.03)
+    c2, rho = I.layered_wavespeed(m, (2.0, 1.5, 1.0, 1.0))
+    S = Solver(m.VX, m.EToV, m.etype, 3, c2, rho, precision="f32")
+    O = Oracle(m.VX, m.EToV, m.etype, 3, c2, rho)
+    q0 = I.standing_mode_unit_cube(O.conn.xyz, 0.0)
+    dt = O.stable_dt(0.5)
+    S.set_fields(q0)
+    S.step(dt, 1000)
+    q_ref = O.step(q0, dt, 1000)
+    err = _rel(S.get_fields(), q_ref)
+    S.close()
+    assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f32", 1e-6)])
+@pytest.mark.parametrize("meshname", ["wavy128", "hybrid"])
+def test_energy(precision, tol, meshname):
+    S, O = _pair(MESHES[meshname](), 3, precision)
+    q = I.random_fields(S.total_nodes, 5)
+    S.set_fields(q)
+    qq = S.get_fields().astype(np.float64)
+    E = S.energy()
+    S.close()
+    assert abs(E - O.energy(qq)) <= tol * E
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_fields_roundtrip_and_rhs_in_place(precision):
+    S, O = _pair(MESHES["hybrid"](), 2, precision)
+    q = I.random_fields(S.total_nodes, 8).astype(S.np_dtype)
+    S.set_fields(q)
+    assert np.array_equal(S.get_fields(), q)                 # pack/unpack is exact
+    dq = torch.from_numpy(q).cuda()
+    ref = S.rhs(dq).cpu().numpy()
+    dg.dg_rhs(S.ctx, dq.data_ptr(), dq.data_ptr())           # in place
+    S.sync()
+    assert np.array_equal(dq.cpu().numpy(), ref)
+    assert np.array_equal(S.get_fields(), q)                 # state untouched by dg_rhs
+    S.close()
+
+
+def test_nonfinite_state_reported():
+    S, _ = _pair(MESHES["wavy128"](), 2, "f32")
+    q = I.random_fields(S.total_nodes, 1).astype(np.float32)
+    q[2, 17] = np.nan
+    S.set_fields(q)
+    with pytest.raises(dg.DGError) as ei:
+        S.energy()
+    assert ei.value.code == dg.DG_ERR_NONFINITE
+    q[2, 17] = 0.0
+    S.set_fields(q)
+    assert np.isfinite(S.energy())
+    S.close()
+
+
+def test_two_contexts_interleaved():
+    """Contexts of different order and precision on one device keep their own
+    operator tables."""
+    A, OA = _pair(MESHES["wavy128"](), 3, "f32")
+    B, OB = _pair(MESHES["hybrid"](), 2, "f64")
+    qa = I.random_fields(A.total_nodes, 1).astype(np.float32)
+    qb = I.random_fields(B.total_nodes, 2)
+    for _ in range(2):
+        assert _rel(A.rhs(qa).cpu().numpy(), OA.rhs(qa.astype(np.float64))) <= 1e-5
+        assert _rel(B.rhs(qb).cpu().numpy(), OB.rhs(qb)) <= 1e-12
+    A.close()
+    B.close()
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_full_size_sampled(N):
+    """The 524288-wedge layered workload (2x128x128 triangles x 16 bumpy
+    layers, layered wavespeed) in FP32 as the benchmark runs it: sampled
+    elements of one right-hand side and of one full LSRK45 step (5 stages)
+    against oracle patches of radius 1 and 5."""
+    m = I.bumpy_layered_mesh(128, 16)
+    c2, rho = I.layered_wavespeed(m)
+    S = Solver(m.VX, m.EToV, m.etype, N, c2, rho, precision="f32")
+    Np = (N + 1) ** 2 * (N + 2) // 2
+    rng = np.random.default_rng(N)
+    q = rng.uniform(-1, 1, size=(4, S.total_nodes)).astype(np.float32)
+    nbr = face_adjacency(m.EToV, m.etype)
+    # include the first and last block and both domain boundaries
+    seeds = np.unique(np.concatenate([[0, 31, m.K - 1], rng.integers(0, m.K, 13)]))
+    r_gpu = S.rhs(q).cpu().numpy()
+    dt = S.stable_dt(0.5)
+    S.set_fields(q)
+    S.step(dt, 1)
+    q1_gpu = S.get_fields()
+    S.close()
+    for radius, what in ((1, "rhs"), (5, "step")):
+        for s in seeds:
+            elems = patch(nbr, [s], radius)
+            VXs, Es, ts = submesh(m.VX, m.EToV, m.etype, elems)
+            O = Oracle(VXs, Es, ts, N, c2[elems], rho[elems])
+            gid = node_index(np.full(m.K, Np), elems)
+            qs = q[:, gid].astype(np.float64)
+            loc = int(np.searchsorted(elems, s))
+            sl = slice(loc * Np, (loc + 1) * Np)
+            glob = slice(s * Np, (s + 1) * Np)
+            if what == "rhs":
+                ref = O.rhs(qs)[:, sl]
+                got = r_gpu[:, glob]
+            else:
+                ref = O.step(qs, dt, 1)[:, sl]
+                got = q1_gpu[:, glob]
+            assert _rel(got, ref) <= 1e-5, (what, s)

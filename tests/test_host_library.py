@@ -1,0 +1,150 @@
+"""CPU tests of the C-ABI library's host side (no GPU calls): the shared
+library loads and exports every entry point declared in include/dgwedge.h,
+its independently built reference operators, node coordinates, face-node
+connectivity and stable time step agree with the oracle, and invalid meshes
+or call orders are rejected with the documented status codes."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import reference as R
+from oracle.dg import Solver as OracleSolver
+from paper_1607_03399_gb300 import dg
+from paper_1607_03399_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "dgwedge.h")).read()
+    declared = set(re.findall(r"\b(dg_[a-z0-9_]+)\s*\(", hdr))
+    L = dg.lib()
+    for name in sorted(declared):
+        assert hasattr(L, name), name
+    assert declared == set(dg.EXPORTS)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_reference_operators_match_oracle(N):
+    m = I.cube_wavy_mesh(1, 1, 0.0)
+    H = dg.HostMesh(m.VX, m.EToV, m.etype, N)
+    tri, line, tet = R.Triangle(N), R.Line(N), R.Tet(N)
+    assert np.allclose(H.operator("tri.r"), tri.x[:, 0], atol=1e-14)
+    assert np.allclose(H.operator("tri.s"), tri.x[:, 1], atol=1e-14)
+    assert np.allclose(H.operator("line.r"), line.x, atol=1e-15)
+    for name, ref in (("tri.Dr", tri.Dr), ("tri.Ds", tri.Ds), ("tri.M", tri.M), ("tri.M0", tri.Ma[0]),
+                      ("tri.M1", tri.Ma[1]), ("tri.M2", tri.Ma[2]), ("line.D", line.D), ("line.M", line.M),
+                      ("line.Ma", line.Ma), ("line.Mb", line.Mb), ("tet.Dr", tet.Dr), ("tet.Ds", tet.Ds),
+                      ("tet.Dt", tet.Dt), ("tet.M", tet.M)):
+        got = H.operator(name)
+        assert np.allclose(got, ref, atol=1e-12 * max(1.0, np.abs(ref).max())), name
+    assert np.allclose(H.operator("line.ell0"), line.ell0, atol=1e-12)
+    assert np.allclose(H.operator("line.ellN"), line.ellN, atol=1e-12)
+    assert np.allclose(H.operator("tet.r"), tet.x[:, 0], atol=1e-14)
+    assert np.allclose(H.operator("tet.s"), tet.x[:, 1], atol=1e-14)
+    assert np.allclose(H.operator("tet.t"), tet.x[:, 2], atol=1e-14)
+    # reference lift of every tet face: M^-1 E_f M^tri
+    Minv = np.linalg.inv(tet.M)
+    lift = np.concatenate([Minv[:, tet.faces[f]] @ tri.M for f in range(4)], axis=1)
+    assert np.allclose(H.operator("tet.LIFT"), lift, atol=1e-11)
+
+
+MESHES = {
+    "wavy": lambda: I.cube_wavy_mesh(3, 3, 0.05),
+    "bumpy": lambda: I.bumpy_layered_mesh(3, 4),
+    "hybrid": lambda: I.hybrid_mesh(3, 2, 2),
+    "tets": lambda: I.tet_box_mesh(2, 2),
+}
+
+
+@pytest.mark.parametrize("meshname", list(MESHES))
+@pytest.mark.parametrize("N", [1, 3, 4])
+def test_nodes_and_face_neighbours_match_oracle(meshname, N):
+    m = MESHES[meshname]()
+    H = dg.HostMesh(m.VX, m.EToV, m.etype, N)
+    S = OracleSolver(m.VX, m.EToV, m.etype, N)
+    C = S.conn
+    assert H.wedge_nodes + H.tet_nodes == C.total_nodes
+    assert np.allclose(H.node_coords(), C.xyz, atol=1e-13)
+    nb = H.face_neighbors()
+    expect = []
+    for k in range(C.K):
+        for f in range(C.nfaces(k)):
+            gP = C.vmapP[(k, f)].copy()
+            if C.EToE[k, f] < 0:
+                gP[:] = -1
+            expect.append(gP)
+    assert np.array_equal(nb, np.concatenate(expect))
+
+
+@pytest.mark.parametrize("meshname", ["wavy", "hybrid"])
+def test_stable_dt_matches_oracle(meshname):
+    m = MESHES[meshname]()
+    c2, rho = I.random_material(m.K, 2, 1.0, 3.0, 1.0, 2.0)
+    H = dg.HostMesh(m.VX, m.EToV, m.etype, 3, c2, rho)
+    S = OracleSolver(m.VX, m.EToV, m.etype, 3, c2, rho)
+    assert abs(H.stable_dt(0.5) - S.stable_dt(0.5)) < 1e-14 * S.stable_dt(0.5)
+
+
+def _expect_error(code, fn):
+    with pytest.raises(dg.DGError) as ei:
+        fn()
+    assert ei.value.code == code, str(ei.value)
+    return str(ei.value)
+
+
+def test_invalid_meshes_are_rejected():
+    m = I.cube_wavy_mesh(2, 2, 0.0)
+    # top vertex moved sideways: not vertically mapped
+    VX = m.VX.copy()
+    VX[m.EToV[3, 3], 0] += 0.01
+    msg = _expect_error(dg.DG_ERR_MESH, lambda: dg.dg_mesh_create(VX, m.EToV, m.etype))
+    assert "vertically mapped" in msg
+    # clockwise bottom triangle: J < 0
+    E = m.EToV.copy()
+    E[5, [1, 2]] = E[5, [2, 1]]
+    E[5, [4, 5]] = E[5, [5, 4]]
+    _expect_error(dg.DG_ERR_MESH, lambda: dg.dg_mesh_create(m.VX, E, m.etype))
+    # vertex id out of range
+    E = m.EToV.copy()
+    E[0, 0] = m.VX.shape[0]
+    _expect_error(dg.DG_ERR_MESH, lambda: dg.dg_mesh_create(m.VX, E, m.etype))
+    # a face shared by three elements
+    E = np.vstack([m.EToV, m.EToV[:1]])
+    t = np.concatenate([m.etype, m.etype[:1]])
+    _expect_error(dg.DG_ERR_MESH, lambda: dg.dg_mesh_create(m.VX, E, t))
+    # negative tet
+    tm = I.tet_box_mesh(1, 1)
+    E = tm.EToV.copy()
+    E[0, [1, 2]] = E[0, [2, 1]]
+    _expect_error(dg.DG_ERR_MESH, lambda: dg.dg_mesh_create(tm.VX, E, tm.etype))
+    # unknown element type
+    t = m.etype.copy()
+    t[0] = 5
+    _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_mesh_create(m.VX, m.EToV, t))
+
+
+def test_call_order_and_argument_errors():
+    m = I.cube_wavy_mesh(2, 2, 0.0)
+    ctx = dg.dg_mesh_create(m.VX, m.EToV, m.etype)
+    try:
+        _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_num_nodes(ctx))
+        _expect_error(dg.DG_ERR_ORDER, lambda: dg.dg_set_order(ctx, 0))
+        _expect_error(dg.DG_ERR_ORDER, lambda: dg.dg_set_order(ctx, 5))
+        dg.dg_set_order(ctx, 2)
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_set_options(ctx, 7, 0, 0))
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_set_material(ctx, -np.ones(m.K), np.ones(m.K)))
+        _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_step(ctx, 0.1, 1))
+        _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_energy(ctx))
+        buf = np.zeros(8)
+        _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_set_fields(ctx, buf.ctypes.data, 0))
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_bind(ctx, 0, 0, 0, 0, 0))
+        mb, fb = dg.dg_device_bytes(ctx)
+        assert mb > 0 and fb >= 4 * 4 * dg.dg_num_nodes(ctx)[0]
+        dg.dg_set_options(ctx, dg.DG_BC_DIRICHLET, dg.DG_FLUX_CENTRAL, dg.DG_F64)
+        mb2, fb2 = dg.dg_device_bytes(ctx)
+        assert fb2 == 2 * fb
+    finally:
+        dg.dg_destroy(ctx)
