@@ -640,7 +640,7 @@ int dg_set_order(dg_ctx* c, int N) {
 
 int dg_set_material(dg_ctx* c, const double* c2, const double* rho) {
   if (!c) return DG_ERR_ARG;
-  if (!c2 || !rho) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!c2 || !rho) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (c->bound) return c->fail(DG_ERR_STATE, "dg_set_material after dg_bind");
   for (int64_t k = 0; k < c->K; ++k)
     if (!(c2[k] > 0) || !(rho[k] > 0) || !std::isfinite(c2[k]) || !std::isfinite(rho[k]))
@@ -664,7 +664,7 @@ int dg_set_options(dg_ctx* c, int bc, int flux, int precision) {
 
 int dg_num_nodes(const dg_ctx* c, int64_t* wn, int64_t* tn) {
   if (!c) return DG_ERR_ARG;
-  if (!wn || !tn) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!wn || !tn) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
   *wn = c->wedge_nodes;
   *tn = c->tet_nodes;
@@ -673,7 +673,7 @@ int dg_num_nodes(const dg_ctx* c, int64_t* wn, int64_t* tn) {
 
 int dg_node_coords(const dg_ctx* c, double* xyz) {
   if (!c) return DG_ERR_ARG;
-  if (!xyz) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!xyz) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
   const RefElems& R = *c->ref;
   const int64_t tot = c->wedge_nodes + c->tet_nodes;
@@ -710,7 +710,7 @@ int dg_node_coords(const dg_ctx* c, double* xyz) {
 
 int dg_face_neighbors(const dg_ctx* c, int64_t* out, int64_t* count) {
   if (!c) return DG_ERR_ARG;
-  if (!count) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!count) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
   const RefElems& R = *c->ref;
   int64_t n = 0;
@@ -746,7 +746,7 @@ int dg_face_neighbors(const dg_ctx* c, int64_t* out, int64_t* count) {
 
 int dg_reference_operator(const dg_ctx* c, const char* name, double* out, int64_t* rows, int64_t* cols) {
   if (!c) return DG_ERR_ARG;
-  if (!name || !rows || !cols) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!name || !rows || !cols) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
   const RefElems& R = *c->ref;
   const Mat* M = nullptr;
@@ -790,7 +790,7 @@ int dg_reference_operator(const dg_ctx* c, const char* name, double* out, int64_
 
 int dg_device_bytes(const dg_ctx* c, size_t* mesh_bytes, size_t* field_bytes) {
   if (!c) return DG_ERR_ARG;
-  if (!mesh_bytes || !field_bytes) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!mesh_bytes || !field_bytes) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
   *mesh_bytes = blob_layout(c).total;
   *field_bytes = field_bytes_of(c);
@@ -799,7 +799,7 @@ int dg_device_bytes(const dg_ctx* c, size_t* mesh_bytes, size_t* field_bytes) {
 
 int dg_bind(dg_ctx* c, void* d_mesh, void* d_q0, void* d_q1, void* d_res, void* stream) {
   if (!c) return DG_ERR_ARG;
-  if (!d_mesh || !d_q0 || !d_q1 || !d_res) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!d_mesh || !d_q0 || !d_q1 || !d_res) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->N) return c->fail(DG_ERR_STATE, "dg_bind before dg_set_order");
   if (c->bound) return c->fail(DG_ERR_STATE, "context already bound");
   for (void* p : {d_mesh, d_q0, d_q1, d_res})
@@ -843,7 +843,7 @@ int dg_bind(dg_ctx* c, void* d_mesh, void* d_q0, void* d_q1, void* d_res, void* 
 
 int dg_set_fields(dg_ctx* c, const void* q, int on_device) {
   if (!c) return DG_ERR_ARG;
-  if (!q) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!q) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_set_fields before dg_bind");
   int rc = ensure_ops(c);
   if (rc) return rc;
@@ -870,7 +870,7 @@ int dg_set_fields(dg_ctx* c, const void* q, int on_device) {
 
 int dg_get_fields(dg_ctx* c, void* q, int on_device) {
   if (!c) return DG_ERR_ARG;
-  if (!q) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!q) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_get_fields before dg_bind");
   const size_t rs = c->prec == DG_F64 ? 8 : 4;
   const size_t bytes = size_t(4) * (c->wedge_nodes + c->tet_nodes) * rs;
@@ -887,7 +887,7 @@ int dg_get_fields(dg_ctx* c, void* q, int on_device) {
 
 int dg_rhs(dg_ctx* c, const void* d_q, void* d_rhs) {
   if (!c) return DG_ERR_ARG;
-  if (!d_q || !d_rhs) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!d_q || !d_rhs) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_rhs before dg_bind");
   int rc = ensure_ops(c);
   if (rc) return rc;
@@ -948,7 +948,7 @@ int dg_step(dg_ctx* c, double dt, int64_t nsteps) {
 
 int dg_energy(dg_ctx* c, double* E) {
   if (!c) return DG_ERR_ARG;
-  if (!E) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!E) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_energy before dg_bind");
   int rc = ensure_ops(c);
   if (rc) return rc;
@@ -978,14 +978,14 @@ int dg_sync(dg_ctx* c) {
 
 int dg_time(const dg_ctx* c, double* t) {
   if (!c) return DG_ERR_ARG;
-  if (!t) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!t) return c->fail(DG_ERR_ARG, "null or invalid argument");
   *t = c->t;
   return DG_OK;
 }
 
 int dg_stable_dt(const dg_ctx* c, double cfl, double* dt) {
   if (!c) return DG_ERR_ARG;
-  if (!dt || !(cfl > 0)) return c->fail(DG_ERR_ARG, \"null or invalid argument\");
+  if (!dt || !(cfl > 0)) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
   double best = INFINITY;
   for (int64_t k = 0; k < c->K; ++k) {
