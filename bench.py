@@ -40,6 +40,9 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+WORKLOADS = {"full": (128, 16), "medium": (96, 16), "small": (32, 16)}
+
+
 def _mesh(ntri=128, nlayers=16):
     from paper_1607_03399_gb300 import inputs as I
     m = I.bumpy_layered_mesh(ntri, nlayers)
@@ -205,9 +208,11 @@ def run_ours(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    m, c2, rho = _mesh()
+    ntri, nlay = WORKLOADS[args.workload]
+    m, c2, rho = _mesh(ntri, nlay)
+    orders = [int(x) for x in args.orders.split(",")]
     out = {}
-    for N in (3, 4):
+    for N in orders:
         if world > 1:
             dist.barrier()
         r = measure_order(N, args, torch, dev, m, c2, rho)
@@ -218,7 +223,7 @@ def run_ours(args, rank, world):
             ms = float(t.item())
         r["ms_max"] = ms
         out[N] = r
-        if N == 3:
+        if N == orders[0] and not args.no_e2e:
             S = r["solver"]
             # end to end through the public API with host buffers: per step
             # upload the state from pinned memory, one LSRK45 step, download
@@ -243,7 +248,7 @@ def run_ours(args, rank, world):
             dist.destroy_process_group()
         return
     peak, peak_kind = _peaks()
-    r3 = out[3]
+    r3 = out[orders[0]]
     K, nverts = m.K, m.VX.shape[0]
     ms_step = r3["ms_max"] / args.steps
     value = r3["dof"] * 5 * args.steps / (r3["ms_max"] / 1e3) / 1e9 * world
@@ -258,19 +263,20 @@ def run_ours(args, rank, world):
                             "ms_per_step": r["ms_max"] / args.steps, "stage_us": st * 1e6,
                             "alg_bytes_per_stage": a, "achieved_gbs": a / st / 1e9,
                             "frac": a / st / 1e9 / peak, "dof": r["dof"]}
-    cpu = _cpu_baseline() if world == 1 else None
+    cpu = _cpu_baseline() if (world == 1 and not args.no_cpu) else None
     line = {
         "metric": METRIC, "value": value, "unit": "GDOF-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "wedges": K, "order": 3, "field_dof": r3["dof"],
+        "config": {"workload": WORKLOAD if args.workload == "full" else f"layered_wedges_2x{ntri}x{ntri}x{nlay}",
+                   "wedges": K, "order": orders[0], "field_dof": r3["dof"],
                    "l2_flush": "inputs larger than L2 (3 state buffers of %.0f MB)" % (r3["dof"] * 4 / 1e6),
                    "bc": "rigid", "flux": "upwind"},
-        "roofline": {"kernel": "k_wedge_stage<3>", "bound": "hbm", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": f"k_wedge_stage<{orders[0]}>", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "alg_bytes_per_launch": alg},
         "by_order": by_order,
-        "e2e": r3["e2e"],
+        "e2e": r3.get("e2e"),
         "gpu_launches": 5 * args.steps,
         "clocks": r3["clocks"],
         "cpu_baseline": cpu,
@@ -286,6 +292,10 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
+    ap.add_argument("--orders", default="3,4", help="orders to measure; the first is the headline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
