@@ -102,6 +102,41 @@ __device__ __forceinline__ void taus(int flux, real zM, real zP, real& tau_p, re
 // ---------------------------------------------------------------------------
 // wedge stage
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// bulk asynchronous copies (TMA engine) with mbarrier completion; every wait
+// is bounded and reports a timeout through the device error word
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// About a second of polling at most (each try_wait may itself suspend briefly).
+constexpr long long kWaitLimit = 1ll << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+  for (long long it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
 // per-element geometric factors kept in shared memory ([item][32])
 enum WGeo : int {
   G_RX, G_RY, G_SX, G_SY, G_A, G_J0, G_J1, G_J2, G_NB0, G_NB1, G_NB2, G_NT0, G_NT1, G_NT2, G_JFB, G_JFT,
@@ -109,9 +144,33 @@ enum WGeo : int {
   G_KAPPA, G_IRHO, G_Z, G_TX0, G_TX1, G_TY0, G_TY1, G_COUNT
 };
 
+// Residual slab staged in shared memory by the bulk copy (N <= 3) or read
+// from global memory in per-field batches (N = 4, to keep two CTAs per SM).
+template <int N>
+__host__ __device__ constexpr bool stage_res() {
+  return N <= 3;
+}
+
+template <int N>
+struct WedgeSmem {
+  static constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
+  static constexpr int q = 0;                                        // [4][Np][32]
+  static constexpr int r = q + 4 * Np * kB;                          // [4][Np][32] (if staged)
+  static constexpr int L = r + (stage_res<N>() ? 4 * Np * kB : 0);   // [Nt(Nt+1)/2][32]
+  static constexpr int F = L + (Nt * (Nt + 1) / 2) * kB;             // [4][Nt][32]
+  static constexpr int Fq = F + 4 * Nt * kB;                         // [3][2][Nq][Nq][32]
+  static constexpr int G = Fq + 6 * Nq * Nq * kB;                    // [G_COUNT][32]
+  static constexpr int reals = G + G_COUNT * kB;
+};
+
 template <int N>
 __host__ __device__ constexpr int wedge_smem_reals() {
-  return 4 * npw_of(N) * kB + (nt_of(N) * (nt_of(N) + 1) / 2) * kB + 4 * nt_of(N) * kB + G_COUNT * kB;
+  return WedgeSmem<N>::reals;
+}
+// bytes: two mbarriers + a status word ahead of the reals (16-byte aligned)
+template <int N>
+__host__ __device__ constexpr int wedge_smem_bytes() {
+  return 32 + wedge_smem_reals<N>() * int(sizeof(real));
 }
 
 // Lemma 3.1 for the wedge of lane e: everything the stage needs, from the six
@@ -183,35 +242,118 @@ __device__ __forceinline__ void wedge_geometry(const DevMesh<real>& M, int e, re
 }
 
 template <int N>
-__global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 2 : 4) : 1) k_wedge_stage(const StageArgs<real> A, bool rk) {
+__global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 2 : 3) : 1)
+    k_wedge_stage(const StageArgs<real> A, bool rk) {
   constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
-  constexpr int NL = Nt * (Nt + 1) / 2;
+  using SM = WedgeSmem<N>;
   const AllOps<N, real>& O = OPS<N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  real* sq = reinterpret_cast<real*>(smem_raw);  // [4][Np][32]  state slab
-  real* sL = sq + 4 * Np * kB;                   // [NL][32]     Cholesky factor
-  real* sF = sL + NL * kB;                       // [4][Nt][32]  bottom/top F_p, F_u
-  real* sG = sF + 4 * Nt * kB;                   // [G_COUNT][32] geometry
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // [0] state slab, [1] residual slab
+  int* status = reinterpret_cast<int*>(smem_raw + 16);
+  real* base = reinterpret_cast<real*>(smem_raw + 32);
+  real* sq = base + SM::q;
+  real* sr = base + SM::r;
+  real* sL = base + SM::L;
+  real* sF = base + SM::F;
+  real* sFq = base + SM::Fq;
+  real* sG = base + SM::G;
   const DevMesh<real>& M = A.m;
   const int lane = threadIdx.x & 31;
   const int j = threadIdx.x >> 5;
   const int blk = blockIdx.x;
   const int e = blk * kB + lane;
   const int Kp = M.Kw_pad;
+  constexpr uint32_t slab_bytes = uint32_t(4 * Np * kB * sizeof(real));
+  const bool res_async = rk && stage_res<N>();
 #define GEO(item) sG[(item) * kB + lane]
 
-  // 0. state slab of this block -> shared memory (one contiguous range);
-  //    warp 0 also evaluates the geometric factors
-  {
-    constexpr int nvec = 4 * Np * kB * int(sizeof(real)) / 16;
-    const int4* src = reinterpret_cast<const int4*>(A.q_in + int64_t(blk) * 4 * Np * kB);
-    int4* dst = reinterpret_cast<int4*>(sq);
-    for (int v = threadIdx.x; v < nvec; v += blockDim.x) dst[v] = __ldg(src + v);
+  // 0. bulk copies of the block's state (and residual) slabs; geometry meanwhile
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    mbar_expect_tx(&bar[0], slab_bytes);
+    bulk_g2s(sq, A.q_in + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[0]);
+    if (res_async) {
+      mbar_expect_tx(&bar[1], slab_bytes);
+      bulk_g2s(sr, A.res + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[1]);
+    }
   }
   if (j == 0) wedge_geometry(M, e, sG, lane);
+  int qnbr[3], qcode[3];
+#pragma unroll
+  for (int ed = 0; ed < 3; ++ed) {
+    qnbr[ed] = M.w_nbr[(2 + ed) * Kp + e];
+    qcode[ed] = M.w_code[(2 + ed) * Kp + e];
+  }
+  if (threadIdx.x == 0) *status = mbar_wait_bounded(&bar[0], 0) ? 1 : 0;
   __syncthreads();
+  if (*status == 0) {
+    // the state slab never arrived: report, let any residual copy drain, leave
+    if (threadIdx.x == 0) {
+      atomicOr(M.err, kErrTimeout);
+      if (res_async) mbar_wait_bounded(&bar[1], 0);
+      mbar_wait_bounded(&bar[0], 0);
+    }
+    return;
+  }
 
-  // 1. prologue: triangle-face fluxes (warps 0 and N), Cholesky (warp 1, or 0 if N = 1)
+  // 1. prologue: quadrilateral-face fluxes of slice j (every warp), triangle-face
+  //    fluxes (warps 0 and N), Cholesky factor of M^{tri,k} (warp 1, or 0 if N = 1)
+  {
+    const real zM = GEO(G_Z);
+#pragma unroll
+    for (int ed = 0; ed < 3; ++ed) {
+      const real nx = GEO(G_QNX0 + ed), ny = GEO(G_QNY0 + ed);
+      const int nbr = qnbr[ed], code = qcode[ed];
+      real* Fo = sFq + (ed * 2 * Nq * Nq + j) * kB + lane;  // [(w*Nq + m)*Nq] stride
+      if (nbr < 0) {
+        real tau_p, tau_u;
+        taus(A.flux, zM, zM, tau_p, tau_u);
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          const int no = j * Nt + edge_node(N, ed, m);
+          const real pM = sq[(0 * Np + no) * kB + lane];
+          const real unM = nx * sq[(1 * Np + no) * kB + lane] + ny * sq[(2 * Np + no) * kB + lane];
+          real dp, dun, Fp, Fu;
+          boundary_jumps(A.bc, pM, unM, dp, dun);
+          penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
+          Fo[(0 * Nq + m) * Nq * kB] = Fp;
+          Fo[(1 * Nq + m) * Nq * kB] = Fu;
+        }
+      } else {
+        const real zP = M.w_mat[2 * Kp + nbr];
+        real tau_p, tau_u;
+        taus(A.flux, zM, zP, tau_p, tau_u);
+        const int ep = code >> 1, rev = code & 1;
+        const bool inblk = (nbr >> 5) == blk;
+        real pP[Nq], uxP[Nq], uyP[Nq];
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          const int nn = j * Nt + O.tab.edge[ep][rev ? N - m : m];
+          if (inblk) {
+            pP[m] = sq[(0 * Np + nn) * kB + (nbr & 31)];
+            uxP[m] = sq[(1 * Np + nn) * kB + (nbr & 31)];
+            uyP[m] = sq[(2 * Np + nn) * kB + (nbr & 31)];
+          } else {
+            pP[m] = __ldg(A.q_in + widx<N>(nbr >> 5, 0, nn, nbr & 31));
+            uxP[m] = __ldg(A.q_in + widx<N>(nbr >> 5, 1, nn, nbr & 31));
+            uyP[m] = __ldg(A.q_in + widx<N>(nbr >> 5, 2, nn, nbr & 31));
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          const int no = j * Nt + edge_node(N, ed, m);
+          const real pM = sq[(0 * Np + no) * kB + lane];
+          const real unM = nx * sq[(1 * Np + no) * kB + lane] + ny * sq[(2 * Np + no) * kB + lane];
+          real Fp, Fu;
+          penalty_flux(pP[m] - pM, nx * uxP[m] + ny * uyP[m] - unM, tau_p, tau_u, Fp, Fu);
+          Fo[(0 * Nq + m) * Nq * kB] = Fp;
+          Fo[(1 * Nq + m) * Nq * kB] = Fu;
+        }
+      }
+    }
+  }
   if (j == 0 || j == N) {
     const int fb = (j == 0) ? 0 : 1;
     const real nn0 = fb ? GEO(G_NT0) : GEO(G_NB0), nn1 = fb ? GEO(G_NT1) : GEO(G_NB1), nn2 = fb ? GEO(G_NT2) : GEO(G_NB2);
@@ -303,71 +445,6 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
   real Wp[Nt], Wu[3][Nt];
 #pragma unroll
   for (int i = 0; i < Nt; ++i) Wp[i] = Wu[0][i] = Wu[1][i] = Wu[2][i] = real(0);
-  // (a) quadrilateral faces at slice j: W += M~_e F, M~_e = (L_e/4)(h_a Mea + h_b Meb)
-  {
-    const real zM = GEO(G_Z);
-#pragma unroll
-    for (int ed = 0; ed < 3; ++ed) {
-      const real nx = GEO(G_QNX0 + ed), ny = GEO(G_QNY0 + ed);
-      const int nbr = M.w_nbr[(2 + ed) * Kp + e];
-      const int code = M.w_code[(2 + ed) * Kp + e];
-      real Fp[Nq], Fu[Nq];
-      if (nbr < 0) {
-        real tau_p, tau_u;
-        taus(A.flux, zM, zM, tau_p, tau_u);
-#pragma unroll
-        for (int m = 0; m < Nq; ++m) {
-          const int no = j * Nt + edge_node(N, ed, m);
-          const real pM = sq[(0 * Np + no) * kB + lane];
-          const real unM = nx * sq[(1 * Np + no) * kB + lane] + ny * sq[(2 * Np + no) * kB + lane];
-          real dp, dun;
-          boundary_jumps(A.bc, pM, unM, dp, dun);
-          penalty_flux(dp, dun, tau_p, tau_u, Fp[m], Fu[m]);
-        }
-      } else {
-        const real zP = M.w_mat[2 * Kp + nbr];
-        real tau_p, tau_u;
-        taus(A.flux, zM, zP, tau_p, tau_u);
-        const int ep = code >> 1, rev = code & 1;
-        const bool inblk = (nbr >> 5) == blk;
-#pragma unroll
-        for (int m = 0; m < Nq; ++m) {
-          const int no = j * Nt + edge_node(N, ed, m);
-          const int nn = j * Nt + O.tab.edge[ep][rev ? N - m : m];
-          real pP, uxP, uyP;
-          if (inblk) {
-            pP = sq[(0 * Np + nn) * kB + (nbr & 31)];
-            uxP = sq[(1 * Np + nn) * kB + (nbr & 31)];
-            uyP = sq[(2 * Np + nn) * kB + (nbr & 31)];
-          } else {
-            pP = __ldg(A.q_in + widx<N>(nbr >> 5, 0, nn, nbr & 31));
-            uxP = __ldg(A.q_in + widx<N>(nbr >> 5, 1, nn, nbr & 31));
-            uyP = __ldg(A.q_in + widx<N>(nbr >> 5, 2, nn, nbr & 31));
-          }
-          const real pM = sq[(0 * Np + no) * kB + lane];
-          const real unM = nx * sq[(1 * Np + no) * kB + lane] + ny * sq[(2 * Np + no) * kB + lane];
-          penalty_flux(pP - pM, nx * uxP + ny * uyP - unM, tau_p, tau_u, Fp[m], Fu[m]);
-        }
-      }
-      const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
-#pragma unroll
-      for (int m = 0; m < Nq; ++m) {
-        real gpa = 0, gpb = 0, gua = 0, gub = 0;
-#pragma unroll
-        for (int n = 0; n < Nq; ++n) {
-          gpa += O.w.Mea[m * Nq + n] * Fp[n];
-          gpb += O.w.Meb[m * Nq + n] * Fp[n];
-          gua += O.w.Mea[m * Nq + n] * Fu[n];
-          gub += O.w.Meb[m * Nq + n] * Fu[n];
-        }
-        const real gp = ca * gpa + cbq * gpb, gu = ca * gua + cbq * gub;
-        const int i = edge_node(N, ed, m);
-        Wp[i] += gp;
-        Wu[0][i] += nx * gu;
-        Wu[1][i] += ny * gu;
-      }
-    }
-  }
   {
     real dtr[Nq];
 #pragma unroll
@@ -378,7 +455,7 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
     const real Aj = GEO(G_A);
     const real cb = GEO(G_JFB) * O.w.ell0[j];
     const real ct = GEO(G_JFT) * O.w.ellN[j];
-    // (b) pressure: G = -(t_xJ D_t u_x + t_yJ D_t u_y + A D_t u_z) + lifts; W += M^tri G
+    // (a) pressure: G = -(t_xJ D_t u_x + t_yJ D_t u_y + A D_t u_z) + lifts; W = M^tri G
     {
       real G[Nt];
 #pragma unroll
@@ -397,10 +474,10 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
         real acc = 0;
 #pragma unroll
         for (int l = 0; l < Nt; ++l) acc += O.w.M[i * Nt + l] * G[l];
-        Wp[i] += acc;
+        Wp[i] = acc;
       }
     }
-    // (c) velocity: G_c = -t_cJ D_t p + n_c lifts; W += M^tri G
+    // (b) velocity: G_c = -t_cJ D_t p + n_c lifts; W = M^tri G
     {
       real dp[Nt];
 #pragma unroll
@@ -423,9 +500,38 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
           real acc = 0;
 #pragma unroll
           for (int l = 0; l < Nt; ++l) acc += O.w.M[i * Nt + l] * G[l];
-          Wu[c][i] += acc;
+          Wu[c][i] = acc;
         }
       }
+    }
+  }
+  // (c) quadrilateral faces at slice j: W += M~_e F, M~_e = (L_e/4)(h_a Mea + h_b Meb)
+#pragma unroll
+  for (int ed = 0; ed < 3; ++ed) {
+    const real nx = GEO(G_QNX0 + ed), ny = GEO(G_QNY0 + ed);
+    const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
+    const real* Fo = sFq + (ed * 2 * Nq * Nq + j) * kB + lane;
+    real Fp[Nq], Fu[Nq];
+#pragma unroll
+    for (int n = 0; n < Nq; ++n) {
+      Fp[n] = Fo[(0 * Nq + n) * Nq * kB];
+      Fu[n] = Fo[(1 * Nq + n) * Nq * kB];
+    }
+#pragma unroll
+    for (int m = 0; m < Nq; ++m) {
+      real gpa = 0, gpb = 0, gua = 0, gub = 0;
+#pragma unroll
+      for (int n = 0; n < Nq; ++n) {
+        gpa += O.w.Mea[m * Nq + n] * Fp[n];
+        gpb += O.w.Meb[m * Nq + n] * Fp[n];
+        gua += O.w.Mea[m * Nq + n] * Fu[n];
+        gub += O.w.Meb[m * Nq + n] * Fu[n];
+      }
+      const real gp = ca * gpa + cbq * gpb, gu = ca * gua + cbq * gub;
+      const int i = edge_node(N, ed, m);
+      Wp[i] += gp;
+      Wu[0][i] += nx * gu;
+      Wu[1][i] += ny * gu;
     }
   }
   // (d) X = (M^{tri,k})^{-1} W: forward and backward substitution, 4 right-hand sides
@@ -500,17 +606,30 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
     }
   }
   // (f) fused low-storage Runge-Kutta update (or plain right-hand side)
+  if (res_async && !mbar_wait_bounded(&bar[1], 0)) {
+    if (lane == 0) atomicOr(M.err, kErrTimeout);
+    mbar_wait_bounded(&bar[1], 0);
+    return;
+  }
   if (e < M.Kw) {
     const real kappa = GEO(G_KAPPA), irho = GEO(G_IRHO);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
+      real rv[Nt];
+      if (rk) {
+#pragma unroll
+        for (int i = 0; i < Nt; ++i) {
+          const int n = j * Nt + i;
+          rv[i] = stage_res<N>() ? sr[(f * Np + n) * kB + lane] : A.res[widx<N>(blk, f, n, lane)];
+        }
+      }
 #pragma unroll
       for (int i = 0; i < Nt; ++i) {
         const int n = j * Nt + i;
         const int64_t g = widx<N>(blk, f, n, lane);
         const real r = (f == 0) ? kappa * Wp[i] : irho * Wu[f - 1][i];
         if (rk) {
-          const real rr = A.rk_a * A.res[g] + A.dt * r;
+          const real rr = A.rk_a * rv[i] + A.dt * r;
           A.res[g] = rr;
           A.q_out[g] = sq[(f * Np + n) * kB + lane] + A.rk_b * rr;
         } else {
@@ -911,7 +1030,7 @@ __global__ void k_energy_final(const double* __restrict__ partials, int n, doubl
 template <int N>
 int prepare_n() {
   cudaError_t err = cudaFuncSetAttribute(k_wedge_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         wedge_smem_reals<N>() * int(sizeof(real)));
+                                         wedge_smem_bytes<N>());
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_tet_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                tet_smem_reals<N>() * int(sizeof(real)));
@@ -921,7 +1040,7 @@ int prepare_n() {
 template <int N>
 int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s) {
   if (a.m.nblk_w > 0) {
-    k_wedge_stage<N><<<a.m.nblk_w, 32 * (N + 1), wedge_smem_reals<N>() * int(sizeof(real)), s>>>(a, rk);
+    k_wedge_stage<N><<<a.m.nblk_w, 32 * (N + 1), wedge_smem_bytes<N>(), s>>>(a, rk);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return int(err);
   }
