@@ -2,8 +2,9 @@
 //
 // Device data layout (all element-indexed arrays are structure-of-arrays over
 // 32-element blocks so that one warp reads one 128-byte line per item):
-//   field buffers  wedge region [nblk_w][4 fields][Np_w][32], then
-//                  tet region   [nblk_t][4 fields][Np_t][32]   (packed state)
+//   field buffers  wedge region [nblk_w][Np_w][32][4 fields], then
+//                  tet region   [nblk_t][Np_t][32][4 fields]   (packed state,
+//                  a node's four fields adjacent: one 16-byte access)
 //   w_vid   [6][Kw_pad]  vertex ids            t_vid  [4][Kt_pad]
 //   w_nbr   [5][Kw_pad]  neighbour index       t_nbr  [4][Kt_pad]
 //   w_code  [5][Kw_pad]  orientation code      t_code [4][Kt_pad]

@@ -60,15 +60,64 @@ __host__ __device__ constexpr int tet_face_node(int N, int f, int k) {
   return -1;
 }
 
+// Packed state layout: node-major, the four fields innermost, so one thread
+// moves a node's (p, u_x, u_y, u_z) with one 16-byte (FP32) access and a warp
+// moves 512 contiguous bytes:
+//   wedge region [nblk_w][Np][32 lanes][4 fields], tet region likewise.
 template <int N>
-__device__ __forceinline__ int64_t widx(int blk_e, int f, int node, int lane) {
+__device__ __forceinline__ int64_t widx(int blk_e, int node, int lane) {
   constexpr int Np = npw_of(N);
-  return ((int64_t(blk_e) * 4 + f) * Np + node) * kB + lane;
+  return ((int64_t(blk_e) * Np + node) * kB + lane) * 4;
 }
 template <int N>
-__device__ __forceinline__ int64_t tidx(int64_t off, int blk_e, int f, int node, int lane) {
+__device__ __forceinline__ int64_t tidx(int64_t off, int blk_e, int node, int lane) {
   constexpr int Np = npt_of(N);
-  return off + ((int64_t(blk_e) * 4 + f) * Np + node) * kB + lane;
+  return off + ((int64_t(blk_e) * Np + node) * kB + lane) * 4;
+}
+
+struct Q4 {
+  real p, u, v, w;
+};
+__device__ __forceinline__ Q4 q4_from(const float4 t) { return Q4{real(t.x), real(t.y), real(t.z), real(t.w)}; }
+// shared-memory slab [Np][32][4]
+__device__ __forceinline__ Q4 lds4(const real* slab, int node, int lane) {
+  const real* a = slab + ((node * kB + lane) << 2);
+  if constexpr (sizeof(real) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(a);
+    return Q4{real(t.x), real(t.y), real(t.z), real(t.w)};
+  } else {
+    const double2 t0 = reinterpret_cast<const double2*>(a)[0], t1 = reinterpret_cast<const double2*>(a)[1];
+    return Q4{real(t0.x), real(t0.y), real(t1.x), real(t1.y)};
+  }
+}
+// global, read-only for the kernel's lifetime (the stage input)
+__device__ __forceinline__ Q4 ldg4(const real* __restrict__ q, int64_t idx) {
+  if constexpr (sizeof(real) == 4) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(q + idx));
+    return Q4{real(t.x), real(t.y), real(t.z), real(t.w)};
+  } else {
+    const double2 t0 = __ldg(reinterpret_cast<const double2*>(q + idx));
+    const double2 t1 = __ldg(reinterpret_cast<const double2*>(q + idx) + 1);
+    return Q4{real(t0.x), real(t0.y), real(t1.x), real(t1.y)};
+  }
+}
+// global, coherent (the residual, rewritten by the same thread)
+__device__ __forceinline__ Q4 ld4(const real* q, int64_t idx) {
+  if constexpr (sizeof(real) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(q + idx);
+    return Q4{real(t.x), real(t.y), real(t.z), real(t.w)};
+  } else {
+    const double2 t0 = reinterpret_cast<const double2*>(q + idx)[0], t1 = reinterpret_cast<const double2*>(q + idx)[1];
+    return Q4{real(t0.x), real(t0.y), real(t1.x), real(t1.y)};
+  }
+}
+__device__ __forceinline__ void st4(real* q, int64_t idx, const Q4& v) {
+  if constexpr (sizeof(real) == 4) {
+    *reinterpret_cast<float4*>(q + idx) = make_float4(float(v.p), float(v.u), float(v.v), float(v.w));
+  } else {
+    reinterpret_cast<double2*>(q + idx)[0] = make_double2(double(v.p), double(v.u));
+    reinterpret_cast<double2*>(q + idx)[1] = make_double2(double(v.v), double(v.w));
+  }
 }
 
 // Penalty fluxes of eq. (1): F_p = 1/2 (tau_p [p] - [u_n]), F_u = 1/2 (tau_u [u_n] - [p]).
@@ -258,6 +307,9 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
   real* sFq = base + SM::Fq;
   real* sG = base + SM::G;
   const DevMesh<real>& M = A.m;
+  const real* __restrict__ qin = A.q_in;
+  real* __restrict__ qout = A.q_out;
+  real* __restrict__ resg = A.res;
   const int lane = threadIdx.x & 31;
   const int j = threadIdx.x >> 5;
   const int blk = blockIdx.x;
@@ -273,10 +325,10 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
     mbar_init(&bar[1], 1);
     fence_mbar_init();
     mbar_expect_tx(&bar[0], slab_bytes);
-    bulk_g2s(sq, A.q_in + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[0]);
+    bulk_g2s(sq, qin + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[0]);
     if (res_async) {
       mbar_expect_tx(&bar[1], slab_bytes);
-      bulk_g2s(sr, A.res + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[1]);
+      bulk_g2s(sr, resg + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[1]);
     }
   }
   if (j == 0) wedge_geometry(M, e, sG, lane);
@@ -312,11 +364,9 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
         taus(A.flux, zM, zM, tau_p, tau_u);
 #pragma unroll
         for (int m = 0; m < Nq; ++m) {
-          const int no = j * Nt + edge_node(N, ed, m);
-          const real pM = sq[(0 * Np + no) * kB + lane];
-          const real unM = nx * sq[(1 * Np + no) * kB + lane] + ny * sq[(2 * Np + no) * kB + lane];
+          const Q4 o = lds4(sq, j * Nt + edge_node(N, ed, m), lane);
           real dp, dun, Fp, Fu;
-          boundary_jumps(A.bc, pM, unM, dp, dun);
+          boundary_jumps(A.bc, o.p, nx * o.u + ny * o.v, dp, dun);
           penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
           Fo[(0 * Nq + m) * Nq * kB] = Fp;
           Fo[(1 * Nq + m) * Nq * kB] = Fu;
@@ -327,27 +377,17 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
         taus(A.flux, zM, zP, tau_p, tau_u);
         const int ep = code >> 1, rev = code & 1;
         const bool inblk = (nbr >> 5) == blk;
-        real pP[Nq], uxP[Nq], uyP[Nq];
+        Q4 nv[Nq];
 #pragma unroll
         for (int m = 0; m < Nq; ++m) {
           const int nn = j * Nt + O.tab.edge[ep][rev ? N - m : m];
-          if (inblk) {
-            pP[m] = sq[(0 * Np + nn) * kB + (nbr & 31)];
-            uxP[m] = sq[(1 * Np + nn) * kB + (nbr & 31)];
-            uyP[m] = sq[(2 * Np + nn) * kB + (nbr & 31)];
-          } else {
-            pP[m] = __ldg(A.q_in + widx<N>(nbr >> 5, 0, nn, nbr & 31));
-            uxP[m] = __ldg(A.q_in + widx<N>(nbr >> 5, 1, nn, nbr & 31));
-            uyP[m] = __ldg(A.q_in + widx<N>(nbr >> 5, 2, nn, nbr & 31));
-          }
+          nv[m] = inblk ? lds4(sq, nn, nbr & 31) : ldg4(qin, widx<N>(nbr >> 5, nn, nbr & 31));
         }
 #pragma unroll
         for (int m = 0; m < Nq; ++m) {
-          const int no = j * Nt + edge_node(N, ed, m);
-          const real pM = sq[(0 * Np + no) * kB + lane];
-          const real unM = nx * sq[(1 * Np + no) * kB + lane] + ny * sq[(2 * Np + no) * kB + lane];
+          const Q4 o = lds4(sq, j * Nt + edge_node(N, ed, m), lane);
           real Fp, Fu;
-          penalty_flux(pP[m] - pM, nx * uxP[m] + ny * uyP[m] - unM, tau_p, tau_u, Fp, Fu);
+          penalty_flux(nv[m].p - o.p, nx * (nv[m].u - o.u) + ny * (nv[m].v - o.v), tau_p, tau_u, Fp, Fu);
           Fo[(0 * Nq + m) * Nq * kB] = Fp;
           Fo[(1 * Nq + m) * Nq * kB] = Fu;
         }
@@ -366,11 +406,9 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
       taus(A.flux, zM, zM, tau_p, tau_u);
 #pragma unroll
       for (int k = 0; k < Nt; ++k) {
-        const real pM = sq[(0 * Np + own0 + k) * kB + lane];
-        const real unM = nn0 * sq[(1 * Np + own0 + k) * kB + lane] + nn1 * sq[(2 * Np + own0 + k) * kB + lane] +
-                         nn2 * sq[(3 * Np + own0 + k) * kB + lane];
+        const Q4 o = lds4(sq, own0 + k, lane);
         real dp, dun, Fp, Fu;
-        boundary_jumps(A.bc, pM, unM, dp, dun);
+        boundary_jumps(A.bc, o.p, nn0 * o.u + nn1 * o.v + nn2 * o.w, dp, dun);
         penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
         sF[((2 * fb + 0) * Nt + k) * kB + lane] = Fp;
         sF[((2 * fb + 1) * Nt + k) * kB + lane] = Fu;
@@ -385,33 +423,16 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
 #pragma unroll
       for (int k = 0; k < Nt; ++k) {
         const int nk = O.tab.tri_perm[perm][k];
-        real pP, uxP, uyP, uzP;
+        Q4 nv;
         if (ntet) {
-          const int node = O.tab.tet_face[nf][nk];
-          pP = __ldg(A.q_in + tidx<N>(M.tet_off, nbr >> 5, 0, node, nbr & 31));
-          uxP = __ldg(A.q_in + tidx<N>(M.tet_off, nbr >> 5, 1, node, nbr & 31));
-          uyP = __ldg(A.q_in + tidx<N>(M.tet_off, nbr >> 5, 2, node, nbr & 31));
-          uzP = __ldg(A.q_in + tidx<N>(M.tet_off, nbr >> 5, 3, node, nbr & 31));
+          nv = ldg4(qin, tidx<N>(M.tet_off, nbr >> 5, O.tab.tet_face[nf][nk], nbr & 31));
         } else {
           const int node = (nf ? N * Nt : 0) + nk;
-          if (inblk) {
-            pP = sq[(0 * Np + node) * kB + (nbr & 31)];
-            uxP = sq[(1 * Np + node) * kB + (nbr & 31)];
-            uyP = sq[(2 * Np + node) * kB + (nbr & 31)];
-            uzP = sq[(3 * Np + node) * kB + (nbr & 31)];
-          } else {
-            pP = __ldg(A.q_in + widx<N>(nbr >> 5, 0, node, nbr & 31));
-            uxP = __ldg(A.q_in + widx<N>(nbr >> 5, 1, node, nbr & 31));
-            uyP = __ldg(A.q_in + widx<N>(nbr >> 5, 2, node, nbr & 31));
-            uzP = __ldg(A.q_in + widx<N>(nbr >> 5, 3, node, nbr & 31));
-          }
+          nv = inblk ? lds4(sq, node, nbr & 31) : ldg4(qin, widx<N>(nbr >> 5, node, nbr & 31));
         }
-        const real pM = sq[(0 * Np + own0 + k) * kB + lane];
-        const real unM = nn0 * sq[(1 * Np + own0 + k) * kB + lane] + nn1 * sq[(2 * Np + own0 + k) * kB + lane] +
-                         nn2 * sq[(3 * Np + own0 + k) * kB + lane];
-        const real unP = nn0 * uxP + nn1 * uyP + nn2 * uzP;
+        const Q4 o = lds4(sq, own0 + k, lane);
         real Fp, Fu;
-        penalty_flux(pP - pM, unP - unM, tau_p, tau_u, Fp, Fu);
+        penalty_flux(nv.p - o.p, nn0 * (nv.u - o.u) + nn1 * (nv.v - o.v) + nn2 * (nv.w - o.w), tau_p, tau_u, Fp, Fu);
         sF[((2 * fb + 0) * Nt + k) * kB + lane] = Fp;
         sF[((2 * fb + 1) * Nt + k) * kB + lane] = Fu;
       }
@@ -443,8 +464,6 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
 
   // 2. slice j of every element of the block
   real Wp[Nt], Wu[3][Nt];
-#pragma unroll
-  for (int i = 0; i < Nt; ++i) Wp[i] = Wu[0][i] = Wu[1][i] = Wu[2][i] = real(0);
   {
     real dtr[Nq];
 #pragma unroll
@@ -456,17 +475,21 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
     const real cb = GEO(G_JFB) * O.w.ell0[j];
     const real ct = GEO(G_JFT) * O.w.ellN[j];
     // (a) pressure: G = -(t_xJ D_t u_x + t_yJ D_t u_y + A D_t u_z) + lifts; W = M^tri G
+    real dp[Nt];
     {
       real G[Nt];
 #pragma unroll
       for (int i = 0; i < Nt; ++i) {
-        real dux = 0, duy = 0, duz = 0;
+        real dpp = 0, dux = 0, duy = 0, duz = 0;
 #pragma unroll
         for (int m = 0; m < Nq; ++m) {
-          dux += dtr[m] * sq[(1 * Np + m * Nt + i) * kB + lane];
-          duy += dtr[m] * sq[(2 * Np + m * Nt + i) * kB + lane];
-          duz += dtr[m] * sq[(3 * Np + m * Nt + i) * kB + lane];
+          const Q4 v = lds4(sq, m * Nt + i, lane);
+          dpp += dtr[m] * v.p;
+          dux += dtr[m] * v.u;
+          duy += dtr[m] * v.v;
+          duz += dtr[m] * v.w;
         }
+        dp[i] = dpp;
         G[i] = cb * sF[(0 * Nt + i) * kB + lane] + ct * sF[(2 * Nt + i) * kB + lane] - (txJ * dux + tyJ * duy + Aj * duz);
       }
 #pragma unroll
@@ -478,30 +501,20 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
       }
     }
     // (b) velocity: G_c = -t_cJ D_t p + n_c lifts; W = M^tri G
-    {
-      real dp[Nt];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const real tc = (c == 0) ? txJ : (c == 1 ? tyJ : Aj);
+      const real nbc = GEO(G_NB0 + c) * cb, ntc = GEO(G_NT0 + c) * ct;
+      real G[Nt];
+#pragma unroll
+      for (int i = 0; i < Nt; ++i)
+        G[i] = nbc * sF[(1 * Nt + i) * kB + lane] + ntc * sF[(3 * Nt + i) * kB + lane] - tc * dp[i];
 #pragma unroll
       for (int i = 0; i < Nt; ++i) {
         real acc = 0;
 #pragma unroll
-        for (int m = 0; m < Nq; ++m) acc += dtr[m] * sq[(0 * Np + m * Nt + i) * kB + lane];
-        dp[i] = acc;
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const real tc = (c == 0) ? txJ : (c == 1 ? tyJ : Aj);
-        const real nbc = GEO(G_NB0 + c) * cb, ntc = GEO(G_NT0 + c) * ct;
-        real G[Nt];
-#pragma unroll
-        for (int i = 0; i < Nt; ++i)
-          G[i] = nbc * sF[(1 * Nt + i) * kB + lane] + ntc * sF[(3 * Nt + i) * kB + lane] - tc * dp[i];
-#pragma unroll
-        for (int i = 0; i < Nt; ++i) {
-          real acc = 0;
-#pragma unroll
-          for (int l = 0; l < Nt; ++l) acc += O.w.M[i * Nt + l] * G[l];
-          Wu[c][i] = acc;
-        }
+        for (int l = 0; l < Nt; ++l) acc += O.w.M[i * Nt + l] * G[l];
+        Wu[c][i] = acc;
       }
     }
   }
@@ -568,39 +581,27 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
     Wu[2][i] *= d;
   }
   // (e) strong r, s parts of slice j (constant metric terms, Lemma 3.1)
-  const real rx = GEO(G_RX), ry = GEO(G_RY), sx = GEO(G_SX), sy = GEO(G_SY);
   {
-    real av[Nt], bv[Nt];
+    const real rx = GEO(G_RX), ry = GEO(G_RY), sx = GEO(G_SX), sy = GEO(G_SY);
+    real pv[Nt], av[Nt], bv[Nt];
 #pragma unroll
     for (int l = 0; l < Nt; ++l) {
-      const real ux = sq[(1 * Np + j * Nt + l) * kB + lane];
-      const real uy = sq[(2 * Np + j * Nt + l) * kB + lane];
-      av[l] = rx * ux + ry * uy;
-      bv[l] = sx * ux + sy * uy;
+      const Q4 v = lds4(sq, j * Nt + l, lane);
+      pv[l] = v.p;
+      av[l] = rx * v.u + ry * v.v;
+      bv[l] = sx * v.u + sy * v.v;
     }
 #pragma unroll
     for (int i = 0; i < Nt; ++i) {
-      real dv = 0;
+      real dv = 0, pr = 0, ps = 0;
 #pragma unroll
       for (int l = 0; l < Nt; ++l) {
         dv += O.w.Dr[i * Nt + l] * av[l];
         dv += O.w.Ds[i * Nt + l] * bv[l];
-      }
-      Wp[i] -= dv;
-    }
-  }
-  {
-    real pv[Nt];
-#pragma unroll
-    for (int l = 0; l < Nt; ++l) pv[l] = sq[(0 * Np + j * Nt + l) * kB + lane];
-#pragma unroll
-    for (int i = 0; i < Nt; ++i) {
-      real pr = 0, ps = 0;
-#pragma unroll
-      for (int l = 0; l < Nt; ++l) {
         pr += O.w.Dr[i * Nt + l] * pv[l];
         ps += O.w.Ds[i * Nt + l] * pv[l];
       }
+      Wp[i] -= dv;
       Wu[0][i] -= rx * pr + sx * ps;
       Wu[1][i] -= ry * pr + sy * ps;
     }
@@ -614,27 +615,19 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
   if (e < M.Kw) {
     const real kappa = GEO(G_KAPPA), irho = GEO(G_IRHO);
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      real rv[Nt];
+    for (int i = 0; i < Nt; ++i) {
+      const int n = j * Nt + i;
+      const int64_t g = widx<N>(blk, n, lane);
+      const Q4 r{kappa * Wp[i], irho * Wu[0][i], irho * Wu[1][i], irho * Wu[2][i]};
       if (rk) {
-#pragma unroll
-        for (int i = 0; i < Nt; ++i) {
-          const int n = j * Nt + i;
-          rv[i] = stage_res<N>() ? sr[(f * Np + n) * kB + lane] : A.res[widx<N>(blk, f, n, lane)];
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < Nt; ++i) {
-        const int n = j * Nt + i;
-        const int64_t g = widx<N>(blk, f, n, lane);
-        const real r = (f == 0) ? kappa * Wp[i] : irho * Wu[f - 1][i];
-        if (rk) {
-          const real rr = A.rk_a * rv[i] + A.dt * r;
-          A.res[g] = rr;
-          A.q_out[g] = sq[(f * Np + n) * kB + lane] + A.rk_b * rr;
-        } else {
-          A.q_out[g] = r;
-        }
+        const Q4 r0 = stage_res<N>() ? lds4(sr, n, lane) : ld4(resg, g);
+        const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
+                    A.rk_a * r0.w + A.dt * r.w};
+        const Q4 q0 = lds4(sq, n, lane);
+        st4(resg, g, rr);
+        st4(qout, g, Q4{q0.p + A.rk_b * rr.p, q0.u + A.rk_b * rr.u, q0.v + A.rk_b * rr.v, q0.w + A.rk_b * rr.w});
+      } else {
+        st4(qout, g, r);
       }
     }
   }
@@ -726,11 +719,9 @@ __device__ __forceinline__ void tet_face_flux(const StageArgs<real>& A, const Te
     taus(A.flux, g.zM, g.zM, tau_p, tau_u);
 #pragma unroll
     for (int k = 0; k < Nt; ++k) {
-      const int no = tet_face_node(N, F, k);
-      const real pM = sq[(0 * Np + no) * kB + lane];
-      const real unM = nx * sq[(1 * Np + no) * kB + lane] + ny * sq[(2 * Np + no) * kB + lane] + nz * sq[(3 * Np + no) * kB + lane];
+      const Q4 o = lds4(sq, tet_face_node(N, F, k), lane);
       real dp, dun, Fp, Fu;
-      boundary_jumps(A.bc, pM, unM, dp, dun);
+      boundary_jumps(A.bc, o.p, nx * o.u + ny * o.v + nz * o.w, dp, dun);
       penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
       sF[((F * 2 + 0) * Nt + k) * kB + lane] = Fp;
       sF[((F * 2 + 1) * Nt + k) * kB + lane] = Fu;
@@ -744,30 +735,17 @@ __device__ __forceinline__ void tet_face_flux(const StageArgs<real>& A, const Te
     const bool inblk = ntet && ((nbr >> 5) == int(blockIdx.x));
 #pragma unroll
     for (int k = 0; k < Nt; ++k) {
-      const int no = tet_face_node(N, F, k);
       const int nk = O.tab.tri_perm[perm][k];
-      real pP, uP[3];
+      Q4 nv;
       if (!ntet) {
-        const int node = (nf ? N * nt_of(N) : 0) + nk;
-        pP = __ldg(A.q_in + widx<N>(nbr >> 5, 0, node, nbr & 31));
-#pragma unroll
-        for (int d = 0; d < 3; ++d) uP[d] = __ldg(A.q_in + widx<N>(nbr >> 5, 1 + d, node, nbr & 31));
+        nv = ldg4(A.q_in, widx<N>(nbr >> 5, (nf ? N * nt_of(N) : 0) + nk, nbr & 31));
       } else {
         const int node = O.tab.tet_face[nf][nk];
-        if (inblk) {
-          pP = sq[(0 * Np + node) * kB + (nbr & 31)];
-#pragma unroll
-          for (int d = 0; d < 3; ++d) uP[d] = sq[((1 + d) * Np + node) * kB + (nbr & 31)];
-        } else {
-          pP = __ldg(A.q_in + tidx<N>(M.tet_off, nbr >> 5, 0, node, nbr & 31));
-#pragma unroll
-          for (int d = 0; d < 3; ++d) uP[d] = __ldg(A.q_in + tidx<N>(M.tet_off, nbr >> 5, 1 + d, node, nbr & 31));
-        }
+        nv = inblk ? lds4(sq, node, nbr & 31) : ldg4(A.q_in, tidx<N>(M.tet_off, nbr >> 5, node, nbr & 31));
       }
-      const real pM = sq[(0 * Np + no) * kB + lane];
-      const real unM = nx * sq[(1 * Np + no) * kB + lane] + ny * sq[(2 * Np + no) * kB + lane] + nz * sq[(3 * Np + no) * kB + lane];
+      const Q4 o = lds4(sq, tet_face_node(N, F, k), lane);
       real Fp, Fu;
-      penalty_flux(pP - pM, nx * uP[0] + ny * uP[1] + nz * uP[2] - unM, tau_p, tau_u, Fp, Fu);
+      penalty_flux(nv.p - o.p, nx * (nv.u - o.u) + ny * (nv.v - o.v) + nz * (nv.w - o.w), tau_p, tau_u, Fp, Fu);
       sF[((F * 2 + 0) * Nt + k) * kB + lane] = Fp;
       sF[((F * 2 + 1) * Nt + k) * kB + lane] = Fu;
     }
@@ -788,8 +766,8 @@ __device__ __forceinline__ void tet_chunk_out(const StageArgs<real>& A, const Te
     for (int c = 0; c < C; ++c) dr[c] = ds[c] = dt[c] = ap[c] = real(0);
 #pragma unroll
     for (int l = 0; l < Np; ++l) {
-      const real p = sq[(0 * Np + l) * kB + lane];
-      const real ux = sq[(1 * Np + l) * kB + lane], uy = sq[(2 * Np + l) * kB + lane], uz = sq[(3 * Np + l) * kB + lane];
+      const Q4 v = lds4(sq, l, lane);
+      const real p = v.p, ux = v.u, uy = v.v, uz = v.w;
       const real wr = g.Ri[0][0] * ux + g.Ri[0][1] * uy + g.Ri[0][2] * uz;
       const real ws = g.Ri[1][0] * ux + g.Ri[1][1] * uy + g.Ri[1][2] * uz;
       const real wt = g.Ri[2][0] * ux + g.Ri[2][1] * uy + g.Ri[2][2] * uz;
@@ -833,21 +811,23 @@ __device__ __forceinline__ void tet_chunk_out(const StageArgs<real>& A, const Te
       for (int d = 0; d < 3; ++d) au[d][c] += g.n[f][d] * lu[c];
   }
   if (e < M.Kt) {
+    real* __restrict__ resg = A.res;
+    real* __restrict__ qout = A.q_out;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       if (I0 + c < Np) {
         const int i = I0 + c;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const int64_t gi = tidx<N>(M.tet_off, blockIdx.x, f, i, lane);
-          const real r = (f == 0) ? g.kappa * ap[c] : g.irho * au[f - 1][c];
-          if (rk) {
-            const real rr = A.rk_a * A.res[gi] + A.dt * r;
-            A.res[gi] = rr;
-            A.q_out[gi] = sq[(f * Np + i) * kB + lane] + A.rk_b * rr;
-          } else {
-            A.q_out[gi] = r;
-          }
+        const int64_t gi = tidx<N>(M.tet_off, blockIdx.x, i, lane);
+        const Q4 r{g.kappa * ap[c], g.irho * au[0][c], g.irho * au[1][c], g.irho * au[2][c]};
+        if (rk) {
+          const Q4 r0 = ld4(resg, gi);
+          const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
+                      A.rk_a * r0.w + A.dt * r.w};
+          const Q4 q0 = lds4(sq, i, lane);
+          st4(resg, gi, rr);
+          st4(qout, gi, Q4{q0.p + A.rk_b * rr.p, q0.u + A.rk_b * rr.u, q0.v + A.rk_b * rr.v, q0.w + A.rk_b * rr.w});
+        } else {
+          st4(qout, gi, r);
         }
       }
     }
@@ -858,7 +838,7 @@ template <int N>
 __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? 4 : 1) k_tet_stage(const StageArgs<real> A, bool rk) {
   constexpr int Np = npt_of(N), C = tet_chunk<N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  real* sq = reinterpret_cast<real*>(smem_raw);  // [4][Np][32]
+  real* sq = reinterpret_cast<real*>(smem_raw);  // [Np][32][4]
   real* sF = sq + 4 * Np * kB;                   // [4 faces][2][Nt][32]
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -896,27 +876,23 @@ __global__ void k_pack(const DevMesh<real> M, const real* __restrict__ canon, re
   constexpr int Npw = npw_of(N), Npt = npt_of(N);
   const int64_t nw = int64_t(M.Kw) * Npw, nt = int64_t(M.Kt) * Npt;
   for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < nw + nt; idx += int64_t(gridDim.x) * blockDim.x) {
-    int64_t c;
-    int64_t pbase;
-    int64_t stride;
+    int64_t c, pbase;
     if (idx < nw) {
       const int e = int(idx / Npw), n = int(idx % Npw);
       c = M.w_canon[e] + n;
-      pbase = widx<N>(e >> 5, 0, n, e & 31);
-      stride = int64_t(Npw) * kB;
+      pbase = widx<N>(e >> 5, n, e & 31);
     } else {
       const int64_t t = idx - nw;
       const int e = int(t / Npt), n = int(t % Npt);
       c = M.t_canon[e] + n;
-      pbase = tidx<N>(M.tet_off, e >> 5, 0, n, e & 31);
-      stride = int64_t(Npt) * kB;
+      pbase = tidx<N>(M.tet_off, e >> 5, n, e & 31);
     }
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       if (unpack)
-        const_cast<real*>(canon)[f * M.total_nodes + c] = packed[pbase + f * stride];
+        const_cast<real*>(canon)[f * M.total_nodes + c] = packed[pbase + f];
       else
-        packed[pbase + f * stride] = canon[f * M.total_nodes + c];
+        packed[pbase + f] = canon[f * M.total_nodes + c];
     }
   }
 }
@@ -960,9 +936,9 @@ __global__ void __launch_bounds__(128) k_energy(const DevMesh<real> M, const rea
               for (int l = 0; l < Nt; ++l) {
                 const double mt = Ja[0] * double(O.w.Ma[0][i * Nt + l]) + Ja[1] * double(O.w.Ma[1][i * Nt + l]) +
                                   Ja[2] * double(O.w.Ma[2][i * Nt + l]);
-                s += mt * double(q[widx<N>(gw, f, jp * Nt + l, lane)]);
+                s += mt * double(q[widx<N>(gw, jp * Nt + l, lane) + f]);
               }
-              d += double(q[widx<N>(gw, f, jj * Nt + i, lane)]) * s;
+              d += double(q[widx<N>(gw, jj * Nt + i, lane) + f]) * s;
             }
             ef += m1 * d;
           }
@@ -995,8 +971,8 @@ __global__ void __launch_bounds__(128) k_energy(const DevMesh<real> M, const rea
         for (int i = 0; i < Npt; ++i) {
           double s = 0.0;
 #pragma unroll 1
-          for (int l = 0; l < Npt; ++l) s += double(M.tet_mass[i * Npt + l]) * double(q[tidx<N>(M.tet_off, gt, f, l, lane)]);
-          ef += s * double(q[tidx<N>(M.tet_off, gt, f, i, lane)]);
+          for (int l = 0; l < Npt; ++l) s += double(M.tet_mass[i * Npt + l]) * double(q[tidx<N>(M.tet_off, gt, l, lane) + f]);
+          ef += s * double(q[tidx<N>(M.tet_off, gt, i, lane) + f]);
         }
         E += wgt[f] * J * ef;
       }
