@@ -194,33 +194,23 @@ enum WGeo : int {
 };
 
 // Residual slab staged in shared memory by the bulk copy (N <= 3) or read
-// from global memory at the update (N = 4, whose slabs are twice as large).
+// from global memory in per-field batches (N = 4, to keep two CTAs per SM).
 template <int N>
 __host__ __device__ constexpr bool stage_res() {
   return N <= 3;
 }
 
-// Shared memory of the persistent wedge stage.  The state slab (and, for
-// N <= 3, the residual slab) and the geometry table are double buffered: the
-// bulk copy of block b + gridDim.x and its geometry are produced while block
-// b is computed.
-template <int N, int NS>
-struct WedgeSmemT {
-  static constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
-  static constexpr int stages = NS;
-  static constexpr int slab = 4 * Np * kB;                          // reals per slab
-  static constexpr int q = 0;                                       // NS x [Np][32][4]
-  static constexpr int r = q + NS * slab;                           // NS x [Np][32][4] (if staged)
-  static constexpr int G = r + (stage_res<N>() ? NS * slab : 0);    // NS x [G_COUNT][32]
-  static constexpr int L = G + NS * G_COUNT * kB;                   // [Nt(Nt+1)/2][32]
-  static constexpr int F = L + (Nt * (Nt + 1) / 2) * kB;            // [4][Nt][32]
-  static constexpr int Fq = F + 4 * Nt * kB;                        // [3][2][Nq][Nq][32]
-  static constexpr int reals = Fq + 6 * Nq * Nq * kB;
-  static constexpr int bytes = 32 + reals * int(sizeof(real));
-};
-// two stages when they fit in one CTA's shared memory (227 KB), else one
 template <int N>
-using WedgeSmem = WedgeSmemT<N, (WedgeSmemT<N, 2>::bytes <= 227 * 1024) ? 2 : 1>;
+struct WedgeSmem {
+  static constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
+  static constexpr int q = 0;                                        // [4][Np][32]
+  static constexpr int r = q + 4 * Np * kB;                          // [4][Np][32] (if staged)
+  static constexpr int L = r + (stage_res<N>() ? 4 * Np * kB : 0);   // [Nt(Nt+1)/2][32]
+  static constexpr int F = L + (Nt * (Nt + 1) / 2) * kB;             // [4][Nt][32]
+  static constexpr int Fq = F + 4 * Nt * kB;                         // [3][2][Nq][Nq][32]
+  static constexpr int G = Fq + 6 * Nq * Nq * kB;                    // [G_COUNT][32]
+  static constexpr int reals = G + G_COUNT * kB;
+};
 
 template <int N>
 __host__ __device__ constexpr int wedge_smem_reals() {
@@ -229,7 +219,7 @@ __host__ __device__ constexpr int wedge_smem_reals() {
 // bytes: two mbarriers + a status word ahead of the reals (16-byte aligned)
 template <int N>
 __host__ __device__ constexpr int wedge_smem_bytes() {
-  return WedgeSmem<N>::bytes;
+  return 32 + wedge_smem_reals<N>() * int(sizeof(real));
 }
 
 // Lemma 3.1 for the wedge of lane e: everything the stage needs, from the six
@@ -300,85 +290,96 @@ __device__ __forceinline__ void wedge_geometry(const DevMesh<real>& M, int e, re
   put(G_Z, M.w_mat[2 * Kp + e]);
 }
 
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 template <int N>
-__global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 1 : 2) : 1)
+__global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 2 : 3) : 1)
     k_wedge_stage(const StageArgs<real> A, bool rk) {
   constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
   using SM = WedgeSmem<N>;
   const AllOps<N, real>& O = OPS<N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // one mbarrier per buffer stage
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // [0] state slab, [1] residual slab
   int* status = reinterpret_cast<int*>(smem_raw + 16);
   real* base = reinterpret_cast<real*>(smem_raw + 32);
+  real* sq = base + SM::q;
+  real* sr = base + SM::r;
   real* sL = base + SM::L;
   real* sF = base + SM::F;
   real* sFq = base + SM::Fq;
+  real* sG = base + SM::G;
   const DevMesh<real>& M = A.m;
   const real* __restrict__ qin = A.q_in;
   real* __restrict__ qout = A.q_out;
   real* __restrict__ resg = A.res;
   const int lane = threadIdx.x & 31;
   const int j = threadIdx.x >> 5;
+  const int blk = blockIdx.x;
+  const int e = blk * kB + lane;
   const int Kp = M.Kw_pad;
-  const int nblk = M.nblk_w;
   constexpr uint32_t slab_bytes = uint32_t(4 * Np * kB * sizeof(real));
   const bool res_async = rk && stage_res<N>();
-  // bulk copies of block b's state (and residual) slabs into buffer stage st
-  auto issue = [&](int b, int st) {
-    mbar_expect_tx(&bar[st], res_async ? 2 * slab_bytes : slab_bytes);
-    bulk_g2s(base + SM::q + st * SM::slab, qin + int64_t(b) * SM::slab, slab_bytes, &bar[st]);
-    if (res_async) bulk_g2s(base + SM::r + st * SM::slab, resg + int64_t(b) * SM::slab, slab_bytes, &bar[st]);
-  };
+#define GEO(item) sG[(item) * kB + lane]
 
-  int blk = blockIdx.x;
-  if (blk >= nblk) return;
+  // 0. bulk copies of the block's state (and residual) slabs; geometry meanwhile
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
-    issue(blk, 0);
+    mbar_expect_tx(&bar[0], slab_bytes);
+    bulk_g2s(sq, qin + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[0]);
+    if (res_async) {
+      mbar_expect_tx(&bar[1], slab_bytes);
+      bulk_g2s(sr, resg + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[1]);
+    }
   }
-  if (j == 0) wedge_geometry(M, blk * kB + lane, base + SM::G, lane);
+  // Everything latency-bound is started while the slabs are in flight: the
+  // out-of-block quad-face neighbour traces of slice j (into registers), the
+  // geometric factors (warp 0) and the Cholesky factor of M^{tri,k} (warp 1).
   int qnbr[3], qcode[3];
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
-    qnbr[ed] = M.w_nbr[(2 + ed) * Kp + blk * kB + lane];
-    qcode[ed] = M.w_code[(2 + ed) * Kp + blk * kB + lane];
+    qnbr[ed] = M.w_nbr[(2 + ed) * Kp + e];
+    qcode[ed] = M.w_code[(2 + ed) * Kp + e];
   }
-
-  constexpr int NS = SM::stages;
-  for (int it = 0; blk < nblk; ++it, blk += gridDim.x) {
-    const int st = (NS == 2) ? (it & 1) : 0;
-    const uint32_t phase = (NS == 2) ? (uint32_t(it >> 1) & 1u) : (uint32_t(it) & 1u);
-    const int e = blk * kB + lane;
-    const int nb = blk + int(gridDim.x);
-    real* sq = base + SM::q + st * SM::slab;
-    real* sr = base + SM::r + st * SM::slab;
-    real* sG = base + SM::G + st * G_COUNT * kB;
-    // 0. prefetch the next block into the other stage (released at the end of
-    //    the previous iteration) and wait for this block's slabs
-    if (threadIdx.x == 0) {
-      if (NS == 2 && nb < nblk) issue(nb, st ^ 1);
-      *status = mbar_wait_bounded(&bar[st], phase) ? 1 : 0;
+  Q4 qn[3][Nq];
+#pragma unroll
+  for (int ed = 0; ed < 3; ++ed) {
+    const int nbr = qnbr[ed];
+    if (nbr >= 0 && (nbr >> 5) != blk) {
+      const int ep = qcode[ed] >> 1, rev = qcode[ed] & 1;
+#pragma unroll
+      for (int m = 0; m < Nq; ++m)
+        qn[ed][m] = ldg4(qin, widx<N>(nbr >> 5, j * Nt + O.tab.edge[ep][rev ? N - m : m], nbr & 31));
     }
-    __syncthreads();
-    if (*status == 0) {
-      // a slab never arrived: report, let the copies in flight drain, leave
-      if (threadIdx.x == 0) {
-        atomicOr(M.err, kErrTimeout);
-        mbar_wait_bounded(&bar[st], phase);
-        if (NS == 2 && nb < nblk) mbar_wait_bounded(&bar[st ^ 1], uint32_t((it + 1) >> 1) & 1u);
+  }
+  if (j == 0) wedge_geometry(M, e, sG, lane);
+  if (j == 1) {
+    // M^{tri,k} = sum_a J_a M_a with J_a = A h_a / 2 (Lemma 3.1); L L^T factor
+    // row by row, inverse diagonal stored in place of the diagonal.
+    const int v0 = M.w_vid[0 * Kp + e], v1 = M.w_vid[1 * Kp + e], v2 = M.w_vid[2 * Kp + e];
+    const int v3 = M.w_vid[3 * Kp + e], v4 = M.w_vid[4 * Kp + e], v5 = M.w_vid[5 * Kp + e];
+    const real x0 = M.vx[v0], y0 = M.vy[v0];
+    const real Ah = real(0.125) * ((M.vx[v1] - x0) * (M.vy[v2] - y0) - (M.vx[v2] - x0) * (M.vy[v1] - y0));
+    const real J0 = Ah * (M.vz[v3] - M.vz[v0]), J1 = Ah * (M.vz[v4] - M.vz[v1]), J2 = Ah * (M.vz[v5] - M.vz[v2]);
+#pragma unroll
+    for (int i = 0; i < Nt; ++i) {
+      real row[Nt];
+#pragma unroll
+      for (int l = 0; l < i; ++l) {
+        real s = J0 * O.w.Ma[0][i * Nt + l] + J1 * O.w.Ma[1][i * Nt + l] + J2 * O.w.Ma[2][i * Nt + l];
+#pragma unroll
+        for (int k = 0; k < l; ++k) s -= row[k] * sL[(l * (l + 1) / 2 + k) * kB + lane];
+        row[l] = s * sL[(l * (l + 1) / 2 + l) * kB + lane];
       }
-      return;
+      real d = J0 * O.w.Ma[0][i * Nt + i] + J1 * O.w.Ma[1][i * Nt + i] + J2 * O.w.Ma[2][i * Nt + i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) d -= row[k] * row[k];
+#pragma unroll
+      for (int l = 0; l < i; ++l) sL[(i * (i + 1) / 2 + l) * kB + lane] = row[l];
+      sL[(i * (i + 1) / 2 + i) * kB + lane] = rsqrt_r(d);
     }
-#define GEO(item) sG[(item) * kB + lane]
-
-  // 1. prologue: quadrilateral-face fluxes of slice j (every warp), triangle-face
-  //    fluxes (warps 0 and N), Cholesky factor of M^{tri,k} (warp 1, or 0 if N = 1)
+  }
+  // 1. prologue: quadrilateral-face fluxes of slice j (every warp) and
+  //    triangle-face fluxes (warps 0 and N)
   {
     const real zM = GEO(G_Z);
 #pragma unroll
@@ -406,10 +407,8 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
         const bool inblk = (nbr >> 5) == blk;
         Q4 nv[Nq];
 #pragma unroll
-        for (int m = 0; m < Nq; ++m) {
-          const int nn = j * Nt + O.tab.edge[ep][rev ? N - m : m];
-          nv[m] = inblk ? lds4(sq, nn, nbr & 31) : ldg4(qin, widx<N>(nbr >> 5, nn, nbr & 31));
-        }
+        for (int m = 0; m < Nq; ++m)
+          nv[m] = inblk ? lds4(sq, j * Nt + O.tab.edge[ep][rev ? N - m : m], nbr & 31) : qn[ed][m];
 #pragma unroll
         for (int m = 0; m < Nq; ++m) {
           const Q4 o = lds4(sq, j * Nt + edge_node(N, ed, m), lane);
@@ -463,28 +462,6 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
         sF[((2 * fb + 0) * Nt + k) * kB + lane] = Fp;
         sF[((2 * fb + 1) * Nt + k) * kB + lane] = Fu;
       }
-    }
-  }
-  if (j == (N >= 2 ? 1 : 0)) {
-    // M^{tri,k} = sum_a J_a M_a; L L^T factor row by row, inverse diagonal
-    // stored in place of the diagonal.
-    const real J0 = GEO(G_J0), J1 = GEO(G_J1), J2 = GEO(G_J2);
-#pragma unroll
-    for (int i = 0; i < Nt; ++i) {
-      real row[Nt];
-#pragma unroll
-      for (int l = 0; l < i; ++l) {
-        real s = J0 * O.w.Ma[0][i * Nt + l] + J1 * O.w.Ma[1][i * Nt + l] + J2 * O.w.Ma[2][i * Nt + l];
-#pragma unroll
-        for (int k = 0; k < l; ++k) s -= row[k] * sL[(l * (l + 1) / 2 + k) * kB + lane];
-        row[l] = s * sL[(l * (l + 1) / 2 + l) * kB + lane];
-      }
-      real d = J0 * O.w.Ma[0][i * Nt + i] + J1 * O.w.Ma[1][i * Nt + i] + J2 * O.w.Ma[2][i * Nt + i];
-#pragma unroll
-      for (int k = 0; k < i; ++k) d -= row[k] * row[k];
-#pragma unroll
-      for (int l = 0; l < i; ++l) sL[(i * (i + 1) / 2 + l) * kB + lane] = row[l];
-      sL[(i * (i + 1) / 2 + i) * kB + lane] = rsqrt_r(d);
     }
   }
   __syncthreads();
@@ -634,6 +611,11 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
     }
   }
   // (f) fused low-storage Runge-Kutta update (or plain right-hand side)
+  if (res_async && !mbar_wait_bounded(&bar[1], 0)) {
+    if (lane == 0) atomicOr(M.err, kErrTimeout);
+    mbar_wait_bounded(&bar[1], 0);
+    return;
+  }
   if (e < M.Kw) {
     const real kappa = GEO(G_KAPPA), irho = GEO(G_IRHO);
 #pragma unroll
@@ -653,23 +635,6 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
       }
     }
   }
-  // 3. geometry and quad-face neighbours of the next block; release this stage
-  if (nb < nblk) {
-    if (NS == 2 && j == 0) wedge_geometry(M, nb * kB + lane, base + SM::G + (st ^ 1) * G_COUNT * kB, lane);
-#pragma unroll
-    for (int ed = 0; ed < 3; ++ed) {
-      qnbr[ed] = M.w_nbr[(2 + ed) * Kp + nb * kB + lane];
-      qcode[ed] = M.w_code[(2 + ed) * Kp + nb * kB + lane];
-    }
-  }
-  fence_proxy_async_smem();
-  __syncthreads();
-  if (NS == 1 && nb < nblk) {
-    // single stage: the next block's copies and geometry start once it is free
-    if (threadIdx.x == 0) issue(nb, 0);
-    if (j == 0) wedge_geometry(M, nb * kB + lane, base + SM::G, lane);
-  }
-  }  // block loop
 #undef GEO
 }
 
@@ -1041,10 +1006,7 @@ __global__ void k_energy_final(const double* __restrict__ partials, int n, doubl
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-// one-time per device: opt in to the dynamic shared memory the stages use and
-// size the persistent wedge grid (resident CTAs per SM x SMs)
-static int g_wedge_grid[64];
-
+// one-time per device: opt in to the dynamic shared memory the stages use
 template <int N>
 int prepare_n() {
   cudaError_t err = cudaFuncSetAttribute(k_wedge_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1052,23 +1014,13 @@ int prepare_n() {
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_tet_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                tet_smem_reals<N>() * int(sizeof(real)));
-  int dev = 0, sms = 0, per_sm = 0;
-  if (err == cudaSuccess) err = cudaGetDevice(&dev);
-  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (err == cudaSuccess)
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wedge_stage<N>, 32 * (N + 1), wedge_smem_bytes<N>());
-  if (err == cudaSuccess) g_wedge_grid[dev & 63] = (per_sm > 0 ? per_sm : 1) * sms;
   return int(err);
 }
 
 template <int N>
 int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s) {
   if (a.m.nblk_w > 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int grid = g_wedge_grid[dev & 63];
-    if (grid <= 0 || grid > a.m.nblk_w) grid = a.m.nblk_w;
-    k_wedge_stage<N><<<grid, 32 * (N + 1), wedge_smem_bytes<N>(), s>>>(a, rk);
+    k_wedge_stage<N><<<a.m.nblk_w, 32 * (N + 1), wedge_smem_bytes<N>(), s>>>(a, rk);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return int(err);
   }
