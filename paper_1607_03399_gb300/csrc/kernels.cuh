@@ -378,6 +378,18 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
       sL[(i * (i + 1) / 2 + i) * kB + lane] = rsqrt_r(d);
     }
   }
+  if (threadIdx.x == 0) *status = mbar_wait_bounded(&bar[0], 0) ? 1 : 0;
+  __syncthreads();
+  if (*status == 0) {
+    // the state slab never arrived: report, let any residual copy drain, leave
+    if (threadIdx.x == 0) {
+      atomicOr(M.err, kErrTimeout);
+      if (res_async) mbar_wait_bounded(&bar[1], 0);
+      mbar_wait_bounded(&bar[0], 0);
+    }
+    return;
+  }
+
   // 1. prologue: quadrilateral-face fluxes of slice j (every warp) and
   //    triangle-face fluxes (warps 0 and N)
   {
