@@ -190,7 +190,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase)
 enum WGeo : int {
   G_RX, G_RY, G_SX, G_SY, G_A, G_J0, G_J1, G_J2, G_NB0, G_NB1, G_NB2, G_NT0, G_NT1, G_NT2, G_JFB, G_JFT,
   G_QNX0, G_QNX1, G_QNX2, G_QNY0, G_QNY1, G_QNY2, G_QCA0, G_QCA1, G_QCA2, G_QCB0, G_QCB1, G_QCB2,
-  G_KAPPA, G_IRHO, G_Z, G_TX0, G_TX1, G_TY0, G_TY1, G_COUNT
+  G_TX0, G_TX1, G_TY0, G_TY1, G_COUNT
 };
 
 // Residual slab staged in shared memory by the bulk copy (N <= 3) or read
@@ -207,8 +207,7 @@ struct WedgeSmem {
   static constexpr int r = q + 4 * Np * kB;                          // [4][Np][32] (if staged)
   static constexpr int L = r + (stage_res<N>() ? 4 * Np * kB : 0);   // [Nt(Nt+1)/2][32]
   static constexpr int F = L + (Nt * (Nt + 1) / 2) * kB;             // [4][Nt][32]
-  static constexpr int Fq = F + 4 * Nt * kB;                         // [3][2][Nq][Nq][32]
-  static constexpr int G = Fq + 6 * Nq * Nq * kB;                    // [G_COUNT][32]
+  static constexpr int G = F + 4 * Nt * kB;                          // [G_COUNT][32]
   static constexpr int reals = G + G_COUNT * kB;
 };
 
@@ -285,13 +284,10 @@ __device__ __forceinline__ void wedge_geometry(const DevMesh<real>& M, int e, re
     put(G_QCA0 + ed, real(0.25) * Le * hh[ia]);  // M~_e = ca Mea + cb Meb
     put(G_QCB0 + ed, real(0.25) * Le * hh[ib]);
   }
-  put(G_KAPPA, M.w_mat[0 * Kp + e]);
-  put(G_IRHO, M.w_mat[1 * Kp + e]);
-  put(G_Z, M.w_mat[2 * Kp + e]);
 }
 
 template <int N>
-__global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 2 : 3) : 1)
+__global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 2 : 4) : 1)
     k_wedge_stage(const StageArgs<real> A, bool rk) {
   constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
   using SM = WedgeSmem<N>;
@@ -304,7 +300,6 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
   real* sr = base + SM::r;
   real* sL = base + SM::L;
   real* sF = base + SM::F;
-  real* sFq = base + SM::Fq;
   real* sG = base + SM::G;
   const DevMesh<real>& M = A.m;
   const real* __restrict__ qin = A.q_in;
@@ -331,52 +326,12 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
       bulk_g2s(sr, resg + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[1]);
     }
   }
-  // Everything latency-bound is started while the slabs are in flight: the
-  // out-of-block quad-face neighbour traces of slice j (into registers), the
-  // geometric factors (warp 0) and the Cholesky factor of M^{tri,k} (warp 1).
+  if (j == 0) wedge_geometry(M, e, sG, lane);
   int qnbr[3], qcode[3];
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
     qnbr[ed] = M.w_nbr[(2 + ed) * Kp + e];
     qcode[ed] = M.w_code[(2 + ed) * Kp + e];
-  }
-  Q4 qn[3][Nq];
-#pragma unroll
-  for (int ed = 0; ed < 3; ++ed) {
-    const int nbr = qnbr[ed];
-    if (nbr >= 0 && (nbr >> 5) != blk) {
-      const int ep = qcode[ed] >> 1, rev = qcode[ed] & 1;
-#pragma unroll
-      for (int m = 0; m < Nq; ++m)
-        qn[ed][m] = ldg4(qin, widx<N>(nbr >> 5, j * Nt + O.tab.edge[ep][rev ? N - m : m], nbr & 31));
-    }
-  }
-  if (j == 0) wedge_geometry(M, e, sG, lane);
-  if (j == 1) {
-    // M^{tri,k} = sum_a J_a M_a with J_a = A h_a / 2 (Lemma 3.1); L L^T factor
-    // row by row, inverse diagonal stored in place of the diagonal.
-    const int v0 = M.w_vid[0 * Kp + e], v1 = M.w_vid[1 * Kp + e], v2 = M.w_vid[2 * Kp + e];
-    const int v3 = M.w_vid[3 * Kp + e], v4 = M.w_vid[4 * Kp + e], v5 = M.w_vid[5 * Kp + e];
-    const real x0 = M.vx[v0], y0 = M.vy[v0];
-    const real Ah = real(0.125) * ((M.vx[v1] - x0) * (M.vy[v2] - y0) - (M.vx[v2] - x0) * (M.vy[v1] - y0));
-    const real J0 = Ah * (M.vz[v3] - M.vz[v0]), J1 = Ah * (M.vz[v4] - M.vz[v1]), J2 = Ah * (M.vz[v5] - M.vz[v2]);
-#pragma unroll
-    for (int i = 0; i < Nt; ++i) {
-      real row[Nt];
-#pragma unroll
-      for (int l = 0; l < i; ++l) {
-        real s = J0 * O.w.Ma[0][i * Nt + l] + J1 * O.w.Ma[1][i * Nt + l] + J2 * O.w.Ma[2][i * Nt + l];
-#pragma unroll
-        for (int k = 0; k < l; ++k) s -= row[k] * sL[(l * (l + 1) / 2 + k) * kB + lane];
-        row[l] = s * sL[(l * (l + 1) / 2 + l) * kB + lane];
-      }
-      real d = J0 * O.w.Ma[0][i * Nt + i] + J1 * O.w.Ma[1][i * Nt + i] + J2 * O.w.Ma[2][i * Nt + i];
-#pragma unroll
-      for (int k = 0; k < i; ++k) d -= row[k] * row[k];
-#pragma unroll
-      for (int l = 0; l < i; ++l) sL[(i * (i + 1) / 2 + l) * kB + lane] = row[l];
-      sL[(i * (i + 1) / 2 + i) * kB + lane] = rsqrt_r(d);
-    }
   }
   if (threadIdx.x == 0) *status = mbar_wait_bounded(&bar[0], 0) ? 1 : 0;
   __syncthreads();
@@ -390,52 +345,68 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
     return;
   }
 
-  // 1. prologue: quadrilateral-face fluxes of slice j (every warp) and
-  //    triangle-face fluxes (warps 0 and N)
-  {
-    const real zM = GEO(G_Z);
+  // 1. prologue: quadrilateral-face fluxes of slice j applied straight into the
+  //    weak-form accumulators (every warp); triangle-face fluxes (warps 0 and N);
+  //    Cholesky factor of M^{tri,k} (warp 1, or 0 if N = 1)
+  const real zM = M.w_mat[2 * Kp + e];
+  real Wp[Nt], Wu[3][Nt];
 #pragma unroll
-    for (int ed = 0; ed < 3; ++ed) {
-      const real nx = GEO(G_QNX0 + ed), ny = GEO(G_QNY0 + ed);
-      const int nbr = qnbr[ed], code = qcode[ed];
-      real* Fo = sFq + (ed * 2 * Nq * Nq + j) * kB + lane;  // [(w*Nq + m)*Nq] stride
-      if (nbr < 0) {
-        real tau_p, tau_u;
-        taus(A.flux, zM, zM, tau_p, tau_u);
+  for (int i = 0; i < Nt; ++i) Wp[i] = Wu[0][i] = Wu[1][i] = Wu[2][i] = real(0);
 #pragma unroll
-        for (int m = 0; m < Nq; ++m) {
-          const Q4 o = lds4(sq, j * Nt + edge_node(N, ed, m), lane);
-          real dp, dun, Fp, Fu;
-          boundary_jumps(A.bc, o.p, nx * o.u + ny * o.v, dp, dun);
-          penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
-          Fo[(0 * Nq + m) * Nq * kB] = Fp;
-          Fo[(1 * Nq + m) * Nq * kB] = Fu;
-        }
-      } else {
-        const real zP = M.w_mat[2 * Kp + nbr];
-        real tau_p, tau_u;
-        taus(A.flux, zM, zP, tau_p, tau_u);
-        const int ep = code >> 1, rev = code & 1;
-        const bool inblk = (nbr >> 5) == blk;
-        Q4 nv[Nq];
+  for (int ed = 0; ed < 3; ++ed) {
+    const real nx = GEO(G_QNX0 + ed), ny = GEO(G_QNY0 + ed);
+    const int nbr = qnbr[ed], code = qcode[ed];
+    real Fp[Nq], Fu[Nq];
+    if (nbr < 0) {
+      real tau_p, tau_u;
+      taus(A.flux, zM, zM, tau_p, tau_u);
 #pragma unroll
-        for (int m = 0; m < Nq; ++m)
-          nv[m] = inblk ? lds4(sq, j * Nt + O.tab.edge[ep][rev ? N - m : m], nbr & 31) : qn[ed][m];
-#pragma unroll
-        for (int m = 0; m < Nq; ++m) {
-          const Q4 o = lds4(sq, j * Nt + edge_node(N, ed, m), lane);
-          real Fp, Fu;
-          penalty_flux(nv[m].p - o.p, nx * (nv[m].u - o.u) + ny * (nv[m].v - o.v), tau_p, tau_u, Fp, Fu);
-          Fo[(0 * Nq + m) * Nq * kB] = Fp;
-          Fo[(1 * Nq + m) * Nq * kB] = Fu;
-        }
+      for (int m = 0; m < Nq; ++m) {
+        const Q4 o = lds4(sq, j * Nt + edge_node(N, ed, m), lane);
+        real dp, dun;
+        boundary_jumps(A.bc, o.p, nx * o.u + ny * o.v, dp, dun);
+        penalty_flux(dp, dun, tau_p, tau_u, Fp[m], Fu[m]);
       }
+    } else {
+      const real zP = M.w_mat[2 * Kp + nbr];
+      real tau_p, tau_u;
+      taus(A.flux, zM, zP, tau_p, tau_u);
+      const int ep = code >> 1, rev = code & 1;
+      const bool inblk = (nbr >> 5) == blk;
+      Q4 nv[Nq];
+#pragma unroll
+      for (int m = 0; m < Nq; ++m) {
+        const int nn = j * Nt + O.tab.edge[ep][rev ? N - m : m];
+        nv[m] = inblk ? lds4(sq, nn, nbr & 31) : ldg4(qin, widx<N>(nbr >> 5, nn, nbr & 31));
+      }
+#pragma unroll
+      for (int m = 0; m < Nq; ++m) {
+        const Q4 o = lds4(sq, j * Nt + edge_node(N, ed, m), lane);
+        penalty_flux(nv[m].p - o.p, nx * (nv[m].u - o.u) + ny * (nv[m].v - o.v), tau_p, tau_u, Fp[m], Fu[m]);
+      }
+    }
+    // W += M~_e F, M~_e = (L_e/4)(h_a Mea + h_b Meb) along the edge, identity in t
+    const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
+#pragma unroll
+    for (int m = 0; m < Nq; ++m) {
+      real gpa = 0, gpb = 0, gua = 0, gub = 0;
+#pragma unroll
+      for (int n = 0; n < Nq; ++n) {
+        gpa += O.w.Mea[m * Nq + n] * Fp[n];
+        gpb += O.w.Meb[m * Nq + n] * Fp[n];
+        gua += O.w.Mea[m * Nq + n] * Fu[n];
+        gub += O.w.Meb[m * Nq + n] * Fu[n];
+      }
+      const real gp = ca * gpa + cbq * gpb, gu = ca * gua + cbq * gub;
+      const int i = edge_node(N, ed, m);
+      Wp[i] += gp;
+      Wu[0][i] += nx * gu;
+      Wu[1][i] += ny * gu;
     }
   }
   if (j == 0 || j == N) {
     const int fb = (j == 0) ? 0 : 1;
     const real nn0 = fb ? GEO(G_NT0) : GEO(G_NB0), nn1 = fb ? GEO(G_NT1) : GEO(G_NB1), nn2 = fb ? GEO(G_NT2) : GEO(G_NB2);
-    const real zM = GEO(G_Z);
     const int nbr = M.w_nbr[fb * Kp + e];
     const int code = M.w_code[fb * Kp + e];
     const int own0 = fb ? N * Nt : 0;
@@ -476,10 +447,31 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
       }
     }
   }
+  if (j == (N >= 2 ? 1 : 0)) {
+    // M^{tri,k} = sum_a J_a M_a; L L^T factor row by row, inverse diagonal
+    // stored in place of the diagonal.
+    const real J0 = GEO(G_J0), J1 = GEO(G_J1), J2 = GEO(G_J2);
+#pragma unroll
+    for (int i = 0; i < Nt; ++i) {
+      real row[Nt];
+#pragma unroll
+      for (int l = 0; l < i; ++l) {
+        real s = J0 * O.w.Ma[0][i * Nt + l] + J1 * O.w.Ma[1][i * Nt + l] + J2 * O.w.Ma[2][i * Nt + l];
+#pragma unroll
+        for (int k = 0; k < l; ++k) s -= row[k] * sL[(l * (l + 1) / 2 + k) * kB + lane];
+        row[l] = s * sL[(l * (l + 1) / 2 + l) * kB + lane];
+      }
+      real d = J0 * O.w.Ma[0][i * Nt + i] + J1 * O.w.Ma[1][i * Nt + i] + J2 * O.w.Ma[2][i * Nt + i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) d -= row[k] * row[k];
+#pragma unroll
+      for (int l = 0; l < i; ++l) sL[(i * (i + 1) / 2 + l) * kB + lane] = row[l];
+      sL[(i * (i + 1) / 2 + i) * kB + lane] = rsqrt_r(d);
+    }
+  }
   __syncthreads();
 
   // 2. slice j of every element of the block
-  real Wp[Nt], Wu[3][Nt];
   {
     real dtr[Nq];
 #pragma unroll
@@ -513,7 +505,7 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
         real acc = 0;
 #pragma unroll
         for (int l = 0; l < Nt; ++l) acc += O.w.M[i * Nt + l] * G[l];
-        Wp[i] = acc;
+        Wp[i] += acc;
       }
     }
     // (b) velocity: G_c = -t_cJ D_t p + n_c lifts; W = M^tri G
@@ -530,37 +522,8 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
         real acc = 0;
 #pragma unroll
         for (int l = 0; l < Nt; ++l) acc += O.w.M[i * Nt + l] * G[l];
-        Wu[c][i] = acc;
+        Wu[c][i] += acc;
       }
-    }
-  }
-  // (c) quadrilateral faces at slice j: W += M~_e F, M~_e = (L_e/4)(h_a Mea + h_b Meb)
-#pragma unroll
-  for (int ed = 0; ed < 3; ++ed) {
-    const real nx = GEO(G_QNX0 + ed), ny = GEO(G_QNY0 + ed);
-    const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
-    const real* Fo = sFq + (ed * 2 * Nq * Nq + j) * kB + lane;
-    real Fp[Nq], Fu[Nq];
-#pragma unroll
-    for (int n = 0; n < Nq; ++n) {
-      Fp[n] = Fo[(0 * Nq + n) * Nq * kB];
-      Fu[n] = Fo[(1 * Nq + n) * Nq * kB];
-    }
-#pragma unroll
-    for (int m = 0; m < Nq; ++m) {
-      real gpa = 0, gpb = 0, gua = 0, gub = 0;
-#pragma unroll
-      for (int n = 0; n < Nq; ++n) {
-        gpa += O.w.Mea[m * Nq + n] * Fp[n];
-        gpb += O.w.Meb[m * Nq + n] * Fp[n];
-        gua += O.w.Mea[m * Nq + n] * Fu[n];
-        gub += O.w.Meb[m * Nq + n] * Fu[n];
-      }
-      const real gp = ca * gpa + cbq * gpb, gu = ca * gua + cbq * gub;
-      const int i = edge_node(N, ed, m);
-      Wp[i] += gp;
-      Wu[0][i] += nx * gu;
-      Wu[1][i] += ny * gu;
     }
   }
   // (d) X = (M^{tri,k})^{-1} W: forward and backward substitution, 4 right-hand sides
@@ -629,7 +592,7 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
     return;
   }
   if (e < M.Kw) {
-    const real kappa = GEO(G_KAPPA), irho = GEO(G_IRHO);
+    const real kappa = M.w_mat[0 * Kp + e], irho = M.w_mat[1 * Kp + e];
 #pragma unroll
     for (int i = 0; i < Nt; ++i) {
       const int n = j * Nt + i;
