@@ -327,6 +327,33 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
     }
   }
   if (j == 0) wedge_geometry(M, e, sG, lane);
+  if (j == 1) {
+    // While the slabs are in flight: M^{tri,k} = sum_a J_a M_a with
+    // J_a = A h_a / 2 (Lemma 3.1) from the vertices; L L^T factor row by row,
+    // inverse diagonal stored in place of the diagonal.
+    const int v0 = M.w_vid[0 * Kp + e], v1 = M.w_vid[1 * Kp + e], v2 = M.w_vid[2 * Kp + e];
+    const int v3 = M.w_vid[3 * Kp + e], v4 = M.w_vid[4 * Kp + e], v5 = M.w_vid[5 * Kp + e];
+    const real x0 = M.vx[v0], y0 = M.vy[v0];
+    const real Ah = real(0.125) * ((M.vx[v1] - x0) * (M.vy[v2] - y0) - (M.vx[v2] - x0) * (M.vy[v1] - y0));
+    const real J0 = Ah * (M.vz[v3] - M.vz[v0]), J1 = Ah * (M.vz[v4] - M.vz[v1]), J2 = Ah * (M.vz[v5] - M.vz[v2]);
+#pragma unroll
+    for (int i = 0; i < Nt; ++i) {
+      real row[Nt];
+#pragma unroll
+      for (int l = 0; l < i; ++l) {
+        real s = J0 * O.w.Ma[0][i * Nt + l] + J1 * O.w.Ma[1][i * Nt + l] + J2 * O.w.Ma[2][i * Nt + l];
+#pragma unroll
+        for (int k = 0; k < l; ++k) s -= row[k] * sL[(l * (l + 1) / 2 + k) * kB + lane];
+        row[l] = s * sL[(l * (l + 1) / 2 + l) * kB + lane];
+      }
+      real d = J0 * O.w.Ma[0][i * Nt + i] + J1 * O.w.Ma[1][i * Nt + i] + J2 * O.w.Ma[2][i * Nt + i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) d -= row[k] * row[k];
+#pragma unroll
+      for (int l = 0; l < i; ++l) sL[(i * (i + 1) / 2 + l) * kB + lane] = row[l];
+      sL[(i * (i + 1) / 2 + i) * kB + lane] = rsqrt_r(d);
+    }
+  }
   int qnbr[3], qcode[3];
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
@@ -346,8 +373,7 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
   }
 
   // 1. prologue: quadrilateral-face fluxes of slice j applied straight into the
-  //    weak-form accumulators (every warp); triangle-face fluxes (warps 0 and N);
-  //    Cholesky factor of M^{tri,k} (warp 1, or 0 if N = 1)
+  //    weak-form accumulators (every warp); triangle-face fluxes (warps 0 and N)
   const real zM = M.w_mat[2 * Kp + e];
   real Wp[Nt], Wu[3][Nt];
 #pragma unroll
@@ -445,28 +471,6 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
         sF[((2 * fb + 0) * Nt + k) * kB + lane] = Fp;
         sF[((2 * fb + 1) * Nt + k) * kB + lane] = Fu;
       }
-    }
-  }
-  if (j == (N >= 2 ? 1 : 0)) {
-    // M^{tri,k} = sum_a J_a M_a; L L^T factor row by row, inverse diagonal
-    // stored in place of the diagonal.
-    const real J0 = GEO(G_J0), J1 = GEO(G_J1), J2 = GEO(G_J2);
-#pragma unroll
-    for (int i = 0; i < Nt; ++i) {
-      real row[Nt];
-#pragma unroll
-      for (int l = 0; l < i; ++l) {
-        real s = J0 * O.w.Ma[0][i * Nt + l] + J1 * O.w.Ma[1][i * Nt + l] + J2 * O.w.Ma[2][i * Nt + l];
-#pragma unroll
-        for (int k = 0; k < l; ++k) s -= row[k] * sL[(l * (l + 1) / 2 + k) * kB + lane];
-        row[l] = s * sL[(l * (l + 1) / 2 + l) * kB + lane];
-      }
-      real d = J0 * O.w.Ma[0][i * Nt + i] + J1 * O.w.Ma[1][i * Nt + i] + J2 * O.w.Ma[2][i * Nt + i];
-#pragma unroll
-      for (int k = 0; k < i; ++k) d -= row[k] * row[k];
-#pragma unroll
-      for (int l = 0; l < i; ++l) sL[(i * (i + 1) / 2 + l) * kB + lane] = row[l];
-      sL[(i * (i + 1) / 2 + i) * kB + lane] = rsqrt_r(d);
     }
   }
   __syncthreads();
