@@ -430,48 +430,40 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
       Wu[1][i] += ny * gu;
     }
   }
-  if (j == 0 || j == N) {
-    const int fb = (j == 0) ? 0 : 1;
-    const real nn0 = fb ? GEO(G_NT0) : GEO(G_NB0), nn1 = fb ? GEO(G_NT1) : GEO(G_NB1), nn2 = fb ? GEO(G_NT2) : GEO(G_NB2);
+  // triangle-face node fluxes (bottom then top), spread round-robin over the warps
+#pragma unroll 1
+  for (int idx = j; idx < 2 * Nt; idx += Nq) {
+    const int fb = idx >= Nt ? 1 : 0;
+    const int k = idx - fb * Nt;
+    const real nn0 = GEO(fb ? G_NT0 : G_NB0), nn1 = GEO(fb ? G_NT1 : G_NB1), nn2 = GEO(fb ? G_NT2 : G_NB2);
     const int nbr = M.w_nbr[fb * Kp + e];
     const int code = M.w_code[fb * Kp + e];
-    const int own0 = fb ? N * Nt : 0;
-    real tau_p, tau_u;
+    const Q4 o = lds4(sq, (fb ? N * Nt : 0) + k, lane);
+    const real unM = nn0 * o.u + nn1 * o.v + nn2 * o.w;
+    real tau_p, tau_u, dp, dun;
     if (nbr < 0) {
       taus(A.flux, zM, zM, tau_p, tau_u);
-#pragma unroll
-      for (int k = 0; k < Nt; ++k) {
-        const Q4 o = lds4(sq, own0 + k, lane);
-        real dp, dun, Fp, Fu;
-        boundary_jumps(A.bc, o.p, nn0 * o.u + nn1 * o.v + nn2 * o.w, dp, dun);
-        penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
-        sF[((2 * fb + 0) * Nt + k) * kB + lane] = Fp;
-        sF[((2 * fb + 1) * Nt + k) * kB + lane] = Fu;
-      }
+      boundary_jumps(A.bc, o.p, unM, dp, dun);
     } else {
       const bool ntet = (code & kCodeTet) != 0;
       const int nf = (code >> 4) & 3;
-      const int perm = code & 15;
+      const int nk = O.tab.tri_perm[code & 15][k];
       const real zP = ntet ? M.t_mat[2 * M.Kt_pad + nbr] : M.w_mat[2 * Kp + nbr];
       taus(A.flux, zM, zP, tau_p, tau_u);
-      const bool inblk = !ntet && ((nbr >> 5) == blk);
-#pragma unroll
-      for (int k = 0; k < Nt; ++k) {
-        const int nk = O.tab.tri_perm[perm][k];
-        Q4 nv;
-        if (ntet) {
-          nv = ldg4(qin, tidx<N>(M.tet_off, nbr >> 5, O.tab.tet_face[nf][nk], nbr & 31));
-        } else {
-          const int node = (nf ? N * Nt : 0) + nk;
-          nv = inblk ? lds4(sq, node, nbr & 31) : ldg4(qin, widx<N>(nbr >> 5, node, nbr & 31));
-        }
-        const Q4 o = lds4(sq, own0 + k, lane);
-        real Fp, Fu;
-        penalty_flux(nv.p - o.p, nn0 * (nv.u - o.u) + nn1 * (nv.v - o.v) + nn2 * (nv.w - o.w), tau_p, tau_u, Fp, Fu);
-        sF[((2 * fb + 0) * Nt + k) * kB + lane] = Fp;
-        sF[((2 * fb + 1) * Nt + k) * kB + lane] = Fu;
+      Q4 nv;
+      if (ntet) {
+        nv = ldg4(qin, tidx<N>(M.tet_off, nbr >> 5, O.tab.tet_face[nf][nk], nbr & 31));
+      } else {
+        const int node = (nf ? N * Nt : 0) + nk;
+        nv = ((nbr >> 5) == blk) ? lds4(sq, node, nbr & 31) : ldg4(qin, widx<N>(nbr >> 5, node, nbr & 31));
       }
+      dp = nv.p - o.p;
+      dun = nn0 * nv.u + nn1 * nv.v + nn2 * nv.w - unM;
     }
+    real Fp, Fu;
+    penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
+    sF[((2 * fb + 0) * Nt + k) * kB + lane] = Fp;
+    sF[((2 * fb + 1) * Nt + k) * kB + lane] = Fu;
   }
   __syncthreads();
 
