@@ -431,13 +431,17 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
     }
   }
   // triangle-face node fluxes (bottom then top), spread round-robin over the warps
-#pragma unroll 1
-  for (int idx = j; idx < 2 * Nt; idx += Nq) {
+  const int tnbr[2] = {M.w_nbr[0 * Kp + e], M.w_nbr[1 * Kp + e]};
+  const int tcode[2] = {M.w_code[0 * Kp + e], M.w_code[1 * Kp + e]};
+#pragma unroll
+  for (int t = 0; t < (2 * Nt + Nq - 1) / Nq; ++t) {
+    const int idx = j + t * Nq;
+    if (idx >= 2 * Nt) break;
     const int fb = idx >= Nt ? 1 : 0;
     const int k = idx - fb * Nt;
     const real nn0 = GEO(fb ? G_NT0 : G_NB0), nn1 = GEO(fb ? G_NT1 : G_NB1), nn2 = GEO(fb ? G_NT2 : G_NB2);
-    const int nbr = M.w_nbr[fb * Kp + e];
-    const int code = M.w_code[fb * Kp + e];
+    const int nbr = tnbr[fb];
+    const int code = tcode[fb];
     const Q4 o = lds4(sq, (fb ? N * Nt : 0) + k, lane);
     const real unM = nn0 * o.u + nn1 * o.v + nn2 * o.w;
     real tau_p, tau_u, dp, dun;
