@@ -170,6 +170,26 @@ int dg_step(dg_ctx* ctx, double dt, int64_t nsteps);
  * DG_ERR_TIMEOUT if a device-side wait had run out since the last check. */
 int dg_energy(dg_ctx* ctx, double* E);
 
+/* Allocation-free discrete energy of a caller-provided state (no counterpart
+ * in the paper; a service for callers that cannot allocate device memory at
+ * the point of the call -- code running while a framework forbids
+ * allocations, inside host callbacks, or with a locked memory pool).
+ *   d_q  device pointer, canonical layout [4][total_nodes] of the context's
+ *        precision (any state, not only the bound one); not modified.
+ *   E    host pointer; receives the energy (same definition as dg_energy).
+ * The per-block partial sums live in a file-scope device array of 65536
+ * doubles plus one total (512 KB, resident on every GPU that loads the
+ * library until exit), so meshes of at most 65536 * 128 = 8388608 elements
+ * are accepted; larger ones return DG_ERR_ARG.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.  The first call on a device looks up
+ * the array's device address (with that device current); make that first
+ * call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU (other streams, other contexts) race; each call fully
+ * rewrites the partials it sums.  Synchronises the bound stream.
+ * Errors: DG_ERR_ARG, DG_ERR_STATE (before dg_bind), DG_ERR_CUDA,
+ * DG_ERR_NONFINITE. */
+int dg_energy_static(dg_ctx* ctx, const void* d_q, double* E);
+
 /* Synchronise the bound stream and report pending device-side errors. */
 int dg_sync(dg_ctx* ctx);
 

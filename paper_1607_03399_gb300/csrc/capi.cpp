@@ -115,6 +115,7 @@ struct dg_ctx {
   DevMesh<float> m32;
   DevMesh<double> m64;
   size_t mesh_bytes = 0, field_bytes = 0;
+  size_t wops_off = 0;  // offset of the wedge energy operators in the mesh blob
   std::vector<unsigned char> ops_host;
   // graphs: one LSRK step starting from buffer 0 / 1 for a given dt
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -278,7 +279,7 @@ double tet_stable_ratio(const dg_ctx* c, int64_t k) {
 // ----------------------------------------------------------------- blob
 struct BlobLayout {
   size_t w_vid, w_nbr, w_code, w_mat, w_canon, t_vid, t_nbr, t_code, t_mat, t_canon, vx, vy, vz, err, partials, energy,
-      tmass, total;
+      tmass, wops, total;
 };
 
 BlobLayout blob_layout(const dg_ctx* c) {
@@ -309,6 +310,7 @@ BlobLayout blob_layout(const dg_ctx* c) {
   L.partials = take(nparts * 8);
   L.energy = take(8);
   L.tmass = take(size_t(npt_of(c->N)) * npt_of(c->N) * rs);
+  L.wops = take(size_t(3 * nt_of(c->N) * nt_of(c->N) + (c->N + 1) * (c->N + 1)) * rs);
   L.total = o;
   return L;
 }
@@ -361,6 +363,12 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
   real* vz = reinterpret_cast<real*>(blob.data() + L.vz);
   real* tm = reinterpret_cast<real*>(blob.data() + L.tmass);
   for (int i = 0; i < c->ref->Npt * c->ref->Npt; ++i) tm[i] = real(c->ref->tM.a[i]);
+  // wedge energy operators: barycentric-weighted triangle masses, then the line mass
+  real* wo = reinterpret_cast<real*>(blob.data() + L.wops);
+  const int nt2 = c->ref->Nt * c->ref->Nt;
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < nt2; ++i) wo[a * nt2 + i] = real(c->ref->Ma[a].a[i]);
+  for (int i = 0; i < c->ref->Nq * c->ref->Nq; ++i) wo[3 * nt2 + i] = real(c->ref->M1.a[i]);
   for (int64_t v = 0; v < c->nverts; ++v) {
     vx[v] = real(c->VX[v * 3 + 0]);
     vy[v] = real(c->VX[v * 3 + 1]);
@@ -821,6 +829,7 @@ int dg_bind(dg_ctx* c, void* d_mesh, void* d_q0, void* d_q1, void* d_res, void* 
     fill_devmesh<float>(c, L, c->m32);
   }
   c->mesh_bytes = L.total;
+  c->wops_off = L.wops;
   c->field_bytes = field_bytes_of(c);
   e = cudaMemcpyAsync(d_mesh, blob.data(), blob.size(), cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "mesh upload");
@@ -966,6 +975,33 @@ int dg_energy(dg_ctx* c, double* E) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "energy download");
   return check_device_error(c);
+}
+
+int dg_energy_static(dg_ctx* c, const void* d_q, double* E) {
+  if (!c) return DG_ERR_ARG;
+  if (!d_q || !E) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_energy_static before dg_bind");
+  const int64_t K = int64_t(c->wedges.size()) + int64_t(c->tets.size());
+  const int64_t nblocks = (K + 127) / 128;
+  if (nblocks > kStaticPartials)
+    return c->fail(DG_ERR_ARG, "dg_energy_static supports at most " + std::to_string(int64_t(kStaticPartials) * 128) +
+                                   " elements");
+  double* scratch = nullptr;
+  int rc = energy_static_scratch(c->device, &scratch);
+  if (rc) return cuda_fail(c, cudaError_t(rc), "static scratch address");
+  const unsigned char* blob = static_cast<const unsigned char*>(c->d_mesh);
+  if (c->prec == DG_F64)
+    rc = launch_energy_static<double>(c->N, c->m64, static_cast<const double*>(d_q),
+                                      reinterpret_cast<const double*>(blob + c->wops_off), scratch, int(nblocks), c->stream);
+  else
+    rc = launch_energy_static<float>(c->N, c->m32, static_cast<const float*>(d_q),
+                                     reinterpret_cast<const float*>(blob + c->wops_off), scratch, int(nblocks), c->stream);
+  if (rc) return cuda_fail(c, cudaError_t(rc), "static energy launch");
+  cudaError_t e = cudaMemcpyAsync(E, scratch + kStaticPartials, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "static energy download");
+  if (!std::isfinite(*E)) return c->fail(DG_ERR_NONFINITE, "non-finite energy");
+  return DG_OK;
 }
 
 int dg_sync(dg_ctx* c) {

@@ -25,6 +25,8 @@ namespace dgw {
 constexpr int kB = 32;            // elements per block (one warp lane each)
 constexpr int kMaxOrder = 4;
 constexpr int kCodeTet = 64;
+// energy partial sums held by the allocation-free entry point (128 elements each)
+constexpr int kStaticPartials = 1 << 16;
 
 __host__ __device__ constexpr int nt_of(int N) { return (N + 1) * (N + 2) / 2; }
 __host__ __device__ constexpr int npw_of(int N) { return nt_of(N) * (N + 1); }
@@ -111,5 +113,11 @@ DGW_DECLARE_LAUNCHERS(f64, double, 1)
 DGW_DECLARE_LAUNCHERS(f64, double, 2)
 DGW_DECLARE_LAUNCHERS(f64, double, 3)
 DGW_DECLARE_LAUNCHERS(f64, double, 4)
+
+// allocation-free energy (energy_static.cu)
+int energy_static_scratch(int device, double** out);
+template <typename real>
+int launch_energy_static(int N, const DevMesh<real>& m, const real* q, const real* wops, double* scratch, int nblocks,
+                         void* stream);
 
 }  // namespace dgw

@@ -28,7 +28,7 @@ DG_F32, DG_F64 = 0, 1
 
 EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_set_options", "dg_num_nodes",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
-           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_sync", "dg_time",
+           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_sync", "dg_time",
            "dg_stable_dt", "dg_last_error", "dg_destroy")
 
 _lib = None
@@ -66,6 +66,7 @@ def lib():
         "dg_rhs": (c_int, [P, P, P]),
         "dg_step": (c_int, [P, c_double, c_int64]),
         "dg_energy": (c_int, [P, POINTER(c_double)]),
+        "dg_energy_static": (c_int, [P, P, POINTER(c_double)]),
         "dg_sync": (c_int, [P]),
         "dg_time": (c_int, [P, POINTER(c_double)]),
         "dg_stable_dt": (c_int, [P, c_double, POINTER(c_double)]),
@@ -183,6 +184,12 @@ def dg_step(ctx, dt: float, nsteps: int):
 def dg_energy(ctx) -> float:
     E = c_double()
     _check(ctx, lib().dg_energy(ctx, ctypes.byref(E)))
+    return E.value
+
+
+def dg_energy_static(ctx, d_q: int) -> float:
+    E = c_double()
+    _check(ctx, lib().dg_energy_static(ctx, c_void_p(d_q), ctypes.byref(E)))
     return E.value
 
 
