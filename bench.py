@@ -43,6 +43,23 @@ def _peaks():
 WORKLOADS = {"full": (128, 16), "medium": (96, 16), "small": (32, 16)}
 
 
+def _traffic_per_launch():
+    """DRAM bytes per wedge-stage launch from the committed ncu summary, or None
+    when the kernel source has changed since those counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "wedge_stage_n3_layered524k_dram.md")
+    src = os.path.join(ROOT, "paper_1607_03399_gb300", "csrc", "kernels.cuh")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    fields = dict(line.split(":", 1) for line in text.splitlines() if line.startswith(("traffic_bytes", "kernel_source")))
+    if fields.get("kernel_source_sha256_16", "").strip() != sha:
+        return None
+    return int(fields["traffic_bytes_per_launch"].strip())
+
+
 def _mesh(ntri=128, nlayers=16):
     from paper_1607_03399_gb300 import inputs as I
     m = I.bumpy_layered_mesh(ntri, nlayers)
@@ -273,7 +290,8 @@ def run_ours(args, rank, world):
                    "l2_flush": "inputs larger than L2 (3 state buffers of %.0f MB)" % (r3["dof"] * 4 / 1e6),
                    "bc": "rigid", "flux": "upwind"},
         "roofline": {"kernel": f"k_wedge_stage<{orders[0]}>", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": _traffic_per_launch() if (args.workload == "full" and orders[0] == 3) else None,
                      "alg_bytes_per_launch": alg},
         "by_order": by_order,
         "e2e": r3.get("e2e"),
