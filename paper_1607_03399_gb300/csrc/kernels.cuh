@@ -193,11 +193,11 @@ enum WGeo : int {
   G_TX0, G_TX1, G_TY0, G_TY1, G_COUNT
 };
 
-// Residual slab staged in shared memory by the bulk copy (N <= 3) or read
-// from global memory in per-field batches (N = 4, to keep two CTAs per SM).
+// Residual slab staged in shared memory by the bulk copy (all orders: at N = 4
+// registers, not shared memory, bound the CTAs per SM).
 template <int N>
 __host__ __device__ constexpr bool stage_res() {
-  return N <= 3;
+  return true;
 }
 
 template <int N>
