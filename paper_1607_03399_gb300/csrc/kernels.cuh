@@ -193,11 +193,12 @@ enum WGeo : int {
   G_TX0, G_TX1, G_TY0, G_TY1, G_COUNT
 };
 
-// Residual slab staged in shared memory by the bulk copy (all orders: at N = 4
-// registers, not shared memory, bound the CTAs per SM).
+// Residual slab staged in shared memory by the bulk copy (N <= 3).  At N = 4
+// the staged slab measured slower (77 KB of copies per block in flight at two
+// CTAs per SM), so the residual is read from global memory at the update.
 template <int N>
 __host__ __device__ constexpr bool stage_res() {
-  return true;
+  return N <= 3;
 }
 
 template <int N>
