@@ -4,8 +4,9 @@ stage on the layered-medium workload.
 Workload (one GPU): [0,1]^3 footprint of 2x128x128 triangles extruded
 through 16 layers with seeded Gaussian-bump interfaces (amplitude 0.2 of a
 layer) = 524288 vertically mapped wedges, layered wavespeed c = 2.5, 2.0,
-1.5, 1.0 by depth quartile, rho = 1, rigid walls, upwind flux, FP32 state
-and arithmetic, synthetic seeded state.  N = 3 is the headline; N = 4 is
+1.5, 1.0 by depth quartile, rho = 1, rigid walls, upwind flux, a Ricker
+point source (f0 = 10, t0 = 0.1) at the domain centre, FP32 state and
+arithmetic, synthetic seeded state.  N = 3 is the headline; N = 4 is
 measured too.  A step is one LSRK45 step (5 stages, one fused wedge kernel
 each, replayed from a CUDA graph); value = 4 * nodes * 5 * steps / time.
 
@@ -197,7 +198,8 @@ print(json.dumps({{"dof": 4 * S.conn.total_nodes, "K": S.K, "sec": el}}))
 
 def measure_order(N, args, torch, dev, m, c2, rho):
     from paper_1607_03399_gb300.dg import Solver
-    S = Solver(m.VX, m.EToV, m.etype, N, c2, rho, precision="f32", device=str(dev))
+    S = Solver(m.VX, m.EToV, m.etype, N, c2, rho, precision="f32", device=str(dev),
+               sources=[(0.5, 0.5, 0.5, 10.0, 0.1, 1.0)])
     q = np.random.default_rng(1).uniform(-1, 1, size=(4, S.total_nodes)).astype(np.float32)
     S.set_fields(q)
     dt = S.stable_dt(0.5)
@@ -288,7 +290,7 @@ def run_ours(args, rank, world):
         "config": {"workload": WORKLOAD if args.workload == "full" else f"layered_wedges_2x{ntri}x{ntri}x{nlay}",
                    "wedges": K, "order": orders[0], "field_dof": r3["dof"],
                    "l2_flush": "inputs larger than L2 (3 state buffers of %.0f MB)" % (r3["dof"] * 4 / 1e6),
-                   "bc": "rigid", "flux": "upwind"},
+                   "bc": "rigid", "flux": "upwind", "source": "Ricker f0=10 t0=0.1 at (0.5,0.5,0.5)"},
         "roofline": {"kernel": f"k_wedge_stage<{orders[0]}>", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": _traffic_per_launch() if (args.workload == "full" and orders[0] == 3) else None,

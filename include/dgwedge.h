@@ -102,6 +102,16 @@ int dg_set_order(dg_ctx* ctx, int N);
  * Default: c^2 = rho = 1. */
 int dg_set_material(dg_ctx* ctx, const double* c2, const double* rho);
 
+/* Point source in the pressure equation (not in the paper; the seismic
+ * workloads need one): the element containing (x, y, z) (lowest id on ties)
+ * gets rhs_p += amp * R(t) * kappa_k (M^k)^{-1} l(x_s), where l(x_s) are its
+ * Lagrange basis functions at the point, M^k its exact mass matrix and
+ * R(t) = (1 - 2a) exp(-a), a = (pi f0 (t - t0))^2 a Ricker wavelet evaluated
+ * at each Runge-Kutta stage time.  At most 64 sources; after dg_set_order and
+ * before dg_bind.  Errors: DG_ERR_ARG (point outside the mesh, f0 <= 0),
+ * DG_ERR_STATE. */
+int dg_add_source(dg_ctx* ctx, double x, double y, double z, double f0, double t0, double amp);
+
 /* Boundary condition (DG_BC_*), flux (DG_FLUX_*), arithmetic precision
  * (DG_F32: fields and arithmetic in float; DG_F64: double).
  * Default: rigid walls, upwind, DG_F32. */
@@ -152,7 +162,8 @@ int dg_bind(dg_ctx* ctx, void* d_mesh, void* d_q0, void* d_q1, void* d_res, void
 int dg_set_fields(dg_ctx* ctx, const void* q, int on_device);
 int dg_get_fields(dg_ctx* ctx, void* q, int on_device);
 
-/* Semi-discrete right-hand side dq/dt = rhs(q) (Section 2.1), canonical
+/* Semi-discrete right-hand side dq/dt = rhs(q, t) (Section 2.1) at the
+ * current simulation time t (sources), canonical
  * layout, device pointers (d_q may equal d_rhs).  Uses the inactive state
  * buffer and the residual buffer as scratch: call between steps only.  The
  * current state is not modified.  Asynchronous. */

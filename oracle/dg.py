@@ -59,6 +59,7 @@ class Solver:
         self.kappa = rho * c2
         self.rhoc = rho * np.sqrt(c2)
         self.W, self.T = C.W, C.T
+        self.sources = []   # (element, g = kappa M^{-1} l(x_s), f0, t0, amp)
         self._wedge_geometry()
         self._tet_geometry()
         self._face_tables()
@@ -205,16 +206,70 @@ class Solver:
         return Fp, Fu
 
     # ------------------------------------------------------------------
+    # point sources (pressure equation; not part of the paper)
+    # ------------------------------------------------------------------
+    def reference_coords(self, k: int, x) -> np.ndarray:
+        """Invert the vertex map of element k at physical point x by Newton
+        iteration on the generic map (no Lemma 3.1 shortcut)."""
+        C = self.conn
+        wedge = C.etype[k] == WEDGE
+        vf = R.wedge_vertex_functions if wedge else R.tet_vertex_functions
+        verts = C.VX[C.EToV[k, :6 if wedge else 4]]
+        X = np.array([[-1.0 / 3, -1.0 / 3, 0.0]]) if wedge else np.array([[-0.5, -0.5, -0.5]])
+        for _ in range(50):
+            v, gv = vf(X)
+            F = v[0] @ verts - np.asarray(x, dtype=np.float64)
+            G = np.einsum("vm,vd->dm", gv[0], verts)
+            dX = np.linalg.solve(G, F)
+            X = X - dX
+            if np.max(np.abs(dX)) < 1e-15:
+                break
+        return X[0]
+
+    def _inside(self, k: int, X, tol: float = 1e-12) -> bool:
+        r, s, t = X
+        if self.conn.etype[k] == WEDGE:
+            return r >= -1 - tol and s >= -1 - tol and r + s <= tol and abs(t) <= 1 + tol
+        return r >= -1 - tol and s >= -1 - tol and t >= -1 - tol and r + s + t <= -1 + tol
+
+    def add_source(self, x, y, z, f0: float, t0: float, amp: float):
+        """rhs_p += amp R(t) kappa_k M_k^{-1} l(x_s) in the lowest-id element
+        containing (x, y, z); R is the Ricker wavelet (1 - 2a) e^{-a},
+        a = (pi f0 (t - t0))^2."""
+        for k in range(self.K):
+            X = self.reference_coords(k, (x, y, z))
+            if not self._inside(k, X):
+                continue
+            ref = self.W if self.conn.etype[k] == WEDGE else self.T
+            ell = ref.eval(X[None, :])[0]
+            M, _, _ = self.element_matrices(k)
+            g = self.kappa[k] * np.linalg.solve(M, ell)
+            self.sources.append((k, g, f0, t0, amp))
+            return k
+        raise ValueError("source point outside the mesh")
+
+    @staticmethod
+    def ricker(f0: float, tau: float) -> float:
+        a = (np.pi * f0 * tau) ** 2
+        return (1.0 - 2.0 * a) * np.exp(-a)
+
+    # ------------------------------------------------------------------
     # method form (Section 4.2)
     # ------------------------------------------------------------------
-    def rhs(self, q: np.ndarray) -> np.ndarray:
+    def rhs(self, q: np.ndarray, t: float = 0.0) -> np.ndarray:
         q = np.asarray(q, dtype=np.float64)
         out = np.zeros_like(q)
         if self.Kw:
             self._rhs_wedge(q, out)
         if self.Kt:
             self._rhs_tet(q, out)
+        self._add_sources(out, t)
         return out
+
+    def _add_sources(self, out, t):
+        C = self.conn
+        for (k, g, f0, t0, amp) in self.sources:
+            out[0, C.offset[k]:C.offset[k + 1]] += amp * self.ricker(f0, t - t0) * g
 
     def wedge_tri_mass(self):
         """M^{tri,k} = sum_a J_a M_a  (Kw, Nt, Nt)."""
@@ -398,7 +453,7 @@ class Solver:
             self._brute = [self.element_matrices(k) for k in range(self.K)]
         return self._brute
 
-    def rhs_brute(self, q: np.ndarray) -> np.ndarray:
+    def rhs_brute(self, q: np.ndarray, t: float = 0.0) -> np.ndarray:
         C = self.conn
         mats = self.brute_setup()
         q = np.asarray(q, dtype=np.float64)
@@ -417,6 +472,7 @@ class Solver:
             out[0, sl] = self.kappa[k] * np.linalg.solve(M, bp)
             for c in range(3):
                 out[1 + c, sl] = np.linalg.solve(M, bu[c]) / self.rho[k]
+        self._add_sources(out, t)
         return out
 
     def _single_face_flux(self, q, k, f, nrm):
@@ -534,9 +590,10 @@ class Solver:
     # ------------------------------------------------------------------
     # time stepping and errors
     # ------------------------------------------------------------------
-    def step(self, q: np.ndarray, dt: float, nsteps: int, rhs=None) -> np.ndarray:
-        """LSRK45 (Carpenter-Kennedy 2N-storage), nsteps steps of size dt."""
-        return lsrk45(self.rhs if rhs is None else rhs, q, dt, nsteps)
+    def step(self, q: np.ndarray, dt: float, nsteps: int, rhs=None, t0: float = 0.0) -> np.ndarray:
+        """LSRK45 (Carpenter-Kennedy 2N-storage), nsteps steps of size dt from
+        time t0 (stage times t + c_s dt reach the sources)."""
+        return lsrk45(self.rhs if rhs is None else rhs, q, dt, nsteps, t0)
 
     def stable_dt(self, cfl: float) -> float:
         """dt = CFL * min_k 1 / (c_k (N+1)^2 max_f(area_f / vol_k))."""

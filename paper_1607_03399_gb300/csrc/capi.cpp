@@ -49,6 +49,8 @@ int pack_f64(int N, const DevMesh<double>& m, const double* c, double* p, bool u
   DGW_SWITCH_N(N, launch_pack_f64, (m, c, p, u, s))
 }
 int energy_f32(int N, const DevMesh<float>& m, const float* q, void* s) { DGW_SWITCH_N(N, launch_energy_f32, (m, q, s)) }
+int clock_f32(int N, double* c, double dt, void* s) { DGW_SWITCH_N(N, launch_clock_f32, (c, dt, s)) }
+int clock_f64(int N, double* c, double dt, void* s) { DGW_SWITCH_N(N, launch_clock_f64, (c, dt, s)) }
 int energy_f64(int N, const DevMesh<double>& m, const double* q, void* s) { DGW_SWITCH_N(N, launch_energy_f64, (m, q, s)) }
 }  // namespace
 
@@ -102,6 +104,13 @@ struct dg_ctx {
   std::vector<double> c2, rho;
   // options
   int bc = DG_BC_RIGID, flux = DG_FLUX_UPWIND, prec = DG_F32;
+  // point sources (pressure equation)
+  struct Source {
+    int64_t elem;
+    double f0, t0, amp;
+    std::vector<double> g;  // (M^k)^{-1} l(x_s), element node order (times kappa at upload)
+  };
+  std::vector<Source> sources;
   // binding
   bool bound = false;
   int device = 0;
@@ -279,7 +288,7 @@ double tet_stable_ratio(const dg_ctx* c, int64_t k) {
 // ----------------------------------------------------------------- blob
 struct BlobLayout {
   size_t w_vid, w_nbr, w_code, w_mat, w_canon, t_vid, t_nbr, t_code, t_mat, t_canon, vx, vy, vz, err, partials, energy,
-      tmass, wops, total;
+      tmass, wops, src, srcg, clock, total;
 };
 
 BlobLayout blob_layout(const dg_ctx* c) {
@@ -311,6 +320,11 @@ BlobLayout blob_layout(const dg_ctx* c) {
   L.energy = take(8);
   L.tmass = take(size_t(npt_of(c->N)) * npt_of(c->N) * rs);
   L.wops = take(size_t(3 * nt_of(c->N) * nt_of(c->N) + (c->N + 1) * (c->N + 1)) * rs);
+  L.src = take(sizeof(SourceDev) * kMaxSources);
+  size_t ng = 0;
+  for (const auto& sc : c->sources) ng += sc.g.size();
+  L.srcg = take((ng > 0 ? ng : 1) * rs);
+  L.clock = take(sizeof(double));
   L.total = o;
   return L;
 }
@@ -358,6 +372,22 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
     t_mat[2 * Ktp + t] = real(c->rho[k] * cc);
     if (t < Kt) t_canon[t] = c->node_off[k];
   }
+  SourceDev* sd = reinterpret_cast<SourceDev*>(blob.data() + L.src);
+  real* sg = reinterpret_cast<real*>(blob.data() + L.srcg);
+  int goff = 0;
+  for (size_t i = 0; i < c->sources.size(); ++i) {
+    const auto& sc = c->sources[i];
+    sd[i].type = c->etype[sc.elem];
+    sd[i].elem = int(c->local[sc.elem]);
+    sd[i].goff = goff;
+    sd[i].pad = 0;
+    sd[i].f0 = sc.f0;
+    sd[i].t0 = sc.t0;
+    sd[i].amp = sc.amp;
+    const double kappa = c->rho[sc.elem] * c->c2[sc.elem];
+    for (size_t n = 0; n < sc.g.size(); ++n) sg[goff + n] = real(kappa * sc.g[n]);
+    goff += int(sc.g.size());
+  }
   real* vx = reinterpret_cast<real*>(blob.data() + L.vx);
   real* vy = reinterpret_cast<real*>(blob.data() + L.vy);
   real* vz = reinterpret_cast<real*>(blob.data() + L.vz);
@@ -403,6 +433,10 @@ void fill_devmesh(const dg_ctx* c, const BlobLayout& L, DevMesh<real>& m) {
   m.partials = reinterpret_cast<double*>(b + L.partials);
   m.energy = reinterpret_cast<double*>(b + L.energy);
   m.tet_mass = reinterpret_cast<const real*>(b + L.tmass);
+  m.src = reinterpret_cast<const SourceDev*>(b + L.src);
+  m.src_g = reinterpret_cast<const real*>(b + L.srcg);
+  m.nsrc = int(c->sources.size());
+  m.clock = reinterpret_cast<double*>(b + L.clock);
   m.tet_off = int64_t(m.nblk_w) * 4 * npw_of(c->N) * kB;
   m.total_nodes = c->wedge_nodes + c->tet_nodes;
 }
@@ -414,7 +448,7 @@ size_t field_bytes_of(const dg_ctx* c) {
 }
 
 int launch_stage(dg_ctx* c, const void* q_in, void* q_out, void* res, double a, double b, double dt, bool rk,
-                 cudaStream_t s) {
+                 cudaStream_t s, double cst = 0.0) {
   int rc;
   if (c->prec == DG_F64) {
     StageArgs<double> A;
@@ -425,6 +459,7 @@ int launch_stage(dg_ctx* c, const void* q_in, void* q_out, void* res, double a, 
     A.rk_a = a;
     A.rk_b = b;
     A.dt = dt;
+    A.c_stage = cst;
     A.bc = c->bc;
     A.flux = c->flux;
     rc = stage_f64(c->N, A, rk, s);
@@ -437,6 +472,7 @@ int launch_stage(dg_ctx* c, const void* q_in, void* q_out, void* res, double a, 
     A.rk_a = float(a);
     A.rk_b = float(b);
     A.dt = float(dt);
+    A.c_stage = cst;
     A.bc = c->bc;
     A.flux = c->flux;
     rc = stage_f32(c->N, A, rk, s);
@@ -636,6 +672,7 @@ int dg_set_order(dg_ctx* c, int N) {
     return c->fail(DG_ERR_ORDER, ex.what());
   }
   c->N = N;
+  c->sources.clear();
   c->node_off.assign(c->K + 1, 0);
   c->wedge_nodes = c->tet_nodes = 0;
   for (int64_t k = 0; k < c->K; ++k) {
@@ -656,6 +693,97 @@ int dg_set_material(dg_ctx* c, const double* c2, const double* rho) {
   c->c2.assign(c2, c2 + c->K);
   c->rho.assign(rho, rho + c->K);
   return DG_OK;
+}
+
+int dg_add_source(dg_ctx* c, double x, double y, double z, double f0, double t0, double amp) {
+  if (!c) return DG_ERR_ARG;
+  if (c->bound) return c->fail(DG_ERR_STATE, "dg_add_source after dg_bind");
+  if (!c->N) return c->fail(DG_ERR_STATE, "dg_add_source needs dg_set_order first");
+  if (!(f0 > 0) || !std::isfinite(t0) || !std::isfinite(amp))
+    return c->fail(DG_ERR_ARG, "source frequency must be positive and t0, amp finite");
+  if (int(c->sources.size()) >= kMaxSources) return c->fail(DG_ERR_ARG, "too many sources");
+  const RefElems& R = *c->ref;
+  const double* V = c->VX.data();
+  const double tol = 1e-12;
+  for (int64_t k = 0; k < c->K; ++k) {
+    auto P = [&](int a, int d) { return V[c->EToV[k * 6 + a] * 3 + d]; };
+    double ref[3];
+    bool inside = false;
+    if (c->etype[k] == DG_WEDGE) {
+      // barycentric coordinates in the (affine) footprint, then t along the column
+      const double a11 = P(1, 0) - P(0, 0), a12 = P(2, 0) - P(0, 0), a21 = P(1, 1) - P(0, 1), a22 = P(2, 1) - P(0, 1);
+      const double det = a11 * a22 - a12 * a21;
+      const double bx = x - P(0, 0), by = y - P(0, 1);
+      const double l1 = (a22 * bx - a12 * by) / det, l2 = (a11 * by - a21 * bx) / det, l0 = 1.0 - l1 - l2;
+      const double zb = l0 * P(0, 2) + l1 * P(1, 2) + l2 * P(2, 2), zt = l0 * P(3, 2) + l1 * P(4, 2) + l2 * P(5, 2);
+      const double t = (2.0 * z - zb - zt) / (zt - zb);
+      inside = l0 >= -tol && l1 >= -tol && l2 >= -tol && std::fabs(t) <= 1.0 + tol;
+      ref[0] = 2.0 * l1 - 1.0;
+      ref[1] = 2.0 * l2 - 1.0;
+      ref[2] = t;
+    } else {
+      double G[3][3], Gi[3][3];
+      for (int d = 0; d < 3; ++d)
+        for (int m = 0; m < 3; ++m) G[d][m] = P(m + 1, d) - P(0, d);
+      const double det = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) - G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+                         G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+      Gi[0][0] = (G[1][1] * G[2][2] - G[1][2] * G[2][1]) / det;
+      Gi[0][1] = (G[0][2] * G[2][1] - G[0][1] * G[2][2]) / det;
+      Gi[0][2] = (G[0][1] * G[1][2] - G[0][2] * G[1][1]) / det;
+      Gi[1][0] = (G[1][2] * G[2][0] - G[1][0] * G[2][2]) / det;
+      Gi[1][1] = (G[0][0] * G[2][2] - G[0][2] * G[2][0]) / det;
+      Gi[1][2] = (G[0][2] * G[1][0] - G[0][0] * G[1][2]) / det;
+      Gi[2][0] = (G[1][0] * G[2][1] - G[1][1] * G[2][0]) / det;
+      Gi[2][1] = (G[0][1] * G[2][0] - G[0][0] * G[2][1]) / det;
+      Gi[2][2] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) / det;
+      const double b[3] = {x - P(0, 0), y - P(0, 1), z - P(0, 2)};
+      double l[3];
+      for (int m = 0; m < 3; ++m) l[m] = Gi[m][0] * b[0] + Gi[m][1] * b[1] + Gi[m][2] * b[2];
+      inside = l[0] >= -tol && l[1] >= -tol && l[2] >= -tol && (1.0 - l[0] - l[1] - l[2]) >= -tol;
+      for (int m = 0; m < 3; ++m) ref[m] = 2.0 * l[m] - 1.0;
+    }
+    if (!inside) continue;
+    dg_ctx::Source sc;
+    sc.elem = k;
+    sc.f0 = f0;
+    sc.t0 = t0;
+    sc.amp = amp;
+    if (c->etype[k] == DG_WEDGE) {
+      // (M^k)^{-1} = (M^{tri,k})^{-1} (x) (M^1D)^{-1},  M^{tri,k} = sum_a J_a M_a
+      const double A = 0.25 * ((P(1, 0) - P(0, 0)) * (P(2, 1) - P(0, 1)) - (P(2, 0) - P(0, 0)) * (P(1, 1) - P(0, 1)));
+      Mat Mt(R.Nt, R.Nt), Mti, M1i;
+      for (int a = 0; a < 3; ++a) {
+        const double Ja = 0.5 * A * (P(a + 3, 2) - P(a, 2));
+        for (size_t i = 0; i < Mt.a.size(); ++i) Mt.a[i] += Ja * R.Ma[a].a[i];
+      }
+      invert(Mt, Mti);
+      invert(R.M1, M1i);
+      std::vector<double> lt(R.Nt), l1(R.Nq), gt(R.Nt, 0.0), g1(R.Nq, 0.0);
+      tri_lagrange(R, ref[0], ref[1], lt.data());
+      line_lagrange(R, ref[2], l1.data());
+      for (int i = 0; i < R.Nt; ++i)
+        for (int l = 0; l < R.Nt; ++l) gt[i] += Mti(i, l) * lt[l];
+      for (int j = 0; j < R.Nq; ++j)
+        for (int l = 0; l < R.Nq; ++l) g1[j] += M1i(j, l) * l1[l];
+      sc.g.resize(R.Npw);
+      for (int j = 0; j < R.Nq; ++j)
+        for (int i = 0; i < R.Nt; ++i) sc.g[j * R.Nt + i] = gt[i] * g1[j];
+    } else {
+      const double J = tet_det(c, k) / 8.0;
+      Mat Mi;
+      invert(R.tM, Mi);
+      std::vector<double> lv(R.Npt);
+      tet_lagrange(R, ref[0], ref[1], ref[2], lv.data());
+      sc.g.assign(R.Npt, 0.0);
+      for (int i = 0; i < R.Npt; ++i) {
+        for (int l = 0; l < R.Npt; ++l) sc.g[i] += Mi(i, l) * lv[l];
+        sc.g[i] /= J;
+      }
+    }
+    c->sources.push_back(sc);
+    return DG_OK;
+  }
+  return c->fail(DG_ERR_ARG, "source point lies outside the mesh");
 }
 
 int dg_set_options(dg_ctx* c, int bc, int flux, int precision) {
@@ -869,6 +997,8 @@ int dg_set_fields(dg_ctx* c, const void* q, int on_device) {
   if (rc) return rc;
   cudaError_t e = cudaMemsetAsync(c->d_res, 0, c->field_bytes, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "residual clear");
+  e = cudaMemsetAsync((c->prec == DG_F64) ? c->m64.clock : c->m32.clock, 0, sizeof(double), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "clock reset");
   if (!on_device) {
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "state upload synchronize");
@@ -933,8 +1063,14 @@ int dg_step(dg_ctx* c, double dt, int64_t nsteps) {
       int src = p;
       int lrc = DG_OK;
       for (int s = 0; s < 5 && lrc == DG_OK; ++s) {
-        lrc = launch_stage(c, c->d_q[src], c->d_q[1 - src], c->d_res, kLSRK_A[s], kLSRK_B[s], dt, true, c->cap_stream);
+        lrc = launch_stage(c, c->d_q[src], c->d_q[1 - src], c->d_res, kLSRK_A[s], kLSRK_B[s], dt, true, c->cap_stream,
+                           kLSRK_C[s]);
         src = 1 - src;
+      }
+      if (lrc == DG_OK) {
+        double* clk = (c->prec == DG_F64) ? c->m64.clock : c->m32.clock;
+        const int crc = (c->prec == DG_F64) ? clock_f64(c->N, clk, dt, c->cap_stream) : clock_f32(c->N, clk, dt, c->cap_stream);
+        if (crc) lrc = cuda_fail(c, cudaError_t(crc), "clock launch");
       }
       e = cudaStreamEndCapture(c->cap_stream, &g);
       if (lrc) {

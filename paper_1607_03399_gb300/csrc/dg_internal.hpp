@@ -61,6 +61,17 @@ struct AllOps {
   Tables<N> tab;
 };
 
+// Point source in the pressure equation: rhs_p += amp R(f0, t - t0) g, with
+// g = kappa_k (M^k)^{-1} l(x_s) precomputed on the host (Np reals at goff).
+struct SourceDev {
+  int type;   // 6 wedge, 4 tet
+  int elem;   // index within its element type
+  int goff;   // offset of g in the source vector table
+  int pad;
+  double f0, t0, amp;
+};
+constexpr int kMaxSources = 64;
+
 template <typename real>
 struct DevMesh {
   int Kw = 0, Kw_pad = 0, nblk_w = 0;
@@ -84,6 +95,10 @@ struct DevMesh {
   double* partials = nullptr;        // per-block energy partial sums
   double* energy = nullptr;          // final energy
   const real* tet_mass = nullptr;    // reference tet mass matrix (energy only)
+  const SourceDev* src = nullptr;    // point sources
+  const real* src_g = nullptr;       // their vectors g
+  int nsrc = 0;
+  double* clock = nullptr;           // simulation time of the current step
 };
 
 template <typename real>
@@ -93,6 +108,7 @@ struct StageArgs {
   real* q_out = nullptr;        // RK: packed next state; RHS mode: packed rhs
   real* res = nullptr;          // RK residual (unused in RHS mode)
   real rk_a = 0, rk_b = 0, dt = 0;
+  double c_stage = 0;           // stage time = *clock + c_stage * dt
   int bc = 1, flux = 0;
 };
 
@@ -104,7 +120,8 @@ enum : int { kErrTimeout = 1, kErrNonfinite = 2 };
   int upload_ops_##P##n##N(const void* host_ops, size_t bytes, void* stream);                      \
   int launch_stage_##P##n##N(const StageArgs<T>& a, bool rk, void* stream);                        \
   int launch_pack_##P##n##N(const DevMesh<T>& m, const T* canon, T* packed, bool unpack, void* s); \
-  int launch_energy_##P##n##N(const DevMesh<T>& m, const T* q, void* stream);
+  int launch_energy_##P##n##N(const DevMesh<T>& m, const T* q, void* stream);                      \
+  int launch_clock_##P##n##N(double* clock, double dt, void* stream);
 DGW_DECLARE_LAUNCHERS(f32, float, 1)
 DGW_DECLARE_LAUNCHERS(f32, float, 2)
 DGW_DECLARE_LAUNCHERS(f32, float, 3)

@@ -148,6 +148,31 @@ __device__ __forceinline__ void taus(int flux, real zM, real zP, real& tau_p, re
   }
 }
 
+// Ricker wavelet (1 - 2 a) exp(-a), a = (pi f0 (t - t0))^2 (c13 reading).
+__device__ __forceinline__ double ricker(double f0, double tau) {
+  const double a = (3.14159265358979323846 * f0 * tau) * (3.14159265358979323846 * f0 * tau);
+  return (1.0 - 2.0 * a) * exp(-a);
+}
+// Source contribution to the pressure right-hand side at node n of element
+// (type, elem) at time t: sum over the sources placed in that element.
+__device__ __forceinline__ bool has_source(const DevMesh<real>& M, int type, int elem) {
+  for (int s = 0; s < M.nsrc; ++s)
+    if (M.src[s].type == type && M.src[s].elem == elem) return true;
+  return false;
+}
+__device__ __forceinline__ real source_term(const DevMesh<real>& M, int type, int elem, int n, double t) {
+  double acc = 0.0;
+  for (int s = 0; s < M.nsrc; ++s) {
+    const SourceDev& sd = M.src[s];
+    if (sd.type == type && sd.elem == elem) acc += sd.amp * ricker(sd.f0, t - sd.t0) * double(M.src_g[sd.goff + n]);
+  }
+  return real(acc);
+}
+
+__global__ void k_clock(double* clock, double dt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *clock += dt;
+}
+
 // ---------------------------------------------------------------------------
 // wedge stage
 // ---------------------------------------------------------------------------
@@ -594,11 +619,14 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
   }
   if (e < M.Kw) {
     const real kappa = M.w_mat[0 * Kp + e], irho = M.w_mat[1 * Kp + e];
+    const bool src = M.nsrc > 0 && has_source(M, 6, e);
+    const double tst = src ? *M.clock + A.c_stage * double(A.dt) : 0.0;
 #pragma unroll
     for (int i = 0; i < Nt; ++i) {
       const int n = j * Nt + i;
       const int64_t g = widx<N>(blk, n, lane);
-      const Q4 r{kappa * Wp[i], irho * Wu[0][i], irho * Wu[1][i], irho * Wu[2][i]};
+      Q4 r{kappa * Wp[i], irho * Wu[0][i], irho * Wu[1][i], irho * Wu[2][i]};
+      if (src) r.p += source_term(M, 6, e, n, tst);
       if (rk) {
         const Q4 r0 = stage_res<N>() ? lds4(sr, n, lane) : ld4(resg, g);
         const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
@@ -793,12 +821,15 @@ __device__ __forceinline__ void tet_chunk_out(const StageArgs<real>& A, const Te
   if (e < M.Kt) {
     real* __restrict__ resg = A.res;
     real* __restrict__ qout = A.q_out;
+    const bool src = M.nsrc > 0 && has_source(M, 4, e);
+    const double tst = src ? *M.clock + A.c_stage * double(A.dt) : 0.0;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       if (I0 + c < Np) {
         const int i = I0 + c;
         const int64_t gi = tidx<N>(M.tet_off, blockIdx.x, i, lane);
-        const Q4 r{g.kappa * ap[c], g.irho * au[0][c], g.irho * au[1][c], g.irho * au[2][c]};
+        Q4 r{g.kappa * ap[c], g.irho * au[0][c], g.irho * au[1][c], g.irho * au[2][c]};
+        if (src) r.p += source_term(M, 4, e, i, tst);
         if (rk) {
           const Q4 r0 = ld4(resg, gi);
           const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
@@ -1048,5 +1079,9 @@ int DGW_CAT(launch_pack_, REALNS)(const DevMesh<REAL>& m, const REAL* canon, REA
 }
 int DGW_CAT(launch_energy_, REALNS)(const DevMesh<REAL>& m, const REAL* q, void* stream) {
   return REALNS::launch_energy_n<NORD>(m, q, cudaStream_t(stream));
+}
+int DGW_CAT(launch_clock_, REALNS)(double* clock, double dt, void* stream) {
+  REALNS::k_clock<<<1, 32, 0, cudaStream_t(stream)>>>(clock, dt);
+  return int(cudaGetLastError());
 }
 }  // namespace dgw

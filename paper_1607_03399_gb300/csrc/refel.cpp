@@ -305,6 +305,7 @@ RefElems build_reference(int N) {
         Vr(i, n) = djacobi(n, 0, 0, R.gll[i]);
       }
     invert(V, Vinv);
+    R.line_Vinv = Vinv;
     Mat VVt = matmul(V, transpose(V));  // = (M^1D)^{-1}
     invert(VVt, R.M1);
     R.D1 = matmul(Vr, Vinv);
@@ -359,6 +360,7 @@ RefElems build_reference(int N) {
       }
     }
     if (!invert(V, Vinv)) throw std::runtime_error("singular triangle Vandermonde");
+    R.tri_Vinv = Vinv;
     R.Dr = matmul(Vr, Vinv);
     R.Ds = matmul(Vs, Vinv);
     Mat VVt = matmul(V, transpose(V));
@@ -475,6 +477,7 @@ RefElems build_reference(int N) {
       }
     }
     if (!invert(V, Vinv)) throw std::runtime_error("singular tet Vandermonde");
+    R.tet_Vinv = Vinv;
     R.tDr = matmul(Vr, Vinv);
     R.tDs = matmul(Vs, Vinv);
     R.tDt = matmul(Vt, Vinv);
@@ -490,6 +493,34 @@ RefElems build_reference(int N) {
         }
   }
   return R;
+}
+
+void line_lagrange(const RefElems& R, double t, double* out) {
+  for (int j = 0; j < R.Nq; ++j) {
+    double v = 0.0;
+    for (int n = 0; n < R.Nq; ++n) v += jacobi(n, 0, 0, t) * R.line_Vinv(n, j);
+    out[j] = v;
+  }
+}
+
+void tri_lagrange(const RefElems& R, double r, double s, double* out) {
+  std::vector<double> v, vr, vs;
+  tri_basis(R.N, r, s, v, vr, vs);
+  for (int i = 0; i < R.Nt; ++i) {
+    double acc = 0.0;
+    for (int m = 0; m < R.Nt; ++m) acc += v[m] * R.tri_Vinv(m, i);
+    out[i] = acc;
+  }
+}
+
+void tet_lagrange(const RefElems& R, double r, double s, double t, double* out) {
+  std::vector<double> v, vr, vs, vt;
+  tet_basis(R.N, r, s, t, v, vr, vs, vt);
+  for (int i = 0; i < R.Npt; ++i) {
+    double acc = 0.0;
+    for (int m = 0; m < R.Npt; ++m) acc += v[m] * R.tet_Vinv(m, i);
+    out[i] = acc;
+  }
 }
 
 }  // namespace dgw

@@ -52,7 +52,14 @@ struct RefElems {
   // pos[m] = position in the own face vertex list of the neighbour's m-th
   // face vertex, code = pos[0]*3 + pos[1] (a permutation of 0,1,2).
   std::vector<std::vector<int>> tri_perm;  // 9 x Nt (invalid codes empty)
+  // inverse Vandermonde matrices (Lagrange basis = modal basis x Vinv)
+  Mat line_Vinv, tri_Vinv, tet_Vinv;
 };
+
+// Lagrange basis values at a reference point
+void line_lagrange(const RefElems& R, double t, double* out);
+void tri_lagrange(const RefElems& R, double r, double s, double* out);
+void tet_lagrange(const RefElems& R, double r, double s, double t, double* out);
 
 RefElems build_reference(int N);
 

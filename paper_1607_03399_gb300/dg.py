@@ -26,7 +26,7 @@ DG_BC_DIRICHLET, DG_BC_RIGID = 0, 1
 DG_FLUX_UPWIND, DG_FLUX_CENTRAL = 0, 1
 DG_F32, DG_F64 = 0, 1
 
-EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_set_options", "dg_num_nodes",
+EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_options", "dg_num_nodes",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
            "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_sync", "dg_time",
            "dg_stable_dt", "dg_last_error", "dg_destroy")
@@ -54,6 +54,7 @@ def lib():
         "dg_mesh_create": (c_int, [POINTER(P), c_int64, P, c_int64, P, P]),
         "dg_set_order": (c_int, [P, c_int]),
         "dg_set_material": (c_int, [P, P, P]),
+        "dg_add_source": (c_int, [P, c_double, c_double, c_double, c_double, c_double, c_double]),
         "dg_set_options": (c_int, [P, c_int, c_int, c_int]),
         "dg_num_nodes": (c_int, [P, POINTER(c_int64), POINTER(c_int64)]),
         "dg_node_coords": (c_int, [P, P]),
@@ -119,6 +120,10 @@ def dg_set_material(ctx, c2, rho):
     c2 = np.ascontiguousarray(c2, dtype=np.float64)
     rho = np.ascontiguousarray(rho, dtype=np.float64)
     _check(ctx, lib().dg_set_material(ctx, _ptr(c2), _ptr(rho)))
+
+
+def dg_add_source(ctx, x: float, y: float, z: float, f0: float, t0: float, amp: float):
+    _check(ctx, lib().dg_add_source(ctx, x, y, z, f0, t0, amp))
 
 
 def dg_set_options(ctx, bc: int, flux: int, precision: int):
@@ -230,7 +235,7 @@ class Solver:
     torch uint8 tensors and handed to the library by pointer."""
 
     def __init__(self, VX, EToV, etype, N: int, c2=None, rho=None, bc: str = "rigid", flux: str = "upwind",
-                 precision: str = "f32", device: str = "cuda:0", stream=None):
+                 precision: str = "f32", device: str = "cuda:0", stream=None, sources=()):
         import torch
         self.torch = torch
         self.ctx = dg_mesh_create(VX, EToV, etype)
@@ -240,6 +245,8 @@ class Solver:
             if c2 is not None or rho is not None:
                 dg_set_material(self.ctx, np.ones(K) if c2 is None else c2, np.ones(K) if rho is None else rho)
             dg_set_options(self.ctx, BC[bc], FLUX[flux], PREC[precision])
+            for src in sources:       # (x, y, z, f0, t0, amp)
+                dg_add_source(self.ctx, *src)
             self.N = N
             self.precision = precision
             self.dtype = torch.float32 if precision == "f32" else torch.float64

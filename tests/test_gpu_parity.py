@@ -205,3 +205,31 @@ def test_full_size_sampled(N):
                 ref = O.step(qs, dt, 1)[:, sl]
                 got = q1_gpu[:, glob]
             assert _rel(got, ref) <= 1e-5, (what, s)
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_point_sources(precision, tol):
+    """Ricker point sources (one inside a wedge, one on a vertex shared by
+    several elements: the lowest element id takes it, one in a tet) over 40
+    LSRK45 steps from rest, and dg_rhs at the resulting simulation time."""
+    m = I.hybrid_mesh(3, 2, 2)
+    c2, rho = I.random_material(m.K, 2, 1.0, 3.0, 0.5, 2.0)
+    srcs = [(0.41, 0.37, 0.22, 6.0, 0.05, 1.0),          # inside a wedge
+            (1.0 / 3.0, 2.0 / 3.0, 0.75, 8.0, 0.08, -2.0),  # footprint vertex inside the tet layers
+            (0.5, 0.5, 0.3, 5.0, 0.0, 0.5)]
+    S = Solver(m.VX, m.EToV, m.etype, 3, c2, rho, precision=precision, sources=srcs)
+    O = Oracle(m.VX, m.EToV, m.etype, 3, c2, rho)
+    for sc in srcs:
+        O.add_source(*sc)
+    dt = O.stable_dt(0.4)
+    q0 = np.zeros((4, S.total_nodes))
+    S.set_fields(q0)
+    S.step(dt, 40)
+    q_ref = O.step(q0, dt, 40)
+    q = S.get_fields()
+    assert np.linalg.norm(q_ref) > 0
+    assert _rel(q, q_ref) <= tol
+    r_ref = O.rhs(q_ref, 40 * dt)
+    r = S.rhs(q_ref.astype(S.np_dtype)).cpu().numpy()
+    assert _rel(r, r_ref) <= 10 * tol
+    S.close()

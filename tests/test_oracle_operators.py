@@ -181,3 +181,27 @@ def test_stable_dt_formula():
     # triangle with legs 1/4: area (sqrt2/4)(1/4), volume (1/32)(1/4)
     ratio = (np.sqrt(2) / 16) / (1 / 128)
     assert abs(S.stable_dt(0.5) - 0.5 / (16 * ratio)) < 1e-14
+
+
+def test_point_source_is_the_weak_delta():
+    """The source vector g = kappa M^{-1} l(x_s) satisfies v^T M g / kappa = v(x_s)
+    for every v in the element space (the weak form of a point load), and the
+    Ricker wavelet has its closed-form peak and zeros."""
+    m = I.cube_wavy_mesh(2, 2, 0.05)
+    S = Solver(m.VX, m.EToV, m.etype, 3, np.full(m.K, 2.0), np.full(m.K, 0.5))
+    k = S.add_source(0.3, 0.6, 0.45, 10.0, 0.1, 1.0)
+    _, g, _, _, _ = S.sources[0]
+    M, _, _ = S.element_matrices(k)
+    X = S.reference_coords(k, (0.3, 0.6, 0.45))
+    xyz = S.conn.xyz[:, S.conn.offset[k]:S.conn.offset[k + 1]]
+    for v in (np.ones(xyz.shape[1]), xyz[0] ** 2 - xyz[2], xyz[1] * xyz[2] ** 3):
+        val = S.W.eval(X[None, :])[0] @ v
+        assert abs(v @ M @ g / S.kappa[k] - val) < 1e-12
+    assert abs(S.ricker(10.0, 0.0) - 1.0) < 1e-15
+    tz = 1.0 / (np.sqrt(2.0) * np.pi * 10.0)
+    assert abs(S.ricker(10.0, tz)) < 1e-15
+    # the source enters only the pressure rows of its element
+    q = np.zeros((4, S.conn.total_nodes))
+    r = S.rhs(q, t=0.1)
+    assert np.count_nonzero(r[1:]) == 0
+    assert np.allclose(r[0, S.conn.offset[k]:S.conn.offset[k + 1]], g)
