@@ -108,7 +108,7 @@ struct dg_ctx {
   struct Source {
     int64_t elem;
     double f0, t0, amp;
-    std::vector<double> g;  // (M^k)^{-1} l(x_s), element node order (times kappa at upload)
+    std::vector<double> g;  // (M^k)^{-1} l(x_s), element node order (kappa applied in the kernels)
   };
   std::vector<Source> sources;
   // binding
@@ -384,8 +384,7 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
     sd[i].f0 = sc.f0;
     sd[i].t0 = sc.t0;
     sd[i].amp = sc.amp;
-    const double kappa = c->rho[sc.elem] * c->c2[sc.elem];
-    for (size_t n = 0; n < sc.g.size(); ++n) sg[goff + n] = real(kappa * sc.g[n]);
+    for (size_t n = 0; n < sc.g.size(); ++n) sg[goff + n] = real(sc.g[n]);
     goff += int(sc.g.size());
   }
   real* vx = reinterpret_cast<real*>(blob.data() + L.vx);

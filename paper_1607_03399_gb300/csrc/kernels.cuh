@@ -111,6 +111,16 @@ __device__ __forceinline__ Q4 ld4(const real* q, int64_t idx) {
     return Q4{real(t0.x), real(t0.y), real(t1.x), real(t1.y)};
   }
 }
+// generic address: the block's slab in shared memory or the stage input in global memory
+__device__ __forceinline__ Q4 ldx4(const real* a) {
+  if constexpr (sizeof(real) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(a);
+    return Q4{real(t.x), real(t.y), real(t.z), real(t.w)};
+  } else {
+    const double2 t0 = reinterpret_cast<const double2*>(a)[0], t1 = reinterpret_cast<const double2*>(a)[1];
+    return Q4{real(t0.x), real(t0.y), real(t1.x), real(t1.y)};
+  }
+}
 __device__ __forceinline__ void st4(real* q, int64_t idx, const Q4& v) {
   if constexpr (sizeof(real) == 4) {
     *reinterpret_cast<float4*>(q + idx) = make_float4(float(v.p), float(v.u), float(v.v), float(v.w));
@@ -128,24 +138,17 @@ __device__ __forceinline__ void penalty_flux(real dp, real dun, real tau_p, real
 // Boundary ghosts: Dirichlet p+ = -p-, u+ = u-  -> [p] = -2p, [u_n] = 0;
 // rigid p+ = p-, u+ = u- - 2 u_n n             -> [p] = 0, [u_n] = -2 u_n.
 __device__ __forceinline__ void boundary_jumps(int bc, real pM, real unM, real& dp, real& dun) {
-  if (bc == 0) {
-    dp = real(-2) * pM;
-    dun = real(0);
-  } else {
-    dp = real(0);
-    dun = real(-2) * unM;
-  }
+  const bool dir = bc == 0;
+  dp = dir ? real(-2) * pM : real(0);
+  dun = dir ? real(0) : real(-2) * unM;
 }
 
 __device__ __forceinline__ void taus(int flux, real zM, real zP, real& tau_p, real& tau_u) {
   const real zavg = real(0.5) * (zM + zP);
-  if (flux == 0) {
-    tau_p = real(1) / zavg;
-    tau_u = zavg;
-  } else {
-    tau_p = real(0);
-    tau_u = real(0);
-  }
+  const real izavg = real(1) / zavg;
+  const bool up = flux == 0;
+  tau_p = up ? izavg : real(0);
+  tau_u = up ? zavg : real(0);
 }
 
 // Ricker wavelet (1 - 2 a) exp(-a), a = (pi f0 (t - t0))^2 (c13 reading).
@@ -153,20 +156,29 @@ __device__ __forceinline__ double ricker(double f0, double tau) {
   const double a = (3.14159265358979323846 * f0 * tau) * (3.14159265358979323846 * f0 * tau);
   return (1.0 - 2.0 * a) * exp(-a);
 }
-// Source contribution to the pressure right-hand side at node n of element
-// (type, elem) at time t: sum over the sources placed in that element.
+// True when a point source lies in element (type, elem).
 __device__ __forceinline__ bool has_source(const DevMesh<real>& M, int type, int elem) {
   for (int s = 0; s < M.nsrc; ++s)
     if (M.src[s].type == type && M.src[s].elem == elem) return true;
   return false;
 }
-__device__ __forceinline__ real source_term(const DevMesh<real>& M, int type, int elem, int n, double t) {
-  double acc = 0.0;
+// Point-source forcing of element (type, elem) at time t added to the pressure
+// accumulators acc[c] of element nodes n0 + c (c < C, n0 + c < np), before the
+// kappa scaling: acc += w_s(t) g_s with g_s = (M^k)^{-1} l(x_s) and w_s the
+// source's Ricker amplitude.  The time function is evaluated once per source.
+template <int C>
+__device__ __forceinline__ void add_sources(const DevMesh<real>& M, int type, int elem, int n0, int np, double t,
+                                            real (&acc)[C]) {
+#pragma unroll 1
   for (int s = 0; s < M.nsrc; ++s) {
     const SourceDev& sd = M.src[s];
-    if (sd.type == type && sd.elem == elem) acc += sd.amp * ricker(sd.f0, t - sd.t0) * double(M.src_g[sd.goff + n]);
+    if (sd.type != type || sd.elem != elem) continue;
+    const real w = real(sd.amp * ricker(sd.f0, t - sd.t0));
+    const real* __restrict__ g = M.src_g + sd.goff + n0;
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+      if (n0 + c < np) acc[c] += w * g[c];
   }
-  return real(acc);
 }
 
 __global__ void k_clock(double* clock, double dt) {
@@ -241,10 +253,18 @@ template <int N>
 __host__ __device__ constexpr int wedge_smem_reals() {
   return WedgeSmem<N>::reals;
 }
-// bytes: two mbarriers + a status word ahead of the reals (16-byte aligned)
+// Element blocks per CTA.  The warps that work on slice j of the CTA's blocks
+// share an SM sub-partition and run the same straight-line code side by side,
+// so they share its instruction cache lines (measured faster at N = 3 FP32).
+template <int N>
+__host__ __device__ constexpr int wedge_bpc() {
+  return (sizeof(real) == 4 && N == 3) ? 2 : 1;
+}
+// bytes: per block two mbarriers and a status word (32 bytes), then per block
+// the reals (each block's slabs start 16-byte aligned)
 template <int N>
 __host__ __device__ constexpr int wedge_smem_bytes() {
-  return 32 + wedge_smem_reals<N>() * int(sizeof(real));
+  return wedge_bpc<N>() * (32 + wedge_smem_reals<N>() * int(sizeof(real)));
 }
 
 // Lemma 3.1 for the wedge of lane e: everything the stage needs, from the six
@@ -313,15 +333,20 @@ __device__ __forceinline__ void wedge_geometry(const DevMesh<real>& M, int e, re
 }
 
 template <int N>
-__global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 2 : 4) : 1)
+__global__ void __launch_bounds__(32 * (N + 1) * wedge_bpc<N>(), (sizeof(REAL) == 4) ? (N >= 4 ? 2 : 4 / wedge_bpc<N>()) : 1)
     k_wedge_stage(const StageArgs<real> A, bool rk) {
   constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
+  constexpr int BPC = wedge_bpc<N>();
   using SM = WedgeSmem<N>;
   const AllOps<N, real>& O = OPS<N>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // [0] state slab, [1] residual slab
-  int* status = reinterpret_cast<int*>(smem_raw + 16);
-  real* base = reinterpret_cast<real*>(smem_raw + 32);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // block sb of this CTA: warps sb (N+1) .. sb (N+1) + N, one per slice
+  const int sb = threadIdx.x / (32 * Nq);
+  const int j = (threadIdx.x >> 5) - sb * Nq;
+  const bool leader = int(threadIdx.x) == sb * 32 * Nq;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 32 * sb);  // [0] state slab, [1] residual slab
+  int* status = reinterpret_cast<int*>(smem_raw + 32 * sb + 16);
+  real* base = reinterpret_cast<real*>(smem_raw + 32 * BPC) + sb * SM::reals;
   real* sq = base + SM::q;
   real* sr = base + SM::r;
   real* sL = base + SM::L;
@@ -332,16 +357,26 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
   real* __restrict__ qout = A.q_out;
   real* __restrict__ resg = A.res;
   const int lane = threadIdx.x & 31;
-  const int j = threadIdx.x >> 5;
-  const int blk = blockIdx.x;
+  const int blk = blockIdx.x * BPC + sb;
+  const bool live = blk < M.nblk_w;  // false only for padding blocks of the last CTA
   const int e = blk * kB + lane;
   const int Kp = M.Kw_pad;
   constexpr uint32_t slab_bytes = uint32_t(4 * Np * kB * sizeof(real));
   const bool res_async = rk && stage_res<N>();
 #define GEO(item) sG[(item) * kB + lane]
 
+  if (!live) return;  // padding block of the last CTA
+  // the warps of one block synchronise among themselves (named barrier 1 + sb)
+  // (immediate barrier ids, so that only BPC + 1 hardware barriers are reserved)
+  auto block_sync = [&]() {
+    static_assert(BPC <= 4, "at most four blocks per CTA");
+    if (sb == 0) asm volatile("bar.sync 1, %0;" ::"n"(32 * Nq) : "memory");
+    else if (BPC > 1 && sb == 1) asm volatile("bar.sync 2, %0;" ::"n"(32 * Nq) : "memory");
+    else if (BPC > 2 && sb == 2) asm volatile("bar.sync 3, %0;" ::"n"(32 * Nq) : "memory");
+    else if (BPC > 3) asm volatile("bar.sync 4, %0;" ::"n"(32 * Nq) : "memory");
+  };
   // 0. bulk copies of the block's state (and residual) slabs; geometry meanwhile
-  if (threadIdx.x == 0) {
+  if (leader) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
@@ -380,17 +415,31 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
       sL[(i * (i + 1) / 2 + i) * kB + lane] = rsqrt_r(d);
     }
   }
+  // face neighbours, their impedances and the source flag, loaded while the
+  // slabs are in flight
+  const real zM = M.w_mat[2 * Kp + e];
   int qnbr[3], qcode[3];
+  real zPq[3];
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
     qnbr[ed] = M.w_nbr[(2 + ed) * Kp + e];
     qcode[ed] = M.w_code[(2 + ed) * Kp + e];
   }
-  if (threadIdx.x == 0) *status = mbar_wait_bounded(&bar[0], 0) ? 1 : 0;
-  __syncthreads();
-  if (*status == 0) {
-    // the state slab never arrived: report, let any residual copy drain, leave
-    if (threadIdx.x == 0) {
+#pragma unroll
+  for (int ed = 0; ed < 3; ++ed) zPq[ed] = qnbr[ed] < 0 ? zM : M.w_mat[2 * Kp + qnbr[ed]];
+  const int tnbr[2] = {M.w_nbr[0 * Kp + e], M.w_nbr[1 * Kp + e]};
+  const int tcode[2] = {M.w_code[0 * Kp + e], M.w_code[1 * Kp + e]};
+  real zPt[2];
+#pragma unroll
+  for (int fb = 0; fb < 2; ++fb)
+    zPt[fb] = tnbr[fb] < 0 ? zM
+                           : ((tcode[fb] & kCodeTet) ? M.t_mat[2 * M.Kt_pad + tnbr[fb]] : M.w_mat[2 * Kp + tnbr[fb]]);
+  const bool src = M.nsrc > 0 && has_source(M, 6, e);
+  if (leader) *status = mbar_wait_bounded(&bar[0], 0) ? 1 : 0;
+  block_sync();
+  if (*reinterpret_cast<volatile int*>(status) == 0) {
+    // the state slab never arrived: report, let any copy in flight drain, leave
+    if (leader) {
       atomicOr(M.err, kErrTimeout);
       if (res_async) mbar_wait_bounded(&bar[1], 0);
       mbar_wait_bounded(&bar[0], 0);
@@ -400,42 +449,39 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
 
   // 1. prologue: quadrilateral-face fluxes of slice j applied straight into the
   //    weak-form accumulators (every warp); triangle-face fluxes (warps 0 and N)
-  const real zM = M.w_mat[2 * Kp + e];
   real Wp[Nt], Wu[3][Nt];
 #pragma unroll
   for (int i = 0; i < Nt; ++i) Wp[i] = Wu[0][i] = Wu[1][i] = Wu[2][i] = real(0);
+  // neighbour traces of all three quadrilateral faces requested at once, one
+  // generic load per node whether the neighbour lies in this block (shared
+  // memory) or not (global memory); a boundary face reads its own trace,
+  // which the ghost state then replaces
+  Q4 nv[3][Nq];
+#pragma unroll
+  for (int ed = 0; ed < 3; ++ed) {
+    const int nbr = qnbr[ed];
+    const bool bnd = nbr < 0;
+    const int ep = bnd ? ed : qcode[ed] >> 1, rev = bnd ? 0 : qcode[ed] & 1;
+    const bool inblk = bnd || (nbr >> 5) == blk;
+    const real* base = inblk ? sq + ((bnd ? lane : (nbr & 31)) << 2) : qin + widx<N>(nbr >> 5, 0, nbr & 31);
+#pragma unroll
+    for (int m = 0; m < Nq; ++m) nv[ed][m] = ldx4(base + (j * Nt + O.tab.edge[ep][rev ? N - m : m]) * (kB * 4));
+  }
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
     const real nx = GEO(G_QNX0 + ed), ny = GEO(G_QNY0 + ed);
-    const int nbr = qnbr[ed], code = qcode[ed];
     real Fp[Nq], Fu[Nq];
-    if (nbr < 0) {
-      real tau_p, tau_u;
-      taus(A.flux, zM, zM, tau_p, tau_u);
+    real tau_p, tau_u;
+    taus(A.flux, zM, zPq[ed], tau_p, tau_u);
 #pragma unroll
-      for (int m = 0; m < Nq; ++m) {
-        const Q4 o = lds4(sq, j * Nt + edge_node(N, ed, m), lane);
-        real dp, dun;
-        boundary_jumps(A.bc, o.p, nx * o.u + ny * o.v, dp, dun);
-        penalty_flux(dp, dun, tau_p, tau_u, Fp[m], Fu[m]);
-      }
-    } else {
-      const real zP = M.w_mat[2 * Kp + nbr];
-      real tau_p, tau_u;
-      taus(A.flux, zM, zP, tau_p, tau_u);
-      const int ep = code >> 1, rev = code & 1;
-      const bool inblk = (nbr >> 5) == blk;
-      Q4 nv[Nq];
-#pragma unroll
-      for (int m = 0; m < Nq; ++m) {
-        const int nn = j * Nt + O.tab.edge[ep][rev ? N - m : m];
-        nv[m] = inblk ? lds4(sq, nn, nbr & 31) : ldg4(qin, widx<N>(nbr >> 5, nn, nbr & 31));
-      }
-#pragma unroll
-      for (int m = 0; m < Nq; ++m) {
-        const Q4 o = lds4(sq, j * Nt + edge_node(N, ed, m), lane);
-        penalty_flux(nv[m].p - o.p, nx * (nv[m].u - o.u) + ny * (nv[m].v - o.v), tau_p, tau_u, Fp[m], Fu[m]);
-      }
+    for (int m = 0; m < Nq; ++m) {
+      const Q4 o = lds4(sq, j * Nt + edge_node(N, ed, m), lane);
+      real bdp, bdun;
+      boundary_jumps(A.bc, o.p, nx * o.u + ny * o.v, bdp, bdun);
+      const bool bnd = qnbr[ed] < 0;
+      const real dp = bnd ? bdp : nv[ed][m].p - o.p;
+      const real dun = bnd ? bdun : nx * (nv[ed][m].u - o.u) + ny * (nv[ed][m].v - o.v);
+      penalty_flux(dp, dun, tau_p, tau_u, Fp[m], Fu[m]);
     }
     // W += M~_e F, M~_e = (L_e/4)(h_a Mea + h_b Meb) along the edge, identity in t
     const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
@@ -457,8 +503,6 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
     }
   }
   // triangle-face node fluxes (bottom then top), spread round-robin over the warps
-  const int tnbr[2] = {M.w_nbr[0 * Kp + e], M.w_nbr[1 * Kp + e]};
-  const int tcode[2] = {M.w_code[0 * Kp + e], M.w_code[1 * Kp + e]};
 #pragma unroll
   for (int t = 0; t < (2 * Nt + Nq - 1) / Nq; ++t) {
     const int idx = j + t * Nq;
@@ -470,34 +514,32 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
     const int code = tcode[fb];
     const Q4 o = lds4(sq, (fb ? N * Nt : 0) + k, lane);
     const real unM = nn0 * o.u + nn1 * o.v + nn2 * o.w;
-    real tau_p, tau_u, dp, dun;
-    if (nbr < 0) {
-      taus(A.flux, zM, zM, tau_p, tau_u);
-      boundary_jumps(A.bc, o.p, unM, dp, dun);
-    } else {
-      const bool ntet = (code & kCodeTet) != 0;
-      const int nf = (code >> 4) & 3;
-      const int nk = O.tab.tri_perm[code & 15][k];
-      const real zP = ntet ? M.t_mat[2 * M.Kt_pad + nbr] : M.w_mat[2 * Kp + nbr];
-      taus(A.flux, zM, zP, tau_p, tau_u);
-      Q4 nv;
-      if (ntet) {
-        nv = ldg4(qin, tidx<N>(M.tet_off, nbr >> 5, O.tab.tet_face[nf][nk], nbr & 31));
-      } else {
-        const int node = (nf ? N * Nt : 0) + nk;
-        nv = ((nbr >> 5) == blk) ? lds4(sq, node, nbr & 31) : ldg4(qin, widx<N>(nbr >> 5, node, nbr & 31));
-      }
-      dp = nv.p - o.p;
-      dun = nn0 * nv.u + nn1 * nv.v + nn2 * nv.w - unM;
-    }
+    real tau_p, tau_u, bdp, bdun;
+    taus(A.flux, zM, fb ? zPt[1] : zPt[0], tau_p, tau_u);
+    boundary_jumps(A.bc, o.p, unM, bdp, bdun);
+    // neighbour node: a tet's face node, or a wedge's bottom/top node (in this
+    // block's slab or in global memory); a boundary face reads its own node
+    const bool bnd = nbr < 0;
+    const bool ntet = !bnd && (code & kCodeTet) != 0;
+    const int nf = bnd ? fb : (code >> 4) & 3;
+    const int nk = bnd ? k : O.tab.tri_perm[code & 15][k];
+    const int nbe = bnd ? e : nbr;
+    const int node = ntet ? O.tab.tet_face[nf][nk] : (nf ? N * Nt : 0) + nk;
+    const bool inblk = !ntet && (nbe >> 5) == blk;
+    const real* a = inblk ? sq + ((node * kB + (nbe & 31)) << 2)
+                          : qin + (ntet ? tidx<N>(M.tet_off, nbe >> 5, node, nbe & 31) : widx<N>(nbe >> 5, node, nbe & 31));
+    const Q4 nv = ldx4(a);
+    const real dp = bnd ? bdp : nv.p - o.p;
+    const real dun = bnd ? bdun : nn0 * nv.u + nn1 * nv.v + nn2 * nv.w - unM;
     real Fp, Fu;
     penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
     sF[((2 * fb + 0) * Nt + k) * kB + lane] = Fp;
     sF[((2 * fb + 1) * Nt + k) * kB + lane] = Fu;
   }
-  __syncthreads();
+  block_sync();
 
   // 2. slice j of every element of the block
+  const real kappa = M.w_mat[0 * Kp + e], irho = M.w_mat[1 * Kp + e];
   {
     real dtr[Nq];
 #pragma unroll
@@ -617,16 +659,13 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(REAL) == 4) ? (N >= 4 ? 
     mbar_wait_bounded(&bar[1], 0);
     return;
   }
+  if (src) add_sources(M, 6, e, j * Nt, Np, *M.clock + A.c_stage * double(A.dt), Wp);
   if (e < M.Kw) {
-    const real kappa = M.w_mat[0 * Kp + e], irho = M.w_mat[1 * Kp + e];
-    const bool src = M.nsrc > 0 && has_source(M, 6, e);
-    const double tst = src ? *M.clock + A.c_stage * double(A.dt) : 0.0;
 #pragma unroll
     for (int i = 0; i < Nt; ++i) {
       const int n = j * Nt + i;
       const int64_t g = widx<N>(blk, n, lane);
       Q4 r{kappa * Wp[i], irho * Wu[0][i], irho * Wu[1][i], irho * Wu[2][i]};
-      if (src) r.p += source_term(M, 6, e, n, tst);
       if (rk) {
         const Q4 r0 = stage_res<N>() ? lds4(sr, n, lane) : ld4(resg, g);
         const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
@@ -821,15 +860,13 @@ __device__ __forceinline__ void tet_chunk_out(const StageArgs<real>& A, const Te
   if (e < M.Kt) {
     real* __restrict__ resg = A.res;
     real* __restrict__ qout = A.q_out;
-    const bool src = M.nsrc > 0 && has_source(M, 4, e);
-    const double tst = src ? *M.clock + A.c_stage * double(A.dt) : 0.0;
+    if (M.nsrc > 0 && has_source(M, 4, e)) add_sources(M, 4, e, I0, Np, *M.clock + A.c_stage * double(A.dt), ap);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       if (I0 + c < Np) {
         const int i = I0 + c;
         const int64_t gi = tidx<N>(M.tet_off, blockIdx.x, i, lane);
         Q4 r{g.kappa * ap[c], g.irho * au[0][c], g.irho * au[1][c], g.irho * au[2][c]};
-        if (src) r.p += source_term(M, 4, e, i, tst);
         if (rk) {
           const Q4 r0 = ld4(resg, gi);
           const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
@@ -1027,7 +1064,8 @@ int prepare_n() {
 template <int N>
 int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s) {
   if (a.m.nblk_w > 0) {
-    k_wedge_stage<N><<<a.m.nblk_w, 32 * (N + 1), wedge_smem_bytes<N>(), s>>>(a, rk);
+    constexpr int bpc = wedge_bpc<N>();
+    k_wedge_stage<N><<<(a.m.nblk_w + bpc - 1) / bpc, 32 * (N + 1) * bpc, wedge_smem_bytes<N>(), s>>>(a, rk);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return int(err);
   }
