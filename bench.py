@@ -44,9 +44,9 @@ def _peaks():
 WORKLOADS = {"full": (128, 16), "medium": (96, 16), "small": (32, 16)}
 
 
-def _traffic_per_launch():
+def _traffic_per_launch(mass):
     """DRAM bytes per wedge-stage launch from the committed ncu summary, or None
-    when the kernel source has changed since those counters were taken."""
+    when the kernel source or the mass mode differ from those of the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "wedge_stage_n3_layered524k_dram.md")
     src = os.path.join(ROOT, "paper_1607_03399_gb300", "csrc", "kernels.cuh")
@@ -55,8 +55,9 @@ def _traffic_per_launch():
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    fields = dict(line.split(":", 1) for line in text.splitlines() if line.startswith(("traffic_bytes", "kernel_source")))
-    if fields.get("kernel_source_sha256_16", "").strip() != sha:
+    fields = dict(line.split(":", 1) for line in text.splitlines()
+                  if line.startswith(("traffic_bytes", "kernel_source", "mass_mode")))
+    if fields.get("kernel_source_sha256_16", "").strip() != sha or fields.get("mass_mode", "").strip() != mass:
         return None
     return int(fields["traffic_bytes_per_launch"].strip())
 
@@ -68,13 +69,16 @@ def _mesh(ntri=128, nlayers=16):
     return m, c2, rho
 
 
-def _alg_bytes_per_stage(K, nverts, total_nodes, real_bytes=4):
+def _alg_bytes_per_stage(K, nverts, total_nodes, real_bytes=4, N=3, mass="stored"):
     """Minimum HBM bytes one fused stage must move: read q, read res, write
     res, write q (4 reals per field-DOF); per wedge 6 vertex ids, 5
-    neighbour ids, 5 orientation codes (int32) and 3 material reals; 3
+    neighbour ids, 5 orientation codes (int32) and 3 material reals, plus
+    the stored mass factor (Nt (Nt + 1) / 2 reals) in the stored mode; 3
     coordinates per vertex."""
     dof = 4 * total_nodes
-    return 4 * real_bytes * dof + K * (6 * 4 + 10 * 4 + 3 * real_bytes) + nverts * 3 * real_bytes
+    nt = (N + 1) * (N + 2) // 2
+    fac = nt * (nt + 1) // 2 if mass == "stored" else 0
+    return (4 * real_bytes * dof + K * (6 * 4 + 10 * 4 + (3 + fac) * real_bytes) + nverts * 3 * real_bytes)
 
 
 class Clocks:
@@ -196,10 +200,10 @@ print(json.dumps({{"dof": 4 * S.conn.total_nodes, "K": S.K, "sec": el}}))
     print(json.dumps(line), flush=True)
 
 
-def measure_order(N, args, torch, dev, m, c2, rho):
+def measure_order(N, args, torch, dev, m, c2, rho, mass):
     from paper_1607_03399_gb300.dg import Solver
     S = Solver(m.VX, m.EToV, m.etype, N, c2, rho, precision="f32", device=str(dev),
-               sources=[(0.5, 0.5, 0.5, 10.0, 0.1, 1.0)])
+               sources=[(0.5, 0.5, 0.5, 10.0, 0.1, 1.0)], mass=mass)
     q = np.random.default_rng(1).uniform(-1, 1, size=(4, S.total_nodes)).astype(np.float32)
     S.set_fields(q)
     dt = S.stable_dt(0.5)
@@ -234,7 +238,7 @@ def run_ours(args, rank, world):
     for N in orders:
         if world > 1:
             dist.barrier()
-        r = measure_order(N, args, torch, dev, m, c2, rho)
+        r = measure_order(N, args, torch, dev, m, c2, rho, args.mass)
         ms = r["ms"]
         if world > 1:
             t = torch.tensor([ms], device=dev)
@@ -262,6 +266,15 @@ def run_ours(args, rank, world):
                         "h2d_bytes_per_step": int(qh.numel() * 4), "d2h_bytes_per_step": int(qo.numel() * 4)}
         r["solver"].close()
         r["solver"] = None
+    # the headline order once more with the other way of applying the mass inverse
+    other = {"stored": "onthefly", "onthefly": "stored"}[args.mass]
+    alt = None
+    if not args.no_alt:
+        if world > 1:
+            dist.barrier()
+        alt = measure_order(orders[0], args, torch, dev, m, c2, rho, other)
+        alt["solver"].close()
+        alt["solver"] = None
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -272,16 +285,23 @@ def run_ours(args, rank, world):
     ms_step = r3["ms_max"] / args.steps
     value = r3["dof"] * 5 * args.steps / (r3["ms_max"] / 1e3) / 1e9 * world
     stage_s = r3["ms"] / 1e3 / (5 * args.steps)
-    alg = _alg_bytes_per_stage(K, nverts, r3["dof"] // 4)
+    alg = _alg_bytes_per_stage(K, nverts, r3["dof"] // 4, N=orders[0], mass=args.mass)
     achieved = alg / stage_s / 1e9
     by_order = {}
     for N, r in out.items():
         st = r["ms"] / 1e3 / (5 * args.steps)
-        a = _alg_bytes_per_stage(K, nverts, r["dof"] // 4)
+        a = _alg_bytes_per_stage(K, nverts, r["dof"] // 4, N=N, mass=args.mass)
         by_order[str(N)] = {"value": r["dof"] * 5 * args.steps / (r["ms_max"] / 1e3) / 1e9 * world,
                             "ms_per_step": r["ms_max"] / args.steps, "stage_us": st * 1e6,
                             "alg_bytes_per_stage": a, "achieved_gbs": a / st / 1e9,
                             "frac": a / st / 1e9 / peak, "dof": r["dof"]}
+    by_mass = {}
+    if alt is not None:
+        for mode, r in ((args.mass, r3), (other, alt)):
+            st = r["ms"] / 1e3 / (5 * args.steps)
+            a = _alg_bytes_per_stage(K, nverts, r["dof"] // 4, N=orders[0], mass=mode)
+            by_mass[mode] = {"value": r["dof"] * 5 * args.steps / (r["ms"] / 1e3) / 1e9, "stage_us": st * 1e6,
+                             "alg_bytes_per_stage": a, "frac": a / st / 1e9 / peak}
     cpu = _cpu_baseline() if (world == 1 and not args.no_cpu) else None
     line = {
         "metric": METRIC, "value": value, "unit": "GDOF-updates/s", "n_gpus": world, "steps": args.steps,
@@ -290,14 +310,16 @@ def run_ours(args, rank, world):
         "config": {"workload": WORKLOAD if args.workload == "full" else f"layered_wedges_2x{ntri}x{ntri}x{nlay}",
                    "wedges": K, "order": orders[0], "field_dof": r3["dof"],
                    "l2_flush": "inputs larger than L2 (3 state buffers of %.0f MB)" % (r3["dof"] * 4 / 1e6),
-                   "bc": "rigid", "flux": "upwind", "source": "Ricker f0=10 t0=0.1 at (0.5,0.5,0.5)"},
+                   "bc": "rigid", "flux": "upwind", "source": "Ricker f0=10 t0=0.1 at (0.5,0.5,0.5)",
+                   "mass": args.mass},
         "roofline": {"kernel": f"k_wedge_stage<{orders[0]}>", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": _traffic_per_launch() if (args.workload == "full" and orders[0] == 3) else None,
+                     "traffic": _traffic_per_launch(args.mass) if (args.workload == "full" and orders[0] == 3) else None,
                      "alg_bytes_per_launch": alg},
         "by_order": by_order,
+        "by_mass": by_mass or None,
         "e2e": r3.get("e2e"),
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": 6 * args.steps,  # per step: 5 stage launches and one clock launch
         "clocks": r3["clocks"],
         "cpu_baseline": cpu,
     }
@@ -316,6 +338,9 @@ def main():
     ap.add_argument("--orders", default="3,4", help="orders to measure; the first is the headline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--mass", default="stored", choices=["stored", "onthefly"],
+                    help="how the stage applies the wedge mass inverse (stored factor or factored in the stage)")
+    ap.add_argument("--no-alt", action="store_true", help="skip the headline order in the other mass mode")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -44,7 +44,7 @@
  * Work is issued asynchronously on the stream given to dg_bind.
  *
  * Call order: dg_mesh_create -> dg_set_order -> [dg_set_material]
- *   -> [dg_set_options] -> dg_device_bytes -> dg_bind -> dg_set_fields
+ *   -> [dg_set_options] -> [dg_set_mass_mode] -> dg_device_bytes -> dg_bind -> dg_set_fields
  *   -> dg_step / dg_rhs / dg_energy / dg_get_fields.
  * Setters after dg_bind return DG_ERR_STATE.  Several contexts may live in one
  * process; contexts with different (N, precision) must not run concurrently
@@ -79,6 +79,7 @@ enum { DG_TET = 4, DG_WEDGE = 6 };
 enum { DG_BC_DIRICHLET = 0, DG_BC_RIGID = 1 };
 enum { DG_FLUX_UPWIND = 0, DG_FLUX_CENTRAL = 1 };
 enum { DG_F32 = 0, DG_F64 = 1 };
+enum { DG_MASS_ONTHEFLY = 0, DG_MASS_STORED = 1 };
 
 /* Create a mesh context from vertices and element-to-vertex lists
  * (Section 2.1 "triangulation of the domain"; Section 3.2 vertex maps).
@@ -116,6 +117,20 @@ int dg_add_source(dg_ctx* ctx, double x, double y, double z, double f0, double t
  * (DG_F32: fields and arithmetic in float; DG_F64: double).
  * Default: rigid walls, upwind, DG_F32. */
 int dg_set_options(dg_ctx* ctx, int bc, int flux, int precision);
+
+/* How the stage applies (M^{tri,k})^{-1}, the inverse of the Jacobian-weighted
+ * triangle mass matrix M^{tri,k} = sum_a J_a M_a of each wedge (Section 4.2;
+ * the wedge mass matrix is M^{tri,k} (x) M^1D):
+ *   DG_MASS_ONTHEFLY  the stage factors M^{tri,k} = L L^T from the element's
+ *                     vertices every time (nothing per element is stored);
+ *   DG_MASS_STORED    the factor is computed once in double precision at
+ *                     dg_bind and kept in the mesh blob, (N+1)(N+2)/2 x
+ *                     ((N+1)(N+2)/2 + 1) / 2 reals per wedge, which the stage
+ *                     reads with the state.  Section 4.3 stores the related
+ *                     triangular lift (M^{tri,k})^{-1} M^tri per element.
+ * Both give the same operator up to rounding.  Default: DG_MASS_STORED.
+ * Before dg_bind.  Errors: DG_ERR_ARG (unknown mode), DG_ERR_STATE. */
+int dg_set_mass_mode(dg_ctx* ctx, int mode);
 
 /* Node counts: total wedge nodes and total tet nodes; the canonical layout
  * holds wedge_nodes + tet_nodes nodes. */

@@ -104,6 +104,7 @@ struct dg_ctx {
   std::vector<double> c2, rho;
   // options
   int bc = DG_BC_RIGID, flux = DG_FLUX_UPWIND, prec = DG_F32;
+  int mass = DG_MASS_STORED;
   // point sources (pressure equation)
   struct Source {
     int64_t elem;
@@ -288,7 +289,7 @@ double tet_stable_ratio(const dg_ctx* c, int64_t k) {
 // ----------------------------------------------------------------- blob
 struct BlobLayout {
   size_t w_vid, w_nbr, w_code, w_mat, w_canon, t_vid, t_nbr, t_code, t_mat, t_canon, vx, vy, vz, err, partials, energy,
-      tmass, wops, src, srcg, clock, total;
+      tmass, wops, src, srcg, clock, wfac, total;
 };
 
 BlobLayout blob_layout(const dg_ctx* c) {
@@ -325,6 +326,9 @@ BlobLayout blob_layout(const dg_ctx* c) {
   for (const auto& sc : c->sources) ng += sc.g.size();
   L.srcg = take((ng > 0 ? ng : 1) * rs);
   L.clock = take(sizeof(double));
+  // stored mass factors: per wedge block [Nt (Nt + 1) / 2][32], the stage's shared-memory layout
+  const int64_t nl = int64_t(nt_of(c->N)) * (nt_of(c->N) + 1) / 2;
+  L.wfac = take(c->mass == DG_MASS_STORED ? size_t(Kwp * nl) * rs : 0);
   L.total = o;
   return L;
 }
@@ -403,6 +407,37 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
     vy[v] = real(c->VX[v * 3 + 1]);
     vz[v] = real(c->VX[v * 3 + 2]);
   }
+  if (c->mass == DG_MASS_STORED) {
+    // M^{tri,k} = sum_a J_a M_a with J_a = A h_a / 2 at the three columns
+    // (Lemma 3.1, bi-unit reference: A = x_r y_s - x_s y_r), factored L L^T in
+    // double; entry (i, l <= i) at i (i + 1) / 2 + l with 1 / L_ii on the diagonal
+    const RefElems& R = *c->ref;
+    const int nt = R.Nt, nl = nt * (nt + 1) / 2;
+    real* fac = reinterpret_cast<real*>(blob.data() + L.wfac);
+    std::vector<double> Mk(size_t(nt) * nt), Lk(size_t(nt) * nt);
+    for (int64_t w = 0; w < Kwp; ++w) {
+      const int64_t k = c->wedges[w < Kw ? w : 0];
+      const int64_t* ev = &c->EToV[k * 6];
+      const double* P[6];
+      for (int v = 0; v < 6; ++v) P[v] = &c->VX[ev[v] * 3];
+      const double A = 0.25 * ((P[1][0] - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * (P[1][1] - P[0][1]));
+      double J[3];
+      for (int a = 0; a < 3; ++a) J[a] = 0.5 * A * (P[a + 3][2] - P[a][2]);
+      for (int i = 0; i < nt * nt; ++i) Mk[i] = J[0] * R.Ma[0].a[i] + J[1] * R.Ma[1].a[i] + J[2] * R.Ma[2].a[i];
+      for (int i = 0; i < nt; ++i) {
+        for (int l = 0; l <= i; ++l) {
+          double sum = Mk[size_t(i) * nt + l];
+          for (int q = 0; q < l; ++q) sum -= Lk[size_t(i) * nt + q] * Lk[size_t(l) * nt + q];
+          Lk[size_t(i) * nt + l] = (l < i) ? sum / Lk[size_t(l) * nt + l] : std::sqrt(sum);
+        }
+      }
+      const int64_t b = w / kB, lane = w % kB;
+      for (int i = 0; i < nt; ++i)
+        for (int l = 0; l <= i; ++l)
+          fac[(b * nl + i * (i + 1) / 2 + l) * kB + lane] =
+              real(l < i ? Lk[size_t(i) * nt + l] : 1.0 / Lk[size_t(i) * nt + i]);
+    }
+  }
 }
 
 template <typename real>
@@ -436,6 +471,7 @@ void fill_devmesh(const dg_ctx* c, const BlobLayout& L, DevMesh<real>& m) {
   m.src_g = reinterpret_cast<const real*>(b + L.srcg);
   m.nsrc = int(c->sources.size());
   m.clock = reinterpret_cast<double*>(b + L.clock);
+  m.w_fac = c->mass == DG_MASS_STORED ? reinterpret_cast<const real*>(b + L.wfac) : nullptr;
   m.tet_off = int64_t(m.nblk_w) * 4 * npw_of(c->N) * kB;
   m.total_nodes = c->wedge_nodes + c->tet_nodes;
 }
@@ -794,6 +830,14 @@ int dg_set_options(dg_ctx* c, int bc, int flux, int precision) {
   c->bc = bc;
   c->flux = flux;
   c->prec = precision;
+  return DG_OK;
+}
+
+int dg_set_mass_mode(dg_ctx* c, int mode) {
+  if (!c) return DG_ERR_ARG;
+  if (c->bound) return c->fail(DG_ERR_STATE, "dg_set_mass_mode after dg_bind");
+  if (mode != DG_MASS_ONTHEFLY && mode != DG_MASS_STORED) return c->fail(DG_ERR_ARG, "mass mode out of range");
+  c->mass = mode;
   return DG_OK;
 }
 

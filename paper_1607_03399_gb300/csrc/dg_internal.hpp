@@ -99,6 +99,7 @@ struct DevMesh {
   const real* src_g = nullptr;       // their vectors g
   int nsrc = 0;
   double* clock = nullptr;           // simulation time of the current step
+  const real* w_fac = nullptr;       // stored mass factors per wedge block, or null (factor in the stage)
 };
 
 template <typename real>

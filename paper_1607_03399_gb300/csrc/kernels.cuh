@@ -255,16 +255,18 @@ __host__ __device__ constexpr int wedge_smem_reals() {
 }
 // Element blocks per CTA.  The warps that work on slice j of the CTA's blocks
 // share an SM sub-partition and run the same straight-line code side by side,
-// so they share its instruction cache lines (measured faster at N = 3 FP32).
+// so they share its instruction cache lines.  With the mass factor computed in
+// the stage (a long serial factorisation on one warp per block) two blocks per
+// CTA measured faster at N = 3 FP32; with the stored factor, one.
 template <int N>
-__host__ __device__ constexpr int wedge_bpc() {
+__host__ __device__ constexpr int wedge_bpc_onthefly() {
   return (sizeof(real) == 4 && N == 3) ? 2 : 1;
 }
 // bytes: per block two mbarriers and a status word (32 bytes), then per block
 // the reals (each block's slabs start 16-byte aligned)
-template <int N>
+template <int N, int BPC>
 __host__ __device__ constexpr int wedge_smem_bytes() {
-  return wedge_bpc<N>() * (32 + wedge_smem_reals<N>() * int(sizeof(real)));
+  return BPC * (32 + wedge_smem_reals<N>() * int(sizeof(real)));
 }
 
 // Lemma 3.1 for the wedge of lane e: everything the stage needs, from the six
@@ -332,11 +334,10 @@ __device__ __forceinline__ void wedge_geometry(const DevMesh<real>& M, int e, re
   }
 }
 
-template <int N>
-__global__ void __launch_bounds__(32 * (N + 1) * wedge_bpc<N>(), (sizeof(REAL) == 4) ? (N >= 4 ? 2 : 4 / wedge_bpc<N>()) : 1)
+template <int N, int BPC>
+__global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >= 4 ? 2 : 4 / BPC) : 1)
     k_wedge_stage(const StageArgs<real> A, bool rk) {
   constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
-  constexpr int BPC = wedge_bpc<N>();
   using SM = WedgeSmem<N>;
   const AllOps<N, real>& O = OPS<N>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -376,19 +377,24 @@ __global__ void __launch_bounds__(32 * (N + 1) * wedge_bpc<N>(), (sizeof(REAL) =
     else if (BPC > 3) asm volatile("bar.sync 4, %0;" ::"n"(32 * Nq) : "memory");
   };
   // 0. bulk copies of the block's state (and residual) slabs; geometry meanwhile
+  constexpr int NL = Nt * (Nt + 1) / 2;
+  constexpr uint32_t fac_bytes = uint32_t(NL * kB * sizeof(real));
+  const bool stored = M.w_fac != nullptr;
   if (leader) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
-    mbar_expect_tx(&bar[0], slab_bytes);
+    mbar_expect_tx(&bar[0], slab_bytes + (stored ? fac_bytes : 0u));
     bulk_g2s(sq, qin + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[0]);
+    // stored mass factor: straight into the factor table with the state slab
+    if (stored) bulk_g2s(sL, M.w_fac + int64_t(blk) * NL * kB, fac_bytes, &bar[0]);
     if (res_async) {
       mbar_expect_tx(&bar[1], slab_bytes);
       bulk_g2s(sr, resg + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[1]);
     }
   }
   if (j == 0) wedge_geometry(M, e, sG, lane);
-  if (j == 1) {
+  if (j == 1 && !stored) {
     // While the slabs are in flight: M^{tri,k} = sum_a J_a M_a with
     // J_a = A h_a / 2 (Lemma 3.1) from the vertices; L L^T factor row by row,
     // inverse diagonal stored in place of the diagonal.
@@ -1053,8 +1059,12 @@ __global__ void k_energy_final(const double* __restrict__ partials, int n, doubl
 // one-time per device: opt in to the dynamic shared memory the stages use
 template <int N>
 int prepare_n() {
-  cudaError_t err = cudaFuncSetAttribute(k_wedge_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         wedge_smem_bytes<N>());
+  constexpr int b2 = wedge_bpc_onthefly<N>();
+  cudaError_t err = cudaFuncSetAttribute(k_wedge_stage<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         wedge_smem_bytes<N, 1>());
+  if (err == cudaSuccess && b2 != 1)
+    err = cudaFuncSetAttribute(k_wedge_stage<N, b2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               wedge_smem_bytes<N, b2>());
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_tet_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                tet_smem_reals<N>() * int(sizeof(real)));
@@ -1064,8 +1074,11 @@ int prepare_n() {
 template <int N>
 int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s) {
   if (a.m.nblk_w > 0) {
-    constexpr int bpc = wedge_bpc<N>();
-    k_wedge_stage<N><<<(a.m.nblk_w + bpc - 1) / bpc, 32 * (N + 1) * bpc, wedge_smem_bytes<N>(), s>>>(a, rk);
+    constexpr int b2 = wedge_bpc_onthefly<N>();
+    if (a.m.w_fac != nullptr || b2 == 1)
+      k_wedge_stage<N, 1><<<a.m.nblk_w, 32 * (N + 1), wedge_smem_bytes<N, 1>(), s>>>(a, rk);
+    else
+      k_wedge_stage<N, b2><<<(a.m.nblk_w + b2 - 1) / b2, 32 * (N + 1) * b2, wedge_smem_bytes<N, b2>(), s>>>(a, rk);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return int(err);
   }

@@ -25,8 +25,9 @@ DG_TET, DG_WEDGE = 4, 6
 DG_BC_DIRICHLET, DG_BC_RIGID = 0, 1
 DG_FLUX_UPWIND, DG_FLUX_CENTRAL = 0, 1
 DG_F32, DG_F64 = 0, 1
+DG_MASS_ONTHEFLY, DG_MASS_STORED = 0, 1
 
-EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_options", "dg_num_nodes",
+EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_options", "dg_set_mass_mode", "dg_num_nodes",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
            "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_sync", "dg_time",
            "dg_stable_dt", "dg_last_error", "dg_destroy")
@@ -56,6 +57,7 @@ def lib():
         "dg_set_material": (c_int, [P, P, P]),
         "dg_add_source": (c_int, [P, c_double, c_double, c_double, c_double, c_double, c_double]),
         "dg_set_options": (c_int, [P, c_int, c_int, c_int]),
+        "dg_set_mass_mode": (c_int, [P, c_int]),
         "dg_num_nodes": (c_int, [P, POINTER(c_int64), POINTER(c_int64)]),
         "dg_node_coords": (c_int, [P, P]),
         "dg_face_neighbors": (c_int, [P, P, POINTER(c_int64)]),
@@ -128,6 +130,10 @@ def dg_add_source(ctx, x: float, y: float, z: float, f0: float, t0: float, amp: 
 
 def dg_set_options(ctx, bc: int, flux: int, precision: int):
     _check(ctx, lib().dg_set_options(ctx, bc, flux, precision))
+
+
+def dg_set_mass_mode(ctx, mode: int):
+    _check(ctx, lib().dg_set_mass_mode(ctx, mode))
 
 
 def dg_num_nodes(ctx):
@@ -226,6 +232,7 @@ def dg_destroy(ctx):
 BC = {"dirichlet": DG_BC_DIRICHLET, "rigid": DG_BC_RIGID}
 FLUX = {"upwind": DG_FLUX_UPWIND, "central": DG_FLUX_CENTRAL}
 PREC = {"f32": DG_F32, "f64": DG_F64}
+MASS = {"onthefly": DG_MASS_ONTHEFLY, "stored": DG_MASS_STORED}
 
 
 class Solver:
@@ -235,7 +242,7 @@ class Solver:
     torch uint8 tensors and handed to the library by pointer."""
 
     def __init__(self, VX, EToV, etype, N: int, c2=None, rho=None, bc: str = "rigid", flux: str = "upwind",
-                 precision: str = "f32", device: str = "cuda:0", stream=None, sources=()):
+                 precision: str = "f32", device: str = "cuda:0", stream=None, sources=(), mass: str = "stored"):
         import torch
         self.torch = torch
         self.ctx = dg_mesh_create(VX, EToV, etype)
@@ -245,6 +252,7 @@ class Solver:
             if c2 is not None or rho is not None:
                 dg_set_material(self.ctx, np.ones(K) if c2 is None else c2, np.ones(K) if rho is None else rho)
             dg_set_options(self.ctx, BC[bc], FLUX[flux], PREC[precision])
+            dg_set_mass_mode(self.ctx, MASS[mass])
             for src in sources:       # (x, y, z, f0, t0, amp)
                 dg_add_source(self.ctx, *src)
             self.N = N

@@ -40,9 +40,9 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / np.linalg.norm(b))
 
 
-def _pair(mesh, N, precision, bc="rigid", flux="upwind", seed=3):
+def _pair(mesh, N, precision, bc="rigid", flux="upwind", seed=3, mass="stored"):
     c2, rho = I.random_material(mesh.K, seed, 1.0, 3.0, 0.5, 2.0)
-    S = Solver(mesh.VX, mesh.EToV, mesh.etype, N, c2, rho, bc=bc, flux=flux, precision=precision)
+    S = Solver(mesh.VX, mesh.EToV, mesh.etype, N, c2, rho, bc=bc, flux=flux, precision=precision, mass=mass)
     O = Oracle(mesh.VX, mesh.EToV, mesh.etype, N, c2, rho, bc=bc, flux=flux)
     return S, O
 
@@ -50,8 +50,9 @@ def _pair(mesh, N, precision, bc="rigid", flux="upwind", seed=3):
 @pytest.mark.parametrize("meshname", list(MESHES))
 @pytest.mark.parametrize("N", [1, 2, 3, 4])
 @pytest.mark.parametrize("bc,flux", [("rigid", "upwind"), ("dirichlet", "central")])
-def test_rhs_parity_f64(meshname, N, bc, flux):
-    S, O = _pair(MESHES[meshname](), N, "f64", bc, flux)
+@pytest.mark.parametrize("mass", ["stored", "onthefly"])
+def test_rhs_parity_f64(meshname, N, bc, flux, mass):
+    S, O = _pair(MESHES[meshname](), N, "f64", bc, flux, mass=mass)
     q = I.random_fields(S.total_nodes, 11)
     err = _rel(S.rhs(q).cpu().numpy(), O.rhs(q))
     S.close()
@@ -61,20 +62,22 @@ def test_rhs_parity_f64(meshname, N, bc, flux):
 @pytest.mark.parametrize("meshname", list(MESHES))
 @pytest.mark.parametrize("N", [1, 2, 3, 4])
 @pytest.mark.parametrize("bc,flux", [("rigid", "upwind"), ("dirichlet", "upwind"), ("rigid", "central")])
-def test_rhs_parity_f32(meshname, N, bc, flux):
-    S, O = _pair(MESHES[meshname](), N, "f32", bc, flux)
+@pytest.mark.parametrize("mass", ["stored", "onthefly"])
+def test_rhs_parity_f32(meshname, N, bc, flux, mass):
+    S, O = _pair(MESHES[meshname](), N, "f32", bc, flux, mass=mass)
     q = I.random_fields(S.total_nodes, 12).astype(np.float32)
     err = _rel(S.rhs(q).cpu().numpy(), O.rhs(q.astype(np.float64)))
     S.close()
     assert err <= 1e-5, err
 
 
-def test_config1_fp64_200_steps():
+@pytest.mark.parametrize("mass", ["stored", "onthefly"])
+def test_config1_fp64_200_steps(mass):
     """128-wedge wavy unit cube, N=3, rigid walls, upwind, standing mode,
     200 LSRK45 steps at CFL 0.5: state within 1e-12 of the oracle, energy
     within 1e-12 and non-increasing, L2 error to the exact solution small."""
     m = I.cube_wavy_mesh(4, 4, 0.03)
-    S = Solver(m.VX, m.EToV, m.etype, 3, precision="f64")
+    S = Solver(m.VX, m.EToV, m.etype, 3, precision="f64", mass=mass)
     O = Oracle(m.VX, m.EToV, m.etype, 3)
     q0 = I.standing_mode_unit_cube(O.conn.xyz, 0.0)
     dt = O.stable_dt(0.5)
@@ -167,15 +170,15 @@ def test_two_contexts_interleaved():
     B.close()
 
 
-@pytest.mark.parametrize("N", [3, 4])
-def test_full_size_sampled(N):
+@pytest.mark.parametrize("N,mass", [(3, "stored"), (4, "stored"), (3, "onthefly")])
+def test_full_size_sampled(N, mass):
     """The 524288-wedge layered workload (2x128x128 triangles x 16 bumpy
     layers, layered wavespeed) in FP32 as the benchmark runs it: sampled
     elements of one right-hand side and of one full LSRK45 step (5 stages)
     against oracle patches of radius 1 and 5."""
     m = I.bumpy_layered_mesh(128, 16)
     c2, rho = I.layered_wavespeed(m)
-    S = Solver(m.VX, m.EToV, m.etype, N, c2, rho, precision="f32")
+    S = Solver(m.VX, m.EToV, m.etype, N, c2, rho, precision="f32", mass=mass)
     Np = (N + 1) ** 2 * (N + 2) // 2
     rng = np.random.default_rng(N)
     q = rng.uniform(-1, 1, size=(4, S.total_nodes)).astype(np.float32)

@@ -146,5 +146,14 @@ def test_call_order_and_argument_errors():
         dg.dg_set_options(ctx, dg.DG_BC_DIRICHLET, dg.DG_FLUX_CENTRAL, dg.DG_F64)
         mb2, fb2 = dg.dg_device_bytes(ctx)
         assert fb2 == 2 * fb
+        # stored mass factors: Nt (Nt + 1) / 2 reals per (padded) wedge in the mesh blob
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_set_mass_mode(ctx, 2))
+        dg.dg_set_mass_mode(ctx, dg.DG_MASS_ONTHEFLY)
+        mb3, fb3 = dg.dg_device_bytes(ctx)
+        dg.dg_set_mass_mode(ctx, dg.DG_MASS_STORED)
+        mb4, fb4 = dg.dg_device_bytes(ctx)
+        assert fb3 == fb4 == fb2 and mb4 == mb2
+        nl = 6 * 7 // 2
+        assert mb4 - mb3 >= 32 * nl * 8 and mb4 - mb3 < 32 * nl * 8 + 256
     finally:
         dg.dg_destroy(ctx)
