@@ -71,14 +71,17 @@ def _mesh(ntri=128, nlayers=16):
 
 def _alg_bytes_per_stage(K, nverts, total_nodes, real_bytes=4, N=3, mass="stored"):
     """Minimum HBM bytes one fused stage must move: read q, read res, write
-    res, write q (4 reals per field-DOF); per wedge 6 vertex ids, 5
-    neighbour ids, 5 orientation codes (int32) and 3 material reals, plus
-    the stored mass factor (Nt (Nt + 1) / 2 reals) in the stored mode; 3
-    coordinates per vertex."""
+    res, write q (4 reals per field-DOF); per wedge 12 vertex coordinates,
+    5 neighbour ids and 5 orientation codes (int32) and 3 material reals;
+    in the stored mode the mass factor (Nt (Nt + 1) / 2 reals), otherwise
+    the 6 vertex ids and 3 coordinates per vertex the in-stage
+    factorisation gathers."""
     dof = 4 * total_nodes
     nt = (N + 1) * (N + 2) // 2
-    fac = nt * (nt + 1) // 2 if mass == "stored" else 0
-    return (4 * real_bytes * dof + K * (6 * 4 + 10 * 4 + (3 + fac) * real_bytes) + nverts * 3 * real_bytes)
+    per_wedge = 10 * 4 + (12 + 3) * real_bytes
+    if mass == "stored":
+        return 4 * real_bytes * dof + K * (per_wedge + nt * (nt + 1) // 2 * real_bytes)
+    return 4 * real_bytes * dof + K * (per_wedge + 6 * 4) + nverts * 3 * real_bytes
 
 
 class Clocks:

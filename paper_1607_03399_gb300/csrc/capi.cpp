@@ -289,7 +289,7 @@ double tet_stable_ratio(const dg_ctx* c, int64_t k) {
 // ----------------------------------------------------------------- blob
 struct BlobLayout {
   size_t w_vid, w_nbr, w_code, w_mat, w_canon, t_vid, t_nbr, t_code, t_mat, t_canon, vx, vy, vz, err, partials, energy,
-      tmass, wops, src, srcg, clock, wfac, total;
+      tmass, wops, src, srcg, clock, wfac, wxyz, total;
 };
 
 BlobLayout blob_layout(const dg_ctx* c) {
@@ -329,6 +329,8 @@ BlobLayout blob_layout(const dg_ctx* c) {
   // stored mass factors: per wedge block [Nt (Nt + 1) / 2][32], the stage's shared-memory layout
   const int64_t nl = int64_t(nt_of(c->N)) * (nt_of(c->N) + 1) / 2;
   L.wfac = take(c->mass == DG_MASS_STORED ? size_t(Kwp * nl) * rs : 0);
+  // per wedge block [12][32]: x, y of the three bottom vertices, z of the six
+  L.wxyz = take(size_t(Kwp) * 12 * rs);
   L.total = o;
   return L;
 }
@@ -350,6 +352,16 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
       const int64_t n = (w < Kw) ? c->nbr[k][f] : -1;
       w_nbr[f * Kwp + w] = (n < 0) ? -1 : int(c->local[n]);
       w_code[f * Kwp + w] = (n < 0) ? 0 : c->code[k][f];
+    }
+    {
+      real* xyz = reinterpret_cast<real*>(blob.data() + L.wxyz) + (w / kB) * 12 * kB + (w % kB);
+      const int64_t* ev = &c->EToV[k * 6];
+      for (int a = 0; a < 3; ++a) {
+        xyz[(0 + a) * kB] = real(c->VX[ev[a] * 3 + 0]);
+        xyz[(3 + a) * kB] = real(c->VX[ev[a] * 3 + 1]);
+        xyz[(6 + a) * kB] = real(c->VX[ev[a] * 3 + 2]);
+        xyz[(9 + a) * kB] = real(c->VX[ev[a + 3] * 3 + 2]);
+      }
     }
     const double cc = std::sqrt(c->c2[k]);
     w_mat[0 * Kwp + w] = real(c->rho[k] * c->c2[k]);
@@ -472,6 +484,7 @@ void fill_devmesh(const dg_ctx* c, const BlobLayout& L, DevMesh<real>& m) {
   m.nsrc = int(c->sources.size());
   m.clock = reinterpret_cast<double*>(b + L.clock);
   m.w_fac = c->mass == DG_MASS_STORED ? reinterpret_cast<const real*>(b + L.wfac) : nullptr;
+  m.w_xyz = reinterpret_cast<const real*>(b + L.wxyz);
   m.tet_off = int64_t(m.nblk_w) * 4 * npw_of(c->N) * kB;
   m.total_nodes = c->wedge_nodes + c->tet_nodes;
 }

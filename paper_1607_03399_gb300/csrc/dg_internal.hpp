@@ -100,6 +100,7 @@ struct DevMesh {
   int nsrc = 0;
   double* clock = nullptr;           // simulation time of the current step
   const real* w_fac = nullptr;       // stored mass factors per wedge block, or null (factor in the stage)
+  const real* w_xyz = nullptr;       // per wedge block [12][32]: bottom x, y; bottom and top z
 };
 
 template <typename real>

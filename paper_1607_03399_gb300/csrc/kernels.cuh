@@ -269,16 +269,16 @@ __host__ __device__ constexpr int wedge_smem_bytes() {
   return BPC * (32 + wedge_smem_reals<N>() * int(sizeof(real)));
 }
 
-// Lemma 3.1 for the wedge of lane e: everything the stage needs, from the six
-// vertices (bi-unit reference, x = sum_a lambda_a(r,s) [(1-t)/2 X_a + (1+t)/2 X_{a+3}]).
-__device__ __forceinline__ void wedge_geometry(const DevMesh<real>& M, int e, real* sG, int lane) {
-  const int Kp = M.Kw_pad;
-  const int vb0 = M.w_vid[0 * Kp + e], vb1 = M.w_vid[1 * Kp + e], vb2 = M.w_vid[2 * Kp + e];
-  const int vt0 = M.w_vid[3 * Kp + e], vt1 = M.w_vid[4 * Kp + e], vt2 = M.w_vid[5 * Kp + e];
-  const real x0 = M.vx[vb0], x1 = M.vx[vb1], x2 = M.vx[vb2];
-  const real y0 = M.vy[vb0], y1 = M.vy[vb1], y2 = M.vy[vb2];
-  const real zb0 = M.vz[vb0], zb1 = M.vz[vb1], zb2 = M.vz[vb2];
-  const real zt0 = M.vz[vt0], zt1 = M.vz[vt1], zt2 = M.vz[vt2];
+// Lemma 3.1 for the wedge of this lane: everything the stage needs, from the
+// six vertices (bi-unit reference, x = sum_a lambda_a(r,s) [(1-t)/2 X_a + (1+t)/2 X_{a+3}]).
+// The coordinates arrive in the first 12 items of the table ([x_a][y_a][zb_a][zt_a],
+// a = 0..2, one column per lane) and are replaced by the factors.
+__device__ __forceinline__ void wedge_geometry(real* sG, int lane) {
+  const real x0 = sG[0 * kB + lane], x1 = sG[1 * kB + lane], x2 = sG[2 * kB + lane];
+  const real y0 = sG[3 * kB + lane], y1 = sG[4 * kB + lane], y2 = sG[5 * kB + lane];
+  const real zb0 = sG[6 * kB + lane], zb1 = sG[7 * kB + lane], zb2 = sG[8 * kB + lane];
+  const real zt0 = sG[9 * kB + lane], zt1 = sG[10 * kB + lane], zt2 = sG[11 * kB + lane];
+  __syncwarp();
   auto put = [&](int item, real v) { sG[item * kB + lane] = v; };
   const real xr = real(0.5) * (x1 - x0), xs = real(0.5) * (x2 - x0);
   const real yr = real(0.5) * (y1 - y0), ys = real(0.5) * (y2 - y0);
@@ -302,33 +302,36 @@ __device__ __forceinline__ void wedge_geometry(const DevMesh<real>& M, int e, re
   put(G_TY0, zr0 * xs - xr * zs0);
   put(G_TY1, zr1 * xs - xr * zs1);
   {
+    // triangle faces: n = c / |c| with c the edge cross product, J_f = |c| / 4
     const real ax = x1 - x0, ay = y1 - y0, bx = x2 - x0, by = y2 - y0;
     real az = zb1 - zb0, bz = zb2 - zb0;
     real cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
-    real nrm = sqrt_r(cx * cx + cy * cy + cz * cz);
-    put(G_JFB, real(0.25) * nrm);  // J_f = area / 2
-    put(G_NB0, -cx / nrm);
-    put(G_NB1, -cy / nrm);
-    put(G_NB2, -cz / nrm);
+    real cc = cx * cx + cy * cy + cz * cz, ic = rsqrt_r(cc);
+    put(G_JFB, real(0.25) * cc * ic);
+    put(G_NB0, -cx * ic);
+    put(G_NB1, -cy * ic);
+    put(G_NB2, -cz * ic);
     az = zt1 - zt0;
     bz = zt2 - zt0;
     cx = ay * bz - az * by;
     cy = az * bx - ax * bz;
     cz = ax * by - ay * bx;
-    nrm = sqrt_r(cx * cx + cy * cy + cz * cz);
-    put(G_JFT, real(0.25) * nrm);
-    put(G_NT0, cx / nrm);
-    put(G_NT1, cy / nrm);
-    put(G_NT2, cz / nrm);
+    cc = cx * cx + cy * cy + cz * cz;
+    ic = rsqrt_r(cc);
+    put(G_JFT, real(0.25) * cc * ic);
+    put(G_NT0, cx * ic);
+    put(G_NT1, cy * ic);
+    put(G_NT2, cz * ic);
   }
   const real xx[3] = {x0, x1, x2}, yy[3] = {y0, y1, y2}, hh[3] = {h0, h1, h2};
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
     const int ia = ed, ib = (ed + 1) % 3;
     const real dx = xx[ib] - xx[ia], dy = yy[ib] - yy[ia];
-    const real Le = sqrt_r(dx * dx + dy * dy);
-    put(G_QNX0 + ed, dy / Le);  // horizontal outward normal of the quad face
-    put(G_QNY0 + ed, -dx / Le);
+    const real ll = dx * dx + dy * dy, il = rsqrt_r(ll);
+    const real Le = ll * il;
+    put(G_QNX0 + ed, dy * il);  // horizontal outward normal of the quad face
+    put(G_QNY0 + ed, -dx * il);
     put(G_QCA0 + ed, real(0.25) * Le * hh[ia]);  // M~_e = ca Mea + cb Meb
     put(G_QCB0 + ed, real(0.25) * Le * hh[ib]);
   }
@@ -345,8 +348,9 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
   const int sb = threadIdx.x / (32 * Nq);
   const int j = (threadIdx.x >> 5) - sb * Nq;
   const bool leader = int(threadIdx.x) == sb * 32 * Nq;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 32 * sb);  // [0] state slab, [1] residual slab
-  int* status = reinterpret_cast<int*>(smem_raw + 32 * sb + 16);
+  // [0] state slab (and stored factor), [1] residual slab, [2] vertex coordinates
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 32 * sb);
+  int* status = reinterpret_cast<int*>(smem_raw + 32 * sb + 24);
   real* base = reinterpret_cast<real*>(smem_raw + 32 * BPC) + sb * SM::reals;
   real* sq = base + SM::q;
   real* sr = base + SM::r;
@@ -380,10 +384,15 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
   constexpr int NL = Nt * (Nt + 1) / 2;
   constexpr uint32_t fac_bytes = uint32_t(NL * kB * sizeof(real));
   const bool stored = M.w_fac != nullptr;
+  constexpr uint32_t xyz_bytes = uint32_t(12 * kB * sizeof(real));
   if (leader) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
     fence_mbar_init();
+    // the block's vertex coordinates first (the geometry warp waits on them alone)
+    mbar_expect_tx(&bar[2], xyz_bytes);
+    bulk_g2s(sG, M.w_xyz + int64_t(blk) * 12 * kB, xyz_bytes, &bar[2]);
     mbar_expect_tx(&bar[0], slab_bytes + (stored ? fac_bytes : 0u));
     bulk_g2s(sq, qin + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[0]);
     // stored mass factor: straight into the factor table with the state slab
@@ -393,7 +402,13 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
       bulk_g2s(sr, resg + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[1]);
     }
   }
-  if (j == 0) wedge_geometry(M, e, sG, lane);
+  // every lane of the geometry warp observes the coordinate copy itself
+  bool geo_ok = true;
+  __syncwarp();
+  if (j == 0) {
+    geo_ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[2], 0));
+    if (geo_ok) wedge_geometry(sG, lane);
+  }
   if (j == 1 && !stored) {
     // While the slabs are in flight: M^{tri,k} = sum_a J_a M_a with
     // J_a = A h_a / 2 (Lemma 3.1) from the vertices; L L^T factor row by row,
@@ -441,7 +456,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
     zPt[fb] = tnbr[fb] < 0 ? zM
                            : ((tcode[fb] & kCodeTet) ? M.t_mat[2 * M.Kt_pad + tnbr[fb]] : M.w_mat[2 * Kp + tnbr[fb]]);
   const bool src = M.nsrc > 0 && has_source(M, 6, e);
-  if (leader) *status = mbar_wait_bounded(&bar[0], 0) ? 1 : 0;
+  if (leader) *status = (mbar_wait_bounded(&bar[0], 0) && geo_ok) ? 1 : 0;
   block_sync();
   if (*reinterpret_cast<volatile int*>(status) == 0) {
     // the state slab never arrived: report, let any copy in flight drain, leave
@@ -449,6 +464,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
       atomicOr(M.err, kErrTimeout);
       if (res_async) mbar_wait_bounded(&bar[1], 0);
       mbar_wait_bounded(&bar[0], 0);
+      mbar_wait_bounded(&bar[2], 0);
     }
     return;
   }
