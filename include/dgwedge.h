@@ -190,6 +190,16 @@ int dg_rhs(dg_ctx* ctx, const void* d_q, void* d_rhs);
  * (bounded waits) surface at the next synchronising call. */
 int dg_step(dg_ctx* ctx, double dt, int64_t nsteps);
 
+/* Per-element-type timing of the fused stage (diagnostic, not in the paper):
+ * launches the wedge stage kernel nrep times, then the tet stage kernel nrep
+ * times, on the bound stream, each as a full Runge-Kutta stage of the
+ * current state with coefficients a = 1, b = 0 and dt = 0 (the state is not
+ * changed; the residual is rewritten with itself plus 0 * rhs), and returns
+ * the mean device time per launch in microseconds from CUDA events (0 for a
+ * type the mesh does not have).  Synchronous.  Errors: DG_ERR_ARG (nrep < 1,
+ * null outputs), DG_ERR_STATE (before dg_set_fields), DG_ERR_CUDA. */
+int dg_stage_times(dg_ctx* ctx, int nrep, double* us_wedge, double* us_tet);
+
 /* Discrete energy E = 1/2 sum_k (p^T M^k p / kappa_k + rho_k sum_c u_c^T M^k u_c)
  * with the scheme's exact mass matrices (Section 4.1), accumulated in double.
  * Synchronises the stream.  Returns DG_ERR_NONFINITE if E is not finite and

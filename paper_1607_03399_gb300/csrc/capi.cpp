@@ -289,7 +289,7 @@ double tet_stable_ratio(const dg_ctx* c, int64_t k) {
 // ----------------------------------------------------------------- blob
 struct BlobLayout {
   size_t w_vid, w_nbr, w_code, w_mat, w_canon, t_vid, t_nbr, t_code, t_mat, t_canon, vx, vy, vz, err, partials, energy,
-      tmass, wops, src, srcg, clock, wfac, wxyz, total;
+      tmass, wops, src, srcg, clock, wfac, wxyz, txyz, tops, total;
 };
 
 BlobLayout blob_layout(const dg_ctx* c) {
@@ -331,6 +331,14 @@ BlobLayout blob_layout(const dg_ctx* c) {
   L.wfac = take(c->mass == DG_MASS_STORED ? size_t(Kwp * nl) * rs : 0);
   // per wedge block [12][32]: x, y of the three bottom vertices, z of the six
   L.wxyz = take(size_t(Kwp) * 12 * rs);
+  // per tet block [12][32]: x, y, z of the four vertices
+  L.txyz = take(size_t(Ktp) * 12 * rs);
+  // tet stage operators in the stage's shared-memory image: [l][i] (D_r, D_s, D_t, 0)(i, l),
+  // then the lift transposed [f Nt + k][i] with rows padded to an even length
+  {
+    const int np = npt_of(c->N), npe = (np + 1) / 2 * 2;
+    L.tops = take(size_t(4 * np * np + 4 * nt_of(c->N) * npe) * rs);
+  }
   L.total = o;
   return L;
 }
@@ -382,6 +390,11 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
       t_nbr[f * Ktp + t] = (n < 0) ? -1 : int(c->local[n]);
       t_code[f * Ktp + t] = (n < 0) ? 0 : c->code[k][f];
     }
+    {
+      real* xyz = reinterpret_cast<real*>(blob.data() + L.txyz) + (t / kB) * 12 * kB + (t % kB);
+      for (int v = 0; v < 4; ++v)
+        for (int d = 0; d < 3; ++d) xyz[(v * 3 + d) * kB] = real(c->VX[c->EToV[k * 6 + v] * 3 + d]);
+    }
     const double cc = std::sqrt(c->c2[k]);
     t_mat[0 * Ktp + t] = real(c->rho[k] * c->c2[k]);
     t_mat[1 * Ktp + t] = real(1.0 / c->rho[k]);
@@ -409,6 +422,22 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
   real* tm = reinterpret_cast<real*>(blob.data() + L.tmass);
   for (int i = 0; i < c->ref->Npt * c->ref->Npt; ++i) tm[i] = real(c->ref->tM.a[i]);
   // wedge energy operators: barycentric-weighted triangle masses, then the line mass
+  {
+    const RefElems& R = *c->ref;
+    const int np = R.Npt, npe = (np + 1) / 2 * 2, nt = R.Nt;
+    real* to = reinterpret_cast<real*>(blob.data() + L.tops);
+    for (int l = 0; l < np; ++l)
+      for (int i = 0; i < np; ++i) {
+        real* v = to + (size_t(l) * np + i) * 4;
+        v[0] = real(R.tDr(i, l));
+        v[1] = real(R.tDs(i, l));
+        v[2] = real(R.tDt(i, l));
+        v[3] = real(0);
+      }
+    real* lt = to + size_t(4) * np * np;
+    for (int fk = 0; fk < 4 * nt; ++fk)
+      for (int i = 0; i < npe; ++i) lt[size_t(fk) * npe + i] = i < np ? real(R.tLIFT(i, fk)) : real(0);
+  }
   real* wo = reinterpret_cast<real*>(blob.data() + L.wops);
   const int nt2 = c->ref->Nt * c->ref->Nt;
   for (int a = 0; a < 3; ++a)
@@ -485,6 +514,8 @@ void fill_devmesh(const dg_ctx* c, const BlobLayout& L, DevMesh<real>& m) {
   m.clock = reinterpret_cast<double*>(b + L.clock);
   m.w_fac = c->mass == DG_MASS_STORED ? reinterpret_cast<const real*>(b + L.wfac) : nullptr;
   m.w_xyz = reinterpret_cast<const real*>(b + L.wxyz);
+  m.t_xyz = reinterpret_cast<const real*>(b + L.txyz);
+  m.t_ops = reinterpret_cast<const real*>(b + L.tops);
   m.tet_off = int64_t(m.nblk_w) * 4 * npw_of(c->N) * kB;
   m.total_nodes = c->wedge_nodes + c->tet_nodes;
 }
@@ -1145,6 +1176,52 @@ int dg_step(dg_ctx* c, double dt, int64_t nsteps) {
     c->t += dt;
   }
   return DG_OK;
+}
+
+int dg_stage_times(dg_ctx* c, int nrep, double* us_w, double* us_t) {
+  if (!c) return DG_ERR_ARG;
+  if (nrep < 1 || !us_w || !us_t) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_stage_times before dg_bind");
+  int rc = ensure_ops(c);
+  if (rc) return rc;
+  *us_w = *us_t = 0.0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  if (e != cudaSuccess) {
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
+    return cuda_fail(c, e, "event create");
+  }
+  const DevMesh<float> m32 = c->m32;
+  const DevMesh<double> m64 = c->m64;
+  for (int type = 0; type < 2 && rc == DG_OK; ++type) {
+    // restrict the stage to one element type (the other's blocks are not launched)
+    if (type == 0) {
+      c->m32.nblk_t = c->m64.nblk_t = 0;
+      if (m32.nblk_w == 0) continue;
+    } else {
+      c->m32 = m32;
+      c->m64 = m64;
+      c->m32.nblk_w = c->m64.nblk_w = 0;
+      if (m32.nblk_t == 0) continue;
+    }
+    e = cudaEventRecord(ev[0], c->stream);
+    for (int r = 0; r < nrep && rc == DG_OK && e == cudaSuccess; ++r)
+      rc = launch_stage(c, c->d_q[c->cur], c->d_q[1 - c->cur], c->d_res, 1.0, 0.0, 0.0, true, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    if (e != cudaSuccess && rc == DG_OK) rc = cuda_fail(c, e, "stage timing");
+    (type == 0 ? *us_w : *us_t) = 1e3 * double(ms) / nrep;
+  }
+  c->m32 = m32;
+  c->m64 = m64;
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (rc) return rc;
+  return check_device_error(c);
 }
 
 int dg_energy(dg_ctx* c, double* E) {

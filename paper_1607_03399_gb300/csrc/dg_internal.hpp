@@ -101,6 +101,8 @@ struct DevMesh {
   double* clock = nullptr;           // simulation time of the current step
   const real* w_fac = nullptr;       // stored mass factors per wedge block, or null (factor in the stage)
   const real* w_xyz = nullptr;       // per wedge block [12][32]: bottom x, y; bottom and top z
+  const real* t_xyz = nullptr;       // per tet block [12][32]: x, y, z of the four vertices
+  const real* t_ops = nullptr;       // tet stage operators, shared-memory image
 };
 
 template <typename real>

@@ -121,6 +121,27 @@ __device__ __forceinline__ Q4 ldx4(const real* a) {
     return Q4{real(t0.x), real(t0.y), real(t1.x), real(t1.y)};
   }
 }
+// shared-memory operator records: (a, b, c, d) in natural order -> Q4{a, b, c, d}
+__device__ __forceinline__ Q4 ldop4(const real* a) {
+  if constexpr (sizeof(real) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(a);
+    return Q4{real(t.x), real(t.y), real(t.z), real(t.w)};
+  } else {
+    const double2 t0 = reinterpret_cast<const double2*>(a)[0], t1 = reinterpret_cast<const double2*>(a)[1];
+    return Q4{real(t0.x), real(t0.y), real(t1.x), real(t1.y)};
+  }
+}
+__device__ __forceinline__ void ldop2(const real* a, real& x, real& y) {
+  if constexpr (sizeof(real) == 4) {
+    const float2 t = *reinterpret_cast<const float2*>(a);
+    x = real(t.x);
+    y = real(t.y);
+  } else {
+    const double2 t = *reinterpret_cast<const double2*>(a);
+    x = real(t.x);
+    y = real(t.y);
+  }
+}
 __device__ __forceinline__ void st4(real* q, int64_t idx, const Q4& v) {
   if constexpr (sizeof(real) == 4) {
     *reinterpret_cast<float4*>(q + idx) = make_float4(float(v.p), float(v.u), float(v.v), float(v.w));
@@ -206,17 +227,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// One poll of the phase; the thread may be suspended for up to the hint
+// (1 us) while the phase is incomplete, so waiting threads do not spin.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(phase)
+      : "r"(smem_u32(bar)), "r"(phase), "n"(1000)
       : "memory");
   return ok != 0;
 }
-// About a second of polling at most (each try_wait may itself suspend briefly).
-constexpr long long kWaitLimit = 1ll << 22;
+// About a second of polling at most (each poll suspends for at most ~1 us).
+constexpr long long kWaitLimit = 1ll << 20;
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
   for (long long it = 0; it < kWaitLimit; ++it)
     if (mbar_try_wait(bar, phase)) return true;
@@ -704,237 +727,278 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
 }
 
 // ---------------------------------------------------------------------------
-// tet stage: 32 tets x 4 warps per CTA.  Warp f computes the fluxes of face
-// f for the 32 elements; after a barrier warp w produces output nodes
-// [w C, w C + C) of every element (C = ceil(Np/4)).
+// tet stage: lane = tet of a 32-tet block, one block per warp, TPC blocks per
+// CTA.  The CTA copies the tet operators into shared memory once ([l][i]
+// (D_r, D_s, D_t)(i, l) records and the transposed lift); each warp moves its
+// block's vertex coordinates and state slab with bulk copies on its own
+// mbarriers, evaluates the affine geometry and the 4 N_t face fluxes (a
+// per-warp table, each thread reading back only its own), then the volume
+// terms and the lift for the output nodes in passes of C nodes, fused with the
+// update.  Warps never wait for one another after the start.
 // ---------------------------------------------------------------------------
+#ifndef TET_PASSES
+#define TET_PASSES(N) ((N) <= 2 ? 1 : (N) == 3 ? 2 : 3)
+#endif
 template <int N>
-__host__ __device__ constexpr int tet_chunk() {
-  return (npt_of(N) + 3) / 4;
+__host__ __device__ constexpr int tet_passes() {
+  return TET_PASSES(N);
+}
+// output nodes per pass, even (the lift is read in pairs)
+template <int N>
+__host__ __device__ constexpr int tet_pass_nodes() {
+  return ((npt_of(N) + tet_passes<N>() - 1) / tet_passes<N>() + 1) / 2 * 2;
+}
+// blocks (warps) per CTA: as many as two CTAs per SM hold in shared memory
+template <int N>
+__host__ __device__ constexpr int tet_bpc() {
+  return sizeof(real) == 4 ? (N >= 4 ? 2 : 4) : (N >= 4 ? 1 : 2);
 }
 template <int N>
-__host__ __device__ constexpr int tet_smem_reals() {
-  return 4 * npt_of(N) * kB + 8 * nt_of(N) * kB;
+__host__ __device__ constexpr int tet_npe() {
+  return (npt_of(N) + 1) / 2 * 2;
+}
+template <int N>
+__host__ __device__ constexpr int tet_ops_reals() {
+  return 4 * npt_of(N) * npt_of(N) + 4 * nt_of(N) * tet_npe<N>();
+}
+// per warp: slab [Np][32][4], fluxes [4 faces][2][Nt][32], vertex coordinates [12][32]
+template <int N>
+__host__ __device__ constexpr int tet_warp_reals() {
+  return 4 * npt_of(N) * kB + 8 * nt_of(N) * kB + 12 * kB;
+}
+// 128-byte header (operator mbarrier, then two mbarriers per warp), operators, warp regions
+template <int N>
+__host__ __device__ constexpr int tet_smem_bytes() {
+  return 128 + (tet_ops_reals<N>() + tet_bpc<N>() * tet_warp_reals<N>()) * int(sizeof(real));
 }
 
-struct TetGeom {
-  real Ri[3][3];   // d r_m / d x_d
-  real n[4][3];    // outward unit normals
-  real sJ[4];      // J_f / J
-  real kappa, irho, zM;
-};
-
 template <int N>
-__device__ __forceinline__ void tet_geometry(const DevMesh<real>& M, int e, TetGeom& g, real X[4][3]) {
+__global__ void __launch_bounds__(32 * tet_bpc<N>(), 2)
+    k_tet_stage(const StageArgs<real> A, bool rk) {
+  constexpr int Np = npt_of(N), Nt = nt_of(N), C = tet_pass_nodes<N>(), BPC = tet_bpc<N>(), NPE = tet_npe<N>();
+  static_assert(8 + 16 * BPC <= 128, "header");
+  const AllOps<N, real>& O = OPS<N>();
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* obar = reinterpret_cast<uint64_t*>(smem_raw);
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 8 + 16 * wid);  // [0] coordinates, [1] state slab
+  real* sOp = reinterpret_cast<real*>(smem_raw + 128);
+  real* sL = sOp + 4 * Np * Np;  // transposed lift [4 Nt][NPE]
+  real* sq = sOp + tet_ops_reals<N>() + wid * tet_warp_reals<N>();
+  real* sF = sq + 4 * Np * kB;
+  real* sX = sF + 8 * Nt * kB;
+  const DevMesh<real>& M = A.m;
+  const int blk = blockIdx.x * BPC + wid;
+  const int e = blk * kB + lane;
   const int Kp = M.Kt_pad;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int id = M.t_vid[v * Kp + e];
-    X[v][0] = M.vx[id];
-    X[v][1] = M.vy[id];
-    X[v][2] = M.vz[id];
+  constexpr uint32_t slab_bytes = uint32_t(4 * Np * kB * sizeof(real)), xyz_bytes = uint32_t(12 * kB * sizeof(real));
+  constexpr uint32_t ops_bytes = uint32_t(tet_ops_reals<N>() * sizeof(real));
+  if (threadIdx.x == 0) {
+    mbar_init(obar, 1);
+    for (int w = 0; w < BPC; ++w) {
+      mbar_init(reinterpret_cast<uint64_t*>(smem_raw + 8 + 16 * w), 1);
+      mbar_init(reinterpret_cast<uint64_t*>(smem_raw + 16 + 16 * w), 1);
+    }
+    fence_mbar_init();
+    mbar_expect_tx(obar, ops_bytes);
+    bulk_g2s(sOp, M.t_ops, ops_bytes, obar);
   }
-  real G[3][3];  // G[d][m] = d x_d / d r_m, affine map x = sum_v lambda_v X_v
-#pragma unroll
-  for (int d = 0; d < 3; ++d)
-#pragma unroll
-    for (int m = 0; m < 3; ++m) G[d][m] = real(0.5) * (X[m + 1][d] - X[0][d]);
-  const real J = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) - G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
-                 G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
-  const real iJ = real(1) / J;
-  g.Ri[0][0] = (G[1][1] * G[2][2] - G[1][2] * G[2][1]) * iJ;
-  g.Ri[0][1] = (G[0][2] * G[2][1] - G[0][1] * G[2][2]) * iJ;
-  g.Ri[0][2] = (G[0][1] * G[1][2] - G[0][2] * G[1][1]) * iJ;
-  g.Ri[1][0] = (G[1][2] * G[2][0] - G[1][0] * G[2][2]) * iJ;
-  g.Ri[1][1] = (G[0][0] * G[2][2] - G[0][2] * G[2][0]) * iJ;
-  g.Ri[1][2] = (G[0][2] * G[1][0] - G[0][0] * G[1][2]) * iJ;
-  g.Ri[2][0] = (G[1][0] * G[2][1] - G[1][1] * G[2][0]) * iJ;
-  g.Ri[2][1] = (G[0][1] * G[2][0] - G[0][0] * G[2][1]) * iJ;
-  g.Ri[2][2] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) * iJ;
-  constexpr int fv[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
-  constexpr int fo[4] = {3, 2, 0, 1};
+  __syncthreads();
+  if (blk >= M.nblk_t) {  // padding block of the last CTA
+    if (threadIdx.x == 0) mbar_wait_bounded(obar, 0);
+    return;
+  }
+  if (lane == 0) {
+    mbar_expect_tx(&bar[0], xyz_bytes);
+    bulk_g2s(sX, M.t_xyz + int64_t(blk) * 12 * kB, xyz_bytes, &bar[0]);
+    mbar_expect_tx(&bar[1], slab_bytes);
+    bulk_g2s(sq, A.q_in + M.tet_off + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[1]);
+  }
+  __syncwarp();
+  // face neighbours, impedances, material and the source flag while the copies fly
+  const real kappa = M.t_mat[0 * Kp + e], irho = M.t_mat[1 * Kp + e], zM = M.t_mat[2 * Kp + e];
+  int nbr[4], code[4];
+  real zP[4];
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
-    const real ax = X[fv[f][1]][0] - X[fv[f][0]][0], ay = X[fv[f][1]][1] - X[fv[f][0]][1],
-               az = X[fv[f][1]][2] - X[fv[f][0]][2];
-    const real bx = X[fv[f][2]][0] - X[fv[f][0]][0], by = X[fv[f][2]][1] - X[fv[f][0]][1],
-               bz = X[fv[f][2]][2] - X[fv[f][0]][2];
-    const real cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
-    const real nrm = sqrt_r(cx * cx + cy * cy + cz * cz);
-    const real ox = X[fo[f]][0] - X[fv[f][0]][0], oy = X[fo[f]][1] - X[fv[f][0]][1], oz = X[fo[f]][2] - X[fv[f][0]][2];
-    const real sgn = (cx * ox + cy * oy + cz * oz > 0) ? real(-1) : real(1);  // away from the opposite vertex
-    g.n[f][0] = sgn * cx / nrm;
-    g.n[f][1] = sgn * cy / nrm;
-    g.n[f][2] = sgn * cz / nrm;
-    g.sJ[f] = real(0.25) * nrm * iJ;
+    nbr[f] = M.t_nbr[f * Kp + e];
+    code[f] = M.t_code[f * Kp + e];
   }
-  g.kappa = M.t_mat[0 * Kp + e];
-  g.irho = M.t_mat[1 * Kp + e];
-  g.zM = M.t_mat[2 * Kp + e];
-}
-
-// fluxes on tet face F of element e -> sF[F][0/1][k][lane]
-template <int N, int F>
-__device__ __forceinline__ void tet_face_flux(const StageArgs<real>& A, const TetGeom& g, const real* sq, real* sF,
-                                              int e, int lane) {
-  constexpr int Np = npt_of(N), Nt = nt_of(N);
-  const AllOps<N, real>& O = OPS<N>();
-  const DevMesh<real>& M = A.m;
-  const int nbr = M.t_nbr[F * M.Kt_pad + e];
-  const int code = M.t_code[F * M.Kt_pad + e];
-  const real nx = g.n[F][0], ny = g.n[F][1], nz = g.n[F][2];
-  real tau_p, tau_u;
-  if (nbr < 0) {
-    taus(A.flux, g.zM, g.zM, tau_p, tau_u);
 #pragma unroll
-    for (int k = 0; k < Nt; ++k) {
-      const Q4 o = lds4(sq, tet_face_node(N, F, k), lane);
-      real dp, dun, Fp, Fu;
-      boundary_jumps(A.bc, o.p, nx * o.u + ny * o.v + nz * o.w, dp, dun);
-      penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
-      sF[((F * 2 + 0) * Nt + k) * kB + lane] = Fp;
-      sF[((F * 2 + 1) * Nt + k) * kB + lane] = Fu;
-    }
-  } else {
-    const bool ntet = (code & kCodeTet) != 0;
-    const int nf = (code >> 4) & 3;
-    const int perm = code & 15;
-    const real zP = ntet ? M.t_mat[2 * M.Kt_pad + nbr] : M.w_mat[2 * M.Kw_pad + nbr];
-    taus(A.flux, g.zM, zP, tau_p, tau_u);
-    const bool inblk = ntet && ((nbr >> 5) == int(blockIdx.x));
-#pragma unroll
-    for (int k = 0; k < Nt; ++k) {
-      const int nk = O.tab.tri_perm[perm][k];
-      Q4 nv;
-      if (!ntet) {
-        nv = ldg4(A.q_in, widx<N>(nbr >> 5, (nf ? N * nt_of(N) : 0) + nk, nbr & 31));
-      } else {
-        const int node = O.tab.tet_face[nf][nk];
-        nv = inblk ? lds4(sq, node, nbr & 31) : ldg4(A.q_in, tidx<N>(M.tet_off, nbr >> 5, node, nbr & 31));
-      }
-      const Q4 o = lds4(sq, tet_face_node(N, F, k), lane);
-      real Fp, Fu;
-      penalty_flux(nv.p - o.p, nx * (nv.u - o.u) + ny * (nv.v - o.v) + nz * (nv.w - o.w), tau_p, tau_u, Fp, Fu);
-      sF[((F * 2 + 0) * Nt + k) * kB + lane] = Fp;
-      sF[((F * 2 + 1) * Nt + k) * kB + lane] = Fu;
-    }
-  }
-}
+  for (int f = 0; f < 4; ++f)
+    zP[f] = nbr[f] < 0 ? zM : ((code[f] & kCodeTet) ? M.t_mat[2 * Kp + nbr[f]] : M.w_mat[2 * M.Kw_pad + nbr[f]]);
+  const bool src = M.nsrc > 0 && has_source(M, 4, e);
 
-// output nodes [I0, I0 + C) of element e: volume terms, lift, update
-template <int N, int I0, int C>
-__device__ __forceinline__ void tet_chunk_out(const StageArgs<real>& A, const TetGeom& g, const real* sq,
-                                              const real* sF, int e, int lane, bool rk) {
-  constexpr int Np = npt_of(N), Nt = nt_of(N);
-  const AllOps<N, real>& O = OPS<N>();
-  const DevMesh<real>& M = A.m;
-  real ap[C], au[3][C];
+  // affine geometry: x = sum_v lambda_v X_v on the bi-unit reference tet
+  bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[0], 0));
+  real Ri[3][3], nf[4][3], sJ[4];  // d r_m / d x_d, outward unit normals, J_f / J
   {
-    real dr[C], ds[C], dt[C];
+    real X[4][3];
 #pragma unroll
-    for (int c = 0; c < C; ++c) dr[c] = ds[c] = dt[c] = ap[c] = real(0);
+    for (int v = 0; v < 4; ++v)
 #pragma unroll
-    for (int l = 0; l < Np; ++l) {
-      const Q4 v = lds4(sq, l, lane);
-      const real p = v.p, ux = v.u, uy = v.v, uz = v.w;
-      const real wr = g.Ri[0][0] * ux + g.Ri[0][1] * uy + g.Ri[0][2] * uz;
-      const real ws = g.Ri[1][0] * ux + g.Ri[1][1] * uy + g.Ri[1][2] * uz;
-      const real wt = g.Ri[2][0] * ux + g.Ri[2][1] * uy + g.Ri[2][2] * uz;
+      for (int d = 0; d < 3; ++d) X[v][d] = sX[(v * 3 + d) * kB + lane];
+    real G[3][3];  // G[d][m] = d x_d / d r_m
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) G[d][m] = real(0.5) * (X[m + 1][d] - X[0][d]);
+    const real J = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) -
+                   G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) + G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+    const real iJ = real(1) / J;
+    Ri[0][0] = (G[1][1] * G[2][2] - G[1][2] * G[2][1]) * iJ;
+    Ri[0][1] = (G[0][2] * G[2][1] - G[0][1] * G[2][2]) * iJ;
+    Ri[0][2] = (G[0][1] * G[1][2] - G[0][2] * G[1][1]) * iJ;
+    Ri[1][0] = (G[1][2] * G[2][0] - G[1][0] * G[2][2]) * iJ;
+    Ri[1][1] = (G[0][0] * G[2][2] - G[0][2] * G[2][0]) * iJ;
+    Ri[1][2] = (G[0][2] * G[1][0] - G[0][0] * G[1][2]) * iJ;
+    Ri[2][0] = (G[1][0] * G[2][1] - G[1][1] * G[2][0]) * iJ;
+    Ri[2][1] = (G[0][1] * G[2][0] - G[0][0] * G[2][1]) * iJ;
+    Ri[2][2] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) * iJ;
+    constexpr int fv[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
+    constexpr int fo[4] = {3, 2, 0, 1};
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const real ax = X[fv[f][1]][0] - X[fv[f][0]][0], ay = X[fv[f][1]][1] - X[fv[f][0]][1],
+                 az = X[fv[f][1]][2] - X[fv[f][0]][2];
+      const real bx = X[fv[f][2]][0] - X[fv[f][0]][0], by = X[fv[f][2]][1] - X[fv[f][0]][1],
+                 bz = X[fv[f][2]][2] - X[fv[f][0]][2];
+      const real cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+      const real cc = cx * cx + cy * cy + cz * cz, ic = rsqrt_r(cc);
+      const real ox = X[fo[f]][0] - X[fv[f][0]][0], oy = X[fo[f]][1] - X[fv[f][0]][1], oz = X[fo[f]][2] - X[fv[f][0]][2];
+      const real sgn = (cx * ox + cy * oy + cz * oz > 0) ? real(-1) : real(1);  // away from the opposite vertex
+      nf[f][0] = sgn * cx * ic;
+      nf[f][1] = sgn * cy * ic;
+      nf[f][2] = sgn * cz * ic;
+      sJ[f] = real(0.25) * cc * ic * iJ;
+    }
+  }
+  ok = ok && __all_sync(0xffffffffu, mbar_wait_bounded(&bar[1], 0));
+  ok = ok && __all_sync(0xffffffffu, mbar_wait_bounded(obar, 0));
+  if (!ok) {
+    if (lane == 0) {
+      atomicOr(M.err, kErrTimeout);
+      mbar_wait_bounded(&bar[0], 0);
+      mbar_wait_bounded(&bar[1], 0);
+      mbar_wait_bounded(obar, 0);
+    }
+    return;
+  }
+
+  // face fluxes, scaled by J_f / J, into this thread's column of the flux table
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    real tau_p, tau_u;
+    taus(A.flux, zM, zP[f], tau_p, tau_u);
+    const bool bnd = nbr[f] < 0;
+    const bool ntet = !bnd && (code[f] & kCodeTet) != 0;
+    const int nfc = (code[f] >> 4) & 3, perm = code[f] & 15;
+    const int nbe = bnd ? e : nbr[f];
+    const bool inblk = bnd || (ntet && (nbe >> 5) == blk);
+    // the neighbour's slab: this warp's own, another block's in global memory, or a wedge's
+    const real* nb = inblk ? sq + ((nbe & 31) << 2)
+                           : A.q_in + (ntet ? tidx<N>(M.tet_off, nbe >> 5, 0, nbe & 31) : widx<N>(nbe >> 5, 0, nbe & 31));
+#pragma unroll 1
+    for (int k = 0; k < Nt; ++k) {
+      const int own = O.tab.tet_face[f][k];
+      const Q4 o = lds4(sq, own, lane);
+      const real unM = nf[f][0] * o.u + nf[f][1] * o.v + nf[f][2] * o.w;
+      const int nk = bnd ? k : O.tab.tri_perm[perm][k];
+      const int node = bnd ? own : (ntet ? O.tab.tet_face[nfc][nk] : (nfc ? N * Nt : 0) + nk);
+      const Q4 nv = ldx4(nb + node * (kB * 4));
+      real bdp, bdun;
+      boundary_jumps(A.bc, o.p, unM, bdp, bdun);
+      const real dp = bnd ? bdp : nv.p - o.p;
+      const real dun = bnd ? bdun : nf[f][0] * nv.u + nf[f][1] * nv.v + nf[f][2] * nv.w - unM;
+      real Fp, Fu;
+      penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
+      sF[((f * 2 + 0) * Nt + k) * kB + lane] = sJ[f] * Fp;
+      sF[((f * 2 + 1) * Nt + k) * kB + lane] = sJ[f] * Fu;
+    }
+  }
+
+  // volume terms and lift for output nodes [I0, I0 + C), then the update
+#pragma unroll 1
+  for (int pass = 0; pass < tet_passes<N>(); ++pass) {
+    const int I0 = pass * C;
+    const real* opI = sOp + I0 * 4;  // records (l, I0 + c) at opI + (l Np + c) 4
+    const real* ltI = sL + I0;       // lift pairs (f Nt + k, I0 + c) at ltI + (f Nt + k) NPE + c
+    real ap[C], au[3][C];
+    {
+      real dr[C], ds[C], dt[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) dr[c] = ds[c] = dt[c] = ap[c] = real(0);
+#pragma unroll 2
+      for (int l = 0; l < Np; ++l) {
+        const Q4 v = lds4(sq, l, lane);
+        const real wr = Ri[0][0] * v.u + Ri[0][1] * v.v + Ri[0][2] * v.w;
+        const real ws = Ri[1][0] * v.u + Ri[1][1] * v.v + Ri[1][2] * v.w;
+        const real wt = Ri[2][0] * v.u + Ri[2][1] * v.v + Ri[2][2] * v.w;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          if (I0 + c < Np) {
+            const Q4 d = ldop4(opI + (l * Np + c) * 4);
+            dr[c] += d.p * v.p;
+            ds[c] += d.u * v.p;
+            dt[c] += d.v * v.p;
+            ap[c] -= d.p * wr + d.u * ws + d.v * wt;
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) au[d][c] = -(Ri[0][d] * dr[c] + Ri[1][d] * ds[c] + Ri[2][d] * dt[c]);
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      real lu[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) lu[c] = real(0);
+#pragma unroll 2
+      for (int k = 0; k < Nt; ++k) {
+        const real Fp = sF[((f * 2 + 0) * Nt + k) * kB + lane];
+        const real Fu = sF[((f * 2 + 1) * Nt + k) * kB + lane];
+#pragma unroll
+        for (int c = 0; c < C; c += 2) {
+          if (I0 + c < Np) {
+            real L0, L1;
+            ldop2(ltI + (f * Nt + k) * NPE + c, L0, L1);
+            ap[c] += L0 * Fp;
+            lu[c] += L0 * Fu;
+            ap[c + 1] += L1 * Fp;
+            lu[c + 1] += L1 * Fu;
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) au[d][c] += nf[f][d] * lu[c];
+    }
+    if (src) add_sources(M, 4, e, I0, Np, *M.clock + A.c_stage * double(A.dt), ap);
+    if (e < M.Kt) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         if (I0 + c < Np) {
           const int i = I0 + c;
-          dr[c] += O.t.Dr[i * Np + l] * p;
-          ds[c] += O.t.Ds[i * Np + l] * p;
-          dt[c] += O.t.Dt[i * Np + l] * p;
-          ap[c] -= O.t.Dr[i * Np + l] * wr + O.t.Ds[i * Np + l] * ws + O.t.Dt[i * Np + l] * wt;
+          const int64_t gi = tidx<N>(M.tet_off, blk, i, lane);
+          const Q4 r{kappa * ap[c], irho * au[0][c], irho * au[1][c], irho * au[2][c]};
+          if (rk) {
+            const Q4 r0 = ld4(A.res, gi);
+            const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
+                        A.rk_a * r0.w + A.dt * r.w};
+            const Q4 q0 = lds4(sq, i, lane);
+            st4(A.res, gi, rr);
+            st4(A.q_out, gi,
+                Q4{q0.p + A.rk_b * rr.p, q0.u + A.rk_b * rr.u, q0.v + A.rk_b * rr.v, q0.w + A.rk_b * rr.w});
+          } else {
+            st4(A.q_out, gi, r);
+          }
         }
       }
     }
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) au[d][c] = -(g.Ri[0][d] * dr[c] + g.Ri[1][d] * ds[c] + g.Ri[2][d] * dt[c]);
-  }
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    real lu[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) lu[c] = real(0);
-#pragma unroll
-    for (int k = 0; k < Nt; ++k) {
-      const real Fp = g.sJ[f] * sF[((f * 2 + 0) * Nt + k) * kB + lane];
-      const real Fu = g.sJ[f] * sF[((f * 2 + 1) * Nt + k) * kB + lane];
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        if (I0 + c < Np) {
-          const real L = O.t.LIFT[(I0 + c) * 4 * Nt + f * Nt + k];
-          ap[c] += L * Fp;
-          lu[c] += L * Fu;
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) au[d][c] += g.n[f][d] * lu[c];
-  }
-  if (e < M.Kt) {
-    real* __restrict__ resg = A.res;
-    real* __restrict__ qout = A.q_out;
-    if (M.nsrc > 0 && has_source(M, 4, e)) add_sources(M, 4, e, I0, Np, *M.clock + A.c_stage * double(A.dt), ap);
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      if (I0 + c < Np) {
-        const int i = I0 + c;
-        const int64_t gi = tidx<N>(M.tet_off, blockIdx.x, i, lane);
-        Q4 r{g.kappa * ap[c], g.irho * au[0][c], g.irho * au[1][c], g.irho * au[2][c]};
-        if (rk) {
-          const Q4 r0 = ld4(resg, gi);
-          const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
-                      A.rk_a * r0.w + A.dt * r.w};
-          const Q4 q0 = lds4(sq, i, lane);
-          st4(resg, gi, rr);
-          st4(qout, gi, Q4{q0.p + A.rk_b * rr.p, q0.u + A.rk_b * rr.u, q0.v + A.rk_b * rr.v, q0.w + A.rk_b * rr.w});
-        } else {
-          st4(qout, gi, r);
-        }
-      }
-    }
-  }
-}
-
-template <int N>
-__global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? 4 : 1) k_tet_stage(const StageArgs<real> A, bool rk) {
-  constexpr int Np = npt_of(N), C = tet_chunk<N>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  real* sq = reinterpret_cast<real*>(smem_raw);  // [Np][32][4]
-  real* sF = sq + 4 * Np * kB;                   // [4 faces][2][Nt][32]
-  const int lane = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
-  const int e = blockIdx.x * kB + lane;
-  {
-    constexpr int nvec = 4 * Np * kB * int(sizeof(real)) / 16;
-    const int4* src = reinterpret_cast<const int4*>(A.q_in + A.m.tet_off + int64_t(blockIdx.x) * 4 * Np * kB);
-    int4* dst = reinterpret_cast<int4*>(sq);
-    for (int v = threadIdx.x; v < nvec; v += blockDim.x) dst[v] = __ldg(src + v);
-  }
-  TetGeom g;
-  real X[4][3];
-  tet_geometry<N>(A.m, e, g, X);
-  __syncthreads();
-  switch (w) {
-    case 0: tet_face_flux<N, 0>(A, g, sq, sF, e, lane); break;
-    case 1: tet_face_flux<N, 1>(A, g, sq, sF, e, lane); break;
-    case 2: tet_face_flux<N, 2>(A, g, sq, sF, e, lane); break;
-    default: tet_face_flux<N, 3>(A, g, sq, sF, e, lane); break;
-  }
-  __syncthreads();
-  switch (w) {
-    case 0: tet_chunk_out<N, 0 * C, C>(A, g, sq, sF, e, lane, rk); break;
-    case 1: tet_chunk_out<N, 1 * C, C>(A, g, sq, sF, e, lane, rk); break;
-    case 2: tet_chunk_out<N, 2 * C, C>(A, g, sq, sF, e, lane, rk); break;
-    default: tet_chunk_out<N, 3 * C, C>(A, g, sq, sF, e, lane, rk); break;
   }
 }
 
@@ -1082,8 +1146,7 @@ int prepare_n() {
     err = cudaFuncSetAttribute(k_wedge_stage<N, b2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                wedge_smem_bytes<N, b2>());
   if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(k_tet_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               tet_smem_reals<N>() * int(sizeof(real)));
+    err = cudaFuncSetAttribute(k_tet_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, tet_smem_bytes<N>());
   return int(err);
 }
 
@@ -1099,7 +1162,8 @@ int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s) {
     if (err != cudaSuccess) return int(err);
   }
   if (a.m.nblk_t > 0) {
-    k_tet_stage<N><<<a.m.nblk_t, 128, tet_smem_reals<N>() * int(sizeof(real)), s>>>(a, rk);
+    constexpr int tb = tet_bpc<N>();
+    k_tet_stage<N><<<(a.m.nblk_t + tb - 1) / tb, 32 * tb, tet_smem_bytes<N>(), s>>>(a, rk);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return int(err);
   }

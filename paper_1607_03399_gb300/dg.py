@@ -29,7 +29,7 @@ DG_MASS_ONTHEFLY, DG_MASS_STORED = 0, 1
 
 EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_options", "dg_set_mass_mode", "dg_num_nodes",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
-           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_sync", "dg_time",
+           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_stage_times", "dg_sync", "dg_time",
            "dg_stable_dt", "dg_last_error", "dg_destroy")
 
 _lib = None
@@ -70,6 +70,7 @@ def lib():
         "dg_step": (c_int, [P, c_double, c_int64]),
         "dg_energy": (c_int, [P, POINTER(c_double)]),
         "dg_energy_static": (c_int, [P, P, POINTER(c_double)]),
+        "dg_stage_times": (c_int, [P, c_int, POINTER(c_double), POINTER(c_double)]),
         "dg_sync": (c_int, [P]),
         "dg_time": (c_int, [P, POINTER(c_double)]),
         "dg_stable_dt": (c_int, [P, c_double, POINTER(c_double)]),
@@ -204,6 +205,13 @@ def dg_energy_static(ctx, d_q: int) -> float:
     return E.value
 
 
+def dg_stage_times(ctx, nrep: int):
+    """Mean device microseconds per launch of the wedge and of the tet stage kernel."""
+    w, t = c_double(), c_double()
+    _check(ctx, lib().dg_stage_times(ctx, nrep, ctypes.byref(w), ctypes.byref(t)))
+    return w.value, t.value
+
+
 def dg_sync(ctx):
     _check(ctx, lib().dg_sync(ctx))
 
@@ -320,6 +328,11 @@ class Solver:
 
     def step(self, dt: float, nsteps: int):
         dg_step(self.ctx, dt, nsteps)
+
+    def stage_times(self, nrep: int = 20):
+        """(wedge, tet) mean microseconds per stage-kernel launch; the state is unchanged."""
+        self._wait_torch()
+        return dg_stage_times(self.ctx, nrep)
 
     def energy(self) -> float:
         return dg_energy(self.ctx)

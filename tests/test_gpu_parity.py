@@ -236,3 +236,18 @@ def test_point_sources(precision, tol):
     r = S.rhs(q_ref.astype(S.np_dtype)).cpu().numpy()
     assert _rel(r, r_ref) <= 10 * tol
     S.close()
+
+
+def test_stage_times_leave_the_state_alone():
+    """dg_stage_times times both element types and changes neither the state
+    nor the next step (hybrid mesh, FP32)."""
+    S, O = _pair(MESHES["hybrid"](), 3, "f32")
+    q = I.random_fields(S.total_nodes, 4).astype(np.float32)
+    S.set_fields(q)
+    tw, tt = S.stage_times(3)
+    assert tw > 0 and tt > 0
+    assert np.array_equal(S.get_fields(), q)
+    dt = O.stable_dt(0.4)
+    S.step(dt, 2)
+    assert _rel(S.get_fields(), O.step(q.astype(np.float64), dt, 2)) <= 1e-5
+    S.close()
