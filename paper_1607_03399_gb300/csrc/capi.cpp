@@ -334,10 +334,10 @@ BlobLayout blob_layout(const dg_ctx* c) {
   // per tet block [12][32]: x, y, z of the four vertices
   L.txyz = take(size_t(Ktp) * 12 * rs);
   // tet stage operators in the stage's shared-memory image: [l][i] (D_r, D_s, D_t, 0)(i, l),
-  // then the lift transposed [f Nt + k][i] with rows padded to an even length
+  // then the lift per warp chunk of C = ceil(Np/4) output nodes, [warp][f Nt + k][c < CP]
   {
-    const int np = npt_of(c->N), npe = (np + 1) / 2 * 2;
-    L.tops = take(size_t(4 * np * np + 4 * nt_of(c->N) * npe) * rs);
+    const int np = npt_of(c->N), ch = (np + 3) / 4, cp = (ch + 3) / 4 * 4;
+    L.tops = take(size_t(4 * np * np + 4 * 4 * nt_of(c->N) * cp) * rs);
   }
   L.total = o;
   return L;
@@ -424,7 +424,7 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
   // wedge energy operators: barycentric-weighted triangle masses, then the line mass
   {
     const RefElems& R = *c->ref;
-    const int np = R.Npt, npe = (np + 1) / 2 * 2, nt = R.Nt;
+    const int np = R.Npt, nt = R.Nt, ch = (np + 3) / 4, cp = (ch + 3) / 4 * 4;
     real* to = reinterpret_cast<real*>(blob.data() + L.tops);
     for (int l = 0; l < np; ++l)
       for (int i = 0; i < np; ++i) {
@@ -435,8 +435,12 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
         v[3] = real(0);
       }
     real* lt = to + size_t(4) * np * np;
-    for (int fk = 0; fk < 4 * nt; ++fk)
-      for (int i = 0; i < npe; ++i) lt[size_t(fk) * npe + i] = i < np ? real(R.tLIFT(i, fk)) : real(0);
+    for (int w = 0; w < 4; ++w)
+      for (int fk = 0; fk < 4 * nt; ++fk)
+        for (int cc = 0; cc < cp; ++cc) {
+          const int i = w * ch + cc;
+          lt[(size_t(w) * 4 * nt + fk) * cp + cc] = (cc < ch && i < np) ? real(R.tLIFT(i, fk)) : real(0);
+        }
   }
   real* wo = reinterpret_cast<real*>(blob.data() + L.wops);
   const int nt2 = c->ref->Nt * c->ref->Nt;

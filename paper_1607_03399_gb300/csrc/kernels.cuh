@@ -727,111 +727,78 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
 }
 
 // ---------------------------------------------------------------------------
-// tet stage: lane = tet of a 32-tet block, one block per warp, TPC blocks per
-// CTA.  The CTA copies the tet operators into shared memory once ([l][i]
-// (D_r, D_s, D_t)(i, l) records and the transposed lift); each warp moves its
-// block's vertex coordinates and state slab with bulk copies on its own
-// mbarriers, evaluates the affine geometry and the 4 N_t face fluxes (a
-// per-warp table, each thread reading back only its own), then the volume
-// terms and the lift for the output nodes in passes of C nodes, fused with the
-// update.  Warps never wait for one another after the start.
+// tet stage: one 32-tet block per CTA (lane = tet), 4 warps.  Bulk copies move
+// the tet operators ([l][i] (D_r, D_s, D_t)(i, l) records and the lift, laid
+// out per warp chunk), the block's vertex coordinates and its state slab into
+// shared memory.  Every warp evaluates the affine geometry of the 32 tets;
+// warp f forms the fluxes of face f into a shared table; after one barrier
+// warp w produces output nodes [w C, w C + C) (volume terms, lift, update).
+// All warps run the same code.
 // ---------------------------------------------------------------------------
-#ifndef TET_PASSES
-#define TET_PASSES(N) ((N) <= 2 ? 1 : (N) == 3 ? 2 : 3)
-#endif
 template <int N>
-__host__ __device__ constexpr int tet_passes() {
-  return TET_PASSES(N);
-}
-// output nodes per pass, even (the lift is read in pairs)
-template <int N>
-__host__ __device__ constexpr int tet_pass_nodes() {
-  return ((npt_of(N) + tet_passes<N>() - 1) / tet_passes<N>() + 1) / 2 * 2;
-}
-// blocks (warps) per CTA: as many as two CTAs per SM hold in shared memory
-template <int N>
-__host__ __device__ constexpr int tet_bpc() {
-  return sizeof(real) == 4 ? (N >= 4 ? 2 : 4) : (N >= 4 ? 1 : 2);
+__host__ __device__ constexpr int tet_chunk() {  // output nodes per warp
+  return (npt_of(N) + 3) / 4;
 }
 template <int N>
-__host__ __device__ constexpr int tet_npe() {
-  return (npt_of(N) + 1) / 2 * 2;
+__host__ __device__ constexpr int tet_chunk_pad() {  // lift record length per face node (multiple of 4)
+  return (tet_chunk<N>() + 3) / 4 * 4;
 }
 template <int N>
 __host__ __device__ constexpr int tet_ops_reals() {
-  return 4 * npt_of(N) * npt_of(N) + 4 * nt_of(N) * tet_npe<N>();
+  return 4 * npt_of(N) * npt_of(N) + 4 * (4 * nt_of(N)) * tet_chunk_pad<N>();
 }
-// per warp: slab [Np][32][4], fluxes [4 faces][2][Nt][32], vertex coordinates [12][32]
+// 128-byte header (3 mbarriers), operators, slab [Np][32][4], fluxes
+// [4 faces][2][Nt][32], vertex coordinates [12][32]
 template <int N>
-__host__ __device__ constexpr int tet_warp_reals() {
-  return 4 * npt_of(N) * kB + 8 * nt_of(N) * kB + 12 * kB;
+__host__ __device__ constexpr int tet_smem_reals() {
+  return tet_ops_reals<N>() + 4 * npt_of(N) * kB + 8 * nt_of(N) * kB + 12 * kB;
 }
-// 128-byte header (operator mbarrier, then two mbarriers per warp), operators, warp regions
 template <int N>
 __host__ __device__ constexpr int tet_smem_bytes() {
-  return 128 + (tet_ops_reals<N>() + tet_bpc<N>() * tet_warp_reals<N>()) * int(sizeof(real));
+  return 128 + tet_smem_reals<N>() * int(sizeof(real));
 }
 
 template <int N>
-__global__ void __launch_bounds__(32 * tet_bpc<N>(), 2)
+__global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 2)
     k_tet_stage(const StageArgs<real> A, bool rk) {
-  constexpr int Np = npt_of(N), Nt = nt_of(N), C = tet_pass_nodes<N>(), BPC = tet_bpc<N>(), NPE = tet_npe<N>();
-  static_assert(8 + 16 * BPC <= 128, "header");
+  constexpr int Np = npt_of(N), Nt = nt_of(N), C = tet_chunk<N>(), CP = tet_chunk_pad<N>();
   const AllOps<N, real>& O = OPS<N>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* obar = reinterpret_cast<uint64_t*>(smem_raw);
-  const int lane = threadIdx.x & 31;
-  const int wid = threadIdx.x >> 5;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 8 + 16 * wid);  // [0] coordinates, [1] state slab
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // [0] operators, [1] coordinates, [2] state slab
   real* sOp = reinterpret_cast<real*>(smem_raw + 128);
-  real* sL = sOp + 4 * Np * Np;  // transposed lift [4 Nt][NPE]
-  real* sq = sOp + tet_ops_reals<N>() + wid * tet_warp_reals<N>();
+  real* sL = sOp + 4 * Np * Np;  // lift [warp][4 Nt][CP]
+  real* sq = sOp + tet_ops_reals<N>();
   real* sF = sq + 4 * Np * kB;
   real* sX = sF + 8 * Nt * kB;
   const DevMesh<real>& M = A.m;
-  const int blk = blockIdx.x * BPC + wid;
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int blk = blockIdx.x;
   const int e = blk * kB + lane;
   const int Kp = M.Kt_pad;
   constexpr uint32_t slab_bytes = uint32_t(4 * Np * kB * sizeof(real)), xyz_bytes = uint32_t(12 * kB * sizeof(real));
   constexpr uint32_t ops_bytes = uint32_t(tet_ops_reals<N>() * sizeof(real));
   if (threadIdx.x == 0) {
-    mbar_init(obar, 1);
-    for (int w = 0; w < BPC; ++w) {
-      mbar_init(reinterpret_cast<uint64_t*>(smem_raw + 8 + 16 * w), 1);
-      mbar_init(reinterpret_cast<uint64_t*>(smem_raw + 16 + 16 * w), 1);
-    }
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
     fence_mbar_init();
-    mbar_expect_tx(obar, ops_bytes);
-    bulk_g2s(sOp, M.t_ops, ops_bytes, obar);
+    mbar_expect_tx(&bar[1], xyz_bytes);
+    bulk_g2s(sX, M.t_xyz + int64_t(blk) * 12 * kB, xyz_bytes, &bar[1]);
+    mbar_expect_tx(&bar[2], slab_bytes);
+    bulk_g2s(sq, A.q_in + M.tet_off + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[2]);
+    mbar_expect_tx(&bar[0], ops_bytes);
+    bulk_g2s(sOp, M.t_ops, ops_bytes, &bar[0]);
   }
-  __syncthreads();
-  if (blk >= M.nblk_t) {  // padding block of the last CTA
-    if (threadIdx.x == 0) mbar_wait_bounded(obar, 0);
-    return;
-  }
-  if (lane == 0) {
-    mbar_expect_tx(&bar[0], xyz_bytes);
-    bulk_g2s(sX, M.t_xyz + int64_t(blk) * 12 * kB, xyz_bytes, &bar[0]);
-    mbar_expect_tx(&bar[1], slab_bytes);
-    bulk_g2s(sq, A.q_in + M.tet_off + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[1]);
-  }
-  __syncwarp();
   // face neighbours, impedances, material and the source flag while the copies fly
   const real kappa = M.t_mat[0 * Kp + e], irho = M.t_mat[1 * Kp + e], zM = M.t_mat[2 * Kp + e];
-  int nbr[4], code[4];
-  real zP[4];
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    nbr[f] = M.t_nbr[f * Kp + e];
-    code[f] = M.t_code[f * Kp + e];
-  }
-#pragma unroll
-  for (int f = 0; f < 4; ++f)
-    zP[f] = nbr[f] < 0 ? zM : ((code[f] & kCodeTet) ? M.t_mat[2 * Kp + nbr[f]] : M.w_mat[2 * M.Kw_pad + nbr[f]]);
+  int nbr = M.t_nbr[w * Kp + e], code = M.t_code[w * Kp + e];  // this warp's face w
+  const real zP = nbr < 0 ? zM : ((code & kCodeTet) ? M.t_mat[2 * Kp + nbr] : M.w_mat[2 * M.Kw_pad + nbr]);
   const bool src = M.nsrc > 0 && has_source(M, 4, e);
+  __syncthreads();  // the mbarriers are initialised
 
   // affine geometry: x = sum_v lambda_v X_v on the bi-unit reference tet
-  bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[0], 0));
+  bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[1], 0));
   real Ri[3][3], nf[4][3], sJ[4];  // d r_m / d x_d, outward unit normals, J_f / J
   {
     real X[4][3];
@@ -874,83 +841,91 @@ __global__ void __launch_bounds__(32 * tet_bpc<N>(), 2)
       sJ[f] = real(0.25) * cc * ic * iJ;
     }
   }
-  ok = ok && __all_sync(0xffffffffu, mbar_wait_bounded(&bar[1], 0));
-  ok = ok && __all_sync(0xffffffffu, mbar_wait_bounded(obar, 0));
+  ok = ok && __all_sync(0xffffffffu, mbar_wait_bounded(&bar[2], 0));
   if (!ok) {
+    // a copy never arrived: report, let the copies in flight drain, leave
+    if (threadIdx.x == 0) atomicOr(M.err, kErrTimeout);
     if (lane == 0) {
-      atomicOr(M.err, kErrTimeout);
       mbar_wait_bounded(&bar[0], 0);
       mbar_wait_bounded(&bar[1], 0);
-      mbar_wait_bounded(obar, 0);
+      mbar_wait_bounded(&bar[2], 0);
     }
     return;
   }
 
-  // face fluxes, scaled by J_f / J, into this thread's column of the flux table
+  // fluxes of face w, scaled by J_f / J, into the shared flux table
+  {
+    const int f = w;
+    real n0 = nf[0][0], n1 = nf[0][1], n2 = nf[0][2], sj = sJ[0];
 #pragma unroll
-  for (int f = 0; f < 4; ++f) {
+    for (int g = 1; g < 4; ++g)
+      if (f == g) {
+        n0 = nf[g][0];
+        n1 = nf[g][1];
+        n2 = nf[g][2];
+        sj = sJ[g];
+      }
     real tau_p, tau_u;
-    taus(A.flux, zM, zP[f], tau_p, tau_u);
-    const bool bnd = nbr[f] < 0;
-    const bool ntet = !bnd && (code[f] & kCodeTet) != 0;
-    const int nfc = (code[f] >> 4) & 3, perm = code[f] & 15;
-    const int nbe = bnd ? e : nbr[f];
+    taus(A.flux, zM, zP, tau_p, tau_u);
+    const bool bnd = nbr < 0;
+    const bool ntet = !bnd && (code & kCodeTet) != 0;
+    const int nfc = (code >> 4) & 3, perm = code & 15;
+    const int nbe = bnd ? e : nbr;
     const bool inblk = bnd || (ntet && (nbe >> 5) == blk);
-    // the neighbour's slab: this warp's own, another block's in global memory, or a wedge's
+    // the neighbour's slab: this block's own, another tet block's or a wedge block's in global memory
     const real* nb = inblk ? sq + ((nbe & 31) << 2)
                            : A.q_in + (ntet ? tidx<N>(M.tet_off, nbe >> 5, 0, nbe & 31) : widx<N>(nbe >> 5, 0, nbe & 31));
-#pragma unroll 1
+#pragma unroll 2
     for (int k = 0; k < Nt; ++k) {
       const int own = O.tab.tet_face[f][k];
       const Q4 o = lds4(sq, own, lane);
-      const real unM = nf[f][0] * o.u + nf[f][1] * o.v + nf[f][2] * o.w;
+      const real unM = n0 * o.u + n1 * o.v + n2 * o.w;
       const int nk = bnd ? k : O.tab.tri_perm[perm][k];
       const int node = bnd ? own : (ntet ? O.tab.tet_face[nfc][nk] : (nfc ? N * Nt : 0) + nk);
       const Q4 nv = ldx4(nb + node * (kB * 4));
       real bdp, bdun;
       boundary_jumps(A.bc, o.p, unM, bdp, bdun);
       const real dp = bnd ? bdp : nv.p - o.p;
-      const real dun = bnd ? bdun : nf[f][0] * nv.u + nf[f][1] * nv.v + nf[f][2] * nv.w - unM;
+      const real dun = bnd ? bdun : n0 * nv.u + n1 * nv.v + n2 * nv.w - unM;
       real Fp, Fu;
       penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
-      sF[((f * 2 + 0) * Nt + k) * kB + lane] = sJ[f] * Fp;
-      sF[((f * 2 + 1) * Nt + k) * kB + lane] = sJ[f] * Fu;
+      sF[((f * 2 + 0) * Nt + k) * kB + lane] = sj * Fp;
+      sF[((f * 2 + 1) * Nt + k) * kB + lane] = sj * Fu;
     }
   }
+  if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar[0], 0)) && lane == 0) atomicOr(M.err, kErrTimeout);
+  __syncthreads();
 
-  // volume terms and lift for output nodes [I0, I0 + C), then the update
-#pragma unroll 1
-  for (int pass = 0; pass < tet_passes<N>(); ++pass) {
-    const int I0 = pass * C;
+  // output nodes [I0, I0 + C) of this warp: volume terms, lift, update
+  const int I0 = w * C;
+  real ap[C], au[3][C];
+  {
+    real dr[C], ds[C], dt[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) dr[c] = ds[c] = dt[c] = ap[c] = real(0);
     const real* opI = sOp + I0 * 4;  // records (l, I0 + c) at opI + (l Np + c) 4
-    const real* ltI = sL + I0;       // lift pairs (f Nt + k, I0 + c) at ltI + (f Nt + k) NPE + c
-    real ap[C], au[3][C];
-    {
-      real dr[C], ds[C], dt[C];
-#pragma unroll
-      for (int c = 0; c < C; ++c) dr[c] = ds[c] = dt[c] = ap[c] = real(0);
 #pragma unroll 2
-      for (int l = 0; l < Np; ++l) {
-        const Q4 v = lds4(sq, l, lane);
-        const real wr = Ri[0][0] * v.u + Ri[0][1] * v.v + Ri[0][2] * v.w;
-        const real ws = Ri[1][0] * v.u + Ri[1][1] * v.v + Ri[1][2] * v.w;
-        const real wt = Ri[2][0] * v.u + Ri[2][1] * v.v + Ri[2][2] * v.w;
+    for (int l = 0; l < Np; ++l) {
+      const Q4 v = lds4(sq, l, lane);
+      const real wr = Ri[0][0] * v.u + Ri[0][1] * v.v + Ri[0][2] * v.w;
+      const real ws = Ri[1][0] * v.u + Ri[1][1] * v.v + Ri[1][2] * v.w;
+      const real wt = Ri[2][0] * v.u + Ri[2][1] * v.v + Ri[2][2] * v.w;
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          if (I0 + c < Np) {
-            const Q4 d = ldop4(opI + (l * Np + c) * 4);
-            dr[c] += d.p * v.p;
-            ds[c] += d.u * v.p;
-            dt[c] += d.v * v.p;
-            ap[c] -= d.p * wr + d.u * ws + d.v * wt;
-          }
-        }
+      for (int c = 0; c < C; ++c) {
+        const Q4 d = ldop4(opI + (l * Np + c) * 4);  // I0 + c >= Np: unused records, results dropped
+        dr[c] += d.p * v.p;
+        ds[c] += d.u * v.p;
+        dt[c] += d.v * v.p;
+        ap[c] -= d.p * wr + d.u * ws + d.v * wt;
       }
-#pragma unroll
-      for (int c = 0; c < C; ++c)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) au[d][c] = -(Ri[0][d] * dr[c] + Ri[1][d] * ds[c] + Ri[2][d] * dt[c]);
     }
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) au[d][c] = -(Ri[0][d] * dr[c] + Ri[1][d] * ds[c] + Ri[2][d] * dt[c]);
+  }
+  {
+    const real* lw = sL + w * (4 * Nt) * CP;  // this warp's lift records [4 Nt][CP]
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       real lu[C];
@@ -961,14 +936,15 @@ __global__ void __launch_bounds__(32 * tet_bpc<N>(), 2)
         const real Fp = sF[((f * 2 + 0) * Nt + k) * kB + lane];
         const real Fu = sF[((f * 2 + 1) * Nt + k) * kB + lane];
 #pragma unroll
-        for (int c = 0; c < C; c += 2) {
-          if (I0 + c < Np) {
-            real L0, L1;
-            ldop2(ltI + (f * Nt + k) * NPE + c, L0, L1);
-            ap[c] += L0 * Fp;
-            lu[c] += L0 * Fu;
-            ap[c + 1] += L1 * Fp;
-            lu[c + 1] += L1 * Fu;
+        for (int c4 = 0; c4 < CP; c4 += 4) {
+          const Q4 L = ldop4(lw + (f * Nt + k) * CP + c4);
+          const real Lc[4] = {L.p, L.u, L.v, L.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (c4 + q < C) {
+              ap[c4 + q] += Lc[q] * Fp;
+              lu[c4 + q] += Lc[q] * Fu;
+            }
           }
         }
       }
@@ -977,25 +953,25 @@ __global__ void __launch_bounds__(32 * tet_bpc<N>(), 2)
 #pragma unroll
         for (int d = 0; d < 3; ++d) au[d][c] += nf[f][d] * lu[c];
     }
-    if (src) add_sources(M, 4, e, I0, Np, *M.clock + A.c_stage * double(A.dt), ap);
-    if (e < M.Kt) {
+  }
+  if (src) add_sources(M, 4, e, I0, Np, *M.clock + A.c_stage * double(A.dt), ap);
+  if (e < M.Kt) {
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        if (I0 + c < Np) {
-          const int i = I0 + c;
-          const int64_t gi = tidx<N>(M.tet_off, blk, i, lane);
-          const Q4 r{kappa * ap[c], irho * au[0][c], irho * au[1][c], irho * au[2][c]};
-          if (rk) {
-            const Q4 r0 = ld4(A.res, gi);
-            const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
-                        A.rk_a * r0.w + A.dt * r.w};
-            const Q4 q0 = lds4(sq, i, lane);
-            st4(A.res, gi, rr);
-            st4(A.q_out, gi,
-                Q4{q0.p + A.rk_b * rr.p, q0.u + A.rk_b * rr.u, q0.v + A.rk_b * rr.v, q0.w + A.rk_b * rr.w});
-          } else {
-            st4(A.q_out, gi, r);
-          }
+    for (int c = 0; c < C; ++c) {
+      if (I0 + c < Np) {
+        const int i = I0 + c;
+        const int64_t gi = tidx<N>(M.tet_off, blk, i, lane);
+        const Q4 r{kappa * ap[c], irho * au[0][c], irho * au[1][c], irho * au[2][c]};
+        if (rk) {
+          const Q4 r0 = ld4(A.res, gi);
+          const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
+                      A.rk_a * r0.w + A.dt * r.w};
+          const Q4 q0 = lds4(sq, i, lane);
+          st4(A.res, gi, rr);
+          st4(A.q_out, gi,
+              Q4{q0.p + A.rk_b * rr.p, q0.u + A.rk_b * rr.u, q0.v + A.rk_b * rr.v, q0.w + A.rk_b * rr.w});
+        } else {
+          st4(A.q_out, gi, r);
         }
       }
     }
@@ -1162,8 +1138,7 @@ int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s) {
     if (err != cudaSuccess) return int(err);
   }
   if (a.m.nblk_t > 0) {
-    constexpr int tb = tet_bpc<N>();
-    k_tet_stage<N><<<(a.m.nblk_t + tb - 1) / tb, 32 * tb, tet_smem_bytes<N>(), s>>>(a, rk);
+    k_tet_stage<N><<<a.m.nblk_t, 128, tet_smem_bytes<N>(), s>>>(a, rk);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return int(err);
   }
