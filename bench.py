@@ -266,6 +266,93 @@ def measure_hybrid(args, torch, dev):
             "tet_alg_bytes": tet_bytes, "tet_frac": tet_bytes / (tt * 1e-6) / 1e9 / peak}
 
 
+def measure_multishot(args, torch, dev):
+    """Batched shots: 2x64x64 footprint x 32 bumpy layers = 262144 wedges, N=3,
+    FP32, layered wavespeed, 64 shots each with its own Ricker source (f0 = 8)
+    at a seeded position just below the surface, all advanced by one launch per
+    stage; against the same 64 shots advanced one context launch sequence per
+    shot (the per-shot form).  Unit: shot-steps/s."""
+    from paper_1607_03399_gb300 import inputs as I
+    from paper_1607_03399_gb300.dg import Solver
+    S = 64
+    m = I.bumpy_layered_mesh(64, 32)
+    c2, rho = I.layered_wavespeed(m)
+    pos = I.surface_shots(S, 4)
+    B = Solver(m.VX, m.EToV, m.etype, 3, c2, rho, precision="f32", device=str(dev), shots=S,
+               shot_sources=[(s, *pos[s], 8.0, 0.125, 1.0) for s in range(S)])
+    B.set_fields(np.zeros((S, 4, B.total_nodes), dtype=np.float32))
+    dt = B.stable_dt(0.5)
+    n = max(3, min(args.steps // 20, 10))
+    B.step(dt, args.warmup)
+    B.sync()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(B.stream)
+    B.step(dt, n)
+    end.record(B.stream)
+    end.synchronize()
+    ms_b = start.elapsed_time(end)
+    B.close()
+    A = Solver(m.VX, m.EToV, m.etype, 3, c2, rho, precision="f32", device=str(dev),
+               sources=[(*pos[0], 8.0, 0.125, 1.0)])
+    A.set_fields(np.zeros((4, A.total_nodes), dtype=np.float32))
+    A.step(dt, args.warmup)
+    A.sync()
+    start.record(A.stream)
+    for _ in range(S):
+        A.step(dt, n)
+    end.record(A.stream)
+    end.synchronize()
+    ms_a = start.elapsed_time(end)
+    A.close()
+    return {"workload": "multishot_2x64x64x32_N3_64shots", "wedges": m.K, "shots": S, "steps": n,
+            "batched_shot_steps_per_s": S * n / (ms_b / 1e3), "per_shot_shot_steps_per_s": S * n / (ms_a / 1e3),
+            "ratio": ms_a / ms_b, "batched_gdofs": S * 4 * 40 * m.K * 5 * n / (ms_b / 1e3) / 1e9}
+
+
+def measure_multimesh(args, torch, dev):
+    """48 independent layered meshes of uneven size (footprints 2x8x8 .. 2x40x40,
+    4..20 layers, seeded) merged into one context and advanced by one launch per
+    stage; against 48 contexts advanced one after another.  N=3, FP32."""
+    from paper_1607_03399_gb300 import inputs as I
+    from paper_1607_03399_gb300.dg import Solver
+    rng = np.random.default_rng(48)
+    parts = [I.bumpy_layered_mesh(int(rng.integers(4, 21)) * 2, int(rng.integers(4, 21)), seed0=5000 + 50 * i)
+             for i in range(48)]
+    mm = I.merge_meshes(parts)
+    B = Solver(mm.VX, mm.EToV, mm.etype, 3, precision="f32", device=str(dev))
+    B.set_fields(np.zeros((4, B.total_nodes), dtype=np.float32))
+    dt = B.stable_dt(0.5)
+    n = max(5, min(args.steps // 4, 40))
+    B.step(dt, args.warmup)
+    B.sync()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(B.stream)
+    B.step(dt, n)
+    end.record(B.stream)
+    end.synchronize()
+    ms_b = start.elapsed_time(end)
+    Ktot = mm.K
+    B.close()
+    solvers = [Solver(p.VX, p.EToV, p.etype, 3, precision="f32", device=str(dev)) for p in parts]
+    st = torch.cuda.Stream(dev)
+    for A in solvers:
+        A.set_fields(np.zeros((4, A.total_nodes), dtype=np.float32))
+        A.step(dt, args.warmup)
+        A.sync()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for A in solvers:
+        A.step(dt, n)
+    for A in solvers:
+        A.sync()
+    s_a = time.perf_counter() - t0
+    for A in solvers:
+        A.close()
+    return {"workload": "multimesh_48_layered_2x8x8_to_2x40x40_N3", "meshes": 48, "wedges": Ktot, "steps": n,
+            "batched_mesh_steps_per_s": 48 * n / (ms_b / 1e3), "separate_mesh_steps_per_s": 48 * n / s_a,
+            "ratio": s_a / (ms_b / 1e3)}
+
+
 def run_ours(args, rank, world):
     import torch
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -310,6 +397,8 @@ def run_ours(args, rank, world):
         r["solver"].close()
         r["solver"] = None
     hybrid = measure_hybrid(args, torch, dev) if (rank == 0 and not args.no_hybrid) else None
+    multishot = measure_multishot(args, torch, dev) if (rank == 0 and not args.no_batched) else None
+    multimesh = measure_multimesh(args, torch, dev) if (rank == 0 and not args.no_batched) else None
     # the headline order once more with the other way of applying the mass inverse
     other = {"stored": "onthefly", "onthefly": "stored"}[args.mass]
     alt = None
@@ -363,6 +452,8 @@ def run_ours(args, rank, world):
         "by_order": by_order,
         "by_mass": by_mass or None,
         "hybrid": hybrid,
+        "multishot": multishot,
+        "multimesh": multimesh,
         "e2e": r3.get("e2e"),
         "gpu_launches": 6 * args.steps,  # per step: 5 stage launches and one clock launch
         "clocks": r3["clocks"],
@@ -387,6 +478,7 @@ def main():
                     help="how the stage applies the wedge mass inverse (stored factor or factored in the stage)")
     ap.add_argument("--no-alt", action="store_true", help="skip the headline order in the other mass mode")
     ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid wedge + tet workload")
+    ap.add_argument("--no-batched", action="store_true", help="skip the multi-shot and multi-mesh workloads")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

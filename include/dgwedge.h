@@ -44,7 +44,7 @@
  * Work is issued asynchronously on the stream given to dg_bind.
  *
  * Call order: dg_mesh_create -> dg_set_order -> [dg_set_material]
- *   -> [dg_set_options] -> [dg_set_mass_mode] -> dg_device_bytes -> dg_bind -> dg_set_fields
+ *   -> [dg_set_shots] -> [dg_add_source] -> [dg_set_options] -> [dg_set_mass_mode] -> dg_device_bytes -> dg_bind -> dg_set_fields
  *   -> dg_step / dg_rhs / dg_energy / dg_get_fields.
  * Setters after dg_bind return DG_ERR_STATE.  Several contexts may live in one
  * process; contexts with different (N, precision) must not run concurrently
@@ -108,10 +108,27 @@ int dg_set_material(dg_ctx* ctx, const double* c2, const double* rho);
  * gets rhs_p += amp * R(t) * kappa_k (M^k)^{-1} l(x_s), where l(x_s) are its
  * Lagrange basis functions at the point, M^k its exact mass matrix and
  * R(t) = (1 - 2a) exp(-a), a = (pi f0 (t - t0))^2 a Ricker wavelet evaluated
- * at each Runge-Kutta stage time.  At most 64 sources; after dg_set_order and
+ * at each Runge-Kutta stage time.  At most 4096 (source, shot) pairs; after dg_set_order and
  * before dg_bind.  Errors: DG_ERR_ARG (point outside the mesh, f0 <= 0),
  * DG_ERR_STATE. */
 int dg_add_source(dg_ctx* ctx, double x, double y, double z, double f0, double t0, double amp);
+
+/* Shots: S independent states on the same mesh and material (seismic shots,
+ * ensembles), advanced together by every dg_step / dg_rhs launch.  Field
+ * arrays of dg_set_fields / dg_get_fields / dg_rhs then hold S canonical
+ * states one after another ([S][4][total_nodes]); dg_energy returns the sum
+ * over shots.  Inside the library the element tables are laid out shot-major
+ * (shot s of element i is element s K + i of the type's list), so the stage
+ * kernels see one larger mesh; each shot's result equals that of a one-shot
+ * context bit for bit.  After dg_set_order, before dg_bind; default 1.
+ * Errors: DG_ERR_ARG (shots < 1, shots x elements of a type >= 2^30, a source
+ * already placed on a later shot), DG_ERR_STATE. */
+int dg_set_shots(dg_ctx* ctx, int64_t shots);
+
+/* As dg_add_source, for one shot only (dg_add_source places the source in
+ * every shot).  Errors as dg_add_source, and DG_ERR_ARG for a shot index
+ * outside [0, shots). */
+int dg_add_shot_source(dg_ctx* ctx, int64_t shot, double x, double y, double z, double f0, double t0, double amp);
 
 /* Boundary condition (DG_BC_*), flux (DG_FLUX_*), arithmetic precision
  * (DG_F32: fields and arithmetic in float; DG_F64: double).

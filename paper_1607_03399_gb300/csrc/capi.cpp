@@ -105,9 +105,12 @@ struct dg_ctx {
   // options
   int bc = DG_BC_RIGID, flux = DG_FLUX_UPWIND, prec = DG_F32;
   int mass = DG_MASS_STORED;
+  // shots: independent copies of the state on the same mesh, advanced together
+  int64_t shots = 1;
   // point sources (pressure equation)
   struct Source {
     int64_t elem;
+    int64_t shot;  // -1: every shot
     double f0, t0, amp;
     std::vector<double> g;  // (M^k)^{-1} l(x_s), element node order (kappa applied in the kernels)
   };
@@ -289,13 +292,23 @@ double tet_stable_ratio(const dg_ctx* c, int64_t k) {
 // ----------------------------------------------------------------- blob
 struct BlobLayout {
   size_t w_vid, w_nbr, w_code, w_mat, w_canon, t_vid, t_nbr, t_code, t_mat, t_canon, vx, vy, vz, err, partials, energy,
-      tmass, wops, src, srcg, clock, wfac, wxyz, txyz, tops, total;
+      tmass, wops, src, srcg, clock, wfac, wxyz, txyz, tops, wsrng, tsrng, total;
 };
+
+// Shots are laid out shot-major over the type-local element lists: the
+// device-side (virtual) element s K + i is type-local element i of shot s.
+int64_t vKw(const dg_ctx* c) { return c->shots * int64_t(c->wedges.size()); }
+int64_t vKt(const dg_ctx* c) { return c->shots * int64_t(c->tets.size()); }
+int64_t nsrc_dev(const dg_ctx* c) {
+  int64_t n = 0;
+  for (const auto& sc : c->sources) n += sc.shot < 0 ? c->shots : 1;
+  return n;
+}
 
 BlobLayout blob_layout(const dg_ctx* c) {
   const size_t rs = c->prec == DG_F64 ? 8 : 4;
-  const int64_t Kwp = nblk(int64_t(c->wedges.size())) * kB, Ktp = nblk(int64_t(c->tets.size())) * kB;
-  const int64_t nparts = (nblk(int64_t(c->wedges.size())) + 3) / 4 + (nblk(int64_t(c->tets.size())) + 3) / 4 + 1;
+  const int64_t Kwp = nblk(vKw(c)) * kB, Ktp = nblk(vKt(c)) * kB;
+  const int64_t nparts = (nblk(vKw(c)) + 3) / 4 + (nblk(vKt(c)) + 3) / 4 + 1;
   BlobLayout L;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -321,7 +334,10 @@ BlobLayout blob_layout(const dg_ctx* c) {
   L.energy = take(8);
   L.tmass = take(size_t(npt_of(c->N)) * npt_of(c->N) * rs);
   L.wops = take(size_t(3 * nt_of(c->N) * nt_of(c->N) + (c->N + 1) * (c->N + 1)) * rs);
-  L.src = take(sizeof(SourceDev) * kMaxSources);
+  L.src = take(sizeof(SourceDev) * size_t(std::max<int64_t>(1, nsrc_dev(c))));
+  // per block [begin, end) of its sources in the element-sorted source list
+  L.wsrng = take(size_t(2) * nblk(vKw(c)) * 4 + 4);
+  L.tsrng = take(size_t(2) * nblk(vKt(c)) * 4 + 4);
   size_t ng = 0;
   for (const auto& sc : c->sources) ng += sc.g.size();
   L.srcg = take((ng > 0 ? ng : 1) * rs);
@@ -347,18 +363,23 @@ template <typename real>
 void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>& blob) {
   blob.assign(L.total, 0);
   const int64_t Kw = int64_t(c->wedges.size()), Kt = int64_t(c->tets.size());
-  const int64_t Kwp = nblk(Kw) * kB, Ktp = nblk(Kt) * kB;
+  const int64_t S = c->shots, T = c->wedge_nodes + c->tet_nodes;
+  const int64_t VKw = S * Kw, VKt = S * Kt;
+  const int64_t Kwp = nblk(VKw) * kB, Ktp = nblk(VKt) * kB;
+  // virtual id of (shot s, input element n)
+  auto vid = [&](int64_t s, int64_t n) { return s * (c->etype[n] == DG_WEDGE ? Kw : Kt) + c->local[n]; };
   int* w_vid = reinterpret_cast<int*>(blob.data() + L.w_vid);
   int* w_nbr = reinterpret_cast<int*>(blob.data() + L.w_nbr);
   int* w_code = reinterpret_cast<int*>(blob.data() + L.w_code);
   real* w_mat = reinterpret_cast<real*>(blob.data() + L.w_mat);
   int64_t* w_canon = reinterpret_cast<int64_t*>(blob.data() + L.w_canon);
   for (int64_t w = 0; w < Kwp; ++w) {
-    const int64_t k = c->wedges[w < Kw ? w : 0];  // padding replicates a valid element
+    const bool real_slot = w < VKw;  // padding replicates a valid element with no neighbours
+    const int64_t s = real_slot ? w / Kw : 0, k = c->wedges[real_slot ? w % Kw : 0];
     for (int v = 0; v < 6; ++v) w_vid[v * Kwp + w] = int(c->EToV[k * 6 + v]);
     for (int f = 0; f < 5; ++f) {
-      const int64_t n = (w < Kw) ? c->nbr[k][f] : -1;
-      w_nbr[f * Kwp + w] = (n < 0) ? -1 : int(c->local[n]);
+      const int64_t n = real_slot ? c->nbr[k][f] : -1;
+      w_nbr[f * Kwp + w] = (n < 0) ? -1 : int(vid(s, n));
       w_code[f * Kwp + w] = (n < 0) ? 0 : c->code[k][f];
     }
     {
@@ -375,7 +396,7 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
     w_mat[0 * Kwp + w] = real(c->rho[k] * c->c2[k]);
     w_mat[1 * Kwp + w] = real(1.0 / c->rho[k]);
     w_mat[2 * Kwp + w] = real(c->rho[k] * cc);
-    if (w < Kw) w_canon[w] = c->node_off[k];
+    if (real_slot) w_canon[w] = 4 * s * T + c->node_off[k];
   }
   int* t_vid = reinterpret_cast<int*>(blob.data() + L.t_vid);
   int* t_nbr = reinterpret_cast<int*>(blob.data() + L.t_nbr);
@@ -383,11 +404,12 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
   real* t_mat = reinterpret_cast<real*>(blob.data() + L.t_mat);
   int64_t* t_canon = reinterpret_cast<int64_t*>(blob.data() + L.t_canon);
   for (int64_t t = 0; t < Ktp; ++t) {
-    const int64_t k = c->tets[t < Kt ? t : 0];
+    const bool real_slot = t < VKt;
+    const int64_t s = real_slot ? t / Kt : 0, k = c->tets[real_slot ? t % Kt : 0];
     for (int v = 0; v < 4; ++v) t_vid[v * Ktp + t] = int(c->EToV[k * 6 + v]);
     for (int f = 0; f < 4; ++f) {
-      const int64_t n = (t < Kt) ? c->nbr[k][f] : -1;
-      t_nbr[f * Ktp + t] = (n < 0) ? -1 : int(c->local[n]);
+      const int64_t n = real_slot ? c->nbr[k][f] : -1;
+      t_nbr[f * Ktp + t] = (n < 0) ? -1 : int(vid(s, n));
       t_code[f * Ktp + t] = (n < 0) ? 0 : c->code[k][f];
     }
     {
@@ -399,22 +421,48 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
     t_mat[0 * Ktp + t] = real(c->rho[k] * c->c2[k]);
     t_mat[1 * Ktp + t] = real(1.0 / c->rho[k]);
     t_mat[2 * Ktp + t] = real(c->rho[k] * cc);
-    if (t < Kt) t_canon[t] = c->node_off[k];
+    if (real_slot) t_canon[t] = 4 * s * T + c->node_off[k];
   }
-  SourceDev* sd = reinterpret_cast<SourceDev*>(blob.data() + L.src);
-  real* sg = reinterpret_cast<real*>(blob.data() + L.srcg);
-  int goff = 0;
-  for (size_t i = 0; i < c->sources.size(); ++i) {
-    const auto& sc = c->sources[i];
-    sd[i].type = c->etype[sc.elem];
-    sd[i].elem = int(c->local[sc.elem]);
-    sd[i].goff = goff;
-    sd[i].pad = 0;
-    sd[i].f0 = sc.f0;
-    sd[i].t0 = sc.t0;
-    sd[i].amp = sc.amp;
-    for (size_t n = 0; n < sc.g.size(); ++n) sg[goff + n] = real(sc.g[n]);
-    goff += int(sc.g.size());
+  // sources: one device entry per (source, shot), sorted by (type, virtual element);
+  // each element block records the range of its entries
+  {
+    struct Ent {
+      int type;
+      int64_t elem;
+      size_t src;
+    };
+    std::vector<Ent> ents;
+    for (size_t i = 0; i < c->sources.size(); ++i) {
+      const auto& sc = c->sources[i];
+      for (int64_t sh = 0; sh < S; ++sh)
+        if (sc.shot < 0 || sc.shot == sh) ents.push_back({int(c->etype[sc.elem]), vid(sh, sc.elem), i});
+    }
+    std::stable_sort(ents.begin(), ents.end(),
+                     [](const Ent& x, const Ent& y) { return x.type != y.type ? x.type < y.type : x.elem < y.elem; });
+    std::vector<int> goffs(c->sources.size());
+    real* sg = reinterpret_cast<real*>(blob.data() + L.srcg);
+    int goff = 0;
+    for (size_t i = 0; i < c->sources.size(); ++i) {
+      goffs[i] = goff;
+      for (size_t n = 0; n < c->sources[i].g.size(); ++n) sg[goff + n] = real(c->sources[i].g[n]);
+      goff += int(c->sources[i].g.size());
+    }
+    SourceDev* sd = reinterpret_cast<SourceDev*>(blob.data() + L.src);
+    int* wr = reinterpret_cast<int*>(blob.data() + L.wsrng);
+    int* tr = reinterpret_cast<int*>(blob.data() + L.tsrng);
+    for (size_t i = 0; i < ents.size(); ++i) {
+      const auto& sc = c->sources[ents[i].src];
+      sd[i].type = ents[i].type;
+      sd[i].elem = int(ents[i].elem);
+      sd[i].goff = goffs[ents[i].src];
+      sd[i].pad = 0;
+      sd[i].f0 = sc.f0;
+      sd[i].t0 = sc.t0;
+      sd[i].amp = sc.amp;
+      int* rng = (ents[i].type == DG_WEDGE ? wr : tr) + 2 * (ents[i].elem / kB);
+      if (rng[1] == rng[0]) rng[0] = int(i);  // first entry of the block (ranges start empty)
+      rng[1] = int(i) + 1;
+    }
   }
   real* vx = reinterpret_cast<real*>(blob.data() + L.vx);
   real* vy = reinterpret_cast<real*>(blob.data() + L.vy);
@@ -460,8 +508,9 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
     const int nt = R.Nt, nl = nt * (nt + 1) / 2;
     real* fac = reinterpret_cast<real*>(blob.data() + L.wfac);
     std::vector<double> Mk(size_t(nt) * nt), Lk(size_t(nt) * nt);
-    for (int64_t w = 0; w < Kwp; ++w) {
-      const int64_t k = c->wedges[w < Kw ? w : 0];
+    std::vector<real> one(size_t(Kw) * nl);  // per type-local wedge, then copied to every shot's slot
+    for (int64_t w = 0; w < Kw; ++w) {
+      const int64_t k = c->wedges[w];
       const int64_t* ev = &c->EToV[k * 6];
       const double* P[6];
       for (int v = 0; v < 6; ++v) P[v] = &c->VX[ev[v] * 3];
@@ -476,11 +525,13 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
           Lk[size_t(i) * nt + l] = (l < i) ? sum / Lk[size_t(l) * nt + l] : std::sqrt(sum);
         }
       }
-      const int64_t b = w / kB, lane = w % kB;
       for (int i = 0; i < nt; ++i)
         for (int l = 0; l <= i; ++l)
-          fac[(b * nl + i * (i + 1) / 2 + l) * kB + lane] =
-              real(l < i ? Lk[size_t(i) * nt + l] : 1.0 / Lk[size_t(i) * nt + i]);
+          one[size_t(w) * nl + i * (i + 1) / 2 + l] = real(l < i ? Lk[size_t(i) * nt + l] : 1.0 / Lk[size_t(i) * nt + i]);
+    }
+    for (int64_t w = 0; w < Kwp; ++w) {
+      const int64_t lw = w < VKw ? w % Kw : 0, b = w / kB, lane = w % kB;
+      for (int q = 0; q < nl; ++q) fac[(b * nl + q) * kB + lane] = one[size_t(lw) * nl + q];
     }
   }
 }
@@ -488,7 +539,7 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
 template <typename real>
 void fill_devmesh(const dg_ctx* c, const BlobLayout& L, DevMesh<real>& m) {
   unsigned char* b = static_cast<unsigned char*>(c->d_mesh);
-  const int64_t Kw = int64_t(c->wedges.size()), Kt = int64_t(c->tets.size());
+  const int64_t Kw = vKw(c), Kt = vKt(c);
   m.Kw = int(Kw);
   m.Kw_pad = int(nblk(Kw) * kB);
   m.nblk_w = int(nblk(Kw));
@@ -514,7 +565,9 @@ void fill_devmesh(const dg_ctx* c, const BlobLayout& L, DevMesh<real>& m) {
   m.tet_mass = reinterpret_cast<const real*>(b + L.tmass);
   m.src = reinterpret_cast<const SourceDev*>(b + L.src);
   m.src_g = reinterpret_cast<const real*>(b + L.srcg);
-  m.nsrc = int(c->sources.size());
+  m.nsrc = int(nsrc_dev(c));
+  m.w_srng = reinterpret_cast<const int*>(b + L.wsrng);
+  m.t_srng = reinterpret_cast<const int*>(b + L.tsrng);
   m.clock = reinterpret_cast<double*>(b + L.clock);
   m.w_fac = c->mass == DG_MASS_STORED ? reinterpret_cast<const real*>(b + L.wfac) : nullptr;
   m.w_xyz = reinterpret_cast<const real*>(b + L.wxyz);
@@ -526,7 +579,7 @@ void fill_devmesh(const dg_ctx* c, const BlobLayout& L, DevMesh<real>& m) {
 
 size_t field_bytes_of(const dg_ctx* c) {
   const size_t rs = c->prec == DG_F64 ? 8 : 4;
-  const int64_t nw = nblk(int64_t(c->wedges.size())), nt = nblk(int64_t(c->tets.size()));
+  const int64_t nw = nblk(vKw(c)), nt = nblk(vKt(c));
   return align256(size_t(nw * 4 * npw_of(c->N) * kB + nt * 4 * npt_of(c->N) * kB) * rs);
 }
 
@@ -778,13 +831,13 @@ int dg_set_material(dg_ctx* c, const double* c2, const double* rho) {
   return DG_OK;
 }
 
-int dg_add_source(dg_ctx* c, double x, double y, double z, double f0, double t0, double amp) {
-  if (!c) return DG_ERR_ARG;
+static int add_source(dg_ctx* c, int64_t shot, double x, double y, double z, double f0, double t0, double amp) {
   if (c->bound) return c->fail(DG_ERR_STATE, "dg_add_source after dg_bind");
   if (!c->N) return c->fail(DG_ERR_STATE, "dg_add_source needs dg_set_order first");
   if (!(f0 > 0) || !std::isfinite(t0) || !std::isfinite(amp))
     return c->fail(DG_ERR_ARG, "source frequency must be positive and t0, amp finite");
-  if (int(c->sources.size()) >= kMaxSources) return c->fail(DG_ERR_ARG, "too many sources");
+  if (shot >= c->shots) return c->fail(DG_ERR_ARG, "shot index out of range");
+  if (nsrc_dev(c) + (shot < 0 ? c->shots : 1) > kMaxSources) return c->fail(DG_ERR_ARG, "too many sources");
   const RefElems& R = *c->ref;
   const double* V = c->VX.data();
   const double tol = 1e-12;
@@ -828,6 +881,7 @@ int dg_add_source(dg_ctx* c, double x, double y, double z, double f0, double t0,
     if (!inside) continue;
     dg_ctx::Source sc;
     sc.elem = k;
+    sc.shot = shot;
     sc.f0 = f0;
     sc.t0 = t0;
     sc.amp = amp;
@@ -867,6 +921,30 @@ int dg_add_source(dg_ctx* c, double x, double y, double z, double f0, double t0,
     return DG_OK;
   }
   return c->fail(DG_ERR_ARG, "source point lies outside the mesh");
+}
+
+int dg_add_source(dg_ctx* c, double x, double y, double z, double f0, double t0, double amp) {
+  if (!c) return DG_ERR_ARG;
+  return add_source(c, -1, x, y, z, f0, t0, amp);
+}
+
+int dg_add_shot_source(dg_ctx* c, int64_t shot, double x, double y, double z, double f0, double t0, double amp) {
+  if (!c) return DG_ERR_ARG;
+  if (shot < 0) return c->fail(DG_ERR_ARG, "shot index out of range");
+  return add_source(c, shot, x, y, z, f0, t0, amp);
+}
+
+int dg_set_shots(dg_ctx* c, int64_t shots) {
+  if (!c) return DG_ERR_ARG;
+  if (c->bound) return c->fail(DG_ERR_STATE, "dg_set_shots after dg_bind");
+  if (!c->N) return c->fail(DG_ERR_STATE, "dg_set_shots needs dg_set_order first");
+  if (shots < 1) return c->fail(DG_ERR_ARG, "shots must be at least 1");
+  for (const auto& sc : c->sources)
+    if (sc.shot >= shots) return c->fail(DG_ERR_ARG, "a source refers to a shot beyond the new count");
+  const int64_t K = int64_t(std::max(c->wedges.size(), c->tets.size()));
+  if (shots * K >= (int64_t(1) << 30)) return c->fail(DG_ERR_ARG, "shots x elements exceeds 2^30");
+  c->shots = shots;
+  return DG_OK;
 }
 
 int dg_set_options(dg_ctx* c, int bc, int flux, int precision) {
@@ -1076,7 +1154,7 @@ int dg_set_fields(dg_ctx* c, const void* q, int on_device) {
   int rc = ensure_ops(c);
   if (rc) return rc;
   const size_t rs = c->prec == DG_F64 ? 8 : 4;
-  const size_t bytes = size_t(4) * (c->wedge_nodes + c->tet_nodes) * rs;
+  const size_t bytes = size_t(4) * c->shots * (c->wedge_nodes + c->tet_nodes) * rs;
   const void* src = q;
   if (!on_device) {
     cudaError_t e = cudaMemcpyAsync(c->d_q[1 - c->cur], q, bytes, cudaMemcpyHostToDevice, c->stream);
@@ -1103,7 +1181,7 @@ int dg_get_fields(dg_ctx* c, void* q, int on_device) {
   if (!q) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_get_fields before dg_bind");
   const size_t rs = c->prec == DG_F64 ? 8 : 4;
-  const size_t bytes = size_t(4) * (c->wedge_nodes + c->tet_nodes) * rs;
+  const size_t bytes = size_t(4) * c->shots * (c->wedge_nodes + c->tet_nodes) * rs;
   void* dst = on_device ? q : c->d_q[1 - c->cur];
   int rc = launch_pack(c, dst, c->d_q[c->cur], true, c->stream);
   if (rc) return rc;
@@ -1254,7 +1332,7 @@ int dg_energy_static(dg_ctx* c, const void* d_q, double* E) {
   if (!c) return DG_ERR_ARG;
   if (!d_q || !E) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_energy_static before dg_bind");
-  const int64_t K = int64_t(c->wedges.size()) + int64_t(c->tets.size());
+  const int64_t K = vKw(c) + vKt(c);
   const int64_t nblocks = (K + 127) / 128;
   if (nblocks > kStaticPartials)
     return c->fail(DG_ERR_ARG, "dg_energy_static supports at most " + std::to_string(int64_t(kStaticPartials) * 128) +

@@ -70,7 +70,7 @@ struct SourceDev {
   int pad;
   double f0, t0, amp;
 };
-constexpr int kMaxSources = 64;
+constexpr int kMaxSources = 4096;  // device entries: (source, shot) pairs
 
 template <typename real>
 struct DevMesh {
@@ -103,6 +103,8 @@ struct DevMesh {
   const real* w_xyz = nullptr;       // per wedge block [12][32]: bottom x, y; bottom and top z
   const real* t_xyz = nullptr;       // per tet block [12][32]: x, y, z of the four vertices
   const real* t_ops = nullptr;       // tet stage operators, shared-memory image
+  const int* w_srng = nullptr;       // per wedge block [begin, end) of its entries in src
+  const int* t_srng = nullptr;       // per tet block likewise
 };
 
 template <typename real>

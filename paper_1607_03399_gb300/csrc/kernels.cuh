@@ -177,10 +177,13 @@ __device__ __forceinline__ double ricker(double f0, double tau) {
   const double a = (3.14159265358979323846 * f0 * tau) * (3.14159265358979323846 * f0 * tau);
   return (1.0 - 2.0 * a) * exp(-a);
 }
-// True when a point source lies in element (type, elem).
+// True when a point source lies in element (type, elem): the entries, sorted by
+// element, of its 32-element block are scanned.
 __device__ __forceinline__ bool has_source(const DevMesh<real>& M, int type, int elem) {
-  for (int s = 0; s < M.nsrc; ++s)
-    if (M.src[s].type == type && M.src[s].elem == elem) return true;
+  const int* rng = (type == 6 ? M.w_srng : M.t_srng) + 2 * (elem >> 5);
+  const int b = rng[0], e = rng[1];
+  for (int s = b; s < e; ++s)
+    if (M.src[s].elem == elem) return true;
   return false;
 }
 // Point-source forcing of element (type, elem) at time t added to the pressure
@@ -190,10 +193,12 @@ __device__ __forceinline__ bool has_source(const DevMesh<real>& M, int type, int
 template <int C>
 __device__ __forceinline__ void add_sources(const DevMesh<real>& M, int type, int elem, int n0, int np, double t,
                                             real (&acc)[C]) {
+  const int* rng = (type == 6 ? M.w_srng : M.t_srng) + 2 * (elem >> 5);
+  const int sb = rng[0], se = rng[1];
 #pragma unroll 1
-  for (int s = 0; s < M.nsrc; ++s) {
+  for (int s = sb; s < se; ++s) {
     const SourceDev& sd = M.src[s];
-    if (sd.type != type || sd.elem != elem) continue;
+    if (sd.elem != elem) continue;
     const real w = real(sd.amp * ricker(sd.f0, t - sd.t0));
     const real* __restrict__ g = M.src_g + sd.goff + n0;
 #pragma unroll

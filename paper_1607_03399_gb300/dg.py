@@ -27,7 +27,7 @@ DG_FLUX_UPWIND, DG_FLUX_CENTRAL = 0, 1
 DG_F32, DG_F64 = 0, 1
 DG_MASS_ONTHEFLY, DG_MASS_STORED = 0, 1
 
-EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_options", "dg_set_mass_mode", "dg_num_nodes",
+EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_shots", "dg_add_shot_source", "dg_set_options", "dg_set_mass_mode", "dg_num_nodes",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
            "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_stage_times", "dg_sync", "dg_time",
            "dg_stable_dt", "dg_last_error", "dg_destroy")
@@ -56,6 +56,8 @@ def lib():
         "dg_set_order": (c_int, [P, c_int]),
         "dg_set_material": (c_int, [P, P, P]),
         "dg_add_source": (c_int, [P, c_double, c_double, c_double, c_double, c_double, c_double]),
+        "dg_set_shots": (c_int, [P, c_int64]),
+        "dg_add_shot_source": (c_int, [P, c_int64, c_double, c_double, c_double, c_double, c_double, c_double]),
         "dg_set_options": (c_int, [P, c_int, c_int, c_int]),
         "dg_set_mass_mode": (c_int, [P, c_int]),
         "dg_num_nodes": (c_int, [P, POINTER(c_int64), POINTER(c_int64)]),
@@ -127,6 +129,14 @@ def dg_set_material(ctx, c2, rho):
 
 def dg_add_source(ctx, x: float, y: float, z: float, f0: float, t0: float, amp: float):
     _check(ctx, lib().dg_add_source(ctx, x, y, z, f0, t0, amp))
+
+
+def dg_set_shots(ctx, shots: int):
+    _check(ctx, lib().dg_set_shots(ctx, shots))
+
+
+def dg_add_shot_source(ctx, shot: int, x, y, z, f0, t0, amp):
+    _check(ctx, lib().dg_add_shot_source(ctx, shot, x, y, z, f0, t0, amp))
 
 
 def dg_set_options(ctx, bc: int, flux: int, precision: int):
@@ -247,10 +257,14 @@ class Solver:
     """One mesh, one order, bound to one CUDA device and stream.
 
     Device memory (mesh blob, two state buffers, residual) is allocated as
-    torch uint8 tensors and handed to the library by pointer."""
+    torch uint8 tensors and handed to the library by pointer.  With shots > 1
+    the state arrays are [shots][4][total_nodes] (else [4][total_nodes]);
+    `sources` go into every shot, `shot_sources` ((shot, x, y, z, f0, t0, amp))
+    into one."""
 
     def __init__(self, VX, EToV, etype, N: int, c2=None, rho=None, bc: str = "rigid", flux: str = "upwind",
-                 precision: str = "f32", device: str = "cuda:0", stream=None, sources=(), mass: str = "stored"):
+                 precision: str = "f32", device: str = "cuda:0", stream=None, sources=(), mass: str = "stored",
+                 shots: int = 1, shot_sources=()):
         import torch
         self.torch = torch
         self.ctx = dg_mesh_create(VX, EToV, etype)
@@ -261,14 +275,19 @@ class Solver:
                 dg_set_material(self.ctx, np.ones(K) if c2 is None else c2, np.ones(K) if rho is None else rho)
             dg_set_options(self.ctx, BC[bc], FLUX[flux], PREC[precision])
             dg_set_mass_mode(self.ctx, MASS[mass])
+            dg_set_shots(self.ctx, shots)
+            self.shots = shots
             for src in sources:       # (x, y, z, f0, t0, amp)
                 dg_add_source(self.ctx, *src)
+            for src in shot_sources:  # (shot, x, y, z, f0, t0, amp)
+                dg_add_shot_source(self.ctx, *src)
             self.N = N
             self.precision = precision
             self.dtype = torch.float32 if precision == "f32" else torch.float64
             self.np_dtype = np.float32 if precision == "f32" else np.float64
             self.wedge_nodes, self.tet_nodes = dg_num_nodes(self.ctx)
             self.total_nodes = self.wedge_nodes + self.tet_nodes
+            self.field_shape = (4, self.total_nodes) if shots == 1 else (shots, 4, self.total_nodes)
             self.device = torch.device(device)
             mb, fb = dg_device_bytes(self.ctx)
             self.mesh_bytes, self.field_bytes = mb, fb
@@ -300,16 +319,16 @@ class Solver:
             self._keep = q
         else:
             qh = np.ascontiguousarray(q, dtype=self.np_dtype)
-            assert qh.shape == (4, self.total_nodes)
+            assert qh.shape == self.field_shape
             dg_set_fields(self.ctx, qh.ctypes.data, 0)
 
     def get_fields(self, device: bool = False):
         if device:
-            out = self.torch.empty((4, self.total_nodes), dtype=self.dtype, device=self.device)
+            out = self.torch.empty(self.field_shape, dtype=self.dtype, device=self.device)
             dg_get_fields(self.ctx, out.data_ptr(), 1)
             self.stream.synchronize()
             return out
-        out = np.empty((4, self.total_nodes), dtype=self.np_dtype)
+        out = np.empty(self.field_shape, dtype=self.np_dtype)
         dg_get_fields(self.ctx, out.ctypes.data, 0)
         return out
 

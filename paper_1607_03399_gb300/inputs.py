@@ -299,3 +299,30 @@ def standing_mode_biunit_cube(xyz: np.ndarray, t: float):
     st = math.sin(w * t) / math.sqrt(3.0)
     return np.stack([cx * cy * cz * math.cos(w * t), sx * cy * cz * st,
                      cx * sy * cz * st, cx * cy * sz * st])
+
+
+def merge_meshes(meshes, shift=(2.0, 0.0, 0.0)) -> Mesh:
+    """Disjoint union of meshes (many small meshes advanced in one launch):
+    vertex lists concatenated, mesh i translated by i * shift so the pieces do
+    not touch, element lists concatenated in order.  Returns the merged mesh;
+    meta["offsets"] holds each piece's first element."""
+    VX, EToV, etype, offs = [], [], [], []
+    nv = 0
+    ne = 0
+    for i, m in enumerate(meshes):
+        VX.append(m.VX + np.asarray(shift, dtype=np.float64) * i)
+        E = m.EToV.copy()
+        E[E >= 0] += nv
+        EToV.append(E)
+        etype.append(m.etype)
+        offs.append(ne)
+        nv += m.VX.shape[0]
+        ne += m.K
+    return Mesh(np.vstack(VX), np.vstack(EToV), np.concatenate(etype), name="merged", meta={"offsets": offs})
+
+
+def surface_shots(nshots: int, seed: int, depth: float = 0.01, margin: float = 0.05):
+    """Seeded source positions just below the top surface z = 1 of [0,1]^3."""
+    rng = np.random.default_rng(seed)
+    xy = rng.uniform(margin, 1.0 - margin, size=(nshots, 2))
+    return [(float(x), float(y), 1.0 - depth) for x, y in xy]

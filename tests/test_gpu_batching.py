@@ -1,0 +1,69 @@
+"""Batched forms on the GPU: several shots of one mesh in one launch, and several
+uneven meshes merged into one launch.  Each shot (each mesh) must reproduce the
+result of its own one-shot (one-mesh) context bit for bit: the kernels do the
+same arithmetic per element whatever block an element lands in."""
+import numpy as np
+import pytest
+
+from paper_1607_03399_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("CUDA not available", allow_module_level=True)
+
+from paper_1607_03399_gb300.dg import Solver  # noqa: E402
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+@pytest.mark.parametrize("meshname", ["wedges", "hybrid"])
+def test_shots_match_single_shot_runs(precision, meshname):
+    m = I.cube_wavy_mesh(4, 3, 0.03) if meshname == "wedges" else I.hybrid_mesh(3, 2, 1)
+    c2, rho = I.random_material(m.K, 7, 1.0, 2.0, 0.5, 1.5)
+    S = 3
+    pos = [(0.31, 0.62, 0.4), (0.7, 0.2, 0.55), (0.5, 0.5, 0.2)]
+    shot_sources = [(s, *pos[s], 6.0 + s, 0.05, 1.0 + s) for s in range(S)]
+    B = Solver(m.VX, m.EToV, m.etype, 3, c2, rho, precision=precision, shots=S, shot_sources=shot_sources,
+               sources=[(0.45, 0.4, 0.5, 5.0, 0.0, 0.3)])
+    rng = np.random.default_rng(1)
+    q = rng.uniform(-1, 1, size=(S, 4, B.total_nodes)).astype(B.np_dtype)
+    B.set_fields(q)
+    dt = B.stable_dt(0.4)
+    B.step(dt, 12)
+    qb = B.get_fields()
+    rb = B.rhs(q).cpu().numpy()
+    B.close()
+    for s in range(S):
+        A = Solver(m.VX, m.EToV, m.etype, 3, c2, rho, precision=precision,
+                   sources=[(0.45, 0.4, 0.5, 5.0, 0.0, 0.3), (*pos[s], 6.0 + s, 0.05, 1.0 + s)])
+        A.set_fields(q[s])
+        A.step(dt, 12)
+        assert np.array_equal(A.get_fields(), qb[s]), s
+        assert np.array_equal(A.rhs(q[s]).cpu().numpy(), rb[s]), s
+        A.close()
+
+
+def test_merged_meshes_match_separate_runs():
+    """Three meshes of uneven size (wedge-only, hybrid, one-wedge) in one launch."""
+    parts = [I.cube_wavy_mesh(3, 2, 0.02), I.hybrid_mesh(2, 1, 1), I.cube_wavy_mesh(1, 1, 0.0)]
+    m = I.merge_meshes(parts)
+    c2, rho = I.random_material(m.K, 9, 1.0, 3.0)
+    Bm = Solver(m.VX, m.EToV, m.etype, 2, c2, rho, precision="f32")
+    rng = np.random.default_rng(3)
+    q = rng.uniform(-1, 1, size=(4, Bm.total_nodes)).astype(np.float32)
+    Bm.set_fields(q)
+    dt = Bm.stable_dt(0.4)
+    Bm.step(dt, 8)
+    qm = Bm.get_fields()
+    Bm.close()
+    node0 = 0
+    for i, p in enumerate(parts):
+        o = m.meta["offsets"][i]
+        A = Solver(p.VX, p.EToV, p.etype, 2, c2[o:o + p.K], rho[o:o + p.K], precision="f32")
+        n = A.total_nodes
+        A.set_fields(q[:, node0:node0 + n])
+        A.step(dt, 8)
+        assert np.array_equal(A.get_fields(), qm[:, node0:node0 + n]), i
+        A.close()
+        node0 += n

@@ -157,3 +157,43 @@ def test_call_order_and_argument_errors():
         assert mb4 - mb3 >= 32 * nl * 8 and mb4 - mb3 < 32 * nl * 8 + 256
     finally:
         dg.dg_destroy(ctx)
+
+
+def test_shots_arguments_and_sizes():
+    """dg_set_shots: validation, call order, and the state buffers holding every shot."""
+    m = I.cube_wavy_mesh(2, 2, 0.0)
+    ctx = dg.dg_mesh_create(m.VX, m.EToV, m.etype)
+    try:
+        _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_set_shots(ctx, 2))
+        dg.dg_set_order(ctx, 2)
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_set_shots(ctx, 0))
+        mb1, fb1 = dg.dg_device_bytes(ctx)
+        dg.dg_set_shots(ctx, 5)
+        mb5, fb5 = dg.dg_device_bytes(ctx)
+        wn, _ = dg.dg_num_nodes(ctx)
+        assert fb5 >= 5 * 4 * 4 * wn and fb5 > fb1 and mb5 > mb1
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_add_shot_source(ctx, 5, 0.5, 0.5, 0.5, 5.0, 0.1, 1.0))
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_add_shot_source(ctx, -1, 0.5, 0.5, 0.5, 5.0, 0.1, 1.0))
+        dg.dg_add_shot_source(ctx, 4, 0.5, 0.5, 0.5, 5.0, 0.1, 1.0)
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_set_shots(ctx, 4))   # would orphan the shot-4 source
+        dg.dg_set_shots(ctx, 6)
+    finally:
+        dg.dg_destroy(ctx)
+
+
+def test_merge_meshes_keeps_pieces_apart():
+    a, b = I.cube_wavy_mesh(2, 2, 0.02), I.hybrid_mesh(2, 1, 1)
+    m = I.merge_meshes([a, b])
+    assert m.K == a.K + b.K and m.meta["offsets"] == [0, a.K]
+    ctx = dg.dg_mesh_create(m.VX, m.EToV, m.etype)
+    try:
+        dg.dg_set_order(ctx, 1)
+        wn, tn = dg.dg_num_nodes(ctx)
+        nb = dg.dg_face_neighbors(ctx)
+        # N = 1: a wedge has 2 x 3 + 3 x 4 face nodes, a tet 4 x 3; nodes of piece a come first
+        per = np.where(m.etype == I.WEDGE, 18, 12)
+        Ta = 6 * a.K
+        split = int(per[: a.K].sum())
+        assert nb.size == per.sum() and (nb[:split] < Ta).all() and (nb[split:][nb[split:] >= 0] >= Ta).all()
+    finally:
+        dg.dg_destroy(ctx)
