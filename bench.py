@@ -222,7 +222,9 @@ def measure_order(N, args, torch, dev, m, c2, rho, mass):
     S.sync()
     ms = start.elapsed_time(end)
     dof = 4 * S.total_nodes
-    res = {"ms": ms, "dof": dof, "clocks": clk.summary(), "solver": S, "dt": dt, "q": q}
+    bpc, onthefly, us = S.autotune(10)
+    res = {"ms": ms, "dof": dof, "clocks": clk.summary(), "solver": S, "dt": dt, "q": q,
+           "autotune": {"blocks_per_cta": bpc, "factor_in_stage": onthefly, "stage_us": us}}
     return res
 
 
@@ -424,7 +426,8 @@ def run_ours(args, rank, world):
     for N, r in out.items():
         st = r["ms"] / 1e3 / (5 * args.steps)
         a = _alg_bytes_per_stage(K, nverts, r["dof"] // 4, N=N, mass=args.mass)
-        by_order[str(N)] = {"value": r["dof"] * 5 * args.steps / (r["ms_max"] / 1e3) / 1e9 * world,
+        by_order[str(N)] = {"autotune": r["autotune"],
+                            "value": r["dof"] * 5 * args.steps / (r["ms_max"] / 1e3) / 1e9 * world,
                             "ms_per_step": r["ms_max"] / args.steps, "stage_us": st * 1e6,
                             "alg_bytes_per_stage": a, "achieved_gbs": a / st / 1e9,
                             "frac": a / st / 1e9 / peak, "dof": r["dof"]}

@@ -217,6 +217,17 @@ int dg_step(dg_ctx* ctx, double dt, int64_t nsteps);
  * null outputs), DG_ERR_STATE (before dg_set_fields), DG_ERR_CUDA. */
 int dg_stage_times(dg_ctx* ctx, int nrep, double* us_wedge, double* us_tet);
 
+/* Launch autotuner (diagnostic plus configuration, not in the paper): times
+ * the wedge stage (as dg_stage_times, nrep launches each) in every launch
+ * variant this context can run -- 1 or 2 element blocks of 32 wedges per CTA
+ * (2 only for N = 3 in DG_F32), and, when the context stores the mass
+ * factors, reading them or recomputing them in the stage -- and keeps the
+ * fastest for later dg_step / dg_rhs calls.  *variant = 2 * blocks_per_cta +
+ * (1 if the factor is recomputed), *us = its mean microseconds per launch.
+ * All variants compute the same operator up to rounding.  Synchronous.
+ * Errors: DG_ERR_ARG, DG_ERR_STATE (before dg_bind), DG_ERR_CUDA. */
+int dg_autotune(dg_ctx* ctx, int nrep, int* variant, double* us);
+
 /* Discrete energy E = 1/2 sum_k (p^T M^k p / kappa_k + rho_k sum_c u_c^T M^k u_c)
  * with the scheme's exact mass matrices (Section 4.1), accumulated in double.
  * Synchronises the stream.  Returns DG_ERR_NONFINITE if E is not finite and

@@ -107,6 +107,10 @@ struct dg_ctx {
   int mass = DG_MASS_STORED;
   // shots: independent copies of the state on the same mesh, advanced together
   int64_t shots = 1;
+  // launch variant chosen by dg_autotune: wedge blocks per CTA (0 = default) and
+  // whether the stored mass factor is bypassed (factor recomputed in the stage)
+  int tuned_bpc = 0;
+  bool tuned_onthefly = false;
   // point sources (pressure equation)
   struct Source {
     int64_t elem;
@@ -598,6 +602,8 @@ int launch_stage(dg_ctx* c, const void* q_in, void* q_out, void* res, double a, 
     A.c_stage = cst;
     A.bc = c->bc;
     A.flux = c->flux;
+    A.wedge_bpc = c->tuned_bpc;
+    if (c->tuned_onthefly) A.m.w_fac = nullptr;
     rc = stage_f64(c->N, A, rk, s);
   } else {
     StageArgs<float> A;
@@ -611,6 +617,8 @@ int launch_stage(dg_ctx* c, const void* q_in, void* q_out, void* res, double a, 
     A.c_stage = cst;
     A.bc = c->bc;
     A.flux = c->flux;
+    A.wedge_bpc = c->tuned_bpc;
+    if (c->tuned_onthefly) A.m.w_fac = nullptr;
     rc = stage_f32(c->N, A, rk, s);
   }
   if (rc) return cuda_fail(c, cudaError_t(rc), "stage launch");
@@ -1304,6 +1312,47 @@ int dg_stage_times(dg_ctx* c, int nrep, double* us_w, double* us_t) {
   cudaEventDestroy(ev[1]);
   if (rc) return rc;
   return check_device_error(c);
+}
+
+int dg_autotune(dg_ctx* c, int nrep, int* variant, double* us) {
+  if (!c) return DG_ERR_ARG;
+  if (nrep < 1 || !variant || !us) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_autotune before dg_bind");
+  // candidates: (factor recomputed in the stage?, wedge blocks per CTA)
+  std::vector<std::pair<bool, int>> cand;
+  const int maxb = (c->prec == DG_F32 && c->N == 3) ? 2 : 1;
+  for (int onthefly = 0; onthefly < 2; ++onthefly) {
+    if (!onthefly && c->mass != DG_MASS_STORED) continue;
+    for (int b = 1; b <= maxb; ++b) cand.push_back({onthefly != 0, b});
+  }
+  double best = 0.0;
+  int besti = -1;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    c->tuned_onthefly = cand[i].first;
+    c->tuned_bpc = cand[i].second;
+    double tw = 0.0, tt = 0.0;
+    const int rc = dg_stage_times(c, nrep, &tw, &tt);
+    if (rc) {
+      c->tuned_onthefly = false;
+      c->tuned_bpc = 0;
+      return rc;
+    }
+    if (besti < 0 || tw < best) {
+      best = tw;
+      besti = int(i);
+    }
+  }
+  c->tuned_onthefly = cand[besti].first;
+  c->tuned_bpc = cand[besti].second;
+  // captured step graphs hold the previous launch shape: capture again on the next step
+  for (int p = 0; p < 2; ++p)
+    if (c->gexec[p]) {
+      cudaGraphExecDestroy(c->gexec[p]);
+      c->gexec[p] = nullptr;
+    }
+  *variant = (cand[besti].second << 1) | (cand[besti].first ? 1 : 0);
+  *us = best;
+  return DG_OK;
 }
 
 int dg_energy(dg_ctx* c, double* E) {

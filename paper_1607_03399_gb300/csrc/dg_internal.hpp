@@ -116,6 +116,7 @@ struct StageArgs {
   real rk_a = 0, rk_b = 0, dt = 0;
   double c_stage = 0;           // stage time = *clock + c_stage * dt
   int bc = 1, flux = 0;
+  int wedge_bpc = 0;            // wedge blocks per CTA: 0 = the default for the mass mode
 };
 
 enum : int { kErrTimeout = 1, kErrNonfinite = 2 };

@@ -1135,7 +1135,8 @@ template <int N>
 int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s) {
   if (a.m.nblk_w > 0) {
     constexpr int b2 = wedge_bpc_onthefly<N>();
-    if (a.m.w_fac != nullptr || b2 == 1)
+    const int want = a.wedge_bpc > 0 ? a.wedge_bpc : (a.m.w_fac != nullptr ? 1 : b2);
+    if (want == 1 || b2 == 1)
       k_wedge_stage<N, 1><<<a.m.nblk_w, 32 * (N + 1), wedge_smem_bytes<N, 1>(), s>>>(a, rk);
     else
       k_wedge_stage<N, b2><<<(a.m.nblk_w + b2 - 1) / b2, 32 * (N + 1) * b2, wedge_smem_bytes<N, b2>(), s>>>(a, rk);

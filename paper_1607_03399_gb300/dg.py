@@ -29,7 +29,7 @@ DG_MASS_ONTHEFLY, DG_MASS_STORED = 0, 1
 
 EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_shots", "dg_add_shot_source", "dg_set_options", "dg_set_mass_mode", "dg_num_nodes",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
-           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_stage_times", "dg_sync", "dg_time",
+           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_stage_times", "dg_autotune", "dg_sync", "dg_time",
            "dg_stable_dt", "dg_last_error", "dg_destroy")
 
 _lib = None
@@ -73,6 +73,7 @@ def lib():
         "dg_energy": (c_int, [P, POINTER(c_double)]),
         "dg_energy_static": (c_int, [P, P, POINTER(c_double)]),
         "dg_stage_times": (c_int, [P, c_int, POINTER(c_double), POINTER(c_double)]),
+        "dg_autotune": (c_int, [P, c_int, POINTER(c_int), POINTER(c_double)]),
         "dg_sync": (c_int, [P]),
         "dg_time": (c_int, [P, POINTER(c_double)]),
         "dg_stable_dt": (c_int, [P, c_double, POINTER(c_double)]),
@@ -222,6 +223,13 @@ def dg_stage_times(ctx, nrep: int):
     return w.value, t.value
 
 
+def dg_autotune(ctx, nrep: int):
+    """(variant, microseconds per wedge-stage launch) of the fastest launch variant, now in use."""
+    v, us = c_int(), c_double()
+    _check(ctx, lib().dg_autotune(ctx, nrep, ctypes.byref(v), ctypes.byref(us)))
+    return v.value, us.value
+
+
 def dg_sync(ctx):
     _check(ctx, lib().dg_sync(ctx))
 
@@ -352,6 +360,12 @@ class Solver:
         """(wedge, tet) mean microseconds per stage-kernel launch; the state is unchanged."""
         self._wait_torch()
         return dg_stage_times(self.ctx, nrep)
+
+    def autotune(self, nrep: int = 10):
+        """Pick the fastest wedge-stage launch variant: returns (blocks per CTA, factor in stage?, us)."""
+        self._wait_torch()
+        v, us = dg_autotune(self.ctx, nrep)
+        return v >> 1, bool(v & 1), us
 
     def energy(self) -> float:
         return dg_energy(self.ctx)

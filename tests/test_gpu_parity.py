@@ -251,3 +251,16 @@ def test_stage_times_leave_the_state_alone():
     S.step(dt, 2)
     assert _rel(S.get_fields(), O.step(q.astype(np.float64), dt, 2)) <= 1e-5
     S.close()
+
+
+def test_autotune_keeps_the_operator():
+    """dg_autotune picks a launch variant; steps taken with it still match the oracle."""
+    S, O = _pair(MESHES["bumpy150"](), 3, "f32")
+    q = I.random_fields(S.total_nodes, 6).astype(np.float32)
+    S.set_fields(q)
+    bpc, onthefly, us = S.autotune(3)
+    assert bpc in (1, 2) and us > 0
+    dt = O.stable_dt(0.4)
+    S.step(dt, 3)
+    assert _rel(S.get_fields(), O.step(q.astype(np.float64), dt, 3)) <= 1e-5
+    S.close()

@@ -137,6 +137,8 @@ def test_call_order_and_argument_errors():
         _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_set_options(ctx, 7, 0, 0))
         _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_set_material(ctx, -np.ones(m.K), np.ones(m.K)))
         _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_step(ctx, 0.1, 1))
+        _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_autotune(ctx, 2))
+        _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_stage_times(ctx, 2))
         _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_energy(ctx))
         buf = np.zeros(8)
         _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_set_fields(ctx, buf.ctypes.data, 0))
