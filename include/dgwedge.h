@@ -228,6 +228,61 @@ int dg_stage_times(dg_ctx* ctx, int nrep, double* us_wedge, double* us_tet);
  * Errors: DG_ERR_ARG, DG_ERR_STATE (before dg_bind), DG_ERR_CUDA. */
 int dg_autotune(dg_ctx* ctx, int nrep, int* variant, double* us);
 
+/* ---------------------------------------------------------------- receivers
+ * Pressure receivers (not in the paper; the inversion workloads need them):
+ * p sampled at (x, y, z) by the Lagrange basis of the containing element
+ * (lowest id on ties).  After dg_set_order, before dg_bind.  Returns the
+ * receiver index (>= 0) or DG_ERR_ARG (outside the mesh, more than 65536),
+ * DG_ERR_STATE. */
+int dg_add_receiver(dg_ctx* ctx, double x, double y, double z);
+
+/* Pressure of the current state at every receiver: device array
+ * d_out[shots][receivers] (reals of the context precision).  Async on the
+ * bound stream.  Errors: DG_ERR_ARG, DG_ERR_STATE. */
+int dg_sample(dg_ctx* ctx, void* d_out);
+
+/* Copy of the current packed state (dg_device_bytes' field_bytes) to / from a
+ * caller device buffer, for checkpoints.  dg_load_state also sets the
+ * simulation time to t.  dg_save_state is async; dg_load_state synchronises.
+ * Errors: DG_ERR_ARG, DG_ERR_STATE. */
+int dg_save_state(dg_ctx* ctx, void* d_dst);
+int dg_load_state(dg_ctx* ctx, const void* d_src, double t);
+
+/* ------------------------------------------------------------------ adjoint
+ * Discrete adjoint of dg_step for the misfit J = 1/2 sum_n sum_r
+ * (p_r(t_n) - d_r(t_n))^2 and its gradient with respect to the per-element
+ * kappa = rho c^2 and rho (not in the paper).  The method's operator A splits
+ * into a part that is skew-adjoint in the energy inner product (volume terms
+ * and the p-u couplings of the fluxes) and the symmetric penalty, so A^T =
+ * W P A P W^{-1} with W the energy mass (Section 4.1) and P = diag(1, -I)
+ * (velocity sign flip); in the variable mu = P W^{-1} lambda the adjoint of
+ * one LSRK45 step runs the forward stage with the update coefficients
+ * reversed, and receiver residuals enter exactly like point sources.  Meshes
+ * of wedges only; every shot shares the receivers.
+ *
+ * Use: dg_adjoint_bytes -> allocate -> dg_adjoint_bind (zeroes everything)
+ * -> for n = nsteps .. 1: dg_adjoint_inject(residuals of step n);
+ * dg_load_state(q_{n-1}, t_{n-1}); dg_adjoint_step(dt) -> dg_adjoint_gradient.
+ * dg_adjoint_step recomputes the forward step from the current state and
+ * time (which it leaves unchanged), then applies the five adjoint stages and
+ * accumulates the gradient terms.  Errors: DG_ERR_ARG, DG_ERR_STATE,
+ * DG_ERR_MESH (tetrahedra), DG_ERR_CUDA. */
+int dg_adjoint_bytes(const dg_ctx* ctx, size_t* bytes);
+int dg_adjoint_bind(dg_ctx* ctx, void* d_work);
+int dg_adjoint_reset(dg_ctx* ctx);
+/* d_resid[shots][receivers] (device, context precision) */
+int dg_adjoint_inject(dg_ctx* ctx, const void* d_resid);
+int dg_adjoint_step(dg_ctx* ctx, double dt);
+/* set the adjoint state: mu_Q and the next stage input x (normally b_5 mu_Q),
+ * canonical layout, host or device sources */
+int dg_adjoint_set(dg_ctx* ctx, const void* mu_q, const void* x, int on_device);
+/* the adjoint state in the variables mu = P W^{-1} lambda, canonical layout
+ * ([shots][4][total_nodes]), host or device destination */
+int dg_adjoint_get(dg_ctx* ctx, void* dst, int on_device);
+/* dJ/dkappa and dJ/drho per element (input order, host arrays of nelem; tets
+ * none), summed over shots.  Synchronous. */
+int dg_adjoint_gradient(dg_ctx* ctx, double* g_kappa, double* g_rho);
+
 /* Discrete energy E = 1/2 sum_k (p^T M^k p / kappa_k + rho_k sum_c u_c^T M^k u_c)
  * with the scheme's exact mass matrices (Section 4.1), accumulated in double.
  * Synchronises the stream.  Returns DG_ERR_NONFINITE if E is not finite and

@@ -1,0 +1,146 @@
+"""Receiver misfit and its gradient with respect to the per-element material,
+through the library's discrete adjoint of dg_step (every step of the sweep runs
+in the CUDA library; this module orders the calls and keeps checkpoints).
+
+J(c^2, rho) = 1/2 sum_{n=1..nsteps} sum_shots sum_r (p_r(t_n) - d_r(t_n))^2,
+with p_r the pressure at receiver r after step n.  The forward pass keeps a
+checkpoint of the state every `checkpoint_every` steps; the reverse pass
+re-runs each segment from its checkpoint to recover the step states and calls
+dg_adjoint_step once per step, which recomputes that step's five stages and
+accumulates dJ/dkappa, dJ/drho.  The chain rule to (c^2, rho) uses
+kappa = rho c^2.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .dg import Solver
+
+
+@dataclass
+class Problem:
+    """A seismic-style inversion setup on one mesh of wedges."""
+    VX: np.ndarray
+    EToV: np.ndarray
+    etype: np.ndarray
+    N: int
+    dt: float
+    nsteps: int
+    receivers: list                     # [(x, y, z)]
+    shot_sources: list = field(default_factory=list)   # [(shot, x, y, z, f0, t0, amp)]
+    shots: int = 1
+    precision: str = "f32"
+    bc: str = "rigid"
+    flux: str = "upwind"
+    checkpoint_every: int = 50
+    device: str = "cuda:0"
+
+    def solver(self, c2, rho) -> Solver:
+        return Solver(self.VX, self.EToV, self.etype, self.N, np.asarray(c2, dtype=np.float64),
+                      np.asarray(rho, dtype=np.float64), bc=self.bc, flux=self.flux, precision=self.precision,
+                      device=self.device, shots=self.shots, shot_sources=self.shot_sources,
+                      receivers=self.receivers)
+
+
+def forward(S: Solver, pb: Problem, q0=None):
+    """Traces [nsteps][shots][receivers] (device tensor) and the checkpoints {step: state}."""
+    torch = S.torch
+    S.set_fields(np.zeros(S.field_shape, dtype=S.np_dtype) if q0 is None else q0)
+    traces = torch.empty((pb.nsteps, pb.shots, S.nrec), dtype=S.dtype, device=S.device)
+    ck = {0: S.save_state()}
+    for n in range(1, pb.nsteps + 1):
+        S.step(pb.dt, 1)
+        S.sample(traces[n - 1])
+        if n % pb.checkpoint_every == 0 and n < pb.nsteps:
+            ck[n] = S.save_state()
+    S.sync()
+    return traces, ck
+
+
+def misfit(traces, data) -> float:
+    r = traces.double() - data.double()
+    return 0.5 * float((r * r).sum())
+
+
+def reverse(S: Solver, pb: Problem, traces, data, ck):
+    """dJ/dkappa, dJ/drho per element after a forward() on the same solver."""
+    torch = S.torch
+    resid = (traces - data.to(traces.dtype)).contiguous()
+    if getattr(S, "d_adj", None) is None:
+        S.adjoint_bind()
+    else:
+        S.adjoint_reset()
+    C = pb.checkpoint_every
+    starts = list(range(0, pb.nsteps, C))
+    for s0 in reversed(starts):
+        s1 = min(s0 + C, pb.nsteps)
+        # states q_{s0} .. q_{s1 - 1} of the segment
+        S.load_state(ck[s0], s0 * pb.dt)
+        states = [S.save_state()]
+        for n in range(s0 + 1, s1):
+            S.step(pb.dt, 1)
+            states.append(S.save_state())
+        for n in range(s1, s0, -1):
+            S.adjoint_inject(resid[n - 1])
+            S.load_state(states[n - 1 - s0], (n - 1) * pb.dt)
+            S.adjoint_step(pb.dt)
+    S.sync()
+    return S.adjoint_gradient()
+
+
+def material_gradient(c2, rho, gk, gr):
+    """(dJ/dc^2, dJ/drho at fixed c^2) from (dJ/dkappa, dJ/drho at fixed kappa)."""
+    c2 = np.asarray(c2, dtype=np.float64)
+    rho = np.asarray(rho, dtype=np.float64)
+    return rho * gk, gr + c2 * gk
+
+
+def misfit_and_gradient(pb: Problem, c2, rho, data):
+    S = pb.solver(c2, rho)
+    try:
+        traces, ck = forward(S, pb)
+        J = misfit(traces, data)
+        gk, gr = reverse(S, pb, traces, data, ck)
+    finally:
+        S.close()
+    return J, *material_gradient(c2, rho, gk, gr)
+
+
+def _autograd_function():
+    import torch
+
+    class AcousticMisfit(torch.autograd.Function):
+        """J(c^2, rho) with dJ/dc^2 and dJ/drho from the discrete adjoint.  The
+        forward pass runs the wave simulation and keeps its checkpoints; the
+        backward pass runs the adjoint sweep."""
+
+        @staticmethod
+        def forward(ctx, c2, rho, pb, data):
+            S = pb.solver(c2.detach().cpu().numpy(), rho.detach().cpu().numpy())
+            traces, ck = forward(S, pb)
+            ctx.state = (S, pb, traces, data, ck)
+            ctx.save_for_backward(c2, rho)
+            return torch.tensor(misfit(traces, data), dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            c2, rho = ctx.saved_tensors
+            S, pb, traces, data, ck = ctx.state
+            try:
+                gk, gr = reverse(S, pb, traces, data, ck)
+            finally:
+                S.close()
+                ctx.state = None
+            g2, grho = material_gradient(c2.detach().cpu().numpy(), rho.detach().cpu().numpy(), gk, gr)
+            s = float(gJ)
+            return (torch.as_tensor(s * g2, dtype=c2.dtype, device=c2.device),
+                    torch.as_tensor(s * grho, dtype=rho.dtype, device=rho.device), None, None)
+
+    return AcousticMisfit
+
+
+def acoustic_misfit(c2, rho, pb: Problem, data):
+    """Differentiable J(c^2, rho) (torch tensors of per-element values)."""
+    return _autograd_function().apply(c2, rho, pb, data)

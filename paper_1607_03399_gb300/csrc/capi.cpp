@@ -52,6 +52,26 @@ int energy_f32(int N, const DevMesh<float>& m, const float* q, void* s) { DGW_SW
 int clock_f32(int N, double* c, double dt, void* s) { DGW_SWITCH_N(N, launch_clock_f32, (c, dt, s)) }
 int clock_f64(int N, double* c, double dt, void* s) { DGW_SWITCH_N(N, launch_clock_f64, (c, dt, s)) }
 int energy_f64(int N, const DevMesh<double>& m, const double* q, void* s) { DGW_SWITCH_N(N, launch_energy_f64, (m, q, s)) }
+int sample_f32(int N, const DevMesh<float>& m, const float* q, float* o, int ns, void* s) {
+  DGW_SWITCH_N(N, launch_sample_f32, (m, q, o, ns, s))
+}
+int sample_f64(int N, const DevMesh<double>& m, const double* q, double* o, int ns, void* s) {
+  DGW_SWITCH_N(N, launch_sample_f64, (m, q, o, ns, s))
+}
+int inject_f32(int N, const DevMesh<float>& m, float* mu, float* x, const float* r, int ns, float b5, void* s) {
+  DGW_SWITCH_N(N, launch_inject_f32, (m, mu, x, r, ns, b5, s))
+}
+int inject_f64(int N, const DevMesh<double>& m, double* mu, double* x, const double* r, int ns, double b5, void* s) {
+  DGW_SWITCH_N(N, launch_inject_f64, (m, mu, x, r, ns, b5, s))
+}
+int grad_f32(int N, const DevMesh<float>& m, const float* x, const float* q, const float* r, double dt, int fl, int bc,
+             double* gk, double* gr, void* s) {
+  DGW_SWITCH_N(N, launch_grad_f32, (m, x, q, r, dt, fl, bc, gk, gr, s))
+}
+int grad_f64(int N, const DevMesh<double>& m, const double* x, const double* q, const double* r, double dt, int fl, int bc,
+             double* gk, double* gr, void* s) {
+  DGW_SWITCH_N(N, launch_grad_f64, (m, x, q, r, dt, fl, bc, gk, gr, s))
+}
 }  // namespace
 
 namespace {
@@ -107,10 +127,16 @@ struct dg_ctx {
   int mass = DG_MASS_STORED;
   // shots: independent copies of the state on the same mesh, advanced together
   int64_t shots = 1;
+  double t_stage_host = 0.0;  // staging for clock uploads
   // launch variant chosen by dg_autotune: wedge blocks per CTA (0 = default) and
   // whether the stored mass factor is bypassed (factor recomputed in the stage)
   int tuned_bpc = 0;
   bool tuned_onthefly = false;
+  // adjoint workspace (caller-owned): mu_Q, two stage-input buffers, residual,
+  // forward stage states Q_1..Q_4 and a scratch output, stage right-hand sides
+  // r_1..r_5, then the kappa and rho gradients (doubles per device wedge)
+  unsigned char* adj = nullptr;
+  int adj_x = 0;
   // point sources (pressure equation)
   struct Source {
     int64_t elem;
@@ -119,6 +145,12 @@ struct dg_ctx {
     std::vector<double> g;  // (M^k)^{-1} l(x_s), element node order (kappa applied in the kernels)
   };
   std::vector<Source> sources;
+  // receivers: pressure sampled at points (adjoint misfits)
+  struct Receiver {
+    int64_t elem;
+    std::vector<double> l, g;  // l(x_r) and (M^k)^{-1} l(x_r), element node order
+  };
+  std::vector<Receiver> receivers;
   // binding
   bool bound = false;
   int device = 0;
@@ -296,7 +328,7 @@ double tet_stable_ratio(const dg_ctx* c, int64_t k) {
 // ----------------------------------------------------------------- blob
 struct BlobLayout {
   size_t w_vid, w_nbr, w_code, w_mat, w_canon, t_vid, t_nbr, t_code, t_mat, t_canon, vx, vy, vz, err, partials, energy,
-      tmass, wops, src, srcg, clock, wfac, wxyz, txyz, tops, wsrng, tsrng, total;
+      tmass, wops, src, srcg, clock, wfac, wxyz, txyz, tops, wsrng, tsrng, rec, rgrp, rperm, recl, recg, total;
 };
 
 // Shots are laid out shot-major over the type-local element lists: the
@@ -342,6 +374,16 @@ BlobLayout blob_layout(const dg_ctx* c) {
   // per block [begin, end) of its sources in the element-sorted source list
   L.wsrng = take(size_t(2) * nblk(vKw(c)) * 4 + 4);
   L.tsrng = take(size_t(2) * nblk(vKt(c)) * 4 + 4);
+  {
+    const size_t nr = std::max<size_t>(1, c->receivers.size());
+    size_t nl = 1;
+    for (const auto& r : c->receivers) nl += r.l.size();
+    L.rec = take(sizeof(RecDev) * nr);
+    L.rgrp = take(sizeof(RecGroup) * nr);
+    L.rperm = take(sizeof(int) * nr);
+    L.recl = take(nl * rs);
+    L.recg = take(nl * rs);
+  }
   size_t ng = 0;
   for (const auto& sc : c->sources) ng += sc.g.size();
   L.srcg = take((ng > 0 ? ng : 1) * rs);
@@ -468,6 +510,41 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
       rng[1] = int(i) + 1;
     }
   }
+  {
+    // receivers in the caller's order; groups of receivers sharing an element
+    // (sorted by element) for the deterministic adjoint load
+    RecDev* rd = reinterpret_cast<RecDev*>(blob.data() + L.rec);
+    real* rl = reinterpret_cast<real*>(blob.data() + L.recl);
+    real* rg = reinterpret_cast<real*>(blob.data() + L.recg);
+    int off = 0;
+    const size_t nr = c->receivers.size();
+    for (size_t r = 0; r < nr; ++r) {
+      const auto& rc = c->receivers[r];
+      rd[r].type = c->etype[rc.elem];
+      rd[r].elem = int(c->local[rc.elem]);
+      rd[r].loff = off;
+      rd[r].pad = 0;
+      for (size_t n = 0; n < rc.l.size(); ++n) {
+        rl[off + n] = real(rc.l[n]);
+        rg[off + n] = real(rc.g[n]);
+      }
+      off += int(rc.l.size());
+    }
+    std::vector<int> perm(nr);
+    for (size_t r = 0; r < nr; ++r) perm[r] = int(r);
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+      return rd[a].type != rd[b].type ? rd[a].type < rd[b].type : rd[a].elem < rd[b].elem;
+    });
+    int* rp = reinterpret_cast<int*>(blob.data() + L.rperm);
+    RecGroup* gp = reinterpret_cast<RecGroup*>(blob.data() + L.rgrp);
+    int ng = 0;
+    for (size_t i = 0; i < nr; ++i) {
+      rp[i] = perm[i];
+      if (i == 0 || rd[perm[i]].type != rd[perm[i - 1]].type || rd[perm[i]].elem != rd[perm[i - 1]].elem)
+        gp[ng++] = RecGroup{rd[perm[i]].type, rd[perm[i]].elem, int(i), 0};
+      gp[ng - 1].nr++;
+    }
+  }
   real* vx = reinterpret_cast<real*>(blob.data() + L.vx);
   real* vy = reinterpret_cast<real*>(blob.data() + L.vy);
   real* vz = reinterpret_cast<real*>(blob.data() + L.vz);
@@ -571,6 +648,22 @@ void fill_devmesh(const dg_ctx* c, const BlobLayout& L, DevMesh<real>& m) {
   m.src_g = reinterpret_cast<const real*>(b + L.srcg);
   m.nsrc = int(nsrc_dev(c));
   m.w_srng = reinterpret_cast<const int*>(b + L.wsrng);
+  m.rec = reinterpret_cast<const RecDev*>(b + L.rec);
+  m.rgrp = reinterpret_cast<const RecGroup*>(b + L.rgrp);
+  m.rperm = reinterpret_cast<const int*>(b + L.rperm);
+  m.rec_l = reinterpret_cast<const real*>(b + L.recl);
+  m.rec_g = reinterpret_cast<const real*>(b + L.recg);
+  m.nrec = int(c->receivers.size());
+  {
+    int ng = 0;
+    std::vector<std::pair<int, int64_t>> keys;
+    for (const auto& r : c->receivers) keys.push_back({int(c->etype[r.elem]), c->local[r.elem]});
+    std::sort(keys.begin(), keys.end());
+    ng = int(std::unique(keys.begin(), keys.end()) - keys.begin());
+    m.nrgrp = ng;
+  }
+  m.Kw1 = int(c->wedges.size());
+  m.Kt1 = int(c->tets.size());
   m.t_srng = reinterpret_cast<const int*>(b + L.tsrng);
   m.clock = reinterpret_cast<double*>(b + L.clock);
   m.w_fac = c->mass == DG_MASS_STORED ? reinterpret_cast<const real*>(b + L.wfac) : nullptr;
@@ -587,8 +680,16 @@ size_t field_bytes_of(const dg_ctx* c) {
   return align256(size_t(nw * 4 * npw_of(c->N) * kB + nt * 4 * npt_of(c->N) * kB) * rs);
 }
 
+// extra stage settings: the update coefficient on the input state, a store of the
+// stage right-hand side, and whether the point sources are left out
+struct StageExtra {
+  double g = 1.0;
+  void* rhs_out = nullptr;
+  bool no_sources = false;
+};
+
 int launch_stage(dg_ctx* c, const void* q_in, void* q_out, void* res, double a, double b, double dt, bool rk,
-                 cudaStream_t s, double cst = 0.0) {
+                 cudaStream_t s, double cst = 0.0, const StageExtra& x = StageExtra()) {
   int rc;
   if (c->prec == DG_F64) {
     StageArgs<double> A;
@@ -604,6 +705,9 @@ int launch_stage(dg_ctx* c, const void* q_in, void* q_out, void* res, double a, 
     A.flux = c->flux;
     A.wedge_bpc = c->tuned_bpc;
     if (c->tuned_onthefly) A.m.w_fac = nullptr;
+    A.rk_g = x.g;
+    A.rhs_out = static_cast<double*>(x.rhs_out);
+    if (x.no_sources) A.m.nsrc = 0;
     rc = stage_f64(c->N, A, rk, s);
   } else {
     StageArgs<float> A;
@@ -619,6 +723,9 @@ int launch_stage(dg_ctx* c, const void* q_in, void* q_out, void* res, double a, 
     A.flux = c->flux;
     A.wedge_bpc = c->tuned_bpc;
     if (c->tuned_onthefly) A.m.w_fac = nullptr;
+    A.rk_g = float(x.g);
+    A.rhs_out = static_cast<float*>(x.rhs_out);
+    if (x.no_sources) A.m.nsrc = 0;
     rc = stage_f32(c->N, A, rk, s);
   }
   if (rc) return cuda_fail(c, cudaError_t(rc), "stage launch");
@@ -839,13 +946,11 @@ int dg_set_material(dg_ctx* c, const double* c2, const double* rho) {
   return DG_OK;
 }
 
-static int add_source(dg_ctx* c, int64_t shot, double x, double y, double z, double f0, double t0, double amp) {
-  if (c->bound) return c->fail(DG_ERR_STATE, "dg_add_source after dg_bind");
-  if (!c->N) return c->fail(DG_ERR_STATE, "dg_add_source needs dg_set_order first");
-  if (!(f0 > 0) || !std::isfinite(t0) || !std::isfinite(amp))
-    return c->fail(DG_ERR_ARG, "source frequency must be positive and t0, amp finite");
-  if (shot >= c->shots) return c->fail(DG_ERR_ARG, "shot index out of range");
-  if (nsrc_dev(c) + (shot < 0 ? c->shots : 1) > kMaxSources) return c->fail(DG_ERR_ARG, "too many sources");
+// The element holding (x, y, z) (lowest id on ties), the Lagrange basis values
+// lv = l(x) of its nodes and g = (M^k)^{-1} l(x) (element node order); false
+// when the point lies outside the mesh.
+static bool point_vectors(const dg_ctx* c, double x, double y, double z, int64_t& elem, std::vector<double>& lv,
+                          std::vector<double>& g) {
   const RefElems& R = *c->ref;
   const double* V = c->VX.data();
   const double tol = 1e-12;
@@ -887,12 +992,7 @@ static int add_source(dg_ctx* c, int64_t shot, double x, double y, double z, dou
       for (int m = 0; m < 3; ++m) ref[m] = 2.0 * l[m] - 1.0;
     }
     if (!inside) continue;
-    dg_ctx::Source sc;
-    sc.elem = k;
-    sc.shot = shot;
-    sc.f0 = f0;
-    sc.t0 = t0;
-    sc.amp = amp;
+    elem = k;
     if (c->etype[k] == DG_WEDGE) {
       // (M^k)^{-1} = (M^{tri,k})^{-1} (x) (M^1D)^{-1},  M^{tri,k} = sum_a J_a M_a
       const double A = 0.25 * ((P(1, 0) - P(0, 0)) * (P(2, 1) - P(0, 1)) - (P(2, 0) - P(0, 0)) * (P(1, 1) - P(0, 1)));
@@ -910,25 +1010,58 @@ static int add_source(dg_ctx* c, int64_t shot, double x, double y, double z, dou
         for (int l = 0; l < R.Nt; ++l) gt[i] += Mti(i, l) * lt[l];
       for (int j = 0; j < R.Nq; ++j)
         for (int l = 0; l < R.Nq; ++l) g1[j] += M1i(j, l) * l1[l];
-      sc.g.resize(R.Npw);
+      g.resize(R.Npw);
+      lv.resize(R.Npw);
       for (int j = 0; j < R.Nq; ++j)
-        for (int i = 0; i < R.Nt; ++i) sc.g[j * R.Nt + i] = gt[i] * g1[j];
+        for (int i = 0; i < R.Nt; ++i) {
+          g[j * R.Nt + i] = gt[i] * g1[j];
+          lv[j * R.Nt + i] = lt[i] * l1[j];
+        }
     } else {
       const double J = tet_det(c, k) / 8.0;
       Mat Mi;
       invert(R.tM, Mi);
-      std::vector<double> lv(R.Npt);
+      lv.assign(R.Npt, 0.0);
       tet_lagrange(R, ref[0], ref[1], ref[2], lv.data());
-      sc.g.assign(R.Npt, 0.0);
+      g.assign(R.Npt, 0.0);
       for (int i = 0; i < R.Npt; ++i) {
-        for (int l = 0; l < R.Npt; ++l) sc.g[i] += Mi(i, l) * lv[l];
-        sc.g[i] /= J;
+        for (int l = 0; l < R.Npt; ++l) g[i] += Mi(i, l) * lv[l];
+        g[i] /= J;
       }
     }
-    c->sources.push_back(sc);
-    return DG_OK;
+    return true;
   }
-  return c->fail(DG_ERR_ARG, "source point lies outside the mesh");
+  return false;
+}
+
+
+static int add_source(dg_ctx* c, int64_t shot, double x, double y, double z, double f0, double t0, double amp) {
+  if (c->bound) return c->fail(DG_ERR_STATE, "dg_add_source after dg_bind");
+  if (!c->N) return c->fail(DG_ERR_STATE, "dg_add_source needs dg_set_order first");
+  if (!(f0 > 0) || !std::isfinite(t0) || !std::isfinite(amp))
+    return c->fail(DG_ERR_ARG, "source frequency must be positive and t0, amp finite");
+  if (shot >= c->shots) return c->fail(DG_ERR_ARG, "shot index out of range");
+  if (nsrc_dev(c) + (shot < 0 ? c->shots : 1) > kMaxSources) return c->fail(DG_ERR_ARG, "too many sources");
+  dg_ctx::Source sc;
+  std::vector<double> lv;
+  if (!point_vectors(c, x, y, z, sc.elem, lv, sc.g)) return c->fail(DG_ERR_ARG, "source point lies outside the mesh");
+  sc.shot = shot;
+  sc.f0 = f0;
+  sc.t0 = t0;
+  sc.amp = amp;
+  c->sources.push_back(sc);
+  return DG_OK;
+}
+
+int dg_add_receiver(dg_ctx* c, double x, double y, double z) {
+  if (!c) return DG_ERR_ARG;
+  if (c->bound) return c->fail(DG_ERR_STATE, "dg_add_receiver after dg_bind");
+  if (!c->N) return c->fail(DG_ERR_STATE, "dg_add_receiver needs dg_set_order first");
+  if (c->receivers.size() >= size_t(kMaxReceivers)) return c->fail(DG_ERR_ARG, "too many receivers");
+  dg_ctx::Receiver rc;
+  if (!point_vectors(c, x, y, z, rc.elem, rc.l, rc.g)) return c->fail(DG_ERR_ARG, "receiver point lies outside the mesh");
+  c->receivers.push_back(rc);
+  return int(c->receivers.size()) - 1;
 }
 
 int dg_add_source(dg_ctx* c, double x, double y, double z, double f0, double t0, double amp) {
@@ -1353,6 +1486,205 @@ int dg_autotune(dg_ctx* c, int nrep, int* variant, double* us) {
   *variant = (cand[besti].second << 1) | (cand[besti].first ? 1 : 0);
   *us = best;
   return DG_OK;
+}
+
+// ------------------------------------------------------------ receivers, adjoint
+namespace {
+constexpr int kAdjFields = 14;
+enum { kAdjMuq = 0, kAdjX0 = 1, kAdjX1 = 2, kAdjRes = 3, kAdjQs = 4 /*4 buffers*/, kAdjScr = 8, kAdjRs = 9 /*5*/ };
+size_t adj_grad_bytes(const dg_ctx* c) { return align256(size_t(nblk(vKw(c))) * kB * sizeof(double)); }
+void* adj_field(dg_ctx* c, int i) { return c->adj + size_t(i) * c->field_bytes; }
+double* adj_gk(dg_ctx* c) { return reinterpret_cast<double*>(c->adj + kAdjFields * c->field_bytes); }
+double* adj_gr(dg_ctx* c) { return reinterpret_cast<double*>(c->adj + kAdjFields * c->field_bytes + adj_grad_bytes(c)); }
+}  // namespace
+
+int dg_sample(dg_ctx* c, void* d_out) {
+  if (!c) return DG_ERR_ARG;
+  if (!d_out) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_sample before dg_bind");
+  int rc = ensure_ops(c);
+  if (rc) return rc;
+  if (c->prec == DG_F64)
+    rc = sample_f64(c->N, c->m64, static_cast<const double*>(c->d_q[c->cur]), static_cast<double*>(d_out),
+                    int(c->shots), c->stream);
+  else
+    rc = sample_f32(c->N, c->m32, static_cast<const float*>(c->d_q[c->cur]), static_cast<float*>(d_out),
+                    int(c->shots), c->stream);
+  if (rc) return cuda_fail(c, cudaError_t(rc), "sample launch");
+  return DG_OK;
+}
+
+int dg_save_state(dg_ctx* c, void* d_dst) {
+  if (!c) return DG_ERR_ARG;
+  if (!d_dst) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_save_state before dg_bind");
+  cudaError_t e = cudaMemcpyAsync(d_dst, c->d_q[c->cur], c->field_bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "state save");
+  return DG_OK;
+}
+
+int dg_load_state(dg_ctx* c, const void* d_src, double t) {
+  if (!c) return DG_ERR_ARG;
+  if (!d_src || !std::isfinite(t)) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_load_state before dg_bind");
+  cudaError_t e = cudaMemcpyAsync(c->d_q[c->cur], d_src, c->field_bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "state load");
+  c->t = t;
+  c->t_stage_host = t;
+  e = cudaMemcpyAsync(c->prec == DG_F64 ? c->m64.clock : c->m32.clock, &c->t_stage_host, sizeof(double),
+                      cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "state load");
+  return DG_OK;
+}
+
+int dg_adjoint_bytes(const dg_ctx* c, size_t* bytes) {
+  if (!c) return DG_ERR_ARG;
+  if (!bytes) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
+  *bytes = kAdjFields * field_bytes_of(c) + 2 * adj_grad_bytes(c);
+  return DG_OK;
+}
+
+int dg_adjoint_bind(dg_ctx* c, void* d_work) {
+  if (!c) return DG_ERR_ARG;
+  if (!d_work) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_adjoint_bind before dg_bind");
+  if (!c->tets.empty()) return c->fail(DG_ERR_MESH, "the adjoint takes meshes of wedges only");
+  c->adj = static_cast<unsigned char*>(d_work);
+  return dg_adjoint_reset(c);
+}
+
+int dg_adjoint_reset(dg_ctx* c) {
+  if (!c) return DG_ERR_ARG;
+  if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_reset before dg_adjoint_bind");
+  size_t bytes = 0;
+  dg_adjoint_bytes(c, &bytes);
+  cudaError_t e = cudaMemsetAsync(c->adj, 0, bytes, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint reset");
+  c->adj_x = kAdjX0;
+  return DG_OK;
+}
+
+int dg_adjoint_inject(dg_ctx* c, const void* d_resid) {
+  if (!c) return DG_ERR_ARG;
+  if (!d_resid) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_inject before dg_adjoint_bind");
+  int rc = ensure_ops(c);
+  if (rc) return rc;
+  if (c->prec == DG_F64)
+    rc = inject_f64(c->N, c->m64, static_cast<double*>(adj_field(c, kAdjMuq)), static_cast<double*>(adj_field(c, c->adj_x)),
+                    static_cast<const double*>(d_resid), int(c->shots), kLSRK_B[4], c->stream);
+  else
+    rc = inject_f32(c->N, c->m32, static_cast<float*>(adj_field(c, kAdjMuq)), static_cast<float*>(adj_field(c, c->adj_x)),
+                    static_cast<const float*>(d_resid), int(c->shots), float(kLSRK_B[4]), c->stream);
+  if (rc) return cuda_fail(c, cudaError_t(rc), "adjoint inject launch");
+  return DG_OK;
+}
+
+int dg_adjoint_step(dg_ctx* c, double dt) {
+  if (!c) return DG_ERR_ARG;
+  if (!(dt > 0)) return c->fail(DG_ERR_ARG, "dt must be positive");
+  if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_step before dg_adjoint_bind");
+  int rc = ensure_ops(c);
+  if (rc) return rc;
+  // 1. the forward step from the current state and time, keeping every stage's
+  //    input Q_{s-1} and right-hand side r_s = A Q_{s-1} + f(t + c_s dt)
+  const void* q0 = c->d_q[c->cur];
+  const void* qin = q0;
+  for (int st = 0; st < 5 && rc == DG_OK; ++st) {
+    void* qout = adj_field(c, st < 4 ? kAdjQs + st : kAdjScr);
+    StageExtra x;
+    x.rhs_out = adj_field(c, kAdjRs + st);
+    rc = launch_stage(c, qin, qout, adj_field(c, kAdjRes), kLSRK_A[st], kLSRK_B[st], dt, true, c->stream, kLSRK_C[st], x);
+    qin = qout;
+  }
+  // 2. the stages in reverse (variables mu = P W^{-1} lambda): gradient terms of
+  //    stage s with x = mu_K, then mu_Q += dt A x and x <- a_s x + b_{s-1} mu_Q
+  for (int st = 4; st >= 0 && rc == DG_OK; --st) {
+    const void* Qp = st == 0 ? q0 : adj_field(c, kAdjQs + st - 1);
+    void* xin = adj_field(c, c->adj_x);
+    void* xout = adj_field(c, c->adj_x == kAdjX0 ? kAdjX1 : kAdjX0);
+    int lr;
+    if (c->prec == DG_F64)
+      lr = grad_f64(c->N, c->m64, static_cast<const double*>(xin), static_cast<const double*>(Qp),
+                    static_cast<const double*>(adj_field(c, kAdjRs + st)), dt, c->flux, c->bc, adj_gk(c), adj_gr(c),
+                    c->stream);
+    else
+      lr = grad_f32(c->N, c->m32, static_cast<const float*>(xin), static_cast<const float*>(Qp),
+                    static_cast<const float*>(adj_field(c, kAdjRs + st)), dt, c->flux, c->bc, adj_gk(c), adj_gr(c),
+                    c->stream);
+    if (lr) return cuda_fail(c, cudaError_t(lr), "gradient launch");
+    StageExtra x;
+    x.g = kLSRK_A[st];
+    x.no_sources = true;
+    rc = launch_stage(c, xin, xout, adj_field(c, kAdjMuq), 1.0, kLSRK_B[(st + 4) % 5], dt, true, c->stream, 0.0, x);
+    c->adj_x = c->adj_x == kAdjX0 ? kAdjX1 : kAdjX0;
+  }
+  return rc;
+}
+
+int dg_adjoint_set(dg_ctx* c, const void* mu_q, const void* x, int on_device) {
+  if (!c) return DG_ERR_ARG;
+  if (!mu_q || !x) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_set before dg_adjoint_bind");
+  int rc = ensure_ops(c);
+  if (rc) return rc;
+  const size_t rs = c->prec == DG_F64 ? 8 : 4;
+  const size_t bytes = size_t(4) * c->shots * (c->wedge_nodes + c->tet_nodes) * rs;
+  const void* src[2] = {mu_q, x};
+  void* dst[2] = {adj_field(c, kAdjMuq), adj_field(c, c->adj_x)};
+  for (int i = 0; i < 2; ++i) {
+    const void* from = src[i];
+    if (!on_device) {
+      cudaError_t e = cudaMemcpyAsync(adj_field(c, kAdjScr), src[i], bytes, cudaMemcpyHostToDevice, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "adjoint upload");
+      from = adj_field(c, kAdjScr);
+    }
+    rc = launch_pack(c, from, dst[i], false, c->stream);
+    if (rc) return rc;
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint upload");
+  return DG_OK;
+}
+
+int dg_adjoint_get(dg_ctx* c, void* dst, int on_device) {
+  if (!c) return DG_ERR_ARG;
+  if (!dst) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_get before dg_adjoint_bind");
+  int rc = ensure_ops(c);
+  if (rc) return rc;
+  const size_t rs = c->prec == DG_F64 ? 8 : 4;
+  const size_t bytes = size_t(4) * c->shots * (c->wedge_nodes + c->tet_nodes) * rs;
+  void* out = on_device ? dst : adj_field(c, kAdjScr);
+  rc = launch_pack(c, out, adj_field(c, kAdjMuq), true, c->stream);
+  if (rc) return rc;
+  if (!on_device) {
+    cudaError_t e = cudaMemcpyAsync(dst, out, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint download");
+  }
+  return DG_OK;
+}
+
+int dg_adjoint_gradient(dg_ctx* c, double* g_kappa, double* g_rho) {
+  if (!c) return DG_ERR_ARG;
+  if (!g_kappa || !g_rho) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_gradient before dg_adjoint_bind");
+  const int64_t Kw = int64_t(c->wedges.size()), nv = nblk(vKw(c)) * kB;
+  std::vector<double> gk(nv), gr(nv);
+  cudaError_t e = cudaMemcpyAsync(gk.data(), adj_gk(c), nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(gr.data(), adj_gr(c), nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "gradient download");
+  for (int64_t k = 0; k < c->K; ++k) g_kappa[k] = g_rho[k] = 0.0;
+  for (int64_t s = 0; s < c->shots; ++s)
+    for (int64_t w = 0; w < Kw; ++w) {
+      g_kappa[c->wedges[w]] += gk[s * Kw + w];
+      g_rho[c->wedges[w]] += gr[s * Kw + w];
+    }
+  return check_device_error(c);
 }
 
 int dg_energy(dg_ctx* c, double* E) {

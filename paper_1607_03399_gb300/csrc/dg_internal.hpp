@@ -63,6 +63,19 @@ struct AllOps {
 
 // Point source in the pressure equation: rhs_p += amp R(f0, t - t0) g, with
 // g = kappa_k (M^k)^{-1} l(x_s) precomputed on the host (Np reals at goff).
+// receiver: pressure sampled by l(x_r) (table rec_l); the adjoint injects
+// (M^k)^{-1} l(x_r) (table rec_g, kappa applied in the kernel)
+struct RecDev {
+  int type;   // 6 wedge, 4 tet
+  int elem;   // index within its element type (one shot)
+  int loff;   // offset of l(x_r) and of (M^k)^{-1} l(x_r) in their tables
+  int pad;
+};
+// receivers sharing one element, consecutive in the receiver list
+struct RecGroup {
+  int type, elem, r0, nr;
+};
+
 struct SourceDev {
   int type;   // 6 wedge, 4 tet
   int elem;   // index within its element type
@@ -71,6 +84,7 @@ struct SourceDev {
   double f0, t0, amp;
 };
 constexpr int kMaxSources = 4096;  // device entries: (source, shot) pairs
+constexpr int kMaxReceivers = 65536;
 
 template <typename real>
 struct DevMesh {
@@ -103,6 +117,13 @@ struct DevMesh {
   const real* w_xyz = nullptr;       // per wedge block [12][32]: bottom x, y; bottom and top z
   const real* t_xyz = nullptr;       // per tet block [12][32]: x, y, z of the four vertices
   const real* t_ops = nullptr;       // tet stage operators, shared-memory image
+  const RecDev* rec = nullptr;       // receivers (same for every shot)
+  const RecGroup* rgrp = nullptr;    // receivers grouped by element
+  const int* rperm = nullptr;        // receiver indices sorted by element (groups index this)
+  const real* rec_l = nullptr;
+  const real* rec_g = nullptr;
+  int nrec = 0, nrgrp = 0;
+  int Kw1 = 0, Kt1 = 0;              // wedges / tets of one shot
   const int* w_srng = nullptr;       // per wedge block [begin, end) of its entries in src
   const int* t_srng = nullptr;       // per tet block likewise
 };
@@ -114,6 +135,8 @@ struct StageArgs {
   real* q_out = nullptr;        // RK: packed next state; RHS mode: packed rhs
   real* res = nullptr;          // RK residual (unused in RHS mode)
   real rk_a = 0, rk_b = 0, dt = 0;
+  real rk_g = 1;                // RK: q_out = rk_g q_in + rk_b res' (1 in the forward method)
+  real* rhs_out = nullptr;      // RK: also store the stage right-hand side here (optional)
   double c_stage = 0;           // stage time = *clock + c_stage * dt
   int bc = 1, flux = 0;
   int wedge_bpc = 0;            // wedge blocks per CTA: 0 = the default for the mass mode
@@ -128,7 +151,12 @@ enum : int { kErrTimeout = 1, kErrNonfinite = 2 };
   int launch_stage_##P##n##N(const StageArgs<T>& a, bool rk, void* stream);                        \
   int launch_pack_##P##n##N(const DevMesh<T>& m, const T* canon, T* packed, bool unpack, void* s); \
   int launch_energy_##P##n##N(const DevMesh<T>& m, const T* q, void* stream);                      \
-  int launch_clock_##P##n##N(double* clock, double dt, void* stream);
+  int launch_clock_##P##n##N(double* clock, double dt, void* stream);                              \
+  int launch_sample_##P##n##N(const DevMesh<T>& m, const T* q, T* out, int nshots, void* stream);     \
+  int launch_inject_##P##n##N(const DevMesh<T>& m, T* muq, T* x, const T* resid, int nshots, T b5,     \
+                              void* stream);                                                       \
+  int launch_grad_##P##n##N(const DevMesh<T>& m, const T* x, const T* q, const T* r, double dt, int flux, \
+                            int bc, double* gk, double* gr, void* stream);
 DGW_DECLARE_LAUNCHERS(f32, float, 1)
 DGW_DECLARE_LAUNCHERS(f32, float, 2)
 DGW_DECLARE_LAUNCHERS(f32, float, 3)

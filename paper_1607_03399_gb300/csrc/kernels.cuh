@@ -297,48 +297,43 @@ __host__ __device__ constexpr int wedge_smem_bytes() {
   return BPC * (32 + wedge_smem_reals<N>() * int(sizeof(real)));
 }
 
-// Lemma 3.1 for the wedge of this lane: everything the stage needs, from the
-// six vertices (bi-unit reference, x = sum_a lambda_a(r,s) [(1-t)/2 X_a + (1+t)/2 X_{a+3}]).
-// The coordinates arrive in the first 12 items of the table ([x_a][y_a][zb_a][zt_a],
-// a = 0..2, one column per lane) and are replaced by the factors.
-__device__ __forceinline__ void wedge_geometry(real* sG, int lane) {
-  const real x0 = sG[0 * kB + lane], x1 = sG[1 * kB + lane], x2 = sG[2 * kB + lane];
-  const real y0 = sG[3 * kB + lane], y1 = sG[4 * kB + lane], y2 = sG[5 * kB + lane];
-  const real zb0 = sG[6 * kB + lane], zb1 = sG[7 * kB + lane], zb2 = sG[8 * kB + lane];
-  const real zt0 = sG[9 * kB + lane], zt1 = sG[10 * kB + lane], zt2 = sG[11 * kB + lane];
-  __syncwarp();
-  auto put = [&](int item, real v) { sG[item * kB + lane] = v; };
+// Lemma 3.1 for one wedge: everything the stage needs, from the six vertices
+// (bi-unit reference, x = sum_a lambda_a(r,s) [(1-t)/2 X_a + (1+t)/2 X_{a+3}]),
+// X = [x_a][y_a][zb_a][zt_a] (a = 0..2, bottom x and y; bottom and top z).
+__device__ __forceinline__ void wedge_geometry_vals(const real (&X)[12], real (&G)[G_COUNT]) {
+  const real x0 = X[0], x1 = X[1], x2 = X[2], y0 = X[3], y1 = X[4], y2 = X[5];
+  const real zb0 = X[6], zb1 = X[7], zb2 = X[8], zt0 = X[9], zt1 = X[10], zt2 = X[11];
   const real xr = real(0.5) * (x1 - x0), xs = real(0.5) * (x2 - x0);
   const real yr = real(0.5) * (y1 - y0), ys = real(0.5) * (y2 - y0);
   const real A = xr * ys - xs * yr;  // t_z J (constant)
   const real iA = real(1) / A;
-  put(G_RX, ys * iA);
-  put(G_RY, -xs * iA);
-  put(G_SX, -yr * iA);
-  put(G_SY, xr * iA);
-  put(G_A, A);
+  G[G_RX] = ys * iA;
+  G[G_RY] = -xs * iA;
+  G[G_SX] = -yr * iA;
+  G[G_SY] = xr * iA;
+  G[G_A] = A;
   const real h0 = zt0 - zb0, h1 = zt1 - zb1, h2 = zt2 - zb2;
-  put(G_J0, real(0.5) * A * h0);  // J at the three columns (J linear in r, s)
-  put(G_J1, real(0.5) * A * h1);
-  put(G_J2, real(0.5) * A * h2);
+  G[G_J0] = real(0.5) * A * h0;  // J at the three columns (J linear in r, s)
+  G[G_J1] = real(0.5) * A * h1;
+  G[G_J2] = real(0.5) * A * h2;
   // z_r, z_s are linear in t: z_r(t) = zr0 + t zr1 (likewise z_s), so
   // t_x J = y_r z_s - z_r y_s and t_y J = z_r x_s - x_r z_s are linear in t
   const real zr0 = real(0.25) * ((zb1 - zb0) + (zt1 - zt0)), zr1 = real(0.25) * ((zt1 - zt0) - (zb1 - zb0));
   const real zs0 = real(0.25) * ((zb2 - zb0) + (zt2 - zt0)), zs1 = real(0.25) * ((zt2 - zt0) - (zb2 - zb0));
-  put(G_TX0, yr * zs0 - zr0 * ys);
-  put(G_TX1, yr * zs1 - zr1 * ys);
-  put(G_TY0, zr0 * xs - xr * zs0);
-  put(G_TY1, zr1 * xs - xr * zs1);
+  G[G_TX0] = yr * zs0 - zr0 * ys;
+  G[G_TX1] = yr * zs1 - zr1 * ys;
+  G[G_TY0] = zr0 * xs - xr * zs0;
+  G[G_TY1] = zr1 * xs - xr * zs1;
   {
     // triangle faces: n = c / |c| with c the edge cross product, J_f = |c| / 4
     const real ax = x1 - x0, ay = y1 - y0, bx = x2 - x0, by = y2 - y0;
     real az = zb1 - zb0, bz = zb2 - zb0;
     real cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
     real cc = cx * cx + cy * cy + cz * cz, ic = rsqrt_r(cc);
-    put(G_JFB, real(0.25) * cc * ic);
-    put(G_NB0, -cx * ic);
-    put(G_NB1, -cy * ic);
-    put(G_NB2, -cz * ic);
+    G[G_JFB] = real(0.25) * cc * ic;
+    G[G_NB0] = -cx * ic;
+    G[G_NB1] = -cy * ic;
+    G[G_NB2] = -cz * ic;
     az = zt1 - zt0;
     bz = zt2 - zt0;
     cx = ay * bz - az * by;
@@ -346,10 +341,10 @@ __device__ __forceinline__ void wedge_geometry(real* sG, int lane) {
     cz = ax * by - ay * bx;
     cc = cx * cx + cy * cy + cz * cz;
     ic = rsqrt_r(cc);
-    put(G_JFT, real(0.25) * cc * ic);
-    put(G_NT0, cx * ic);
-    put(G_NT1, cy * ic);
-    put(G_NT2, cz * ic);
+    G[G_JFT] = real(0.25) * cc * ic;
+    G[G_NT0] = cx * ic;
+    G[G_NT1] = cy * ic;
+    G[G_NT2] = cz * ic;
   }
   const real xx[3] = {x0, x1, x2}, yy[3] = {y0, y1, y2}, hh[3] = {h0, h1, h2};
 #pragma unroll
@@ -358,11 +353,24 @@ __device__ __forceinline__ void wedge_geometry(real* sG, int lane) {
     const real dx = xx[ib] - xx[ia], dy = yy[ib] - yy[ia];
     const real ll = dx * dx + dy * dy, il = rsqrt_r(ll);
     const real Le = ll * il;
-    put(G_QNX0 + ed, dy * il);  // horizontal outward normal of the quad face
-    put(G_QNY0 + ed, -dx * il);
-    put(G_QCA0 + ed, real(0.25) * Le * hh[ia]);  // M~_e = ca Mea + cb Meb
-    put(G_QCB0 + ed, real(0.25) * Le * hh[ib]);
+    G[G_QNX0 + ed] = dy * il;  // horizontal outward normal of the quad face
+    G[G_QNY0 + ed] = -dx * il;
+    G[G_QCA0 + ed] = real(0.25) * Le * hh[ia];  // M~_e = ca Mea + cb Meb
+    G[G_QCB0 + ed] = real(0.25) * Le * hh[ib];
   }
+}
+
+// The stage's geometry warp: coordinates arrive in the first 12 items of the
+// shared table (one column per lane) and are replaced by the factors.
+__device__ __forceinline__ void wedge_geometry(real* sG, int lane) {
+  real X[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) X[i] = sG[i * kB + lane];
+  __syncwarp();
+  real G[G_COUNT];
+  wedge_geometry_vals(X, G);
+#pragma unroll
+  for (int i = 0; i < G_COUNT; ++i) sG[i * kB + lane] = G[i];
 }
 
 template <int N, int BPC>
@@ -722,7 +730,10 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
                     A.rk_a * r0.w + A.dt * r.w};
         const Q4 q0 = lds4(sq, n, lane);
         st4(resg, g, rr);
-        st4(qout, g, Q4{q0.p + A.rk_b * rr.p, q0.u + A.rk_b * rr.u, q0.v + A.rk_b * rr.v, q0.w + A.rk_b * rr.w});
+        st4(qout, g,
+            Q4{A.rk_g * q0.p + A.rk_b * rr.p, A.rk_g * q0.u + A.rk_b * rr.u, A.rk_g * q0.v + A.rk_b * rr.v,
+               A.rk_g * q0.w + A.rk_b * rr.w});
+        if (A.rhs_out) st4(A.rhs_out, g, r);
       } else {
         st4(qout, g, r);
       }
@@ -974,7 +985,9 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
           const Q4 q0 = lds4(sq, i, lane);
           st4(A.res, gi, rr);
           st4(A.q_out, gi,
-              Q4{q0.p + A.rk_b * rr.p, q0.u + A.rk_b * rr.u, q0.v + A.rk_b * rr.v, q0.w + A.rk_b * rr.w});
+              Q4{A.rk_g * q0.p + A.rk_b * rr.p, A.rk_g * q0.u + A.rk_b * rr.u, A.rk_g * q0.v + A.rk_b * rr.v,
+                 A.rk_g * q0.w + A.rk_b * rr.w});
+          if (A.rhs_out) st4(A.rhs_out, gi, r);
         } else {
           st4(A.q_out, gi, r);
         }
@@ -1115,6 +1128,230 @@ __global__ void k_energy_final(const double* __restrict__ partials, int n, doubl
 }
 
 // ---------------------------------------------------------------------------
+// receivers and the adjoint (gradient with respect to kappa and rho)
+// ---------------------------------------------------------------------------
+// packed index of field slot 0 (pressure) of node n of the element (type, e)
+template <int N>
+__device__ __forceinline__ int64_t pidx(const DevMesh<real>& M, int type, int e, int n) {
+  return type == 6 ? widx<N>(e >> 5, n, e & 31) : tidx<N>(M.tet_off, e >> 5, n, e & 31);
+}
+
+// out[shot][r] = sum_n l_r(n) p(n) in the receiver's element of that shot
+template <int N>
+__global__ void k_sample(const DevMesh<real> M, const real* __restrict__ q, real* __restrict__ out, int nshots) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nshots * M.nrec) return;
+  const int shot = idx / M.nrec, r = idx - shot * M.nrec;
+  const RecDev rd = M.rec[r];
+  const int e = shot * (rd.type == 6 ? M.Kw1 : M.Kt1) + rd.elem;
+  const int np = rd.type == 6 ? npw_of(N) : npt_of(N);
+  real acc = 0;
+  for (int n = 0; n < np; ++n) acc += M.rec_l[rd.loff + n] * q[pidx<N>(M, rd.type, e, n)];
+  out[idx] = acc;
+}
+
+// Adjoint load of the misfit residuals (in the variables mu = P W^{-1} lambda):
+// mu_Q,p += kappa (M^k)^{-1} sum_r resid_r l(x_r) on each receiver element, and
+// the next stage input x += b5 times the same.  One thread per (shot, element
+// group), receivers of a group in list order: deterministic.
+template <int N>
+__global__ void k_inject(const DevMesh<real> M, real* __restrict__ muq, real* __restrict__ x,
+                         const real* __restrict__ resid, int nshots, real b5) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nshots * M.nrgrp) return;
+  const int shot = idx / M.nrgrp, gi = idx - shot * M.nrgrp;
+  const RecGroup g = M.rgrp[gi];
+  const int e = shot * (g.type == 6 ? M.Kw1 : M.Kt1) + g.elem;
+  const real kappa = g.type == 6 ? M.w_mat[e] : M.t_mat[e];
+  const int np = g.type == 6 ? npw_of(N) : npt_of(N);
+  for (int n = 0; n < np; ++n) {
+    real acc = 0;
+    for (int i = g.r0; i < g.r0 + g.nr; ++i) {
+      const int r = M.rperm[i];
+      acc += resid[shot * M.nrec + r] * M.rec_g[M.rec[r].loff + n];
+    }
+    const int64_t i = pidx<N>(M, g.type, e, n);
+    muq[i] += kappa * acc;
+    x[i] += b5 * kappa * acc;
+  }
+}
+
+// Per wedge and Runge-Kutta stage, with x = mu_K (adjoint stage variable,
+// lambda_K = W P mu_K), q = the forward stage input Q and r = A Q + f its
+// right-hand side:
+//   d/dkappa_k: mu_p^T M^k r_p / kappa^2 + dz/dkappa G,  d/drho_k: mu_u^T M^k r_u + dz/drho G,
+// with z = rho c = sqrt(kappa rho) and G the derivative of the upwind penalty
+// in z summed over the element's faces: interior faces (tau_p = 2/(z- + z+),
+// tau_u = (z- + z+)/2) give tau_p^2/4 int [p][mu_p] + 1/4 int [u_n][mu_un],
+// rigid walls int mu_un u_n, Dirichlet walls int mu_p p / z^2; central fluxes
+// have no penalty.  M^k = M^{tri,k} (x) M^1D (Section 4.2); the face masses are
+// J_f M^tri (triangles) and M~_e (x) M^1D (quadrilaterals).  Accumulated, times
+// dt, in double.  Wedge neighbours only (the adjoint takes wedge meshes).
+template <int N>
+__global__ void __launch_bounds__(128) k_wedge_grad(const DevMesh<real> M, const real* __restrict__ X,
+                                                    const real* __restrict__ Q, const real* __restrict__ R, double dt,
+                                                    int flux, int bc, double* __restrict__ gk, double* __restrict__ gr) {
+  constexpr int Nt = nt_of(N), Nq = N + 1;
+  const AllOps<N, real>& O = OPS<N>();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M.Kw) return;
+  const int blk = e >> 5, lane = e & 31, Kp = M.Kw_pad;
+  real Xc[12], G[G_COUNT];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) Xc[i] = M.w_xyz[(int64_t(blk) * 12 + i) * kB + lane];
+  wedge_geometry_vals(Xc, G);
+  const real kappa = M.w_mat[0 * Kp + e], irho = M.w_mat[1 * Kp + e], zM = M.w_mat[2 * Kp + e];
+  const real J0 = G[G_J0], J1 = G[G_J1], J2 = G[G_J2];
+  auto ldq = [&](const real* b, int n) { return ld4(b, widx<N>(blk, n, lane)); };
+
+  // element terms: sum_j mu[j] . M^tri (sum_j' M1[j][j'] r[j'])
+  double t1k = 0.0, t1r = 0.0;
+#pragma unroll 1
+  for (int j = 0; j < Nq; ++j) {
+    real bt[4][Nt];
+#pragma unroll
+    for (int l = 0; l < Nt; ++l) bt[0][l] = bt[1][l] = bt[2][l] = bt[3][l] = real(0);
+#pragma unroll 1
+    for (int jp = 0; jp < Nq; ++jp) {
+      const real m1 = O.w.M1[j * Nq + jp];
+#pragma unroll
+      for (int l = 0; l < Nt; ++l) {
+        const Q4 v = ldq(R, jp * Nt + l);
+        bt[0][l] += m1 * v.p;
+        bt[1][l] += m1 * v.u;
+        bt[2][l] += m1 * v.v;
+        bt[3][l] += m1 * v.w;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < Nt; ++i) {
+      real c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+#pragma unroll
+      for (int l = 0; l < Nt; ++l) {
+        const real mt = J0 * O.w.Ma[0][i * Nt + l] + J1 * O.w.Ma[1][i * Nt + l] + J2 * O.w.Ma[2][i * Nt + l];
+        c0 += mt * bt[0][l];
+        c1 += mt * bt[1][l];
+        c2 += mt * bt[2][l];
+        c3 += mt * bt[3][l];
+      }
+      const Q4 x = ldq(X, j * Nt + i);
+      t1k += double(x.p) * double(c0);
+      t1r += double(x.u) * double(c1) + double(x.v) * double(c2) + double(x.w) * double(c3);
+    }
+  }
+  t1k /= double(kappa) * double(kappa);
+
+  // face terms: derivative of the upwind penalty in z
+  double gz = 0.0;
+  if (flux == 0) {
+    // triangle faces (bottom, top): face mass J_f M^tri on the face nodes
+#pragma unroll 1
+    for (int fb = 0; fb < 2; ++fb) {
+      const int nbr = M.w_nbr[fb * Kp + e], code = M.w_code[fb * Kp + e];
+      const real n0 = fb ? G[G_NT0] : G[G_NB0], n1 = fb ? G[G_NT1] : G[G_NB1], n2 = fb ? G[G_NT2] : G[G_NB2];
+      const real Jf = fb ? G[G_JFT] : G[G_JFB];
+      const real zP = nbr < 0 ? zM : M.w_mat[2 * Kp + (nbr < 0 ? e : nbr)];
+      real a[Nt], b[Nt], c[Nt], d[Nt];  // [p], [mu_p], [u_n], [mu_un] (boundary: own values)
+#pragma unroll
+      for (int k = 0; k < Nt; ++k) {
+        const int own = (fb ? N * Nt : 0) + k;
+        const Q4 qo = ldq(Q, own), xo = ldq(X, own);
+        if (nbr < 0) {
+          a[k] = qo.p;
+          b[k] = xo.p;
+          c[k] = n0 * qo.u + n1 * qo.v + n2 * qo.w;
+          d[k] = n0 * xo.u + n1 * xo.v + n2 * xo.w;
+        } else {
+          const int nf = (code >> 4) & 3;
+          const int node = (nf ? N * Nt : 0) + O.tab.tri_perm[code & 15][k];
+          const int64_t ni = widx<N>(nbr >> 5, node, nbr & 31);
+          const Q4 qn = ld4(Q, ni), xn = ld4(X, ni);
+          a[k] = qn.p - qo.p;
+          b[k] = xn.p - xo.p;
+          c[k] = n0 * (qn.u - qo.u) + n1 * (qn.v - qo.v) + n2 * (qn.w - qo.w);
+          d[k] = n0 * (xn.u - xo.u) + n1 * (xn.v - xo.v) + n2 * (xn.w - xo.w);
+        }
+      }
+      double Ip = 0.0, Iu = 0.0;
+#pragma unroll
+      for (int k = 0; k < Nt; ++k) {
+        real sp = 0, su = 0;
+#pragma unroll
+        for (int kk = 0; kk < Nt; ++kk) {
+          sp += O.w.M[k * Nt + kk] * b[kk];
+          su += O.w.M[k * Nt + kk] * d[kk];
+        }
+        Ip += double(a[k]) * double(sp);
+        Iu += double(c[k]) * double(su);
+      }
+      Ip *= double(Jf);
+      Iu *= double(Jf);
+      if (nbr >= 0) {
+        const double tp = 2.0 / (double(zM) + double(zP));
+        gz += 0.25 * tp * tp * Ip + 0.25 * Iu;
+      } else {
+        gz += bc == 0 ? Ip / (double(zM) * double(zM)) : Iu;
+      }
+    }
+    // quadrilateral faces: face mass M~_e (x) M^1D, M~_e = ca Mea + cb Meb
+#pragma unroll 1
+    for (int ed = 0; ed < 3; ++ed) {
+      const int nbr = M.w_nbr[(2 + ed) * Kp + e], code = M.w_code[(2 + ed) * Kp + e];
+      const real nx = G[G_QNX0 + ed], ny = G[G_QNY0 + ed], ca = G[G_QCA0 + ed], cbq = G[G_QCB0 + ed];
+      const real zP = nbr < 0 ? zM : M.w_mat[2 * Kp + (nbr < 0 ? e : nbr)];
+      const int ep = nbr < 0 ? ed : code >> 1, rev = nbr < 0 ? 0 : code & 1;
+      real a[Nq][Nq], b[Nq][Nq], c[Nq][Nq], d[Nq][Nq];
+#pragma unroll
+      for (int j = 0; j < Nq; ++j)
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          const int own = j * Nt + edge_node(N, ed, m);
+          const Q4 qo = ldq(Q, own), xo = ldq(X, own);
+          if (nbr < 0) {
+            a[j][m] = qo.p;
+            b[j][m] = xo.p;
+            c[j][m] = nx * qo.u + ny * qo.v;
+            d[j][m] = nx * xo.u + ny * xo.v;
+          } else {
+            const int64_t ni = widx<N>(nbr >> 5, j * Nt + O.tab.edge[ep][rev ? N - m : m], nbr & 31);
+            const Q4 qn = ld4(Q, ni), xn = ld4(X, ni);
+            a[j][m] = qn.p - qo.p;
+            b[j][m] = xn.p - xo.p;
+            c[j][m] = nx * (qn.u - qo.u) + ny * (qn.v - qo.v);
+            d[j][m] = nx * (xn.u - xo.u) + ny * (xn.v - xo.v);
+          }
+        }
+      double Ip = 0.0, Iu = 0.0;
+#pragma unroll
+      for (int j = 0; j < Nq; ++j)
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          real sp = 0, su = 0;
+#pragma unroll
+          for (int jp = 0; jp < Nq; ++jp)
+#pragma unroll
+            for (int mp = 0; mp < Nq; ++mp) {
+              const real w = O.w.M1[j * Nq + jp] * (ca * O.w.Mea[m * Nq + mp] + cbq * O.w.Meb[m * Nq + mp]);
+              sp += w * b[jp][mp];
+              su += w * d[jp][mp];
+            }
+          Ip += double(a[j][m]) * double(sp);
+          Iu += double(c[j][m]) * double(su);
+        }
+      if (nbr >= 0) {
+        const double tp = 2.0 / (double(zM) + double(zP));
+        gz += 0.25 * tp * tp * Ip + 0.25 * Iu;
+      } else {
+        gz += bc == 0 ? Ip / (double(zM) * double(zM)) : Iu;
+      }
+    }
+  }
+  const double rho = 1.0 / double(irho);
+  gk[e] += dt * (t1k + gz * double(zM) / (2.0 * double(kappa)));
+  gr[e] += dt * (t1r + gz * double(zM) / (2.0 * rho));
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 // one-time per device: opt in to the dynamic shared memory the stages use
@@ -1191,6 +1428,23 @@ int DGW_CAT(launch_pack_, REALNS)(const DevMesh<REAL>& m, const REAL* canon, REA
 }
 int DGW_CAT(launch_energy_, REALNS)(const DevMesh<REAL>& m, const REAL* q, void* stream) {
   return REALNS::launch_energy_n<NORD>(m, q, cudaStream_t(stream));
+}
+int DGW_CAT(launch_sample_, REALNS)(const DevMesh<REAL>& m, const REAL* q, REAL* out, int nshots, void* stream) {
+  const int n = nshots * m.nrec;
+  if (n > 0) REALNS::k_sample<NORD><<<(n + 127) / 128, 128, 0, cudaStream_t(stream)>>>(m, q, out, nshots);
+  return int(cudaGetLastError());
+}
+int DGW_CAT(launch_inject_, REALNS)(const DevMesh<REAL>& m, REAL* muq, REAL* x, const REAL* resid, int nshots, REAL b5,
+                                    void* stream) {
+  const int n = nshots * m.nrgrp;
+  if (n > 0) REALNS::k_inject<NORD><<<(n + 127) / 128, 128, 0, cudaStream_t(stream)>>>(m, muq, x, resid, nshots, b5);
+  return int(cudaGetLastError());
+}
+int DGW_CAT(launch_grad_, REALNS)(const DevMesh<REAL>& m, const REAL* x, const REAL* q, const REAL* r, double dt,
+                                  int flux, int bc, double* gk, double* gr, void* stream) {
+  if (m.Kw > 0)
+    REALNS::k_wedge_grad<NORD><<<(m.Kw + 127) / 128, 128, 0, cudaStream_t(stream)>>>(m, x, q, r, dt, flux, bc, gk, gr);
+  return int(cudaGetLastError());
 }
 int DGW_CAT(launch_clock_, REALNS)(double* clock, double dt, void* stream) {
   REALNS::k_clock<<<1, 32, 0, cudaStream_t(stream)>>>(clock, dt);

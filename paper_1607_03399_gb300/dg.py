@@ -29,7 +29,9 @@ DG_MASS_ONTHEFLY, DG_MASS_STORED = 0, 1
 
 EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_shots", "dg_add_shot_source", "dg_set_options", "dg_set_mass_mode", "dg_num_nodes",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
-           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_stage_times", "dg_autotune", "dg_sync", "dg_time",
+           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_stage_times", "dg_autotune", "dg_add_receiver", "dg_sample", "dg_save_state",
+           "dg_load_state", "dg_adjoint_bytes", "dg_adjoint_bind", "dg_adjoint_reset", "dg_adjoint_inject",
+           "dg_adjoint_step", "dg_adjoint_set", "dg_adjoint_get", "dg_adjoint_gradient", "dg_sync", "dg_time",
            "dg_stable_dt", "dg_last_error", "dg_destroy")
 
 _lib = None
@@ -74,6 +76,18 @@ def lib():
         "dg_energy_static": (c_int, [P, P, POINTER(c_double)]),
         "dg_stage_times": (c_int, [P, c_int, POINTER(c_double), POINTER(c_double)]),
         "dg_autotune": (c_int, [P, c_int, POINTER(c_int), POINTER(c_double)]),
+        "dg_add_receiver": (c_int, [P, c_double, c_double, c_double]),
+        "dg_sample": (c_int, [P, P]),
+        "dg_save_state": (c_int, [P, P]),
+        "dg_load_state": (c_int, [P, P, c_double]),
+        "dg_adjoint_bytes": (c_int, [P, POINTER(c_size_t)]),
+        "dg_adjoint_bind": (c_int, [P, P]),
+        "dg_adjoint_reset": (c_int, [P]),
+        "dg_adjoint_inject": (c_int, [P, P]),
+        "dg_adjoint_step": (c_int, [P, c_double]),
+        "dg_adjoint_set": (c_int, [P, P, P, c_int]),
+        "dg_adjoint_get": (c_int, [P, P, c_int]),
+        "dg_adjoint_gradient": (c_int, [P, P, P]),
         "dg_sync": (c_int, [P]),
         "dg_time": (c_int, [P, POINTER(c_double)]),
         "dg_stable_dt": (c_int, [P, c_double, POINTER(c_double)]),
@@ -230,6 +244,60 @@ def dg_autotune(ctx, nrep: int):
     return v.value, us.value
 
 
+def dg_add_receiver(ctx, x, y, z) -> int:
+    r = lib().dg_add_receiver(ctx, x, y, z)
+    _check(ctx, min(r, 0))
+    return r
+
+
+def dg_sample(ctx, d_out: int):
+    _check(ctx, lib().dg_sample(ctx, d_out))
+
+
+def dg_save_state(ctx, d_dst: int):
+    _check(ctx, lib().dg_save_state(ctx, d_dst))
+
+
+def dg_load_state(ctx, d_src: int, t: float):
+    _check(ctx, lib().dg_load_state(ctx, d_src, t))
+
+
+def dg_adjoint_bytes(ctx) -> int:
+    n = c_size_t()
+    _check(ctx, lib().dg_adjoint_bytes(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def dg_adjoint_bind(ctx, d_work: int):
+    _check(ctx, lib().dg_adjoint_bind(ctx, d_work))
+
+
+def dg_adjoint_reset(ctx):
+    _check(ctx, lib().dg_adjoint_reset(ctx))
+
+
+def dg_adjoint_inject(ctx, d_resid: int):
+    _check(ctx, lib().dg_adjoint_inject(ctx, d_resid))
+
+
+def dg_adjoint_step(ctx, dt: float):
+    _check(ctx, lib().dg_adjoint_step(ctx, dt))
+
+
+def dg_adjoint_set(ctx, mu_q: int, x: int, on_device: int):
+    _check(ctx, lib().dg_adjoint_set(ctx, mu_q, x, on_device))
+
+
+def dg_adjoint_get(ctx, dst: int, on_device: int):
+    _check(ctx, lib().dg_adjoint_get(ctx, dst, on_device))
+
+
+def dg_adjoint_gradient(ctx, K: int):
+    gk, gr = np.zeros(K), np.zeros(K)
+    _check(ctx, lib().dg_adjoint_gradient(ctx, gk.ctypes.data, gr.ctypes.data))
+    return gk, gr
+
+
 def dg_sync(ctx):
     _check(ctx, lib().dg_sync(ctx))
 
@@ -272,7 +340,7 @@ class Solver:
 
     def __init__(self, VX, EToV, etype, N: int, c2=None, rho=None, bc: str = "rigid", flux: str = "upwind",
                  precision: str = "f32", device: str = "cuda:0", stream=None, sources=(), mass: str = "stored",
-                 shots: int = 1, shot_sources=()):
+                 shots: int = 1, shot_sources=(), receivers=()):
         import torch
         self.torch = torch
         self.ctx = dg_mesh_create(VX, EToV, etype)
@@ -289,6 +357,11 @@ class Solver:
                 dg_add_source(self.ctx, *src)
             for src in shot_sources:  # (shot, x, y, z, f0, t0, amp)
                 dg_add_shot_source(self.ctx, *src)
+            self.nrec = 0
+            for rc in receivers:      # (x, y, z)
+                dg_add_receiver(self.ctx, *rc)
+                self.nrec += 1
+            self.K = K
             self.N = N
             self.precision = precision
             self.dtype = torch.float32 if precision == "f32" else torch.float64
@@ -366,6 +439,52 @@ class Solver:
         self._wait_torch()
         v, us = dg_autotune(self.ctx, nrep)
         return v >> 1, bool(v & 1), us
+
+    # -- receivers, checkpoints, adjoint ------------------------------------
+    def sample(self, out):
+        """Pressure at the receivers into the device tensor out[shots][receivers]."""
+        self._wait_torch()
+        dg_sample(self.ctx, out.data_ptr())
+
+    def save_state(self, buf=None):
+        """Device copy of the packed current state (a checkpoint)."""
+        if buf is None:
+            buf = self.torch.empty(self.field_bytes, dtype=self.torch.uint8, device=self.device)
+        dg_save_state(self.ctx, buf.data_ptr())
+        return buf
+
+    def load_state(self, buf, t: float):
+        dg_load_state(self.ctx, buf.data_ptr(), t)
+
+    def adjoint_bind(self):
+        n = dg_adjoint_bytes(self.ctx)
+        self.d_adj = self.torch.empty(n, dtype=self.torch.uint8, device=self.device)
+        self.stream.synchronize()
+        dg_adjoint_bind(self.ctx, self.d_adj.data_ptr())
+
+    def adjoint_reset(self):
+        dg_adjoint_reset(self.ctx)
+
+    def adjoint_inject(self, resid):
+        dg_adjoint_inject(self.ctx, resid.data_ptr())
+
+    def adjoint_step(self, dt: float):
+        dg_adjoint_step(self.ctx, dt)
+
+    def adjoint_set(self, mu_q, x):
+        """mu_q, x: numpy arrays of the field shape."""
+        a = np.ascontiguousarray(mu_q, dtype=self.np_dtype)
+        b = np.ascontiguousarray(x, dtype=self.np_dtype)
+        dg_adjoint_set(self.ctx, a.ctypes.data, b.ctypes.data, 0)
+
+    def adjoint_get(self):
+        out = np.empty(self.field_shape, dtype=self.np_dtype)
+        dg_adjoint_get(self.ctx, out.ctypes.data, 0)
+        return out
+
+    def adjoint_gradient(self):
+        """(dJ/dkappa, dJ/drho) per element, input order."""
+        return dg_adjoint_gradient(self.ctx, self.K)
 
     def energy(self) -> float:
         return dg_energy(self.ctx)

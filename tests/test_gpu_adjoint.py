@@ -1,0 +1,138 @@
+"""The discrete adjoint on the GPU (wedge meshes): the adjoint step is the
+transpose of the forward step in the energy inner product (dot test, FP64),
+and the misfit gradient equals the oracle's reverse-mode gradient, central
+differences of the GPU misfit, and the torch.autograd path."""
+import numpy as np
+import pytest
+
+from oracle import adjoint as OA
+from oracle import reference as ORef
+from oracle.dg import Solver as Oracle
+from paper_1607_03399_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("CUDA not available", allow_module_level=True)
+
+from paper_1607_03399_gb300 import adjoint as AD  # noqa: E402
+from paper_1607_03399_gb300.dg import Solver  # noqa: E402
+
+
+@pytest.mark.parametrize("flux,bc", [("upwind", "rigid"), ("central", "rigid"), ("upwind", "dirichlet")])
+def test_adjoint_step_dot_product(flux, bc):
+    """<Phi v, W P mu_n> = <v, W P mu_{n-1}> for one step (mu = P W^{-1} lambda)."""
+    m = I.cube_wavy_mesh(3, 2, 0.05)
+    c2, rho = I.random_material(m.K, 2, 1.0, 2.0, 0.7, 1.3)
+    S = Solver(m.VX, m.EToV, m.etype, 2, c2, rho, precision="f64", flux=flux, bc=bc)
+    O = Oracle(m.VX, m.EToV, m.etype, 2, c2, rho, flux=flux, bc=bc)
+    n = S.total_nodes
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal((4, n))
+    mu = rng.standard_normal((4, n))
+    dt = O.stable_dt(0.4)
+    S.set_fields(v)
+    S.step(dt, 1)
+    phiv = S.get_fields()
+    S.adjoint_bind()
+    S.adjoint_set(mu, ORef.LSRK45_B[4] * mu)
+    S.set_fields(v)
+    S.adjoint_step(dt)
+    mu0 = S.adjoint_get()
+    S.close()
+    W = O.energy_weights()
+    P = np.ones(4 * n)
+    P[n:] = -1.0
+    lhs = phiv.ravel() @ (W @ (P * mu.ravel()))
+    rhs = v.ravel() @ (W @ (P * mu0.ravel()))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def _problem(precision, ck=5):
+    m = I.cube_wavy_mesh(2, 1, 0.05)
+    rng = np.random.default_rng(0)
+    kap, rho = rng.uniform(1, 2, m.K), rng.uniform(0.8, 1.3, m.K)
+    src = (0.4, 0.6, 0.5, 3.0, 0.2, 1.0)
+    recs = [(0.7, 0.3, 0.6), (0.2, 0.2, 0.3)]
+    st = OA.Setup(m, 1, kap, rho, [src], recs, 0.02, 12)
+    data = OA.traces(st) * 0.9 + 0.01
+    pb = AD.Problem(m.VX, m.EToV, m.etype, 1, 0.02, 12, recs, shot_sources=[(0, *src)], precision=precision,
+                    checkpoint_every=ck)
+    return m, st, data, pb, kap, rho
+
+
+def _gpu_gradient(pb, kap, rho, data):
+    S = pb.solver(kap / rho, rho)
+    d = torch.as_tensor(data[:, None, :], dtype=S.dtype, device=S.device)
+    traces, ckp = AD.forward(S, pb)
+    J = AD.misfit(traces, d)
+    gk, gr = AD.reverse(S, pb, traces, d, ckp)
+    S.close()
+    return J, gk, gr
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-9), ("f32", 2e-3)])
+def test_gradient_matches_oracle_reverse_mode(precision, tol):
+    m, st, data, pb, kap, rho = _problem(precision)
+    J, gk, gr = _gpu_gradient(pb, kap, rho, data)
+    ok, orr = OA.gradient_reverse(st, data)
+    assert abs(J - OA.misfit(st, data)) <= (1e-12 if precision == "f64" else 1e-4) * abs(J)
+    g = np.concatenate([gk, gr])
+    go = np.concatenate([ok, orr])
+    assert np.linalg.norm(g - go) <= tol * np.linalg.norm(go)
+
+
+def test_gradient_matches_gpu_finite_differences():
+    m, st, data, pb, kap, rho = _problem("f64", ck=4)
+    J, gk, gr = _gpu_gradient(pb, kap, rho, data)
+    for k in (1, 4, 6):
+        for which in ("kappa", "rho"):
+            base = kap if which == "kappa" else rho
+            h = 1e-6 * base[k]
+            vals = []
+            for sgn in (1, -1):
+                b = base.copy()
+                b[k] += sgn * h
+                kk, rr = (b, rho) if which == "kappa" else (kap, b)
+                S = pb.solver(kk / rr, rr)
+                tr, _ = AD.forward(S, pb)
+                vals.append(AD.misfit(tr, torch.as_tensor(data[:, None, :], dtype=S.dtype, device=S.device)))
+                S.close()
+            fd = (vals[0] - vals[1]) / (2 * h)
+            g = gk[k] if which == "kappa" else gr[k]
+            assert abs(g - fd) <= 1e-6 * abs(fd), (k, which, g, fd)
+
+
+def test_autograd_function():
+    m, st, data, pb, kap, rho = _problem("f64")
+    c2 = torch.tensor(kap / rho, dtype=torch.float64, requires_grad=True)
+    rh = torch.tensor(rho, dtype=torch.float64, requires_grad=True)
+    d = torch.as_tensor(data[:, None, :], dtype=torch.float64, device="cuda")
+    J = AD.acoustic_misfit(c2, rh, pb, d)
+    J.backward()
+    J2, g2, grho = AD.misfit_and_gradient(pb, kap / rho, rho, d)
+    assert abs(float(J.detach()) - J2) <= 1e-12 * J2
+    assert np.allclose(c2.grad.numpy(), g2, rtol=1e-10, atol=0)
+    assert np.allclose(rh.grad.numpy(), grho, rtol=1e-10, atol=0)
+
+
+def test_shots_sum_their_gradients():
+    m = I.cube_wavy_mesh(3, 2, 0.03)
+    c2, rho = I.random_material(m.K, 11, 1.0, 2.0, 0.8, 1.2)
+    recs = [(0.2, 0.7, 0.8), (0.6, 0.4, 0.2), (0.8, 0.8, 0.5)]
+    srcs = [(0, 0.3, 0.3, 0.4, 4.0, 0.25, 1.0), (1, 0.7, 0.6, 0.6, 5.0, 0.2, -0.5)]
+    kw = dict(VX=m.VX, EToV=m.EToV, etype=m.etype, N=2, dt=0.01, nsteps=15, receivers=recs, precision="f64",
+              checkpoint_every=6)
+    rng = np.random.default_rng(2)
+    data = torch.as_tensor(rng.standard_normal((15, 2, 3)) * 1e-3, dtype=torch.float64, device="cuda")
+    pb2 = AD.Problem(shot_sources=srcs, shots=2, **kw)
+    J, g2, gr = AD.misfit_and_gradient(pb2, c2, rho, data)
+    Js, g2s, grs = 0.0, 0.0, 0.0
+    for s in range(2):
+        pb1 = AD.Problem(shot_sources=[(0, *srcs[s][1:])], shots=1, **kw)
+        j, a, b = AD.misfit_and_gradient(pb1, c2, rho, data[:, s:s + 1].contiguous())
+        Js, g2s, grs = Js + j, g2s + a, grs + b
+    assert abs(J - Js) <= 1e-12 * abs(J)
+    assert np.allclose(g2, g2s, rtol=1e-9, atol=1e-14 * np.abs(g2).max())
+    assert np.allclose(gr, grs, rtol=1e-9, atol=1e-14 * np.abs(gr).max())
