@@ -355,6 +355,47 @@ def measure_multimesh(args, torch, dev):
             "ratio": s_a / (ms_b / 1e3)}
 
 
+def measure_adjoint(args, torch, dev):
+    """Differentiation workload: 2x48x48 footprint x 24 layers = 110592 wedges,
+    N=3, FP32 fields, two-layer c^2 with a Gaussian inclusion, 8 shots (Ricker
+    f0 = 8 below the surface) and 256 surface receivers; misfit against traces
+    of the model with a 10% stronger inclusion; checkpoints every 50 steps.
+    Times the forward pass (with receiver sampling and checkpoints) and the
+    adjoint sweep (segment re-runs, per-step stage recomputation, adjoint
+    stages, gradient terms); reports their ratio and the peak device memory."""
+    from paper_1607_03399_gb300 import inputs as I
+    from paper_1607_03399_gb300 import adjoint as AD
+    m = I.bumpy_layered_mesh(48, 24)
+    pos = I.surface_shots(8, 5)
+    recs = I.surface_receivers(16)
+    nsteps = max(50, min(args.steps * 2, 200))
+    pb = AD.Problem(m.VX, m.EToV, m.etype, 3, 0.0, nsteps, recs, shots=8, checkpoint_every=50,
+                    shot_sources=[(s, *pos[s], 8.0, 0.125, 1.0) for s in range(8)], device=str(dev))
+    c2t, rho = I.inclusion_model(m, amp=0.55)
+    c2, _ = I.inclusion_model(m, amp=0.5)
+    S = pb.solver(c2t, rho)
+    pb.dt = S.stable_dt(0.5)
+    data, _ = AD.forward(S, pb)
+    S.close()
+    torch.cuda.synchronize(dev)
+    torch.cuda.reset_peak_memory_stats(dev)
+    S = pb.solver(c2, rho)
+    AD.forward(S, pb)  # untimed: graph capture and first-touch allocations
+    S.sync()
+    t0 = time.perf_counter()
+    traces, ck = AD.forward(S, pb)
+    J = AD.misfit(traces, data)
+    t1 = time.perf_counter()
+    gk, gr = AD.reverse(S, pb, traces, data, ck)
+    t2 = time.perf_counter()
+    peak = torch.cuda.max_memory_allocated(dev)
+    S.close()
+    return {"workload": "adjoint_2x48x48x24_N3_8shots_256rec", "wedges": m.K, "shots": 8, "receivers": len(recs),
+            "steps": nsteps, "checkpoint_every": 50, "misfit": J, "forward_s": t1 - t0, "adjoint_s": t2 - t1,
+            "adjoint_over_forward": (t2 - t1) / (t1 - t0), "peak_device_gb": peak / 1e9,
+            "gradient_norm": float(np.sqrt((gk ** 2).sum() + (gr ** 2).sum()))}
+
+
 def run_ours(args, rank, world):
     import torch
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -401,6 +442,7 @@ def run_ours(args, rank, world):
     hybrid = measure_hybrid(args, torch, dev) if (rank == 0 and not args.no_hybrid) else None
     multishot = measure_multishot(args, torch, dev) if (rank == 0 and not args.no_batched) else None
     multimesh = measure_multimesh(args, torch, dev) if (rank == 0 and not args.no_batched) else None
+    adjoint = measure_adjoint(args, torch, dev) if (rank == 0 and not args.no_adjoint) else None
     # the headline order once more with the other way of applying the mass inverse
     other = {"stored": "onthefly", "onthefly": "stored"}[args.mass]
     alt = None
@@ -457,6 +499,7 @@ def run_ours(args, rank, world):
         "hybrid": hybrid,
         "multishot": multishot,
         "multimesh": multimesh,
+        "adjoint": adjoint,
         "e2e": r3.get("e2e"),
         "gpu_launches": 6 * args.steps,  # per step: 5 stage launches and one clock launch
         "clocks": r3["clocks"],
@@ -482,6 +525,7 @@ def main():
     ap.add_argument("--no-alt", action="store_true", help="skip the headline order in the other mass mode")
     ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid wedge + tet workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the multi-shot and multi-mesh workloads")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) workload")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -1185,38 +1185,59 @@ __global__ void k_inject(const DevMesh<real> M, real* __restrict__ muq, real* __
 // tau_u = (z- + z+)/2) give tau_p^2/4 int [p][mu_p] + 1/4 int [u_n][mu_un],
 // rigid walls int mu_un u_n, Dirichlet walls int mu_p p / z^2; central fluxes
 // have no penalty.  M^k = M^{tri,k} (x) M^1D (Section 4.2); the face masses are
-// J_f M^tri (triangles) and M~_e (x) M^1D (quadrilaterals).  Accumulated, times
-// dt, in double.  Wedge neighbours only (the adjoint takes wedge meshes).
+// J_f M^tri (triangles) and M~_e (x) M^1D (quadrilaterals).  A CTA takes a
+// 32-wedge block, warp j slice j (slabs of x and q in shared memory); the
+// per-slice partial sums are reduced across warps in a fixed order and added,
+// times dt, in double.  Wedge neighbours only (the adjoint takes wedge meshes).
 template <int N>
-__global__ void __launch_bounds__(128) k_wedge_grad(const DevMesh<real> M, const real* __restrict__ X,
-                                                    const real* __restrict__ Q, const real* __restrict__ R, double dt,
-                                                    int flux, int bc, double* __restrict__ gk, double* __restrict__ gr) {
-  constexpr int Nt = nt_of(N), Nq = N + 1;
-  const AllOps<N, real>& O = OPS<N>();
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= M.Kw) return;
-  const int blk = e >> 5, lane = e & 31, Kp = M.Kw_pad;
-  real Xc[12], G[G_COUNT];
-#pragma unroll
-  for (int i = 0; i < 12; ++i) Xc[i] = M.w_xyz[(int64_t(blk) * 12 + i) * kB + lane];
-  wedge_geometry_vals(Xc, G);
-  const real kappa = M.w_mat[0 * Kp + e], irho = M.w_mat[1 * Kp + e], zM = M.w_mat[2 * Kp + e];
-  const real J0 = G[G_J0], J1 = G[G_J1], J2 = G[G_J2];
-  auto ldq = [&](const real* b, int n) { return ld4(b, widx<N>(blk, n, lane)); };
+__host__ __device__ constexpr int grad_smem_bytes() {
+  constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
+  return int(sizeof(real)) * (2 * 4 * Np * kB + G_COUNT * kB + 3 * 2 * Nq * Nq * kB) + 8 * 3 * Nq * kB;
+}
 
-  // element terms: sum_j mu[j] . M^tri (sum_j' M1[j][j'] r[j'])
-  double t1k = 0.0, t1r = 0.0;
-#pragma unroll 1
-  for (int j = 0; j < Nq; ++j) {
+template <int N>
+__global__ void __launch_bounds__(32 * (N + 1)) k_wedge_grad(const DevMesh<real> M, const real* __restrict__ X,
+                                                             const real* __restrict__ Q, const real* __restrict__ R,
+                                                             double dt, int flux, int bc, double* __restrict__ gk,
+                                                             double* __restrict__ gr) {
+  constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
+  const AllOps<N, real>& O = OPS<N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sX = reinterpret_cast<real*>(smem_raw);
+  real* sQ = sX + 4 * Np * kB;
+  real* sG = sQ + 4 * Np * kB;
+  real* sJ = sG + G_COUNT * kB;  // [face][mu_p jump, mu_un jump][slice][edge node][32]
+  double* red = reinterpret_cast<double*>(sJ + 3 * 2 * Nq * Nq * kB);  // [slice][3][32]
+  const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
+  const int blk = blockIdx.x, e = blk * kB + lane;
+  const int Kp = M.Kw_pad;
+  {
+    const int64_t base = int64_t(blk) * 4 * Np * kB;
+    for (int v = threadIdx.x; v < 4 * Np * kB; v += blockDim.x) {
+      sX[v] = X[base + v];
+      sQ[v] = Q[base + v];
+    }
+    for (int v = threadIdx.x; v < 12 * kB; v += blockDim.x) sG[v] = M.w_xyz[int64_t(blk) * 12 * kB + v];
+  }
+  __syncthreads();
+  if (j == 0) wedge_geometry(sG, lane);
+  __syncthreads();
+#define GEO(item) sG[(item) * kB + lane]
+  const real kappa = M.w_mat[0 * Kp + e], irho = M.w_mat[1 * Kp + e], zM = M.w_mat[2 * Kp + e];
+  const real J0 = GEO(G_J0), J1 = GEO(G_J1), J2 = GEO(G_J2);
+
+  // element terms of slice j: mu[j] . M^tri (sum_j' M1[j][j'] r[j'])
+  real t1k = 0, t1r = 0;
+  {
     real bt[4][Nt];
 #pragma unroll
     for (int l = 0; l < Nt; ++l) bt[0][l] = bt[1][l] = bt[2][l] = bt[3][l] = real(0);
-#pragma unroll 1
+#pragma unroll
     for (int jp = 0; jp < Nq; ++jp) {
       const real m1 = O.w.M1[j * Nq + jp];
 #pragma unroll
       for (int l = 0; l < Nt; ++l) {
-        const Q4 v = ldq(R, jp * Nt + l);
+        const Q4 v = ld4(R, widx<N>(blk, jp * Nt + l, lane));
         bt[0][l] += m1 * v.p;
         bt[1][l] += m1 * v.u;
         bt[2][l] += m1 * v.v;
@@ -1234,28 +1255,32 @@ __global__ void __launch_bounds__(128) k_wedge_grad(const DevMesh<real> M, const
         c2 += mt * bt[2][l];
         c3 += mt * bt[3][l];
       }
-      const Q4 x = ldq(X, j * Nt + i);
-      t1k += double(x.p) * double(c0);
-      t1r += double(x.u) * double(c1) + double(x.v) * double(c2) + double(x.w) * double(c3);
+      const Q4 x = lds4(sX, j * Nt + i, lane);
+      t1k += x.p * c0;
+      t1r += x.u * c1 + x.v * c2 + x.w * c3;
     }
   }
-  t1k /= double(kappa) * double(kappa);
+  t1k /= kappa * kappa;
 
   // face terms: derivative of the upwind penalty in z
-  double gz = 0.0;
+  real gz = 0;
   if (flux == 0) {
-    // triangle faces (bottom, top): face mass J_f M^tri on the face nodes
-#pragma unroll 1
-    for (int fb = 0; fb < 2; ++fb) {
+    // a neighbour's node value: this block's slab or global memory
+    auto nbv = [&](const real* slab, const real* glob, int nbr, int node) {
+      return ((nbr >> 5) == blk) ? lds4(slab, node, nbr & 31) : ld4(glob, widx<N>(nbr >> 5, node, nbr & 31));
+    };
+    // triangle faces: warp 0 the bottom, warp N the top (face mass J_f M^tri)
+    if (j == 0 || j == N) {
+      const int fb = j == 0 ? 0 : 1;
       const int nbr = M.w_nbr[fb * Kp + e], code = M.w_code[fb * Kp + e];
-      const real n0 = fb ? G[G_NT0] : G[G_NB0], n1 = fb ? G[G_NT1] : G[G_NB1], n2 = fb ? G[G_NT2] : G[G_NB2];
-      const real Jf = fb ? G[G_JFT] : G[G_JFB];
+      const real n0 = GEO(fb ? G_NT0 : G_NB0), n1 = GEO(fb ? G_NT1 : G_NB1), n2 = GEO(fb ? G_NT2 : G_NB2);
+      const real Jf = GEO(fb ? G_JFT : G_JFB);
       const real zP = nbr < 0 ? zM : M.w_mat[2 * Kp + (nbr < 0 ? e : nbr)];
       real a[Nt], b[Nt], c[Nt], d[Nt];  // [p], [mu_p], [u_n], [mu_un] (boundary: own values)
 #pragma unroll
       for (int k = 0; k < Nt; ++k) {
         const int own = (fb ? N * Nt : 0) + k;
-        const Q4 qo = ldq(Q, own), xo = ldq(X, own);
+        const Q4 qo = lds4(sQ, own, lane), xo = lds4(sX, own, lane);
         if (nbr < 0) {
           a[k] = qo.p;
           b[k] = xo.p;
@@ -1264,15 +1289,14 @@ __global__ void __launch_bounds__(128) k_wedge_grad(const DevMesh<real> M, const
         } else {
           const int nf = (code >> 4) & 3;
           const int node = (nf ? N * Nt : 0) + O.tab.tri_perm[code & 15][k];
-          const int64_t ni = widx<N>(nbr >> 5, node, nbr & 31);
-          const Q4 qn = ld4(Q, ni), xn = ld4(X, ni);
+          const Q4 qn = nbv(sQ, Q, nbr, node), xn = nbv(sX, X, nbr, node);
           a[k] = qn.p - qo.p;
           b[k] = xn.p - xo.p;
           c[k] = n0 * (qn.u - qo.u) + n1 * (qn.v - qo.v) + n2 * (qn.w - qo.w);
           d[k] = n0 * (xn.u - xo.u) + n1 * (xn.v - xo.v) + n2 * (xn.w - xo.w);
         }
       }
-      double Ip = 0.0, Iu = 0.0;
+      real Ip = 0, Iu = 0;
 #pragma unroll
       for (int k = 0; k < Nt; ++k) {
         real sp = 0, su = 0;
@@ -1281,74 +1305,96 @@ __global__ void __launch_bounds__(128) k_wedge_grad(const DevMesh<real> M, const
           sp += O.w.M[k * Nt + kk] * b[kk];
           su += O.w.M[k * Nt + kk] * d[kk];
         }
-        Ip += double(a[k]) * double(sp);
-        Iu += double(c[k]) * double(su);
+        Ip += a[k] * sp;
+        Iu += c[k] * su;
       }
-      Ip *= double(Jf);
-      Iu *= double(Jf);
+      Ip *= Jf;
+      Iu *= Jf;
       if (nbr >= 0) {
-        const double tp = 2.0 / (double(zM) + double(zP));
-        gz += 0.25 * tp * tp * Ip + 0.25 * Iu;
+        const real tp = real(2) / (zM + zP);
+        gz += real(0.25) * tp * tp * Ip + real(0.25) * Iu;
       } else {
-        gz += bc == 0 ? Ip / (double(zM) * double(zM)) : Iu;
+        gz += bc == 0 ? Ip / (zM * zM) : Iu;
       }
     }
-    // quadrilateral faces: face mass M~_e (x) M^1D, M~_e = ca Mea + cb Meb
-#pragma unroll 1
+    // quadrilateral faces (face mass M~_e (x) M^1D): this slice's jumps, the
+    // mu jumps of every slice through the shared table
+    real a[3][Nq], c[3][Nq];
+#pragma unroll
     for (int ed = 0; ed < 3; ++ed) {
       const int nbr = M.w_nbr[(2 + ed) * Kp + e], code = M.w_code[(2 + ed) * Kp + e];
-      const real nx = G[G_QNX0 + ed], ny = G[G_QNY0 + ed], ca = G[G_QCA0 + ed], cbq = G[G_QCB0 + ed];
-      const real zP = nbr < 0 ? zM : M.w_mat[2 * Kp + (nbr < 0 ? e : nbr)];
+      const real nx = GEO(G_QNX0 + ed), ny = GEO(G_QNY0 + ed);
       const int ep = nbr < 0 ? ed : code >> 1, rev = nbr < 0 ? 0 : code & 1;
-      real a[Nq][Nq], b[Nq][Nq], c[Nq][Nq], d[Nq][Nq];
 #pragma unroll
-      for (int j = 0; j < Nq; ++j)
+      for (int m = 0; m < Nq; ++m) {
+        const int own = j * Nt + edge_node(N, ed, m);
+        const Q4 qo = lds4(sQ, own, lane), xo = lds4(sX, own, lane);
+        real bb, dd;
+        if (nbr < 0) {
+          a[ed][m] = qo.p;
+          c[ed][m] = nx * qo.u + ny * qo.v;
+          bb = xo.p;
+          dd = nx * xo.u + ny * xo.v;
+        } else {
+          const int node = j * Nt + O.tab.edge[ep][rev ? N - m : m];
+          const Q4 qn = nbv(sQ, Q, nbr, node), xn = nbv(sX, X, nbr, node);
+          a[ed][m] = qn.p - qo.p;
+          c[ed][m] = nx * (qn.u - qo.u) + ny * (qn.v - qo.v);
+          bb = xn.p - xo.p;
+          dd = nx * (xn.u - xo.u) + ny * (xn.v - xo.v);
+        }
+        sJ[(((ed * 2 + 0) * Nq + j) * Nq + m) * kB + lane] = bb;
+        sJ[(((ed * 2 + 1) * Nq + j) * Nq + m) * kB + lane] = dd;
+      }
+    }
+    __syncthreads();
 #pragma unroll
-        for (int m = 0; m < Nq; ++m) {
-          const int own = j * Nt + edge_node(N, ed, m);
-          const Q4 qo = ldq(Q, own), xo = ldq(X, own);
-          if (nbr < 0) {
-            a[j][m] = qo.p;
-            b[j][m] = xo.p;
-            c[j][m] = nx * qo.u + ny * qo.v;
-            d[j][m] = nx * xo.u + ny * xo.v;
-          } else {
-            const int64_t ni = widx<N>(nbr >> 5, j * Nt + O.tab.edge[ep][rev ? N - m : m], nbr & 31);
-            const Q4 qn = ld4(Q, ni), xn = ld4(X, ni);
-            a[j][m] = qn.p - qo.p;
-            b[j][m] = xn.p - xo.p;
-            c[j][m] = nx * (qn.u - qo.u) + ny * (qn.v - qo.v);
-            d[j][m] = nx * (xn.u - xo.u) + ny * (xn.v - xo.v);
+    for (int ed = 0; ed < 3; ++ed) {
+      const int nbr = M.w_nbr[(2 + ed) * Kp + e];
+      const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
+      const real zP = nbr < 0 ? zM : M.w_mat[2 * Kp + (nbr < 0 ? e : nbr)];
+      real Ip = 0, Iu = 0;
+#pragma unroll
+      for (int m = 0; m < Nq; ++m) {
+        real sp = 0, su = 0;
+#pragma unroll
+        for (int jp = 0; jp < Nq; ++jp) {
+          const real m1 = O.w.M1[j * Nq + jp];
+#pragma unroll
+          for (int mp = 0; mp < Nq; ++mp) {
+            const real w = m1 * (ca * O.w.Mea[m * Nq + mp] + cbq * O.w.Meb[m * Nq + mp]);
+            sp += w * sJ[(((ed * 2 + 0) * Nq + jp) * Nq + mp) * kB + lane];
+            su += w * sJ[(((ed * 2 + 1) * Nq + jp) * Nq + mp) * kB + lane];
           }
         }
-      double Ip = 0.0, Iu = 0.0;
-#pragma unroll
-      for (int j = 0; j < Nq; ++j)
-#pragma unroll
-        for (int m = 0; m < Nq; ++m) {
-          real sp = 0, su = 0;
-#pragma unroll
-          for (int jp = 0; jp < Nq; ++jp)
-#pragma unroll
-            for (int mp = 0; mp < Nq; ++mp) {
-              const real w = O.w.M1[j * Nq + jp] * (ca * O.w.Mea[m * Nq + mp] + cbq * O.w.Meb[m * Nq + mp]);
-              sp += w * b[jp][mp];
-              su += w * d[jp][mp];
-            }
-          Ip += double(a[j][m]) * double(sp);
-          Iu += double(c[j][m]) * double(su);
-        }
+        Ip += a[ed][m] * sp;
+        Iu += c[ed][m] * su;
+      }
       if (nbr >= 0) {
-        const double tp = 2.0 / (double(zM) + double(zP));
-        gz += 0.25 * tp * tp * Ip + 0.25 * Iu;
+        const real tp = real(2) / (zM + zP);
+        gz += real(0.25) * tp * tp * Ip + real(0.25) * Iu;
       } else {
-        gz += bc == 0 ? Ip / (double(zM) * double(zM)) : Iu;
+        gz += bc == 0 ? Ip / (zM * zM) : Iu;
       }
     }
   }
-  const double rho = 1.0 / double(irho);
-  gk[e] += dt * (t1k + gz * double(zM) / (2.0 * double(kappa)));
-  gr[e] += dt * (t1r + gz * double(zM) / (2.0 * rho));
+  // reduce the slices in a fixed order
+  red[(j * 3 + 0) * kB + lane] = double(t1k);
+  red[(j * 3 + 1) * kB + lane] = double(t1r);
+  red[(j * 3 + 2) * kB + lane] = double(gz);
+  __syncthreads();
+  if (j == 0 && e < M.Kw) {
+    double sk = 0.0, sr = 0.0, sz = 0.0;
+    for (int jj = 0; jj < Nq; ++jj) {
+      sk += red[(jj * 3 + 0) * kB + lane];
+      sr += red[(jj * 3 + 1) * kB + lane];
+      sz += red[(jj * 3 + 2) * kB + lane];
+    }
+    const double rho = 1.0 / double(irho);
+    gk[e] += dt * (sk + sz * double(zM) / (2.0 * double(kappa)));
+    gr[e] += dt * (sr + sz * double(zM) / (2.0 * rho));
+  }
+#undef GEO
 }
 
 // ---------------------------------------------------------------------------
@@ -1365,6 +1411,8 @@ int prepare_n() {
                                wedge_smem_bytes<N, b2>());
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_tet_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, tet_smem_bytes<N>());
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_wedge_grad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, grad_smem_bytes<N>());
   return int(err);
 }
 
@@ -1442,8 +1490,11 @@ int DGW_CAT(launch_inject_, REALNS)(const DevMesh<REAL>& m, REAL* muq, REAL* x, 
 }
 int DGW_CAT(launch_grad_, REALNS)(const DevMesh<REAL>& m, const REAL* x, const REAL* q, const REAL* r, double dt,
                                   int flux, int bc, double* gk, double* gr, void* stream) {
-  if (m.Kw > 0)
-    REALNS::k_wedge_grad<NORD><<<(m.Kw + 127) / 128, 128, 0, cudaStream_t(stream)>>>(m, x, q, r, dt, flux, bc, gk, gr);
+  if (m.nblk_w > 0) {
+    constexpr int bytes = REALNS::grad_smem_bytes<NORD>();
+    REALNS::k_wedge_grad<NORD><<<m.nblk_w, 32 * (NORD + 1), bytes, cudaStream_t(stream)>>>(m, x, q, r, dt, flux, bc, gk,
+                                                                                          gr);
+  }
   return int(cudaGetLastError());
 }
 int DGW_CAT(launch_clock_, REALNS)(double* clock, double dt, void* stream) {

@@ -326,3 +326,23 @@ def surface_shots(nshots: int, seed: int, depth: float = 0.01, margin: float = 0
     rng = np.random.default_rng(seed)
     xy = rng.uniform(margin, 1.0 - margin, size=(nshots, 2))
     return [(float(x), float(y), 1.0 - depth) for x, y in xy]
+
+
+def inclusion_model(mesh: Mesh, amp: float = 0.5, center=(0.5, 0.5, 0.45), width: float = 0.15,
+                    c2_top: float = 1.0, c2_bottom: float = 2.25, z_interface: float = 0.5):
+    """Per-element c^2 of a two-layer model (c2_bottom below z_interface, c2_top
+    above, by element centroid) plus a smooth Gaussian inclusion of amplitude
+    `amp`; rho = 1.  Returns (c2, rho)."""
+    V = mesh.VX[np.where(mesh.EToV >= 0, mesh.EToV, mesh.EToV[:, :1])]
+    nv = np.where(mesh.etype == WEDGE, 6, 4)[:, None]
+    cen = np.array([(V[k, :nv[k, 0]]).mean(axis=0) for k in range(mesh.K)])
+    c2 = np.where(cen[:, 2] < z_interface, c2_bottom, c2_top)
+    r2 = ((cen - np.asarray(center)) ** 2).sum(axis=1)
+    c2 = c2 + amp * np.exp(-r2 / width ** 2)
+    return c2, np.ones(mesh.K)
+
+
+def surface_receivers(n_side: int, depth: float = 0.01, margin: float = 0.05):
+    """n_side x n_side grid of receiver points just below the top surface z = 1."""
+    g = np.linspace(margin, 1.0 - margin, n_side)
+    return [(float(x), float(y), 1.0 - depth) for y in g for x in g]
