@@ -199,3 +199,29 @@ def test_merge_meshes_keeps_pieces_apart():
         assert nb.size == per.sum() and (nb[:split] < Ta).all() and (nb[split:][nb[split:] >= 0] >= Ta).all()
     finally:
         dg.dg_destroy(ctx)
+
+
+def _in_block_fractions(m):
+    """Fraction of interior triangle-face and quad-face neighbours that lie in the
+    same 32-element block (their traces come from the block's shared-memory slab)."""
+    ctx = dg.dg_mesh_create(m.VX, m.EToV, m.etype)
+    try:
+        dg.dg_set_order(ctx, 1)
+        nb = dg.dg_face_neighbors(ctx).reshape(m.K, 18)
+    finally:
+        dg.dg_destroy(ctx)
+    k = np.arange(m.K)[:, None]
+    tri = nb[:, [0, 3]] // 6
+    quad = nb[:, [6, 10, 14]] // 6
+    ft = (tri[nb[:, [0, 3]] >= 0] // 32 == np.broadcast_to(k, tri.shape)[nb[:, [0, 3]] >= 0] // 32).mean()
+    fq = (quad[nb[:, [6, 10, 14]] >= 0] // 32 == np.broadcast_to(k, quad.shape)[nb[:, [6, 10, 14]] >= 0] // 32).mean()
+    return ft, fq
+
+
+def test_column_order_keeps_vertical_traces_in_the_block():
+    """Column-major order with 16 layers: a 32-element block holds two whole
+    columns, so every vertical (triangle-face) neighbour is in the same block --
+    the layer-marching reuse of vertical traces, through shared memory."""
+    ft, fq = _in_block_fractions(I.bumpy_layered_mesh(8, 16))
+    assert ft == 1.0
+    assert 0.2 < fq < 0.5
