@@ -222,9 +222,11 @@ def measure_order(N, args, torch, dev, m, c2, rho, mass):
     S.sync()
     ms = start.elapsed_time(end)
     dof = 4 * S.total_nodes
-    bpc, onthefly, us = S.autotune(10)
-    res = {"ms": ms, "dof": dof, "clocks": clk.summary(), "solver": S, "dt": dt, "q": q,
-           "autotune": {"blocks_per_cta": bpc, "factor_in_stage": onthefly, "stage_us": us}}
+    tune = None
+    if not args.no_autotune:
+        bpc, onthefly, us = S.autotune(10)
+        tune = {"blocks_per_cta": bpc, "factor_in_stage": onthefly, "stage_us": us}
+    res = {"ms": ms, "dof": dof, "clocks": clk.summary(), "solver": S, "dt": dt, "q": q, "autotune": tune}
     return res
 
 
@@ -526,6 +528,7 @@ def main():
     ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid wedge + tet workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the multi-shot and multi-mesh workloads")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) workload")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the launch-variant autotuner after timing")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
