@@ -1189,10 +1189,12 @@ __global__ void k_inject(const DevMesh<real> M, real* __restrict__ muq, real* __
 // 32-wedge block, warp j slice j (slabs of x and q in shared memory); the
 // per-slice partial sums are reduced across warps in a fixed order and added,
 // times dt, in double.  Wedge neighbours only (the adjoint takes wedge meshes).
+// (the right-hand side is read from global memory: staging it as a third
+// slab measured slower at N = 3, two CTAs per SM instead of three)
 template <int N>
 __host__ __device__ constexpr int grad_smem_bytes() {
   constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
-  return int(sizeof(real)) * (2 * 4 * Np * kB + G_COUNT * kB + 3 * 2 * Nq * Nq * kB) + 8 * 3 * Nq * kB;
+  return 16 + int(sizeof(real)) * (2 * 4 * Np * kB + G_COUNT * kB + 3 * 2 * Nq * Nq * kB) + 8 * 3 * Nq * kB;
 }
 
 template <int N>
@@ -1203,7 +1205,9 @@ __global__ void __launch_bounds__(32 * (N + 1)) k_wedge_grad(const DevMesh<real>
   constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
   const AllOps<N, real>& O = OPS<N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  real* sX = reinterpret_cast<real*>(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // slabs and coordinates
+  int* failed = reinterpret_cast<int*>(smem_raw + 8);
+  real* sX = reinterpret_cast<real*>(smem_raw + 16);
   real* sQ = sX + 4 * Np * kB;
   real* sG = sQ + 4 * Np * kB;
   real* sJ = sG + G_COUNT * kB;  // [face][mu_p jump, mu_un jump][slice][edge node][32]
@@ -1211,15 +1215,27 @@ __global__ void __launch_bounds__(32 * (N + 1)) k_wedge_grad(const DevMesh<real>
   const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
   const int blk = blockIdx.x, e = blk * kB + lane;
   const int Kp = M.Kw_pad;
-  {
-    const int64_t base = int64_t(blk) * 4 * Np * kB;
-    for (int v = threadIdx.x; v < 4 * Np * kB; v += blockDim.x) {
-      sX[v] = X[base + v];
-      sQ[v] = Q[base + v];
-    }
-    for (int v = threadIdx.x; v < 12 * kB; v += blockDim.x) sG[v] = M.w_xyz[int64_t(blk) * 12 * kB + v];
+  constexpr uint32_t slab_bytes = uint32_t(4 * Np * kB * sizeof(real)), xyz_bytes = uint32_t(12 * kB * sizeof(real));
+  if (threadIdx.x == 0) {
+    *failed = 0;
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    mbar_expect_tx(bar, 2 * slab_bytes + xyz_bytes);
+    bulk_g2s(sX, X + int64_t(blk) * 4 * Np * kB, slab_bytes, bar);
+    bulk_g2s(sQ, Q + int64_t(blk) * 4 * Np * kB, slab_bytes, bar);
+    bulk_g2s(sG, M.w_xyz + int64_t(blk) * 12 * kB, xyz_bytes, bar);
   }
   __syncthreads();
+  if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0)) && lane == 0) atomicOr(failed, 1);
+  __syncthreads();
+  if (*reinterpret_cast<volatile int*>(failed)) {
+    // the copies never completed: report, let them drain, every warp leaves
+    if (threadIdx.x == 0) {
+      atomicOr(M.err, kErrTimeout);
+      mbar_wait_bounded(bar, 0);
+    }
+    return;
+  }
   if (j == 0) wedge_geometry(sG, lane);
   __syncthreads();
 #define GEO(item) sG[(item) * kB + lane]
@@ -1353,19 +1369,29 @@ __global__ void __launch_bounds__(32 * (N + 1)) k_wedge_grad(const DevMesh<real>
       const int nbr = M.w_nbr[(2 + ed) * Kp + e];
       const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
       const real zP = nbr < 0 ? zM : M.w_mat[2 * Kp + (nbr < 0 ? e : nbr)];
+      // (M~_e (x) M^1D) applied as M^1D along the slices first, then M~_e along the edge
+      real bb[Nq], dd[Nq];
+#pragma unroll
+      for (int mp = 0; mp < Nq; ++mp) {
+        real sb = 0, sd = 0;
+#pragma unroll
+        for (int jp = 0; jp < Nq; ++jp) {
+          const real m1 = O.w.M1[j * Nq + jp];
+          sb += m1 * sJ[(((ed * 2 + 0) * Nq + jp) * Nq + mp) * kB + lane];
+          sd += m1 * sJ[(((ed * 2 + 1) * Nq + jp) * Nq + mp) * kB + lane];
+        }
+        bb[mp] = sb;
+        dd[mp] = sd;
+      }
       real Ip = 0, Iu = 0;
 #pragma unroll
       for (int m = 0; m < Nq; ++m) {
         real sp = 0, su = 0;
 #pragma unroll
-        for (int jp = 0; jp < Nq; ++jp) {
-          const real m1 = O.w.M1[j * Nq + jp];
-#pragma unroll
-          for (int mp = 0; mp < Nq; ++mp) {
-            const real w = m1 * (ca * O.w.Mea[m * Nq + mp] + cbq * O.w.Meb[m * Nq + mp]);
-            sp += w * sJ[(((ed * 2 + 0) * Nq + jp) * Nq + mp) * kB + lane];
-            su += w * sJ[(((ed * 2 + 1) * Nq + jp) * Nq + mp) * kB + lane];
-          }
+        for (int mp = 0; mp < Nq; ++mp) {
+          const real w = ca * O.w.Mea[m * Nq + mp] + cbq * O.w.Meb[m * Nq + mp];
+          sp += w * bb[mp];
+          su += w * dd[mp];
         }
         Ip += a[ed][m] * sp;
         Iu += c[ed][m] * su;
