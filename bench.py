@@ -357,6 +357,9 @@ def measure_multimesh(args, torch, dev):
             "ratio": s_a / (ms_b / 1e3)}
 
 
+ADJOINT_SIZES = {"full": (48, 24, 8), "small": (24, 12, 2)}
+
+
 def measure_adjoint(args, torch, dev):
     """Differentiation workload: 2x48x48 footprint x 24 layers = 110592 wedges,
     N=3, FP32 fields, two-layer c^2 with a Gaussian inclusion, 8 shots (Ricker
@@ -364,15 +367,21 @@ def measure_adjoint(args, torch, dev):
     of the model with a 10% stronger inclusion; checkpoints every 50 steps.
     Times the forward pass (with receiver sampling and checkpoints) and the
     adjoint sweep (segment re-runs, per-step stage recomputation, adjoint
-    stages, gradient terms); reports their ratio and the peak device memory."""
+    stages, gradient terms), then both again with checkpoints every 10 steps
+    and stage records (the segment re-run stores the stages, no per-step
+    recomputation); reports the ratios, the peak device memory of each and
+    whether the two gradients agree bit for bit.  The headline ratio is the
+    stage-record one.
+    `--adjoint-size small` (2x24x24 x 12 layers, 2 shots) is the profiling case."""
     from paper_1607_03399_gb300 import inputs as I
     from paper_1607_03399_gb300 import adjoint as AD
-    m = I.bumpy_layered_mesh(48, 24)
-    pos = I.surface_shots(8, 5)
+    side, layers, nshots = ADJOINT_SIZES[args.adjoint_size]
+    m = I.bumpy_layered_mesh(side, layers)
+    pos = I.surface_shots(nshots, 5)
     recs = I.surface_receivers(16)
     nsteps = max(50, min(args.steps * 2, 200))
-    pb = AD.Problem(m.VX, m.EToV, m.etype, 3, 0.0, nsteps, recs, shots=8, checkpoint_every=50,
-                    shot_sources=[(s, *pos[s], 8.0, 0.125, 1.0) for s in range(8)], device=str(dev))
+    pb = AD.Problem(m.VX, m.EToV, m.etype, 3, 0.0, nsteps, recs, shots=nshots, checkpoint_every=50,
+                    shot_sources=[(s, *pos[s], 8.0, 0.125, 1.0) for s in range(nshots)], device=str(dev))
     c2t, rho = I.inclusion_model(m, amp=0.55)
     c2, _ = I.inclusion_model(m, amp=0.5)
     S = pb.solver(c2t, rho)
@@ -391,11 +400,30 @@ def measure_adjoint(args, torch, dev):
     gk, gr = AD.reverse(S, pb, traces, data, ck)
     t2 = time.perf_counter()
     peak = torch.cuda.max_memory_allocated(dev)
+    del traces, ck
+    # the same gradient from stage records: checkpoints every 10 steps, ten
+    # fields per step of the segment, no per-step recomputation
+    pb.checkpoint_every, pb.stage_records = 10, True
+    S.sync()
+    torch.cuda.synchronize(dev)
+    torch.cuda.reset_peak_memory_stats(dev)
+    t3 = time.perf_counter()
+    traces, ck = AD.forward(S, pb)
+    J2 = AD.misfit(traces, data)
+    t4 = time.perf_counter()
+    gk2, gr2 = AD.reverse(S, pb, traces, data, ck)
+    t5 = time.perf_counter()
+    peak2 = torch.cuda.max_memory_allocated(dev)
     S.close()
-    return {"workload": "adjoint_2x48x48x24_N3_8shots_256rec", "wedges": m.K, "shots": 8, "receivers": len(recs),
-            "steps": nsteps, "checkpoint_every": 50, "misfit": J, "forward_s": t1 - t0, "adjoint_s": t2 - t1,
-            "adjoint_over_forward": (t2 - t1) / (t1 - t0), "peak_device_gb": peak / 1e9,
-            "gradient_norm": float(np.sqrt((gk ** 2).sum() + (gr ** 2).sum()))}
+    return {"workload": f"adjoint_2x{side}x{side}x{layers}_N3_{nshots}shots_{len(recs)}rec", "wedges": m.K,
+            "shots": nshots, "receivers": len(recs), "steps": nsteps,
+            "adjoint_over_forward": (t5 - t4) / (t4 - t3), "misfit": J,
+            "gradient_norm": float(np.sqrt((gk ** 2).sum() + (gr ** 2).sum())),
+            "recompute": {"checkpoint_every": 50, "forward_s": t1 - t0, "adjoint_s": t2 - t1,
+                          "adjoint_over_forward": (t2 - t1) / (t1 - t0), "peak_device_gb": peak / 1e9},
+            "stage_records": {"checkpoint_every": 10, "forward_s": t4 - t3, "adjoint_s": t5 - t4,
+                              "adjoint_over_forward": (t5 - t4) / (t4 - t3), "peak_device_gb": peak2 / 1e9,
+                              "same_gradient": bool(J2 == J and np.array_equal(gk, gk2) and np.array_equal(gr, gr2))}}
 
 
 def run_ours(args, rank, world):
@@ -528,6 +556,8 @@ def main():
     ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid wedge + tet workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the multi-shot and multi-mesh workloads")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) workload")
+    ap.add_argument("--adjoint-size", default="full", choices=sorted(ADJOINT_SIZES),
+                    help="size of the adjoint workload (small: the profiling case)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-variant autotuner after timing")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))

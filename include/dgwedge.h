@@ -273,6 +273,30 @@ int dg_adjoint_reset(dg_ctx* ctx);
 /* d_resid[shots][receivers] (device, context precision) */
 int dg_adjoint_inject(dg_ctx* ctx, const void* d_resid);
 int dg_adjoint_step(dg_ctx* ctx, double dt);
+
+/* Stage records: a memory-for-time alternative to the recomputation inside
+ * dg_adjoint_step (not in the paper).  A record of one step holds ten packed
+ * fields (each dg_device_bytes' field_bytes, in this order): the step's input
+ * state q_n, the stage states Q_1..Q_4 and the five stage right-hand sides
+ * r_s = A Q_{s-1} + f(t_n + c_s dt).
+ *   dg_step_record_bytes  bytes of one record (10 x field_bytes).
+ *   dg_step_record        one LSRK45 step of the bound state, like dg_step with
+ *                         nsteps = 1 (same result bit for bit), that also writes
+ *                         the record of the step to d_rec (device memory,
+ *                         caller-owned, 256-byte aligned, overwritten).  Async.
+ *   dg_adjoint_step_recorded
+ *                         dg_adjoint_step with the forward stages read from a
+ *                         record that dg_step_record wrote for that step (same
+ *                         result bit for bit); the bound state and time are
+ *                         neither used nor changed.  d_rec is not modified.
+ * Use: checkpoints every C steps in the forward pass; per segment, from the
+ * last: dg_load_state(checkpoint), C x dg_step_record into C records, then for
+ * n = last .. first: dg_adjoint_inject, dg_adjoint_step_recorded(record n).
+ * Errors: DG_ERR_ARG (null or misaligned d_rec, dt <= 0), DG_ERR_STATE
+ * (unbound context or adjoint), DG_ERR_CUDA. */
+int dg_step_record_bytes(const dg_ctx* ctx, size_t* bytes);
+int dg_step_record(dg_ctx* ctx, double dt, void* d_rec);
+int dg_adjoint_step_recorded(dg_ctx* ctx, double dt, const void* d_rec);
 /* set the adjoint state: mu_Q and the next stage input x (normally b_5 mu_Q),
  * canonical layout, host or device sources */
 int dg_adjoint_set(dg_ctx* ctx, const void* mu_q, const void* x, int on_device);

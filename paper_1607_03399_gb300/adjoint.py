@@ -7,8 +7,12 @@ with p_r the pressure at receiver r after step n.  The forward pass keeps a
 checkpoint of the state every `checkpoint_every` steps; the reverse pass
 re-runs each segment from its checkpoint to recover the step states and calls
 dg_adjoint_step once per step, which recomputes that step's five stages and
-accumulates dJ/dkappa, dJ/drho.  The chain rule to (c^2, rho) uses
-kappa = rho c^2.
+accumulates dJ/dkappa, dJ/drho.  With `stage_records` the segment re-run
+instead stores every step's stage inputs and right-hand sides (ten fields per
+step, dg_step_record) and the reverse steps read them back
+(dg_adjoint_step_recorded): one forward pass less per step for
+checkpoint_every x 10 fields of device memory; the gradient is the same bit
+for bit.  The chain rule to (c^2, rho) uses kappa = rho c^2.
 """
 from __future__ import annotations
 
@@ -35,6 +39,7 @@ class Problem:
     bc: str = "rigid"
     flux: str = "upwind"
     checkpoint_every: int = 50
+    stage_records: bool = False
     device: str = "cuda:0"
 
     def solver(self, c2, rho) -> Solver:
@@ -45,16 +50,19 @@ class Problem:
 
 
 def forward(S: Solver, pb: Problem, q0=None):
-    """Traces [nsteps][shots][receivers] (device tensor) and the checkpoints {step: state}."""
+    """Traces [nsteps][shots][receivers] (device tensor) and the checkpoints
+    {step: (state, time)}; the time is the solver's own (accumulated step by
+    step), so a re-run from a checkpoint evaluates the sources at exactly the
+    forward pass's stage times."""
     torch = S.torch
     S.set_fields(np.zeros(S.field_shape, dtype=S.np_dtype) if q0 is None else q0)
     traces = torch.empty((pb.nsteps, pb.shots, S.nrec), dtype=S.dtype, device=S.device)
-    ck = {0: S.save_state()}
+    ck = {0: (S.save_state(), S.time())}
     for n in range(1, pb.nsteps + 1):
         S.step(pb.dt, 1)
         S.sample(traces[n - 1])
         if n % pb.checkpoint_every == 0 and n < pb.nsteps:
-            ck[n] = S.save_state()
+            ck[n] = (S.save_state(), S.time())
     S.sync()
     return traces, ck
 
@@ -74,17 +82,30 @@ def reverse(S: Solver, pb: Problem, traces, data, ck):
         S.adjoint_reset()
     C = pb.checkpoint_every
     starts = list(range(0, pb.nsteps, C))
+    if pb.stage_records:
+        recs = [S.new_record() for _ in range(min(C, pb.nsteps))]
+        for s0 in reversed(starts):
+            s1 = min(s0 + C, pb.nsteps)
+            # records of the steps q_n -> q_{n+1}, n = s0 .. s1 - 1
+            S.load_state(*ck[s0])
+            for n in range(s0, s1):
+                S.step_record(pb.dt, recs[n - s0])
+            for n in range(s1, s0, -1):
+                S.adjoint_inject(resid[n - 1])
+                S.adjoint_step_recorded(pb.dt, recs[n - 1 - s0])
+        S.sync()
+        return S.adjoint_gradient()
     for s0 in reversed(starts):
         s1 = min(s0 + C, pb.nsteps)
         # states q_{s0} .. q_{s1 - 1} of the segment
-        S.load_state(ck[s0], s0 * pb.dt)
-        states = [S.save_state()]
+        S.load_state(*ck[s0])
+        states = [ck[s0]]
         for n in range(s0 + 1, s1):
             S.step(pb.dt, 1)
-            states.append(S.save_state())
+            states.append((S.save_state(), S.time()))
         for n in range(s1, s0, -1):
             S.adjoint_inject(resid[n - 1])
-            S.load_state(states[n - 1 - s0], (n - 1) * pb.dt)
+            S.load_state(*states[n - 1 - s0])
             S.adjoint_step(pb.dt)
     S.sync()
     return S.adjoint_gradient()

@@ -1582,38 +1582,23 @@ int dg_adjoint_inject(dg_ctx* c, const void* d_resid) {
   return DG_OK;
 }
 
-int dg_adjoint_step(dg_ctx* c, double dt) {
-  if (!c) return DG_ERR_ARG;
-  if (!(dt > 0)) return c->fail(DG_ERR_ARG, "dt must be positive");
-  if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_step before dg_adjoint_bind");
-  int rc = ensure_ops(c);
-  if (rc) return rc;
-  // 1. the forward step from the current state and time, keeping every stage's
-  //    input Q_{s-1} and right-hand side r_s = A Q_{s-1} + f(t + c_s dt)
-  const void* q0 = c->d_q[c->cur];
-  const void* qin = q0;
-  for (int st = 0; st < 5 && rc == DG_OK; ++st) {
-    void* qout = adj_field(c, st < 4 ? kAdjQs + st : kAdjScr);
-    StageExtra x;
-    x.rhs_out = adj_field(c, kAdjRs + st);
-    rc = launch_stage(c, qin, qout, adj_field(c, kAdjRes), kLSRK_A[st], kLSRK_B[st], dt, true, c->stream, kLSRK_C[st], x);
-    qin = qout;
-  }
-  // 2. the stages in reverse (variables mu = P W^{-1} lambda): gradient terms of
-  //    stage s with x = mu_K, then mu_Q += dt A x and x <- a_s x + b_{s-1} mu_Q
+namespace {
+// the five adjoint stages of one step in reverse (variables mu = P W^{-1} lambda):
+// gradient terms of stage s with x = mu_K, then mu_Q += dt A x and x <- a_s x +
+// b_{s-1} mu_Q.  Q[s] is the input of forward stage s (Q[0] = q_n), R[s] its
+// right-hand side.
+int adjoint_reverse_stages(dg_ctx* c, double dt, const void* const* Q, const void* const* R) {
+  int rc = DG_OK;
   for (int st = 4; st >= 0 && rc == DG_OK; --st) {
-    const void* Qp = st == 0 ? q0 : adj_field(c, kAdjQs + st - 1);
     void* xin = adj_field(c, c->adj_x);
     void* xout = adj_field(c, c->adj_x == kAdjX0 ? kAdjX1 : kAdjX0);
     int lr;
     if (c->prec == DG_F64)
-      lr = grad_f64(c->N, c->m64, static_cast<const double*>(xin), static_cast<const double*>(Qp),
-                    static_cast<const double*>(adj_field(c, kAdjRs + st)), dt, c->flux, c->bc, adj_gk(c), adj_gr(c),
-                    c->stream);
+      lr = grad_f64(c->N, c->m64, static_cast<const double*>(xin), static_cast<const double*>(Q[st]),
+                    static_cast<const double*>(R[st]), dt, c->flux, c->bc, adj_gk(c), adj_gr(c), c->stream);
     else
-      lr = grad_f32(c->N, c->m32, static_cast<const float*>(xin), static_cast<const float*>(Qp),
-                    static_cast<const float*>(adj_field(c, kAdjRs + st)), dt, c->flux, c->bc, adj_gk(c), adj_gr(c),
-                    c->stream);
+      lr = grad_f32(c->N, c->m32, static_cast<const float*>(xin), static_cast<const float*>(Q[st]),
+                    static_cast<const float*>(R[st]), dt, c->flux, c->bc, adj_gk(c), adj_gr(c), c->stream);
     if (lr) return cuda_fail(c, cudaError_t(lr), "gradient launch");
     StageExtra x;
     x.g = kLSRK_A[st];
@@ -1622,6 +1607,85 @@ int dg_adjoint_step(dg_ctx* c, double dt) {
     c->adj_x = c->adj_x == kAdjX0 ? kAdjX1 : kAdjX0;
   }
   return rc;
+}
+
+constexpr int kRecFields = 10;  // q_n, Q_1..Q_4, r_1..r_5
+}  // namespace
+
+int dg_adjoint_step(dg_ctx* c, double dt) {
+  if (!c) return DG_ERR_ARG;
+  if (!(dt > 0)) return c->fail(DG_ERR_ARG, "dt must be positive");
+  if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_step before dg_adjoint_bind");
+  int rc = ensure_ops(c);
+  if (rc) return rc;
+  // the forward step from the current state and time, keeping every stage's
+  // input Q_{s-1} and right-hand side r_s = A Q_{s-1} + f(t + c_s dt)
+  const void* Q[5] = {c->d_q[c->cur], adj_field(c, kAdjQs), adj_field(c, kAdjQs + 1), adj_field(c, kAdjQs + 2),
+                      adj_field(c, kAdjQs + 3)};
+  const void* R[5];
+  for (int st = 0; st < 5 && rc == DG_OK; ++st) {
+    void* qout = adj_field(c, st < 4 ? kAdjQs + st : kAdjScr);
+    StageExtra x;
+    x.rhs_out = adj_field(c, kAdjRs + st);
+    R[st] = x.rhs_out;
+    rc = launch_stage(c, Q[st], qout, adj_field(c, kAdjRes), kLSRK_A[st], kLSRK_B[st], dt, true, c->stream, kLSRK_C[st], x);
+  }
+  if (rc) return rc;
+  return adjoint_reverse_stages(c, dt, Q, R);
+}
+
+int dg_step_record_bytes(const dg_ctx* c, size_t* bytes) {
+  if (!c) return DG_ERR_ARG;
+  if (!bytes) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
+  *bytes = kRecFields * field_bytes_of(c);
+  return DG_OK;
+}
+
+int dg_step_record(dg_ctx* c, double dt, void* d_rec) {
+  if (!c) return DG_ERR_ARG;
+  if (!d_rec || reinterpret_cast<uintptr_t>(d_rec) % 256) return c->fail(DG_ERR_ARG, "null or misaligned record");
+  if (!(dt > 0)) return c->fail(DG_ERR_ARG, "dt must be positive");
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_step_record before dg_bind");
+  int rc = ensure_ops(c);
+  if (rc) return rc;
+  unsigned char* rec = static_cast<unsigned char*>(d_rec);
+  const size_t fb = c->field_bytes;
+  // slot 0 takes q_n, the stages run slot s -> slot s + 1 and the last one writes
+  // the bound buffer again (the same launches as one captured step)
+  cudaError_t e = cudaMemcpyAsync(rec, c->d_q[c->cur], fb, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "record copy");
+  for (int st = 0; st < 5 && rc == DG_OK; ++st) {
+    StageExtra x;
+    x.rhs_out = rec + size_t(5 + st) * fb;
+    void* qout = st < 4 ? static_cast<void*>(rec + size_t(st + 1) * fb) : c->d_q[c->cur];
+    rc = launch_stage(c, rec + size_t(st) * fb, qout, c->d_res, kLSRK_A[st], kLSRK_B[st], dt, true, c->stream,
+                      kLSRK_C[st], x);
+  }
+  if (rc) return rc;
+  double* clk = (c->prec == DG_F64) ? c->m64.clock : c->m32.clock;
+  const int crc = (c->prec == DG_F64) ? clock_f64(c->N, clk, dt, c->stream) : clock_f32(c->N, clk, dt, c->stream);
+  if (crc) return cuda_fail(c, cudaError_t(crc), "clock launch");
+  c->t += dt;
+  return DG_OK;
+}
+
+int dg_adjoint_step_recorded(dg_ctx* c, double dt, const void* d_rec) {
+  if (!c) return DG_ERR_ARG;
+  if (!d_rec || reinterpret_cast<uintptr_t>(d_rec) % 256) return c->fail(DG_ERR_ARG, "null or misaligned record");
+  if (!(dt > 0)) return c->fail(DG_ERR_ARG, "dt must be positive");
+  if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_step_recorded before dg_adjoint_bind");
+  int rc = ensure_ops(c);
+  if (rc) return rc;
+  const unsigned char* rec = static_cast<const unsigned char*>(d_rec);
+  const size_t fb = c->field_bytes;
+  const void* Q[5];
+  const void* R[5];
+  for (int st = 0; st < 5; ++st) {
+    Q[st] = rec + size_t(st) * fb;
+    R[st] = rec + size_t(5 + st) * fb;
+  }
+  return adjoint_reverse_stages(c, dt, Q, R);
 }
 
 int dg_adjoint_set(dg_ctx* c, const void* mu_q, const void* x, int on_device) {

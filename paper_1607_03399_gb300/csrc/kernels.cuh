@@ -222,6 +222,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
@@ -1127,301 +1130,14 @@ __global__ void k_energy_final(const double* __restrict__ partials, int n, doubl
   }
 }
 
-// ---------------------------------------------------------------------------
-// receivers and the adjoint (gradient with respect to kappa and rho)
-// ---------------------------------------------------------------------------
-// packed index of field slot 0 (pressure) of node n of the element (type, e)
-template <int N>
-__device__ __forceinline__ int64_t pidx(const DevMesh<real>& M, int type, int e, int n) {
-  return type == 6 ? widx<N>(e >> 5, n, e & 31) : tidx<N>(M.tet_off, e >> 5, n, e & 31);
-}
+}  // namespace REALNS
+}  // namespace dgw
 
-// out[shot][r] = sum_n l_r(n) p(n) in the receiver's element of that shot
-template <int N>
-__global__ void k_sample(const DevMesh<real> M, const real* __restrict__ q, real* __restrict__ out, int nshots) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nshots * M.nrec) return;
-  const int shot = idx / M.nrec, r = idx - shot * M.nrec;
-  const RecDev rd = M.rec[r];
-  const int e = shot * (rd.type == 6 ? M.Kw1 : M.Kt1) + rd.elem;
-  const int np = rd.type == 6 ? npw_of(N) : npt_of(N);
-  real acc = 0;
-  for (int n = 0; n < np; ++n) acc += M.rec_l[rd.loff + n] * q[pidx<N>(M, rd.type, e, n)];
-  out[idx] = acc;
-}
+#include "adjoint_kernels.cuh"
 
-// Adjoint load of the misfit residuals (in the variables mu = P W^{-1} lambda):
-// mu_Q,p += kappa (M^k)^{-1} sum_r resid_r l(x_r) on each receiver element, and
-// the next stage input x += b5 times the same.  One thread per (shot, element
-// group), receivers of a group in list order: deterministic.
-template <int N>
-__global__ void k_inject(const DevMesh<real> M, real* __restrict__ muq, real* __restrict__ x,
-                         const real* __restrict__ resid, int nshots, real b5) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nshots * M.nrgrp) return;
-  const int shot = idx / M.nrgrp, gi = idx - shot * M.nrgrp;
-  const RecGroup g = M.rgrp[gi];
-  const int e = shot * (g.type == 6 ? M.Kw1 : M.Kt1) + g.elem;
-  const real kappa = g.type == 6 ? M.w_mat[e] : M.t_mat[e];
-  const int np = g.type == 6 ? npw_of(N) : npt_of(N);
-  for (int n = 0; n < np; ++n) {
-    real acc = 0;
-    for (int i = g.r0; i < g.r0 + g.nr; ++i) {
-      const int r = M.rperm[i];
-      acc += resid[shot * M.nrec + r] * M.rec_g[M.rec[r].loff + n];
-    }
-    const int64_t i = pidx<N>(M, g.type, e, n);
-    muq[i] += kappa * acc;
-    x[i] += b5 * kappa * acc;
-  }
-}
+namespace dgw {
+namespace REALNS {
 
-// Per wedge and Runge-Kutta stage, with x = mu_K (adjoint stage variable,
-// lambda_K = W P mu_K), q = the forward stage input Q and r = A Q + f its
-// right-hand side:
-//   d/dkappa_k: mu_p^T M^k r_p / kappa^2 + dz/dkappa G,  d/drho_k: mu_u^T M^k r_u + dz/drho G,
-// with z = rho c = sqrt(kappa rho) and G the derivative of the upwind penalty
-// in z summed over the element's faces: interior faces (tau_p = 2/(z- + z+),
-// tau_u = (z- + z+)/2) give tau_p^2/4 int [p][mu_p] + 1/4 int [u_n][mu_un],
-// rigid walls int mu_un u_n, Dirichlet walls int mu_p p / z^2; central fluxes
-// have no penalty.  M^k = M^{tri,k} (x) M^1D (Section 4.2); the face masses are
-// J_f M^tri (triangles) and M~_e (x) M^1D (quadrilaterals).  A CTA takes a
-// 32-wedge block, warp j slice j (slabs of x and q in shared memory); the
-// per-slice partial sums are reduced across warps in a fixed order and added,
-// times dt, in double.  Wedge neighbours only (the adjoint takes wedge meshes).
-// (the right-hand side is read from global memory: staging it as a third
-// slab measured slower at N = 3, two CTAs per SM instead of three)
-template <int N>
-__host__ __device__ constexpr int grad_smem_bytes() {
-  constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
-  return 16 + int(sizeof(real)) * (2 * 4 * Np * kB + G_COUNT * kB + 3 * 2 * Nq * Nq * kB) + 8 * 3 * Nq * kB;
-}
-
-template <int N>
-__global__ void __launch_bounds__(32 * (N + 1)) k_wedge_grad(const DevMesh<real> M, const real* __restrict__ X,
-                                                             const real* __restrict__ Q, const real* __restrict__ R,
-                                                             double dt, int flux, int bc, double* __restrict__ gk,
-                                                             double* __restrict__ gr) {
-  constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
-  const AllOps<N, real>& O = OPS<N>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // slabs and coordinates
-  int* failed = reinterpret_cast<int*>(smem_raw + 8);
-  real* sX = reinterpret_cast<real*>(smem_raw + 16);
-  real* sQ = sX + 4 * Np * kB;
-  real* sG = sQ + 4 * Np * kB;
-  real* sJ = sG + G_COUNT * kB;  // [face][mu_p jump, mu_un jump][slice][edge node][32]
-  double* red = reinterpret_cast<double*>(sJ + 3 * 2 * Nq * Nq * kB);  // [slice][3][32]
-  const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
-  const int blk = blockIdx.x, e = blk * kB + lane;
-  const int Kp = M.Kw_pad;
-  constexpr uint32_t slab_bytes = uint32_t(4 * Np * kB * sizeof(real)), xyz_bytes = uint32_t(12 * kB * sizeof(real));
-  if (threadIdx.x == 0) {
-    *failed = 0;
-    mbar_init(bar, 1);
-    fence_mbar_init();
-    mbar_expect_tx(bar, 2 * slab_bytes + xyz_bytes);
-    bulk_g2s(sX, X + int64_t(blk) * 4 * Np * kB, slab_bytes, bar);
-    bulk_g2s(sQ, Q + int64_t(blk) * 4 * Np * kB, slab_bytes, bar);
-    bulk_g2s(sG, M.w_xyz + int64_t(blk) * 12 * kB, xyz_bytes, bar);
-  }
-  __syncthreads();
-  if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0)) && lane == 0) atomicOr(failed, 1);
-  __syncthreads();
-  if (*reinterpret_cast<volatile int*>(failed)) {
-    // the copies never completed: report, let them drain, every warp leaves
-    if (threadIdx.x == 0) {
-      atomicOr(M.err, kErrTimeout);
-      mbar_wait_bounded(bar, 0);
-    }
-    return;
-  }
-  if (j == 0) wedge_geometry(sG, lane);
-  __syncthreads();
-#define GEO(item) sG[(item) * kB + lane]
-  const real kappa = M.w_mat[0 * Kp + e], irho = M.w_mat[1 * Kp + e], zM = M.w_mat[2 * Kp + e];
-  const real J0 = GEO(G_J0), J1 = GEO(G_J1), J2 = GEO(G_J2);
-
-  // element terms of slice j: mu[j] . M^tri (sum_j' M1[j][j'] r[j'])
-  real t1k = 0, t1r = 0;
-  {
-    real bt[4][Nt];
-#pragma unroll
-    for (int l = 0; l < Nt; ++l) bt[0][l] = bt[1][l] = bt[2][l] = bt[3][l] = real(0);
-#pragma unroll
-    for (int jp = 0; jp < Nq; ++jp) {
-      const real m1 = O.w.M1[j * Nq + jp];
-#pragma unroll
-      for (int l = 0; l < Nt; ++l) {
-        const Q4 v = ld4(R, widx<N>(blk, jp * Nt + l, lane));
-        bt[0][l] += m1 * v.p;
-        bt[1][l] += m1 * v.u;
-        bt[2][l] += m1 * v.v;
-        bt[3][l] += m1 * v.w;
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < Nt; ++i) {
-      real c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-#pragma unroll
-      for (int l = 0; l < Nt; ++l) {
-        const real mt = J0 * O.w.Ma[0][i * Nt + l] + J1 * O.w.Ma[1][i * Nt + l] + J2 * O.w.Ma[2][i * Nt + l];
-        c0 += mt * bt[0][l];
-        c1 += mt * bt[1][l];
-        c2 += mt * bt[2][l];
-        c3 += mt * bt[3][l];
-      }
-      const Q4 x = lds4(sX, j * Nt + i, lane);
-      t1k += x.p * c0;
-      t1r += x.u * c1 + x.v * c2 + x.w * c3;
-    }
-  }
-  t1k /= kappa * kappa;
-
-  // face terms: derivative of the upwind penalty in z
-  real gz = 0;
-  if (flux == 0) {
-    // a neighbour's node value: this block's slab or global memory
-    auto nbv = [&](const real* slab, const real* glob, int nbr, int node) {
-      return ((nbr >> 5) == blk) ? lds4(slab, node, nbr & 31) : ld4(glob, widx<N>(nbr >> 5, node, nbr & 31));
-    };
-    // triangle faces: warp 0 the bottom, warp N the top (face mass J_f M^tri)
-    if (j == 0 || j == N) {
-      const int fb = j == 0 ? 0 : 1;
-      const int nbr = M.w_nbr[fb * Kp + e], code = M.w_code[fb * Kp + e];
-      const real n0 = GEO(fb ? G_NT0 : G_NB0), n1 = GEO(fb ? G_NT1 : G_NB1), n2 = GEO(fb ? G_NT2 : G_NB2);
-      const real Jf = GEO(fb ? G_JFT : G_JFB);
-      const real zP = nbr < 0 ? zM : M.w_mat[2 * Kp + (nbr < 0 ? e : nbr)];
-      real a[Nt], b[Nt], c[Nt], d[Nt];  // [p], [mu_p], [u_n], [mu_un] (boundary: own values)
-#pragma unroll
-      for (int k = 0; k < Nt; ++k) {
-        const int own = (fb ? N * Nt : 0) + k;
-        const Q4 qo = lds4(sQ, own, lane), xo = lds4(sX, own, lane);
-        if (nbr < 0) {
-          a[k] = qo.p;
-          b[k] = xo.p;
-          c[k] = n0 * qo.u + n1 * qo.v + n2 * qo.w;
-          d[k] = n0 * xo.u + n1 * xo.v + n2 * xo.w;
-        } else {
-          const int nf = (code >> 4) & 3;
-          const int node = (nf ? N * Nt : 0) + O.tab.tri_perm[code & 15][k];
-          const Q4 qn = nbv(sQ, Q, nbr, node), xn = nbv(sX, X, nbr, node);
-          a[k] = qn.p - qo.p;
-          b[k] = xn.p - xo.p;
-          c[k] = n0 * (qn.u - qo.u) + n1 * (qn.v - qo.v) + n2 * (qn.w - qo.w);
-          d[k] = n0 * (xn.u - xo.u) + n1 * (xn.v - xo.v) + n2 * (xn.w - xo.w);
-        }
-      }
-      real Ip = 0, Iu = 0;
-#pragma unroll
-      for (int k = 0; k < Nt; ++k) {
-        real sp = 0, su = 0;
-#pragma unroll
-        for (int kk = 0; kk < Nt; ++kk) {
-          sp += O.w.M[k * Nt + kk] * b[kk];
-          su += O.w.M[k * Nt + kk] * d[kk];
-        }
-        Ip += a[k] * sp;
-        Iu += c[k] * su;
-      }
-      Ip *= Jf;
-      Iu *= Jf;
-      if (nbr >= 0) {
-        const real tp = real(2) / (zM + zP);
-        gz += real(0.25) * tp * tp * Ip + real(0.25) * Iu;
-      } else {
-        gz += bc == 0 ? Ip / (zM * zM) : Iu;
-      }
-    }
-    // quadrilateral faces (face mass M~_e (x) M^1D): this slice's jumps, the
-    // mu jumps of every slice through the shared table
-    real a[3][Nq], c[3][Nq];
-#pragma unroll
-    for (int ed = 0; ed < 3; ++ed) {
-      const int nbr = M.w_nbr[(2 + ed) * Kp + e], code = M.w_code[(2 + ed) * Kp + e];
-      const real nx = GEO(G_QNX0 + ed), ny = GEO(G_QNY0 + ed);
-      const int ep = nbr < 0 ? ed : code >> 1, rev = nbr < 0 ? 0 : code & 1;
-#pragma unroll
-      for (int m = 0; m < Nq; ++m) {
-        const int own = j * Nt + edge_node(N, ed, m);
-        const Q4 qo = lds4(sQ, own, lane), xo = lds4(sX, own, lane);
-        real bb, dd;
-        if (nbr < 0) {
-          a[ed][m] = qo.p;
-          c[ed][m] = nx * qo.u + ny * qo.v;
-          bb = xo.p;
-          dd = nx * xo.u + ny * xo.v;
-        } else {
-          const int node = j * Nt + O.tab.edge[ep][rev ? N - m : m];
-          const Q4 qn = nbv(sQ, Q, nbr, node), xn = nbv(sX, X, nbr, node);
-          a[ed][m] = qn.p - qo.p;
-          c[ed][m] = nx * (qn.u - qo.u) + ny * (qn.v - qo.v);
-          bb = xn.p - xo.p;
-          dd = nx * (xn.u - xo.u) + ny * (xn.v - xo.v);
-        }
-        sJ[(((ed * 2 + 0) * Nq + j) * Nq + m) * kB + lane] = bb;
-        sJ[(((ed * 2 + 1) * Nq + j) * Nq + m) * kB + lane] = dd;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ed = 0; ed < 3; ++ed) {
-      const int nbr = M.w_nbr[(2 + ed) * Kp + e];
-      const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
-      const real zP = nbr < 0 ? zM : M.w_mat[2 * Kp + (nbr < 0 ? e : nbr)];
-      // (M~_e (x) M^1D) applied as M^1D along the slices first, then M~_e along the edge
-      real bb[Nq], dd[Nq];
-#pragma unroll
-      for (int mp = 0; mp < Nq; ++mp) {
-        real sb = 0, sd = 0;
-#pragma unroll
-        for (int jp = 0; jp < Nq; ++jp) {
-          const real m1 = O.w.M1[j * Nq + jp];
-          sb += m1 * sJ[(((ed * 2 + 0) * Nq + jp) * Nq + mp) * kB + lane];
-          sd += m1 * sJ[(((ed * 2 + 1) * Nq + jp) * Nq + mp) * kB + lane];
-        }
-        bb[mp] = sb;
-        dd[mp] = sd;
-      }
-      real Ip = 0, Iu = 0;
-#pragma unroll
-      for (int m = 0; m < Nq; ++m) {
-        real sp = 0, su = 0;
-#pragma unroll
-        for (int mp = 0; mp < Nq; ++mp) {
-          const real w = ca * O.w.Mea[m * Nq + mp] + cbq * O.w.Meb[m * Nq + mp];
-          sp += w * bb[mp];
-          su += w * dd[mp];
-        }
-        Ip += a[ed][m] * sp;
-        Iu += c[ed][m] * su;
-      }
-      if (nbr >= 0) {
-        const real tp = real(2) / (zM + zP);
-        gz += real(0.25) * tp * tp * Ip + real(0.25) * Iu;
-      } else {
-        gz += bc == 0 ? Ip / (zM * zM) : Iu;
-      }
-    }
-  }
-  // reduce the slices in a fixed order
-  red[(j * 3 + 0) * kB + lane] = double(t1k);
-  red[(j * 3 + 1) * kB + lane] = double(t1r);
-  red[(j * 3 + 2) * kB + lane] = double(gz);
-  __syncthreads();
-  if (j == 0 && e < M.Kw) {
-    double sk = 0.0, sr = 0.0, sz = 0.0;
-    for (int jj = 0; jj < Nq; ++jj) {
-      sk += red[(jj * 3 + 0) * kB + lane];
-      sr += red[(jj * 3 + 1) * kB + lane];
-      sz += red[(jj * 3 + 2) * kB + lane];
-    }
-    const double rho = 1.0 / double(irho);
-    gk[e] += dt * (sk + sz * double(zM) / (2.0 * double(kappa)));
-    gr[e] += dt * (sr + sz * double(zM) / (2.0 * rho));
-  }
-#undef GEO
-}
 
 // ---------------------------------------------------------------------------
 // launchers

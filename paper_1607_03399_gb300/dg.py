@@ -31,7 +31,7 @@ EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
            "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_stage_times", "dg_autotune", "dg_add_receiver", "dg_sample", "dg_save_state",
            "dg_load_state", "dg_adjoint_bytes", "dg_adjoint_bind", "dg_adjoint_reset", "dg_adjoint_inject",
-           "dg_adjoint_step", "dg_adjoint_set", "dg_adjoint_get", "dg_adjoint_gradient", "dg_sync", "dg_time",
+           "dg_adjoint_step", "dg_step_record_bytes", "dg_step_record", "dg_adjoint_step_recorded", "dg_adjoint_set", "dg_adjoint_get", "dg_adjoint_gradient", "dg_sync", "dg_time",
            "dg_stable_dt", "dg_last_error", "dg_destroy")
 
 _lib = None
@@ -85,6 +85,9 @@ def lib():
         "dg_adjoint_reset": (c_int, [P]),
         "dg_adjoint_inject": (c_int, [P, P]),
         "dg_adjoint_step": (c_int, [P, c_double]),
+        "dg_step_record_bytes": (c_int, [P, POINTER(c_size_t)]),
+        "dg_step_record": (c_int, [P, c_double, P]),
+        "dg_adjoint_step_recorded": (c_int, [P, c_double, P]),
         "dg_adjoint_set": (c_int, [P, P, P, c_int]),
         "dg_adjoint_get": (c_int, [P, P, c_int]),
         "dg_adjoint_gradient": (c_int, [P, P, P]),
@@ -284,6 +287,20 @@ def dg_adjoint_step(ctx, dt: float):
     _check(ctx, lib().dg_adjoint_step(ctx, dt))
 
 
+def dg_step_record_bytes(ctx) -> int:
+    n = c_size_t()
+    _check(ctx, lib().dg_step_record_bytes(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def dg_step_record(ctx, dt: float, d_rec: int):
+    _check(ctx, lib().dg_step_record(ctx, dt, d_rec))
+
+
+def dg_adjoint_step_recorded(ctx, dt: float, d_rec: int):
+    _check(ctx, lib().dg_adjoint_step_recorded(ctx, dt, d_rec))
+
+
 def dg_adjoint_set(ctx, mu_q: int, x: int, on_device: int):
     _check(ctx, lib().dg_adjoint_set(ctx, mu_q, x, on_device))
 
@@ -470,6 +487,18 @@ class Solver:
 
     def adjoint_step(self, dt: float):
         dg_adjoint_step(self.ctx, dt)
+
+    def new_record(self):
+        """Device buffer for one step record (dg_step_record)."""
+        return self.torch.empty(dg_step_record_bytes(self.ctx), dtype=self.torch.uint8, device=self.device)
+
+    def step_record(self, dt: float, rec):
+        """One step that also writes its stage inputs and right-hand sides to rec."""
+        self._wait_torch()
+        dg_step_record(self.ctx, dt, rec.data_ptr())
+
+    def adjoint_step_recorded(self, dt: float, rec):
+        dg_adjoint_step_recorded(self.ctx, dt, rec.data_ptr())
 
     def adjoint_set(self, mu_q, x):
         """mu_q, x: numpy arrays of the field shape."""

@@ -183,6 +183,28 @@ def test_shots_arguments_and_sizes():
         dg.dg_destroy(ctx)
 
 
+def test_step_record_arguments_and_size():
+    """Stage records: ten packed fields; null or misaligned records, dt <= 0 and
+    unbound contexts or adjoints are refused before any device work."""
+    m = I.cube_wavy_mesh(2, 2, 0.0)
+    ctx = dg.dg_mesh_create(m.VX, m.EToV, m.etype)
+    try:
+        _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_step_record_bytes(ctx))
+        dg.dg_set_order(ctx, 3)
+        dg.dg_set_shots(ctx, 3)
+        _, fb = dg.dg_device_bytes(ctx)
+        assert dg.dg_step_record_bytes(ctx) == 10 * fb
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_step_record(ctx, 0.1, 0))
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_step_record(ctx, 0.1, 4096 + 16))
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_step_record(ctx, 0.0, 4096))
+        _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_step_record(ctx, 0.1, 4096))
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_adjoint_step_recorded(ctx, 0.1, 0))
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_adjoint_step_recorded(ctx, -1.0, 4096))
+        _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_adjoint_step_recorded(ctx, 0.1, 4096))
+    finally:
+        dg.dg_destroy(ctx)
+
+
 def test_merge_meshes_keeps_pieces_apart():
     a, b = I.cube_wavy_mesh(2, 2, 0.02), I.hybrid_mesh(2, 1, 1)
     m = I.merge_meshes([a, b])
