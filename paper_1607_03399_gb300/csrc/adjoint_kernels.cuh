@@ -65,41 +65,42 @@ __global__ void k_inject(const DevMesh<real> M, real* __restrict__ muq, real* __
 // rigid walls int mu_un u_n, Dirichlet walls int mu_p p / z^2; central fluxes
 // have no penalty.  M^k = M^{tri,k} (x) M^1D (Section 4.2); the face masses are
 // J_f M^tri (triangles) and M~_e (x) M^1D (quadrilaterals).  A CTA takes a
-// 32-wedge block, warp j slice j (slabs of x and q in shared memory); the
-// per-slice partial sums are reduced across warps in a fixed order and added,
-// times dt, in double.  Wedge neighbours only (the adjoint takes wedge meshes).
-// (the right-hand side is read from global memory, one slice per warp:
-// staging it as a third slab measured slower at N = 3, two CTAs per SM
-// instead of three)
-// Shared memory: x slab, q slab, geometry, face-jump table.  The copy barrier
-// and the failure flag live in the table's first 16 bytes and the cross-slice
-// reduction in the q slab (both free by then), which keeps FP32 N = 3 at four
-// CTAs per SM and FP64 N = 3 at two.
+// 32-wedge block with N+1 warps (slabs of x and q in shared memory): warp j
+// forms the element terms of slice j and the face terms of the faces it owns
+// (grad_tri_warp and quadrilateral face e on warp e mod (N+1)); the warps'
+// partial sums are reduced in a fixed order and added, times dt, in double.
+// Wedge neighbours only (the adjoint takes wedge meshes).  The right-hand
+// side is read from global memory, one slice per warp (staging it as a third
+// slab measured slower at N = 3: fewer CTAs per SM).
+// Shared memory: x slab, q slab, geometry, [warp][3][32] partial sums, the
+// copy barrier and the failure flag.
 template <int N>
 __host__ __device__ constexpr int grad_smem_bytes() {
   constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
-  static_assert(8 * 3 * Nq <= 4 * Np * 4, "reduction fits in the q slab");
-  return int(sizeof(real)) * (2 * 4 * Np * kB + G_COUNT * kB + 3 * 2 * Nq * Nq * kB);
+  return int(sizeof(real)) * (2 * 4 * Np * kB + G_COUNT * kB) + 8 * 3 * Nq * kB + 16;
+}
+
+// the warp that owns triangle face fb (0 bottom, 1 top) in the gradient
+// kernel: the warps left over after the three quadrilateral faces
+__host__ __device__ constexpr int grad_tri_warp(int N, int fb) {
+  return N >= 4 ? 3 + fb : (N == 3 ? 3 : (N == 2 ? fb : 1));
 }
 
 template <int N>
-__global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4 && N <= 3) ? 4 : 1) k_wedge_grad(const DevMesh<real> M, const real* __restrict__ X,
+__global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 4 : 2) : (N <= 3 ? 2 : 1))
+    k_wedge_grad(const DevMesh<real> M, const real* __restrict__ X,
                                                              const real* __restrict__ Q, const real* __restrict__ R,
                                                              double dt, int flux, int bc, double* __restrict__ gk,
                                                              double* __restrict__ gr) {
   constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
   const AllOps<N, real>& O = OPS<N>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   real* sX = reinterpret_cast<real*>(smem_raw);
   real* sQ = sX + 4 * Np * kB;
   real* sG = sQ + 4 * Np * kB;
-  real* sJ = sG + G_COUNT * kB;  // [face][mu_p jump, mu_un jump][slice][edge node][32]
-  // slab/coordinate copy barrier and failure flag: the jump table's first 16
-  // bytes (the barrier is invalidated and the flag read before the table is written)
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sJ);
-  int* failed = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(sJ) + 8);
-  // [slice][3][32] cross-slice sums: the q slab, read by no warp after the face terms
-  double* red = reinterpret_cast<double*>(sQ);
+  double* red = reinterpret_cast<double*>(sG + G_COUNT * kB);  // [warp][3][32]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + 3 * Nq * kB);  // slabs and coordinates
+  int* failed = reinterpret_cast<int*>(bar + 1);
   const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
   const int blk = blockIdx.x, e = blk * kB + lane;
   const int Kp = M.Kw_pad;
@@ -139,7 +140,6 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4 && N <= 3) ? 
     }
     return;
   }
-  if (threadIdx.x == 0) mbar_inval(bar);
   if (j == 0) wedge_geometry(sG, lane);
   __syncthreads();
 #define GEO(item) sG[(item) * kB + lane]
@@ -183,33 +183,121 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4 && N <= 3) ? 
   }
   t1k /= kappa * kappa;
 
-  // face terms: derivative of the upwind penalty in z
+  // face terms: derivative of the upwind penalty in z.  Each face is one
+  // warp's task (quadrilateral face e on warp e mod (N+1), the triangle faces
+  // on the last warps): the warp forms the jumps of the whole face and its
+  // face-mass integrals, with no exchange between warps.
   real gz = 0;
   if (flux == 0) {
     // a neighbour's node value, from global memory also when the neighbour is
     // in this block (a uniform load stream measured faster than choosing the
     // shared slab per lane)
     auto nbv = [&](const real* glob, int nbr, int node) { return ld4(glob, widx<N>(nbr >> 5, node, nbr & 31)); };
-    // triangle faces: warp 0 the bottom, warp N the top (face mass J_f M^tri)
-    if (j == 0 || j == N) {
-      const int fb = j == 0 ? 0 : 1;
+    auto penalty = [&](int nbr, real zP, real Ip, real Iu) {
+      if (nbr >= 0) {
+        const real tp = real(2) / (zM + zP);
+        return real(0.25) * tp * tp * Ip + real(0.25) * Iu;
+      }
+      return bc == 0 ? Ip / (zM * zM) : Iu;
+    };
+    // quadrilateral face ed (face mass M~_e (x) M^1D over slice jj, edge node m)
+#pragma unroll 1
+    for (int ed = j; ed < 3; ed += Nq) {
+      const int nbr = ed == 0 ? nbf[2] : (ed == 1 ? nbf[3] : nbf[4]);
+      const int code = ed == 0 ? cdf[2] : (ed == 1 ? cdf[3] : cdf[4]);
+      const real zP = ed == 0 ? zPf[2] : (ed == 1 ? zPf[3] : zPf[4]);
+      const real nx = GEO(G_QNX0 + ed), ny = GEO(G_QNY0 + ed);
+      const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
+      const int ep = nbr < 0 ? ed : code >> 1, rev = nbr < 0 ? 0 : code & 1;
+      real b[Nq][Nq], d[Nq][Nq];  // [mu_p], [mu_un] (boundary: own values)
+#pragma unroll
+      for (int jj = 0; jj < Nq; ++jj)
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          const Q4 xo = lds4(sX, jj * Nt + edge_node(N, ed, m), lane);
+          if (nbr < 0) {
+            b[jj][m] = xo.p;
+            d[jj][m] = nx * xo.u + ny * xo.v;
+          } else {
+            const Q4 xn = nbv(X, nbr, jj * Nt + O.tab.edge[ep][rev ? N - m : m]);
+            b[jj][m] = xn.p - xo.p;
+            d[jj][m] = nx * (xn.u - xo.u) + ny * (xn.v - xo.v);
+          }
+        }
+      // (M^1D (x) M~_e) [mu]: along the slices, then along the edge
+      real w[Nq][Nq];
+#pragma unroll
+      for (int m = 0; m < Nq; ++m)
+#pragma unroll
+        for (int mp = 0; mp < Nq; ++mp) w[m][mp] = ca * O.w.Mea[m * Nq + mp] + cbq * O.w.Meb[m * Nq + mp];
+      real Bb[Nq][Nq], Bd[Nq][Nq];
+#pragma unroll
+      for (int jj = 0; jj < Nq; ++jj) {
+        real tb[Nq], td[Nq];
+#pragma unroll
+        for (int mp = 0; mp < Nq; ++mp) {
+          real sb = 0, sd = 0;
+#pragma unroll
+          for (int jp = 0; jp < Nq; ++jp) {
+            sb += O.w.M1[jj * Nq + jp] * b[jp][mp];
+            sd += O.w.M1[jj * Nq + jp] * d[jp][mp];
+          }
+          tb[mp] = sb;
+          td[mp] = sd;
+        }
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          real sb = 0, sd = 0;
+#pragma unroll
+          for (int mp = 0; mp < Nq; ++mp) {
+            sb += w[m][mp] * tb[mp];
+            sd += w[m][mp] * td[mp];
+          }
+          Bb[jj][m] = sb;
+          Bd[jj][m] = sd;
+        }
+      }
+      // [q] against it, node by node
+      real Ip = 0, Iu = 0;
+#pragma unroll
+      for (int jj = 0; jj < Nq; ++jj)
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          const Q4 qo = lds4(sQ, jj * Nt + edge_node(N, ed, m), lane);
+          real a, c;  // [p], [u_n] (boundary: own values)
+          if (nbr < 0) {
+            a = qo.p;
+            c = nx * qo.u + ny * qo.v;
+          } else {
+            const Q4 qn = nbv(Q, nbr, jj * Nt + O.tab.edge[ep][rev ? N - m : m]);
+            a = qn.p - qo.p;
+            c = nx * (qn.u - qo.u) + ny * (qn.v - qo.v);
+          }
+          Ip += a * Bb[jj][m];
+          Iu += c * Bd[jj][m];
+        }
+      gz += penalty(nbr, zP, Ip, Iu);
+    }
+    // triangle face fb (bottom, top; face mass J_f M^tri)
+#pragma unroll 1
+    for (int fb = 0; fb < 2; ++fb) {
+      if (j != grad_tri_warp(N, fb)) continue;
       const int nbr = fb ? nbf[1] : nbf[0], code = fb ? cdf[1] : cdf[0];
       const real n0 = GEO(fb ? G_NT0 : G_NB0), n1 = GEO(fb ? G_NT1 : G_NB1), n2 = GEO(fb ? G_NT2 : G_NB2);
       const real Jf = GEO(fb ? G_JFT : G_JFB);
       const real zP = fb ? zPf[1] : zPf[0];
+      const int own0 = fb ? N * Nt : 0, nb0 = ((code >> 4) & 3) ? N * Nt : 0;
       real a[Nt], b[Nt], c[Nt], d[Nt];  // [p], [mu_p], [u_n], [mu_un] (boundary: own values)
 #pragma unroll
       for (int k = 0; k < Nt; ++k) {
-        const int own = (fb ? N * Nt : 0) + k;
-        const Q4 qo = lds4(sQ, own, lane), xo = lds4(sX, own, lane);
+        const Q4 qo = lds4(sQ, own0 + k, lane), xo = lds4(sX, own0 + k, lane);
         if (nbr < 0) {
           a[k] = qo.p;
           b[k] = xo.p;
           c[k] = n0 * qo.u + n1 * qo.v + n2 * qo.w;
           d[k] = n0 * xo.u + n1 * xo.v + n2 * xo.w;
         } else {
-          const int nf = (code >> 4) & 3;
-          const int node = (nf ? N * Nt : 0) + O.tab.tri_perm[code & 15][k];
+          const int node = nb0 + O.tab.tri_perm[code & 15][k];
           const Q4 qn = nbv(Q, nbr, node), xn = nbv(X, nbr, node);
           a[k] = qn.p - qo.p;
           b[k] = xn.p - xo.p;
@@ -229,87 +317,10 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4 && N <= 3) ? 
         Ip += a[k] * sp;
         Iu += c[k] * su;
       }
-      Ip *= Jf;
-      Iu *= Jf;
-      if (nbr >= 0) {
-        const real tp = real(2) / (zM + zP);
-        gz += real(0.25) * tp * tp * Ip + real(0.25) * Iu;
-      } else {
-        gz += bc == 0 ? Ip / (zM * zM) : Iu;
-      }
-    }
-    // quadrilateral faces (face mass M~_e (x) M^1D): this slice's jumps, the
-    // mu jumps of every slice through the shared table
-    real a[3][Nq], c[3][Nq];
-#pragma unroll
-    for (int ed = 0; ed < 3; ++ed) {
-      const int nbr = nbf[2 + ed], code = cdf[2 + ed];
-      const real nx = GEO(G_QNX0 + ed), ny = GEO(G_QNY0 + ed);
-      const int ep = nbr < 0 ? ed : code >> 1, rev = nbr < 0 ? 0 : code & 1;
-#pragma unroll
-      for (int m = 0; m < Nq; ++m) {
-        const int own = j * Nt + edge_node(N, ed, m);
-        const Q4 qo = lds4(sQ, own, lane), xo = lds4(sX, own, lane);
-        real bb, dd;
-        if (nbr < 0) {
-          a[ed][m] = qo.p;
-          c[ed][m] = nx * qo.u + ny * qo.v;
-          bb = xo.p;
-          dd = nx * xo.u + ny * xo.v;
-        } else {
-          const int node = j * Nt + O.tab.edge[ep][rev ? N - m : m];
-          const Q4 qn = nbv(Q, nbr, node), xn = nbv(X, nbr, node);
-          a[ed][m] = qn.p - qo.p;
-          c[ed][m] = nx * (qn.u - qo.u) + ny * (qn.v - qo.v);
-          bb = xn.p - xo.p;
-          dd = nx * (xn.u - xo.u) + ny * (xn.v - xo.v);
-        }
-        sJ[(((ed * 2 + 0) * Nq + j) * Nq + m) * kB + lane] = bb;
-        sJ[(((ed * 2 + 1) * Nq + j) * Nq + m) * kB + lane] = dd;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ed = 0; ed < 3; ++ed) {
-      const int nbr = nbf[2 + ed];
-      const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
-      const real zP = zPf[2 + ed];
-      // (M~_e (x) M^1D) applied as M^1D along the slices first, then M~_e along the edge
-      real bb[Nq], dd[Nq];
-#pragma unroll
-      for (int mp = 0; mp < Nq; ++mp) {
-        real sb = 0, sd = 0;
-#pragma unroll
-        for (int jp = 0; jp < Nq; ++jp) {
-          const real m1 = O.w.M1[j * Nq + jp];
-          sb += m1 * sJ[(((ed * 2 + 0) * Nq + jp) * Nq + mp) * kB + lane];
-          sd += m1 * sJ[(((ed * 2 + 1) * Nq + jp) * Nq + mp) * kB + lane];
-        }
-        bb[mp] = sb;
-        dd[mp] = sd;
-      }
-      real Ip = 0, Iu = 0;
-#pragma unroll
-      for (int m = 0; m < Nq; ++m) {
-        real sp = 0, su = 0;
-#pragma unroll
-        for (int mp = 0; mp < Nq; ++mp) {
-          const real w = ca * O.w.Mea[m * Nq + mp] + cbq * O.w.Meb[m * Nq + mp];
-          sp += w * bb[mp];
-          su += w * dd[mp];
-        }
-        Ip += a[ed][m] * sp;
-        Iu += c[ed][m] * su;
-      }
-      if (nbr >= 0) {
-        const real tp = real(2) / (zM + zP);
-        gz += real(0.25) * tp * tp * Ip + real(0.25) * Iu;
-      } else {
-        gz += bc == 0 ? Ip / (zM * zM) : Iu;
-      }
+      gz += penalty(nbr, zP, Ip * Jf, Iu * Jf);
     }
   }
-  // reduce the slices in a fixed order
+  // reduce the warps' partial sums in a fixed order
   red[(j * 3 + 0) * kB + lane] = double(t1k);
   red[(j * 3 + 1) * kB + lane] = double(t1r);
   red[(j * 3 + 2) * kB + lane] = double(gz);
