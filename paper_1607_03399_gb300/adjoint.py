@@ -11,8 +11,9 @@ accumulates dJ/dkappa, dJ/drho.  With `stage_records` the segment re-run
 instead stores every step's stage inputs and right-hand sides (ten fields per
 step, dg_step_record) and the reverse steps read them back
 (dg_adjoint_step_recorded): one forward pass less per step for
-checkpoint_every x 10 fields of device memory; the gradient is the same bit
-for bit.  The chain rule to (c^2, rho) uses kappa = rho c^2.
+checkpoint_every x 10 fields of device memory; the forward pass records the
+last segment itself, so that segment is not re-run.  The gradient is the same
+bit for bit.  The chain rule to (c^2, rho) uses kappa = rho c^2.
 """
 from __future__ import annotations
 
@@ -49,20 +50,37 @@ class Problem:
                       receivers=self.receivers)
 
 
+@dataclass
+class Checkpoints:
+    """What the forward pass keeps for the reverse pass: the state and the
+    solver's own time at every checkpoint step (accumulated step by step, so a
+    re-run from a checkpoint evaluates the sources at exactly the forward
+    pass's stage times) and, with stage records, the records of the last
+    segment (steps records_from .. nsteps - 1), which the reverse pass then
+    does not re-run."""
+    states: dict
+    records: list | None = None
+    records_from: int = -1
+
+
 def forward(S: Solver, pb: Problem, q0=None):
-    """Traces [nsteps][shots][receivers] (device tensor) and the checkpoints
-    {step: (state, time)}; the time is the solver's own (accumulated step by
-    step), so a re-run from a checkpoint evaluates the sources at exactly the
-    forward pass's stage times."""
+    """Traces [nsteps][shots][receivers] (device tensor) and the Checkpoints."""
     torch = S.torch
     S.set_fields(np.zeros(S.field_shape, dtype=S.np_dtype) if q0 is None else q0)
     traces = torch.empty((pb.nsteps, pb.shots, S.nrec), dtype=S.dtype, device=S.device)
-    ck = {0: (S.save_state(), S.time())}
+    C = pb.checkpoint_every
+    ck = Checkpoints({0: (S.save_state(), S.time())})
+    if pb.stage_records and pb.nsteps > 0:
+        ck.records_from = ((pb.nsteps - 1) // C) * C
+        ck.records = [S.new_record() for _ in range(pb.nsteps - ck.records_from)]
     for n in range(1, pb.nsteps + 1):
-        S.step(pb.dt, 1)
+        if ck.records is not None and n - 1 >= ck.records_from:
+            S.step_record(pb.dt, ck.records[n - 1 - ck.records_from])
+        else:
+            S.step(pb.dt, 1)
         S.sample(traces[n - 1])
-        if n % pb.checkpoint_every == 0 and n < pb.nsteps:
-            ck[n] = (S.save_state(), S.time())
+        if n % C == 0 and n < pb.nsteps:
+            ck.states[n] = (S.save_state(), S.time())
     S.sync()
     return traces, ck
 
@@ -83,13 +101,17 @@ def reverse(S: Solver, pb: Problem, traces, data, ck):
     C = pb.checkpoint_every
     starts = list(range(0, pb.nsteps, C))
     if pb.stage_records:
-        recs = [S.new_record() for _ in range(min(C, pb.nsteps))]
+        recs = ck.records
+        if recs is None or len(recs) < min(C, pb.nsteps):
+            recs = (recs or []) + [S.new_record() for _ in range(min(C, pb.nsteps) - len(recs or []))]
         for s0 in reversed(starts):
             s1 = min(s0 + C, pb.nsteps)
-            # records of the steps q_n -> q_{n+1}, n = s0 .. s1 - 1
-            S.load_state(*ck[s0])
-            for n in range(s0, s1):
-                S.step_record(pb.dt, recs[n - s0])
+            # records of the steps q_n -> q_{n+1}, n = s0 .. s1 - 1 (the last
+            # segment's come from the forward pass)
+            if not (s0 == ck.records_from and ck.records is not None):
+                S.load_state(*ck.states[s0])
+                for n in range(s0, s1):
+                    S.step_record(pb.dt, recs[n - s0])
             for n in range(s1, s0, -1):
                 S.adjoint_inject(resid[n - 1])
                 S.adjoint_step_recorded(pb.dt, recs[n - 1 - s0])
@@ -98,8 +120,8 @@ def reverse(S: Solver, pb: Problem, traces, data, ck):
     for s0 in reversed(starts):
         s1 = min(s0 + C, pb.nsteps)
         # states q_{s0} .. q_{s1 - 1} of the segment
-        S.load_state(*ck[s0])
-        states = [ck[s0]]
+        S.load_state(*ck.states[s0])
+        states = [ck.states[s0]]
         for n in range(s0 + 1, s1):
             S.step(pb.dt, 1)
             states.append((S.save_state(), S.time()))
