@@ -189,8 +189,12 @@ int dg_bind(dg_ctx* ctx, void* d_mesh, void* d_q0, void* d_q1, void* d_res, void
 
 /* Set / read the state in the canonical layout ([4][total_nodes] of float or
  * double per precision).  on_device != 0: a device pointer, else host.  Host
- * transfers synchronise the stream; device ones are asynchronous.
- * dg_set_fields resets the simulation time to 0 and the residual to 0. */
+ * transfers synchronise the stream; device ones are asynchronous.  A host
+ * buffer in pinned, device-mapped memory (cudaHostAlloc / cudaHostRegister, as
+ * cudaPointerGetAttributes reports it) is read or written by the layout kernel
+ * directly over the CPU-GPU link; pageable memory goes through a bulk copy and
+ * the state buffer not in use.  Either way the buffer must hold the whole
+ * state.  dg_set_fields resets the simulation time to 0 and the residual to 0. */
 int dg_set_fields(dg_ctx* ctx, const void* q, int on_device);
 int dg_get_fields(dg_ctx* ctx, void* q, int on_device);
 

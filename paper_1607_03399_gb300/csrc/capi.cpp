@@ -1288,6 +1288,21 @@ int dg_bind(dg_ctx* c, void* d_mesh, void* d_q0, void* d_q1, void* d_res, void* 
   return DG_OK;
 }
 
+namespace {
+// The device address of a pinned, device-mapped host buffer, or nullptr for
+// pageable memory.  With such a buffer the pack kernel reads or writes the
+// host memory itself (over the CPU-GPU link) instead of a bulk copy plus a
+// device-side pass.
+const void* mapped_host_alias(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr) ? at.devicePointer : nullptr;
+}
+}  // namespace
+
 int dg_set_fields(dg_ctx* c, const void* q, int on_device) {
   if (!c) return DG_ERR_ARG;
   if (!q) return c->fail(DG_ERR_ARG, "null or invalid argument");
@@ -1298,10 +1313,13 @@ int dg_set_fields(dg_ctx* c, const void* q, int on_device) {
   const size_t bytes = size_t(4) * c->shots * (c->wedge_nodes + c->tet_nodes) * rs;
   const void* src = q;
   if (!on_device) {
-    cudaError_t e = cudaMemcpyAsync(c->d_q[1 - c->cur], q, bytes, cudaMemcpyHostToDevice, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "state upload");
-    src = c->d_q[1 - c->cur];
-    // pack reads the scratch copy into the current buffer
+    src = mapped_host_alias(q);
+    if (!src) {
+      // pageable memory: pack reads a scratch copy into the current buffer
+      cudaError_t e = cudaMemcpyAsync(c->d_q[1 - c->cur], q, bytes, cudaMemcpyHostToDevice, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "state upload");
+      src = c->d_q[1 - c->cur];
+    }
   }
   rc = launch_pack(c, src, c->d_q[c->cur], false, c->stream);
   if (rc) return rc;
@@ -1321,13 +1339,16 @@ int dg_get_fields(dg_ctx* c, void* q, int on_device) {
   if (!c) return DG_ERR_ARG;
   if (!q) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_get_fields before dg_bind");
+  int rc = ensure_ops(c);  // also opts the pack kernel in to its shared memory
+  if (rc) return rc;
   const size_t rs = c->prec == DG_F64 ? 8 : 4;
   const size_t bytes = size_t(4) * c->shots * (c->wedge_nodes + c->tet_nodes) * rs;
-  void* dst = on_device ? q : c->d_q[1 - c->cur];
-  int rc = launch_pack(c, dst, c->d_q[c->cur], true, c->stream);
+  void* mapped = on_device ? nullptr : const_cast<void*>(mapped_host_alias(q));
+  void* dst = on_device ? q : (mapped ? mapped : c->d_q[1 - c->cur]);
+  rc = launch_pack(c, dst, c->d_q[c->cur], true, c->stream);
   if (rc) return rc;
   if (!on_device) {
-    cudaError_t e = cudaMemcpyAsync(q, dst, bytes, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = mapped ? cudaSuccess : cudaMemcpyAsync(q, dst, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "state download");
   }

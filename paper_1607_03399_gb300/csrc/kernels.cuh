@@ -1002,29 +1002,71 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
 // ---------------------------------------------------------------------------
 // canonical <-> packed layout
 // ---------------------------------------------------------------------------
+// Canonical [shot][field][node] <-> packed [block][node][lane][field] layout.
+// One CTA per 32-element block at a time: the block's values pass through a
+// [field][node][lane] shared tile (lane pitch 33, so neither phase has bank
+// conflicts), the canonical side is read or written one element's contiguous
+// node run at a time and the packed side in 16-byte [node][lane] records.
+// Padding lanes (e >= K) are neither read nor written.
 template <int N>
-__global__ void k_pack(const DevMesh<real> M, const real* __restrict__ canon, real* __restrict__ packed, bool unpack) {
+__host__ __device__ constexpr int pack_smem_bytes() {
+  return 4 * npw_of(N) * 33 * int(sizeof(real));
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_pack(const DevMesh<real> M, const real* __restrict__ canon,
+                                              real* __restrict__ packed, bool unpack) {
   constexpr int Npw = npw_of(N), Npt = npt_of(N);
-  const int64_t nw = int64_t(M.Kw) * Npw, nt = int64_t(M.Kt) * Npt;
-  for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < nw + nt; idx += int64_t(gridDim.x) * blockDim.x) {
-    int64_t c, pbase;
-    if (idx < nw) {
-      const int e = int(idx / Npw), n = int(idx % Npw);
-      c = M.w_canon[e] + n;
-      pbase = widx<N>(e >> 5, n, e & 31);
-    } else {
-      const int64_t t = idx - nw;
-      const int e = int(t / Npt), n = int(t % Npt);
-      c = M.t_canon[e] + n;
-      pbase = tidx<N>(M.tet_off, e >> 5, n, e & 31);
-    }
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  real* tile = reinterpret_cast<real*>(smem_raw);  // [4][Np][33]
+  real* cw = const_cast<real*>(canon);
+  const int64_t T = M.total_nodes;
+  for (int b = blockIdx.x; b < M.nblk_w + M.nblk_t; b += gridDim.x) {
+    const bool tet = b >= M.nblk_w;
+    const int blk = tet ? b - M.nblk_w : b;
+    const int Np = tet ? Npt : Npw, K = tet ? M.Kt : M.Kw;
+    const int64_t* cmap = tet ? M.t_canon : M.w_canon;
+    real* pk = packed + (tet ? tidx<N>(M.tet_off, blk, 0, 0) : widx<N>(blk, 0, 0));
+    const int items = Np * kB;
+    if (!unpack) {
+      for (int t = threadIdx.x; t < items; t += blockDim.x) {
+        const int l = t / Np, n = t - l * Np, e = blk * kB + l;
+        if (e < K) {
+          const int64_t c = cmap[e] + n;
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      if (unpack)
-        const_cast<real*>(canon)[f * M.total_nodes + c] = packed[pbase + f];
-      else
-        packed[pbase + f] = canon[f * M.total_nodes + c];
+          for (int f = 0; f < 4; ++f) tile[(f * Np + n) * 33 + l] = canon[f * T + c];
+        }
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < items; t += blockDim.x) {
+        const int l = t & 31, n = t >> 5;
+        if (blk * kB + l < K)
+          st4(pk, int64_t(t) * 4,
+              Q4{tile[(0 * Np + n) * 33 + l], tile[(1 * Np + n) * 33 + l], tile[(2 * Np + n) * 33 + l],
+                 tile[(3 * Np + n) * 33 + l]});
+      }
+    } else {
+      for (int t = threadIdx.x; t < items; t += blockDim.x) {
+        const int l = t & 31, n = t >> 5;
+        if (blk * kB + l < K) {
+          const Q4 v = ld4(pk, int64_t(t) * 4);
+          tile[(0 * Np + n) * 33 + l] = v.p;
+          tile[(1 * Np + n) * 33 + l] = v.u;
+          tile[(2 * Np + n) * 33 + l] = v.v;
+          tile[(3 * Np + n) * 33 + l] = v.w;
+        }
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < items; t += blockDim.x) {
+        const int l = t / Np, n = t - l * Np, e = blk * kB + l;
+        if (e < K) {
+          const int64_t c = cmap[e] + n;
+#pragma unroll
+          for (int f = 0; f < 4; ++f) cw[f * T + c] = tile[(f * Np + n) * 33 + l];
+        }
+      }
     }
+    __syncthreads();  // the tile is reused by the next block
   }
 }
 
@@ -1154,6 +1196,8 @@ int prepare_n() {
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_tet_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, tet_smem_bytes<N>());
   if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_pack<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, pack_smem_bytes<N>());
+  if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_wedge_grad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, grad_smem_bytes<N>());
   return int(err);
 }
@@ -1180,11 +1224,10 @@ int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s) {
 
 template <int N>
 int launch_pack_n(const DevMesh<real>& m, const real* canon, real* packed, bool unpack, cudaStream_t s) {
-  const int64_t total = int64_t(m.Kw) * npw_of(N) + int64_t(m.Kt) * npt_of(N);
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  int blocks = m.nblk_w + m.nblk_t;
+  if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
-  k_pack<N><<<int(blocks), 256, 0, s>>>(m, canon, packed, unpack);
+  k_pack<N><<<blocks, 256, pack_smem_bytes<N>(), s>>>(m, canon, packed, unpack);
   return int(cudaGetLastError());
 }
 
