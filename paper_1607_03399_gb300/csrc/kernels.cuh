@@ -428,6 +428,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_init(&bar[2], 1);
+    mbar_init(&bar[3], 1);
     fence_mbar_init();
     // the block's vertex coordinates first (the geometry warp waits on them alone)
     mbar_expect_tx(&bar[2], xyz_bytes);
@@ -766,11 +767,18 @@ template <int N>
 __host__ __device__ constexpr int tet_ops_reals() {
   return 4 * npt_of(N) * npt_of(N) + 4 * (4 * nt_of(N)) * tet_chunk_pad<N>();
 }
-// 128-byte header (3 mbarriers), operators, slab [Np][32][4], fluxes
-// [4 faces][2][Nt][32], vertex coordinates [12][32]
+// The residual slab is bulk-copied too where it costs no CTA per SM (FP32,
+// N <= 3); elsewhere the update reads it from global memory.
+template <int N>
+__host__ __device__ constexpr bool tet_stage_res() {
+  return sizeof(real) == 4 && N <= 3;
+}
+// 128-byte header (4 mbarriers), operators, slab [Np][32][4], fluxes
+// [4 faces][2][Nt][32], vertex coordinates [12][32], residual slab [Np][32][4]
 template <int N>
 __host__ __device__ constexpr int tet_smem_reals() {
-  return tet_ops_reals<N>() + 4 * npt_of(N) * kB + 8 * nt_of(N) * kB + 12 * kB;
+  return tet_ops_reals<N>() + 4 * npt_of(N) * kB + 8 * nt_of(N) * kB + 12 * kB +
+         (tet_stage_res<N>() ? 4 * npt_of(N) * kB : 0);
 }
 template <int N>
 __host__ __device__ constexpr int tet_smem_bytes() {
@@ -783,12 +791,14 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
   constexpr int Np = npt_of(N), Nt = nt_of(N), C = tet_chunk<N>(), CP = tet_chunk_pad<N>();
   const AllOps<N, real>& O = OPS<N>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // [0] operators, [1] coordinates, [2] state slab
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // [0] operators, [1] coordinates, [2] state, [3] residual
   real* sOp = reinterpret_cast<real*>(smem_raw + 128);
   real* sL = sOp + 4 * Np * Np;  // lift [warp][4 Nt][CP]
   real* sq = sOp + tet_ops_reals<N>();
   real* sF = sq + 4 * Np * kB;
   real* sX = sF + 8 * Nt * kB;
+  real* sr = sX + 12 * kB;  // residual slab (tet_stage_res)
+  constexpr bool stage_res = tet_stage_res<N>();
   const DevMesh<real>& M = A.m;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -801,6 +811,7 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_init(&bar[2], 1);
+    mbar_init(&bar[3], 1);
     fence_mbar_init();
     mbar_expect_tx(&bar[1], xyz_bytes);
     bulk_g2s(sX, M.t_xyz + int64_t(blk) * 12 * kB, xyz_bytes, &bar[1]);
@@ -808,6 +819,10 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
     bulk_g2s(sq, A.q_in + M.tet_off + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[2]);
     mbar_expect_tx(&bar[0], ops_bytes);
     bulk_g2s(sOp, M.t_ops, ops_bytes, &bar[0]);
+    if (stage_res && rk) {
+      mbar_expect_tx(&bar[3], slab_bytes);
+      bulk_g2s(sr, A.res + M.tet_off + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[3]);
+    }
   }
   // face neighbours, impedances, material and the source flag while the copies fly
   const real kappa = M.t_mat[0 * Kp + e], irho = M.t_mat[1 * Kp + e], zM = M.t_mat[2 * Kp + e];
@@ -868,6 +883,7 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
       mbar_wait_bounded(&bar[0], 0);
       mbar_wait_bounded(&bar[1], 0);
       mbar_wait_bounded(&bar[2], 0);
+      if (stage_res && rk) mbar_wait_bounded(&bar[3], 0);
     }
     return;
   }
@@ -974,6 +990,14 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
     }
   }
   if (src) add_sources(M, 4, e, I0, Np, *M.clock + A.c_stage * double(A.dt), ap);
+  if (stage_res && rk && !__all_sync(0xffffffffu, mbar_wait_bounded(&bar[3], 0))) {
+    // the residual slab never arrived: report, let the copy drain, leave
+    if (lane == 0) {
+      atomicOr(M.err, kErrTimeout);
+      mbar_wait_bounded(&bar[3], 0);
+    }
+    return;
+  }
   if (e < M.Kt) {
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -982,7 +1006,7 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
         const int64_t gi = tidx<N>(M.tet_off, blk, i, lane);
         const Q4 r{kappa * ap[c], irho * au[0][c], irho * au[1][c], irho * au[2][c]};
         if (rk) {
-          const Q4 r0 = ld4(A.res, gi);
+          const Q4 r0 = stage_res ? lds4(sr, i, lane) : ld4(A.res, gi);
           const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
                       A.rk_a * r0.w + A.dt * r.w};
           const Q4 q0 = lds4(sq, i, lane);
