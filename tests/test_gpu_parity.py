@@ -4,7 +4,8 @@ Tolerances (relative L2 over all fields and nodes): FP64 1e-12; FP32 1e-5 per
 right-hand side and 1e-4 after 1000 LSRK45 steps.  Meshes span several
 32-element blocks with ragged tails, wedge-only, tet-only and hybrid cases,
 both boundary conditions and both fluxes; the throughput workload (524288
-wedges, N = 3 and 4) is checked on sampled elements against oracle patches."""
+wedges, N = 3 and 4) and the hybrid workload (221184 wedges + 221184 tets)
+are checked on sampled elements against oracle patches."""
 import numpy as np
 import pytest
 
@@ -264,3 +265,67 @@ def test_autotune_keeps_the_operator():
     S.step(dt, 3)
     assert _rel(S.get_fields(), O.step(q.astype(np.float64), dt, 3)) <= 1e-5
     S.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f32", 1e-4)])
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_hybrid_steps(precision, tol, N):
+    """Hybrid mesh (wedge layers under a tet layer, ragged blocks of both
+    types), 20 LSRK45 steps of a Gaussian pulse: both stage kernels'
+    Runge-Kutta updates against the oracle (the tet residual comes through
+    shared memory in FP32 at N <= 3, from global memory otherwise)."""
+    m = MESHES["hybrid"]()
+    S, O = _pair(m, N, precision, seed=9)
+    q0 = I.gaussian_pulse(O.conn.xyz, (0.45, 0.5, 0.6), 0.2)
+    dt = O.stable_dt(0.4)
+    S.set_fields(q0)
+    S.step(dt, 20)
+    q = S.get_fields()
+    S.close()
+    ref = O.step(q0, dt, 20)
+    assert _rel(q, ref) <= tol
+
+
+def test_full_size_hybrid_sampled():
+    """The hybrid workload as the benchmark runs it (2x96x96 footprint, 12 bumpy
+    wedge layers under 4 flat layers of prisms split into 3 tets, N = 3, FP32):
+    sampled wedges and tets, including both sides of the wedge/tet interface,
+    of one right-hand side and one LSRK45 step against oracle patches."""
+    m = I.hybrid_mesh(96, 12, 4)
+    c2, rho = I.random_material(m.K, 3, 1.0, 3.0)
+    N = 3
+    S = Solver(m.VX, m.EToV, m.etype, N, c2, rho, precision="f32")
+    npe = np.where(m.etype == 6, (N + 1) ** 2 * (N + 2) // 2, (N + 1) * (N + 2) * (N + 3) // 6)
+    off = np.concatenate([[0], np.cumsum(npe)])
+    rng = np.random.default_rng(7)
+    q = rng.uniform(-1, 1, size=(4, S.total_nodes)).astype(np.float32)
+    nbr = face_adjacency(m.EToV, m.etype)
+    tets = np.nonzero(m.etype == 4)[0]
+    wedges = np.nonzero(m.etype == 6)[0]
+    iface = tets[np.any((nbr[tets] >= 0) & (m.etype[np.maximum(nbr[tets], 0)] == 6), axis=1)]
+    seeds = np.unique(np.concatenate([[0, m.K - 1, tets[0], tets[-1]], rng.choice(tets, 3), rng.choice(wedges, 2),
+                                      rng.choice(iface, 3)]))
+    r_gpu = S.rhs(q).cpu().numpy()
+    dt = S.stable_dt(0.5)
+    S.set_fields(q)
+    S.step(dt, 1)
+    q1_gpu = S.get_fields()
+    S.close()
+    for radius, what in ((1, "rhs"), (5, "step")):
+        for s in seeds:
+            elems = patch(nbr, [s], radius)
+            VXs, Es, ts = submesh(m.VX, m.EToV, m.etype, elems)
+            O = Oracle(VXs, Es, ts, N, c2[elems], rho[elems])
+            gid = node_index(npe, elems)
+            qs = q[:, gid].astype(np.float64)
+            loc = int(np.searchsorted(elems, s))
+            lo = int(npe[elems[:loc]].sum())
+            sl = slice(lo, lo + int(npe[s]))
+            glob = slice(int(off[s]), int(off[s + 1]))
+            if what == "rhs":
+                ref = O.rhs(qs)[:, sl]
+                got = r_gpu[:, glob]
+            else:
+                ref = O.step(qs, dt, 1)[:, sl]
+                got = q1_gpu[:, glob]
+            assert _rel(got, ref) <= 1e-5, (what, int(s), int(m.etype[s]))
