@@ -751,8 +751,9 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
 // the tet operators ([l][i] (D_r, D_s, D_t)(i, l) records and the lift, laid
 // out per warp chunk), the block's vertex coordinates and its state slab into
 // shared memory.  Every warp evaluates the affine geometry of the 32 tets;
-// warp f forms the fluxes of face f into a shared table; after one barrier
-// warp w produces output nodes [w C, w C + C) (volume terms, lift, update).
+// warp f forms the fluxes of face f into a shared table; warp w then forms
+// the volume terms of output nodes [w C, w C + C) and, after one barrier,
+// their lift and update.
 // All warps run the same code.
 // ---------------------------------------------------------------------------
 template <int N>
@@ -929,9 +930,10 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
     }
   }
   if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar[0], 0)) && lane == 0) atomicOr(M.err, kErrTimeout);
-  __syncthreads();
 
-  // output nodes [I0, I0 + C) of this warp: volume terms, lift, update
+  // output nodes [I0, I0 + C) of this warp: volume terms (the slab and the
+  // operators only), then, once every warp's face fluxes are in the table,
+  // the lift and the update
   const int I0 = w * C;
   real ap[C], au[3][C];
   {
@@ -959,6 +961,7 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
 #pragma unroll
       for (int d = 0; d < 3; ++d) au[d][c] = -(Ri[0][d] * dr[c] + Ri[1][d] * ds[c] + Ri[2][d] * dt[c]);
   }
+  __syncthreads();
   {
     const real* lw = sL + w * (4 * Nt) * CP;  // this warp's lift records [4 Nt][CP]
 #pragma unroll
