@@ -203,7 +203,10 @@ print(json.dumps({{"dof": 4 * S.conn.total_nodes, "K": S.K, "sec": el}}))
     print(json.dumps(line), flush=True)
 
 
-def measure_order(N, args, torch, dev, m, c2, rho, mass):
+def measure_order(N, args, torch, dev, m, c2, rho, mass, barrier=None):
+    """Time args.steps LSRK45 steps after args.warmup untimed ones with CUDA
+    events on the solver's stream, bracketed by a device synchronisation and
+    (several ranks) a barrier on both sides."""
     from paper_1607_03399_gb300.dg import Solver
     S = Solver(m.VX, m.EToV, m.etype, N, c2, rho, precision="f32", device=str(dev),
                sources=[(0.5, 0.5, 0.5, 10.0, 0.1, 1.0)], mass=mass)
@@ -215,10 +218,15 @@ def measure_order(N, args, torch, dev, m, c2, rho, mass):
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(dev.index or 0) as clk:
         torch.cuda.synchronize(dev)
+        if barrier:
+            barrier()
         start.record(S.stream)
         S.step(dt, args.steps)
         end.record(S.stream)
         end.synchronize()
+        torch.cuda.synchronize(dev)
+        if barrier:
+            barrier()
     S.sync()
     ms = start.elapsed_time(end)
     dof = 4 * S.total_nodes
@@ -434,6 +442,24 @@ def measure_adjoint(args, torch, dev):
                               "same_gradient": bool(J2 == J and np.array_equal(gk, gk2) and np.array_equal(gr, gr2))}}
 
 
+def _max_over_ranks(x, dist, dev):
+    """The largest of the ranks' values of x (the slowest rank times the job);
+    x itself with one process.  Works with the gloo and the NCCL backends."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _gdofs(dof, stages, seconds, world):
+    """Whole-job GDOF-updates/s: every rank advances its own replica of `dof`
+    field DOF through `stages` Runge-Kutta stages in `seconds` (the slowest
+    rank's time)."""
+    return dof * stages / seconds / 1e9 * world
+
+
 def run_ours(args, rank, world):
     import torch
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -446,16 +472,10 @@ def run_ours(args, rank, world):
     m, c2, rho = _mesh(ntri, nlay)
     orders = [int(x) for x in args.orders.split(",")]
     out = {}
+    barrier = dist.barrier if world > 1 else None
     for N in orders:
-        if world > 1:
-            dist.barrier()
-        r = measure_order(N, args, torch, dev, m, c2, rho, args.mass)
-        ms = r["ms"]
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        r["ms_max"] = ms
+        r = measure_order(N, args, torch, dev, m, c2, rho, args.mass, barrier)
+        r["ms_max"] = _max_over_ranks(r["ms"], dist, dev)
         out[N] = r
         if N == orders[0] and not args.no_e2e:
             S = r["solver"]
@@ -466,14 +486,16 @@ def run_ours(args, rank, world):
             ne = max(3, min(args.steps, 20))
             S.set_fields(qh.numpy())
             torch.cuda.synchronize(dev)
+            if barrier:
+                barrier()
             t0 = time.perf_counter()
             for _ in range(ne):
                 S.set_fields(qh.numpy())
                 S.step(r["dt"], 1)
                 from paper_1607_03399_gb300 import dg as _dg
                 _dg.dg_get_fields(S.ctx, qo.data_ptr(), 0)
-            e2e_s = (time.perf_counter() - t0) / ne
-            r["e2e"] = {"value": r["dof"] * 5 / e2e_s / 1e9 * world, "unit": "GDOF-updates/s",
+            e2e_s = _max_over_ranks((time.perf_counter() - t0) / ne, dist, dev)
+            r["e2e"] = {"value": _gdofs(r["dof"], 5, e2e_s, world), "unit": "GDOF-updates/s",
                         "h2d_bytes_per_step": int(qh.numel() * 4), "d2h_bytes_per_step": int(qo.numel() * 4)}
         r["solver"].close()
         r["solver"] = None
@@ -485,9 +507,8 @@ def run_ours(args, rank, world):
     other = {"stored": "onthefly", "onthefly": "stored"}[args.mass]
     alt = None
     if not args.no_alt:
-        if world > 1:
-            dist.barrier()
-        alt = measure_order(orders[0], args, torch, dev, m, c2, rho, other)
+        alt = measure_order(orders[0], args, torch, dev, m, c2, rho, other, barrier)
+        alt["ms_max"] = _max_over_ranks(alt["ms"], dist, dev)
         alt["solver"].close()
         alt["solver"] = None
     if rank != 0:
@@ -498,7 +519,7 @@ def run_ours(args, rank, world):
     r3 = out[orders[0]]
     K, nverts = m.K, m.VX.shape[0]
     ms_step = r3["ms_max"] / args.steps
-    value = r3["dof"] * 5 * args.steps / (r3["ms_max"] / 1e3) / 1e9 * world
+    value = _gdofs(r3["dof"], 5 * args.steps, r3["ms_max"] / 1e3, world)
     stage_s = r3["ms"] / 1e3 / (5 * args.steps)
     alg = _alg_bytes_per_stage(K, nverts, r3["dof"] // 4, N=orders[0], mass=args.mass)
     achieved = alg / stage_s / 1e9
@@ -507,7 +528,7 @@ def run_ours(args, rank, world):
         st = r["ms"] / 1e3 / (5 * args.steps)
         a = _alg_bytes_per_stage(K, nverts, r["dof"] // 4, N=N, mass=args.mass)
         by_order[str(N)] = {"autotune": r["autotune"],
-                            "value": r["dof"] * 5 * args.steps / (r["ms_max"] / 1e3) / 1e9 * world,
+                            "value": _gdofs(r["dof"], 5 * args.steps, r["ms_max"] / 1e3, world),
                             "ms_per_step": r["ms_max"] / args.steps, "stage_us": st * 1e6,
                             "alg_bytes_per_stage": a, "achieved_gbs": a / st / 1e9,
                             "frac": a / st / 1e9 / peak, "dof": r["dof"]}
@@ -516,7 +537,7 @@ def run_ours(args, rank, world):
         for mode, r in ((args.mass, r3), (other, alt)):
             st = r["ms"] / 1e3 / (5 * args.steps)
             a = _alg_bytes_per_stage(K, nverts, r["dof"] // 4, N=orders[0], mass=mode)
-            by_mass[mode] = {"value": r["dof"] * 5 * args.steps / (r["ms"] / 1e3) / 1e9, "stage_us": st * 1e6,
+            by_mass[mode] = {"value": _gdofs(r["dof"], 5 * args.steps, r["ms_max"] / 1e3, world), "stage_us": st * 1e6,
                              "alg_bytes_per_stage": a, "frac": a / st / 1e9 / peak}
     cpu = _cpu_baseline() if (world == 1 and not args.no_cpu) else None
     line = {
