@@ -205,6 +205,30 @@ def test_step_record_arguments_and_size():
         dg.dg_destroy(ctx)
 
 
+def test_empty_mesh_and_table_limits():
+    """Degenerate and maximum sizes on the host side: a mesh with no elements is
+    refused; the (source, shot) table stops at 4096 entries and the receiver
+    table at 65536, each with DG_ERR_ARG and the context still usable."""
+    m = I.cube_wavy_mesh(2, 1, 0.0)
+    _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_mesh_create(m.VX, m.EToV[:0], m.etype[:0]))
+    ctx = dg.dg_mesh_create(m.VX, m.EToV, m.etype)
+    try:
+        dg.dg_set_order(ctx, 1)
+        dg.dg_set_shots(ctx, 2)
+        for _ in range(2048):  # each source goes into both shots
+            dg.dg_add_source(ctx, 0.5, 0.5, 0.5, 5.0, 0.0, 1.0)
+        msg = _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_add_shot_source(ctx, 1, 0.5, 0.5, 0.5, 5.0, 0.0, 1.0))
+        assert "too many sources" in msg
+        for i in range(65536):
+            assert dg.dg_add_receiver(ctx, 0.25 + (i % 7) * 0.05, 0.5, 0.5) == i
+        msg = _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_add_receiver(ctx, 0.5, 0.5, 0.5))
+        assert "too many receivers" in msg
+        _, fb = dg.dg_device_bytes(ctx)
+        assert fb > 0
+    finally:
+        dg.dg_destroy(ctx)
+
+
 def test_merge_meshes_keeps_pieces_apart():
     a, b = I.cube_wavy_mesh(2, 2, 0.02), I.hybrid_mesh(2, 1, 1)
     m = I.merge_meshes([a, b])
