@@ -294,12 +294,21 @@ int dg_adjoint_step(dg_ctx* ctx, double dt);
  *                         result bit for bit); the bound state and time are
  *                         neither used nor changed.  d_rec is not modified.
  * Use: checkpoints every C steps in the forward pass; per segment, from the
- * last: dg_load_state(checkpoint), C x dg_step_record into C records, then for
- * n = last .. first: dg_adjoint_inject, dg_adjoint_step_recorded(record n).
+ * last: dg_load_state(checkpoint), dg_step_record_chain into C records, then
+ * for n = last .. first: dg_adjoint_inject, dg_adjoint_step_recorded(record n).
  * Errors: DG_ERR_ARG (null or misaligned d_rec, dt <= 0), DG_ERR_STATE
  * (unbound context or adjoint), DG_ERR_CUDA. */
 int dg_step_record_bytes(const dg_ctx* ctx, size_t* bytes);
 int dg_step_record(dg_ctx* ctx, double dt, void* d_rec);
+/* dg_step_record over nsteps consecutive steps into the records d_recs[0 ..
+ * nsteps - 1] (a host array of device pointers, each record distinct,
+ * 256-byte aligned, dg_step_record_bytes bytes).  The last stage of step i
+ * writes its result straight into slot 0 of record i + 1, so only the first
+ * step copies the bound state; the records and the final state and time equal
+ * those of nsteps dg_step_record calls bit for bit.  The bound state is only
+ * written by the last step (receivers sampled in between see the first
+ * step's input).  nsteps = 0 does nothing.  Errors as dg_step_record. */
+int dg_step_record_chain(dg_ctx* ctx, double dt, int64_t nsteps, void* const* d_recs);
 int dg_adjoint_step_recorded(dg_ctx* ctx, double dt, const void* d_rec);
 /* set the adjoint state: mu_Q and the next stage input x (normally b_5 mu_Q),
  * canonical layout, host or device sources */

@@ -9,7 +9,7 @@ re-runs each segment from its checkpoint to recover the step states and calls
 dg_adjoint_step once per step, which recomputes that step's five stages and
 accumulates dJ/dkappa, dJ/drho.  With `stage_records` the segment re-run
 instead stores every step's stage inputs and right-hand sides (ten fields per
-step, dg_step_record) and the reverse steps read them back
+step, dg_step_record_chain) and the reverse steps read them back
 (dg_adjoint_step_recorded): one forward pass less per step for
 checkpoint_every x 10 fields of device memory; the forward pass records the
 last segment itself, so that segment is not re-run.  The gradient is the same
@@ -110,8 +110,7 @@ def reverse(S: Solver, pb: Problem, traces, data, ck):
             # segment's come from the forward pass)
             if not (s0 == ck.records_from and ck.records is not None):
                 S.load_state(*ck.states[s0])
-                for n in range(s0, s1):
-                    S.step_record(pb.dt, recs[n - s0])
+                S.step_record_chain(pb.dt, recs[:s1 - s0])
             for n in range(s1, s0, -1):
                 S.adjoint_inject(resid[n - 1])
                 S.adjoint_step_recorded(pb.dt, recs[n - 1 - s0])

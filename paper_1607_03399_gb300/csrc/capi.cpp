@@ -1663,32 +1663,45 @@ int dg_step_record_bytes(const dg_ctx* c, size_t* bytes) {
   return DG_OK;
 }
 
-int dg_step_record(dg_ctx* c, double dt, void* d_rec) {
+int dg_step_record_chain(dg_ctx* c, double dt, int64_t nsteps, void* const* d_recs) {
   if (!c) return DG_ERR_ARG;
-  if (!d_rec || reinterpret_cast<uintptr_t>(d_rec) % 256) return c->fail(DG_ERR_ARG, "null or misaligned record");
+  if (nsteps < 0 || (nsteps > 0 && !d_recs)) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  for (int64_t i = 0; i < nsteps; ++i)
+    if (!d_recs[i] || reinterpret_cast<uintptr_t>(d_recs[i]) % 256) return c->fail(DG_ERR_ARG, "null or misaligned record");
   if (!(dt > 0)) return c->fail(DG_ERR_ARG, "dt must be positive");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_step_record before dg_bind");
   int rc = ensure_ops(c);
-  if (rc) return rc;
-  unsigned char* rec = static_cast<unsigned char*>(d_rec);
+  if (rc || nsteps == 0) return rc;
   const size_t fb = c->field_bytes;
-  // slot 0 takes q_n, the stages run slot s -> slot s + 1 and the last one writes
-  // the bound buffer again (the same launches as one captured step)
-  cudaError_t e = cudaMemcpyAsync(rec, c->d_q[c->cur], fb, cudaMemcpyDeviceToDevice, c->stream);
+  // record i: slot 0 takes q_i, the stages run slot s -> slot s + 1, and the last
+  // one writes slot 0 of record i + 1 (the bound buffer after the last step):
+  // the same launches as captured steps, one state copy per chain
+  cudaError_t e = cudaMemcpyAsync(d_recs[0], c->d_q[c->cur], fb, cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "record copy");
-  for (int st = 0; st < 5 && rc == DG_OK; ++st) {
-    StageExtra x;
-    x.rhs_out = rec + size_t(5 + st) * fb;
-    void* qout = st < 4 ? static_cast<void*>(rec + size_t(st + 1) * fb) : c->d_q[c->cur];
-    rc = launch_stage(c, rec + size_t(st) * fb, qout, c->d_res, kLSRK_A[st], kLSRK_B[st], dt, true, c->stream,
-                      kLSRK_C[st], x);
-  }
-  if (rc) return rc;
   double* clk = (c->prec == DG_F64) ? c->m64.clock : c->m32.clock;
-  const int crc = (c->prec == DG_F64) ? clock_f64(c->N, clk, dt, c->stream) : clock_f32(c->N, clk, dt, c->stream);
-  if (crc) return cuda_fail(c, cudaError_t(crc), "clock launch");
-  c->t += dt;
+  for (int64_t i = 0; i < nsteps; ++i) {
+    unsigned char* rec = static_cast<unsigned char*>(d_recs[i]);
+    for (int st = 0; st < 5 && rc == DG_OK; ++st) {
+      StageExtra x;
+      x.rhs_out = rec + size_t(5 + st) * fb;
+      void* qout = st < 4 ? static_cast<void*>(rec + size_t(st + 1) * fb)
+                          : (i + 1 < nsteps ? d_recs[i + 1] : c->d_q[c->cur]);
+      rc = launch_stage(c, rec + size_t(st) * fb, qout, c->d_res, kLSRK_A[st], kLSRK_B[st], dt, true, c->stream,
+                        kLSRK_C[st], x);
+    }
+    if (rc) return rc;
+    const int crc = (c->prec == DG_F64) ? clock_f64(c->N, clk, dt, c->stream) : clock_f32(c->N, clk, dt, c->stream);
+    if (crc) return cuda_fail(c, cudaError_t(crc), "clock launch");
+    c->t += dt;
+  }
   return DG_OK;
+}
+
+int dg_step_record(dg_ctx* c, double dt, void* d_rec) {
+  if (!c) return DG_ERR_ARG;
+  if (!d_rec) return c->fail(DG_ERR_ARG, "null or misaligned record");
+  void* recs[1] = {d_rec};
+  return dg_step_record_chain(c, dt, 1, recs);
 }
 
 int dg_adjoint_step_recorded(dg_ctx* c, double dt, const void* d_rec) {

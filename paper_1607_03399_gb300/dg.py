@@ -31,7 +31,7 @@ EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
            "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_stage_times", "dg_autotune", "dg_add_receiver", "dg_sample", "dg_save_state",
            "dg_load_state", "dg_adjoint_bytes", "dg_adjoint_bind", "dg_adjoint_reset", "dg_adjoint_inject",
-           "dg_adjoint_step", "dg_step_record_bytes", "dg_step_record", "dg_adjoint_step_recorded", "dg_adjoint_set", "dg_adjoint_get", "dg_adjoint_gradient", "dg_sync", "dg_time",
+           "dg_adjoint_step", "dg_step_record_bytes", "dg_step_record", "dg_step_record_chain", "dg_adjoint_step_recorded", "dg_adjoint_set", "dg_adjoint_get", "dg_adjoint_gradient", "dg_sync", "dg_time",
            "dg_stable_dt", "dg_last_error", "dg_destroy")
 
 _lib = None
@@ -87,6 +87,7 @@ def lib():
         "dg_adjoint_step": (c_int, [P, c_double]),
         "dg_step_record_bytes": (c_int, [P, POINTER(c_size_t)]),
         "dg_step_record": (c_int, [P, c_double, P]),
+        "dg_step_record_chain": (c_int, [P, c_double, c_int64, P]),
         "dg_adjoint_step_recorded": (c_int, [P, c_double, P]),
         "dg_adjoint_set": (c_int, [P, P, P, c_int]),
         "dg_adjoint_get": (c_int, [P, P, c_int]),
@@ -297,6 +298,12 @@ def dg_step_record(ctx, dt: float, d_rec: int):
     _check(ctx, lib().dg_step_record(ctx, dt, d_rec))
 
 
+def dg_step_record_chain(ctx, dt: float, d_recs):
+    """d_recs: sequence of device addresses (int) of the records."""
+    arr = (c_void_p * max(1, len(d_recs)))(*[c_void_p(int(x)) for x in d_recs])
+    _check(ctx, lib().dg_step_record_chain(ctx, dt, len(d_recs), arr))
+
+
 def dg_adjoint_step_recorded(ctx, dt: float, d_rec: int):
     _check(ctx, lib().dg_adjoint_step_recorded(ctx, dt, d_rec))
 
@@ -496,6 +503,12 @@ class Solver:
         """One step that also writes its stage inputs and right-hand sides to rec."""
         self._wait_torch()
         dg_step_record(self.ctx, dt, rec.data_ptr())
+
+    def step_record_chain(self, dt: float, recs):
+        """len(recs) steps, step i's stage inputs and right-hand sides into recs[i]
+        (dg_step_record_chain)."""
+        self._wait_torch()
+        dg_step_record_chain(self.ctx, dt, [r.data_ptr() for r in recs])
 
     def adjoint_step_recorded(self, dt: float, rec):
         dg_adjoint_step_recorded(self.ctx, dt, rec.data_ptr())

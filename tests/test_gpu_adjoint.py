@@ -142,7 +142,8 @@ def test_shots_sum_their_gradients():
 def test_step_record_is_the_step(precision):
     """dg_step_record advances the state and time exactly like dg_step (two
     shots with sources, so the stage times matter) and its slot 0 holds the
-    packed input state of the step."""
+    packed input state of the step; dg_step_record_chain gives the same
+    state and time and records that drive the adjoint identically."""
     m = I.cube_wavy_mesh(3, 2, 0.05)
     c2, rho = I.random_material(m.K, 4, 1.0, 2.0, 0.7, 1.3)
     kw = dict(precision=precision, shots=2,
@@ -166,8 +167,30 @@ def test_step_record_is_the_step(precision):
     nb = B.field_bytes
     for r, q in zip(recs, before):
         assert torch.equal(r[:nb], q)
+    # the chained form: the same records, state and time
+    Cs = Solver(m.VX, m.EToV, m.etype, 3, c2, rho, **kw)
+    Cs.set_fields(v)
+    chain = [Cs.new_record() for _ in range(3)]
+    Cs.step_record_chain(dt, chain)
+    Cs.sync()
+    assert np.array_equal(Cs.get_fields(), fb)
+    assert Cs.time() == B.time()
+    # records are compared through their use (lanes and bytes past the packed
+    # data are never written): three recorded adjoint steps from each set
+    mu = np.random.default_rng(9).standard_normal(B.field_shape)
+    outs = []
+    for S_, rr in ((B, recs), (Cs, chain)):
+        S_.adjoint_bind()
+        S_.adjoint_set(mu, 0.3 * mu)
+        for r in reversed(rr):
+            S_.adjoint_step_recorded(dt, r)
+        outs.append((S_.adjoint_get(), *S_.adjoint_gradient()))
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    assert np.abs(outs[0][1]).max() > 0
     A.close()
     B.close()
+    Cs.close()
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])

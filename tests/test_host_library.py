@@ -198,6 +198,10 @@ def test_step_record_arguments_and_size():
         _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_step_record(ctx, 0.1, 4096 + 16))
         _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_step_record(ctx, 0.0, 4096))
         _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_step_record(ctx, 0.1, 4096))
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_step_record_chain(ctx, 0.1, [4096, 0]))
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_step_record_chain(ctx, 0.1, [4096, 4096 + 64]))
+        _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_step_record_chain(ctx, 0.1, [4096, 8192]))
+        _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_step_record_chain(ctx, 0.1, []))
         _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_adjoint_step_recorded(ctx, 0.1, 0))
         _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_adjoint_step_recorded(ctx, -1.0, 4096))
         _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_adjoint_step_recorded(ctx, 0.1, 4096))
