@@ -62,10 +62,17 @@ def _traffic_per_launch(mass):
     return int(fields["traffic_bytes_per_launch"].strip())
 
 
-def _mesh(ntri=128, nlayers=16):
+def _mesh(ntri=128, nlayers=16, order="column"):
+    """The layered workload mesh in column-major element order (the generator's:
+    each 32-element block holds two whole 16-layer columns), or the same mesh
+    layer by layer (`--element-order layer`, the comparison for the column
+    order's in-block vertical traces)."""
     from paper_1607_03399_gb300 import inputs as I
     m = I.bumpy_layered_mesh(ntri, nlayers)
     c2, rho = I.layered_wavespeed(m)
+    if order == "layer":
+        m, perm = I.layer_major(m, nlayers)
+        c2, rho = c2[perm], rho[perm]
     return m, c2, rho
 
 
@@ -469,7 +476,7 @@ def run_ours(args, rank, world):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     ntri, nlay = WORKLOADS[args.workload]
-    m, c2, rho = _mesh(ntri, nlay)
+    m, c2, rho = _mesh(ntri, nlay, args.element_order)
     orders = [int(x) for x in args.orders.split(",")]
     out = {}
     barrier = dist.barrier if world > 1 else None
@@ -545,13 +552,14 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.workload == "full" else f"layered_wedges_2x{ntri}x{ntri}x{nlay}",
-                   "wedges": K, "order": orders[0], "field_dof": r3["dof"],
+                   "wedges": K, "order": orders[0], "field_dof": r3["dof"], "element_order": args.element_order,
                    "l2_flush": "inputs larger than L2 (3 state buffers of %.0f MB)" % (r3["dof"] * 4 / 1e6),
                    "bc": "rigid", "flux": "upwind", "source": "Ricker f0=10 t0=0.1 at (0.5,0.5,0.5)",
                    "mass": args.mass},
         "roofline": {"kernel": f"k_wedge_stage<{orders[0]}>", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": _traffic_per_launch(args.mass) if (args.workload == "full" and orders[0] == 3) else None,
+                     "traffic": _traffic_per_launch(args.mass) if (args.workload == "full" and orders[0] == 3
+                                                                   and args.element_order == "column") else None,
                      "alg_bytes_per_launch": alg},
         "by_order": by_order,
         "by_mass": by_mass or None,
@@ -585,6 +593,8 @@ def main():
     ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid wedge + tet workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the multi-shot and multi-mesh workloads")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) workload")
+    ap.add_argument("--element-order", default="column", choices=["column", "layer"],
+                    help="element order of the layered workload (layer: the comparison for the column order)")
     ap.add_argument("--adjoint-size", default="full", choices=sorted(ADJOINT_SIZES),
                     help="size of the adjoint workload (small: the profiling case)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-variant autotuner after timing")

@@ -321,6 +321,16 @@ def merge_meshes(meshes, shift=(2.0, 0.0, 0.0)) -> Mesh:
     return Mesh(np.vstack(VX), np.vstack(EToV), np.concatenate(etype), name="merged", meta={"offsets": offs})
 
 
+def layer_major(mesh: Mesh, nlayers: int) -> tuple:
+    """The same column-major layered mesh (element k = column * nlayers + layer)
+    listed layer by layer instead, so that no vertical neighbour shares a
+    32-element block: the reference order for measuring what the column order
+    saves.  Returns (mesh, perm) with new element i = old element perm[i]."""
+    k = np.arange(mesh.EToV.shape[0])
+    perm = np.lexsort((k // nlayers, k % nlayers))
+    return Mesh(mesh.VX, mesh.EToV[perm], mesh.etype[perm], mesh.name + "_layer_major", dict(mesh.meta)), perm
+
+
 def surface_shots(nshots: int, seed: int, depth: float = 0.01, margin: float = 0.05):
     """Seeded source positions just below the top surface z = 1 of [0,1]^3."""
     rng = np.random.default_rng(seed)

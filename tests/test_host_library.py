@@ -275,3 +275,8 @@ def test_column_order_keeps_vertical_traces_in_the_block():
     ft, fq = _in_block_fractions(I.bumpy_layered_mesh(8, 16))
     assert ft == 1.0
     assert 0.2 < fq < 0.5
+    # the comparison order: the same mesh layer by layer keeps none of them
+    lm, perm = I.layer_major(I.bumpy_layered_mesh(8, 16), 16)
+    assert sorted(perm.tolist()) == list(range(lm.K))
+    ft, fq = _in_block_fractions(lm)
+    assert ft == 0.0
