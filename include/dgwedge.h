@@ -80,6 +80,7 @@ enum { DG_BC_DIRICHLET = 0, DG_BC_RIGID = 1 };
 enum { DG_FLUX_UPWIND = 0, DG_FLUX_CENTRAL = 1 };
 enum { DG_F32 = 0, DG_F64 = 1 };
 enum { DG_MASS_ONTHEFLY = 0, DG_MASS_STORED = 1 };
+enum { DG_SHOTS_OUTER = 0, DG_SHOTS_INNER = 1 };
 
 /* Create a mesh context from vertices and element-to-vertex lists
  * (Section 2.1 "triangulation of the domain"; Section 3.2 vertex maps).
@@ -129,6 +130,18 @@ int dg_set_shots(dg_ctx* ctx, int64_t shots);
  * every shot).  Errors as dg_add_source, and DG_ERR_ARG for a shot index
  * outside [0, shots). */
 int dg_add_shot_source(dg_ctx* ctx, int64_t shot, double x, double y, double z, double f0, double t0, double amp);
+
+/* How the shots of dg_set_shots are laid out in the stage kernels' element
+ * blocks (32 consecutive virtual elements, one per lane).  DG_SHOTS_OUTER
+ * (default): shot-major, virtual element s K + i, so a block holds 32
+ * elements of one shot and keeps the column-order reuse of vertical traces.
+ * DG_SHOTS_INNER: virtual element i S + s, so a block holds the shots of one
+ * or a few elements; every lane of a warp then reads the same neighbour
+ * element, for all shots at once, in one contiguous record (the shot-lane
+ * layout), while vertical traces leave the block.  Results are identical
+ * bit for bit either way; the field layout of dg_set_fields etc. does not
+ * change.  Before dg_bind.  Errors: DG_ERR_ARG (unknown order), DG_ERR_STATE. */
+int dg_set_shot_order(dg_ctx* ctx, int order);
 
 /* Boundary condition (DG_BC_*), flux (DG_FLUX_*), arithmetic precision
  * (DG_F32: fields and arithmetic in float; DG_F64: double).

@@ -41,13 +41,14 @@ class Problem:
     flux: str = "upwind"
     checkpoint_every: int = 50
     stage_records: bool = False
+    shot_order: str = "outer"
     device: str = "cuda:0"
 
     def solver(self, c2, rho) -> Solver:
         return Solver(self.VX, self.EToV, self.etype, self.N, np.asarray(c2, dtype=np.float64),
                       np.asarray(rho, dtype=np.float64), bc=self.bc, flux=self.flux, precision=self.precision,
                       device=self.device, shots=self.shots, shot_sources=self.shot_sources,
-                      receivers=self.receivers)
+                      receivers=self.receivers, shot_order=self.shot_order)
 
 
 @dataclass

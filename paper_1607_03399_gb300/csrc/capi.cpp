@@ -127,6 +127,7 @@ struct dg_ctx {
   int mass = DG_MASS_STORED;
   // shots: independent copies of the state on the same mesh, advanced together
   int64_t shots = 1;
+  bool shot_inner = false;  // DG_SHOTS_INNER: the shots of one element are neighbouring lanes
   double t_stage_host = 0.0;  // staging for clock uploads
   // launch variant chosen by dg_autotune: wedge blocks per CTA (0 = default) and
   // whether the stored mass factor is bypassed (factor recomputed in the stage)
@@ -412,8 +413,11 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
   const int64_t S = c->shots, T = c->wedge_nodes + c->tet_nodes;
   const int64_t VKw = S * Kw, VKt = S * Kt;
   const int64_t Kwp = nblk(VKw) * kB, Ktp = nblk(VKt) * kB;
-  // virtual id of (shot s, input element n)
-  auto vid = [&](int64_t s, int64_t n) { return s * (c->etype[n] == DG_WEDGE ? Kw : Kt) + c->local[n]; };
+  // virtual id of (shot s, input element n): shot-major (s K + i) or shot-inner (i S + s)
+  const bool inner = c->shot_inner;
+  auto vid = [&](int64_t s, int64_t n) {
+    return inner ? c->local[n] * S + s : s * (c->etype[n] == DG_WEDGE ? Kw : Kt) + c->local[n];
+  };
   int* w_vid = reinterpret_cast<int*>(blob.data() + L.w_vid);
   int* w_nbr = reinterpret_cast<int*>(blob.data() + L.w_nbr);
   int* w_code = reinterpret_cast<int*>(blob.data() + L.w_code);
@@ -421,7 +425,8 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
   int64_t* w_canon = reinterpret_cast<int64_t*>(blob.data() + L.w_canon);
   for (int64_t w = 0; w < Kwp; ++w) {
     const bool real_slot = w < VKw;  // padding replicates a valid element with no neighbours
-    const int64_t s = real_slot ? w / Kw : 0, k = c->wedges[real_slot ? w % Kw : 0];
+    const int64_t s = real_slot ? (inner ? w % S : w / Kw) : 0;
+    const int64_t k = c->wedges[real_slot ? (inner ? w / S : w % Kw) : 0];
     for (int v = 0; v < 6; ++v) w_vid[v * Kwp + w] = int(c->EToV[k * 6 + v]);
     for (int f = 0; f < 5; ++f) {
       const int64_t n = real_slot ? c->nbr[k][f] : -1;
@@ -451,7 +456,8 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
   int64_t* t_canon = reinterpret_cast<int64_t*>(blob.data() + L.t_canon);
   for (int64_t t = 0; t < Ktp; ++t) {
     const bool real_slot = t < VKt;
-    const int64_t s = real_slot ? t / Kt : 0, k = c->tets[real_slot ? t % Kt : 0];
+    const int64_t s = real_slot ? (inner ? t % S : t / Kt) : 0;
+    const int64_t k = c->tets[real_slot ? (inner ? t / S : t % Kt) : 0];
     for (int v = 0; v < 4; ++v) t_vid[v * Ktp + t] = int(c->EToV[k * 6 + v]);
     for (int f = 0; f < 4; ++f) {
       const int64_t n = real_slot ? c->nbr[k][f] : -1;
@@ -611,7 +617,7 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
           one[size_t(w) * nl + i * (i + 1) / 2 + l] = real(l < i ? Lk[size_t(i) * nt + l] : 1.0 / Lk[size_t(i) * nt + i]);
     }
     for (int64_t w = 0; w < Kwp; ++w) {
-      const int64_t lw = w < VKw ? w % Kw : 0, b = w / kB, lane = w % kB;
+      const int64_t lw = w < VKw ? (inner ? w / S : w % Kw) : 0, b = w / kB, lane = w % kB;
       for (int q = 0; q < nl; ++q) fac[(b * nl + q) * kB + lane] = one[size_t(lw) * nl + q];
     }
   }
@@ -664,6 +670,8 @@ void fill_devmesh(const dg_ctx* c, const BlobLayout& L, DevMesh<real>& m) {
   }
   m.Kw1 = int(c->wedges.size());
   m.Kt1 = int(c->tets.size());
+  m.shot_inner = c->shot_inner ? 1 : 0;
+  m.nshots = int(c->shots);
   m.t_srng = reinterpret_cast<const int*>(b + L.tsrng);
   m.clock = reinterpret_cast<double*>(b + L.clock);
   m.w_fac = c->mass == DG_MASS_STORED ? reinterpret_cast<const real*>(b + L.wfac) : nullptr;
@@ -1085,6 +1093,14 @@ int dg_set_shots(dg_ctx* c, int64_t shots) {
   const int64_t K = int64_t(std::max(c->wedges.size(), c->tets.size()));
   if (shots * K >= (int64_t(1) << 30)) return c->fail(DG_ERR_ARG, "shots x elements exceeds 2^30");
   c->shots = shots;
+  return DG_OK;
+}
+
+int dg_set_shot_order(dg_ctx* c, int order) {
+  if (!c) return DG_ERR_ARG;
+  if (c->bound) return c->fail(DG_ERR_STATE, "dg_set_shot_order after dg_bind");
+  if (order != DG_SHOTS_OUTER && order != DG_SHOTS_INNER) return c->fail(DG_ERR_ARG, "unknown shot order");
+  c->shot_inner = order == DG_SHOTS_INNER;
   return DG_OK;
 }
 
@@ -1779,8 +1795,9 @@ int dg_adjoint_gradient(dg_ctx* c, double* g_kappa, double* g_rho) {
   for (int64_t k = 0; k < c->K; ++k) g_kappa[k] = g_rho[k] = 0.0;
   for (int64_t s = 0; s < c->shots; ++s)
     for (int64_t w = 0; w < Kw; ++w) {
-      g_kappa[c->wedges[w]] += gk[s * Kw + w];
-      g_rho[c->wedges[w]] += gr[s * Kw + w];
+      const int64_t v = c->shot_inner ? w * c->shots + s : s * Kw + w;
+      g_kappa[c->wedges[w]] += gk[v];
+      g_rho[c->wedges[w]] += gr[v];
     }
   return check_device_error(c);
 }

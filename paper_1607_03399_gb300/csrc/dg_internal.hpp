@@ -124,6 +124,7 @@ struct DevMesh {
   const real* rec_g = nullptr;
   int nrec = 0, nrgrp = 0;
   int Kw1 = 0, Kt1 = 0;              // wedges / tets of one shot
+  int shot_inner = 0, nshots = 1;    // virtual element of (shot s, element i): i S + s, else s K1 + i
   const int* w_srng = nullptr;       // per wedge block [begin, end) of its entries in src
   const int* t_srng = nullptr;       // per tet block likewise
 };

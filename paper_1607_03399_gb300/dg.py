@@ -26,8 +26,9 @@ DG_BC_DIRICHLET, DG_BC_RIGID = 0, 1
 DG_FLUX_UPWIND, DG_FLUX_CENTRAL = 0, 1
 DG_F32, DG_F64 = 0, 1
 DG_MASS_ONTHEFLY, DG_MASS_STORED = 0, 1
+DG_SHOTS_OUTER, DG_SHOTS_INNER = 0, 1
 
-EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_shots", "dg_add_shot_source", "dg_set_options", "dg_set_mass_mode", "dg_num_nodes",
+EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_shots", "dg_add_shot_source", "dg_set_shot_order", "dg_set_options", "dg_set_mass_mode", "dg_num_nodes",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
            "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_stage_times", "dg_autotune", "dg_add_receiver", "dg_sample", "dg_save_state",
            "dg_load_state", "dg_adjoint_bytes", "dg_adjoint_bind", "dg_adjoint_reset", "dg_adjoint_inject",
@@ -60,6 +61,7 @@ def lib():
         "dg_add_source": (c_int, [P, c_double, c_double, c_double, c_double, c_double, c_double]),
         "dg_set_shots": (c_int, [P, c_int64]),
         "dg_add_shot_source": (c_int, [P, c_int64, c_double, c_double, c_double, c_double, c_double, c_double]),
+        "dg_set_shot_order": (c_int, [P, c_int]),
         "dg_set_options": (c_int, [P, c_int, c_int, c_int]),
         "dg_set_mass_mode": (c_int, [P, c_int]),
         "dg_num_nodes": (c_int, [P, POINTER(c_int64), POINTER(c_int64)]),
@@ -152,6 +154,10 @@ def dg_add_source(ctx, x: float, y: float, z: float, f0: float, t0: float, amp: 
 
 def dg_set_shots(ctx, shots: int):
     _check(ctx, lib().dg_set_shots(ctx, shots))
+
+
+def dg_set_shot_order(ctx, order: int):
+    _check(ctx, lib().dg_set_shot_order(ctx, order))
 
 
 def dg_add_shot_source(ctx, shot: int, x, y, z, f0, t0, amp):
@@ -364,7 +370,7 @@ class Solver:
 
     def __init__(self, VX, EToV, etype, N: int, c2=None, rho=None, bc: str = "rigid", flux: str = "upwind",
                  precision: str = "f32", device: str = "cuda:0", stream=None, sources=(), mass: str = "stored",
-                 shots: int = 1, shot_sources=(), receivers=()):
+                 shots: int = 1, shot_sources=(), receivers=(), shot_order: str = "outer"):
         import torch
         self.torch = torch
         self.ctx = dg_mesh_create(VX, EToV, etype)
@@ -376,6 +382,7 @@ class Solver:
             dg_set_options(self.ctx, BC[bc], FLUX[flux], PREC[precision])
             dg_set_mass_mode(self.ctx, MASS[mass])
             dg_set_shots(self.ctx, shots)
+            dg_set_shot_order(self.ctx, {"outer": DG_SHOTS_OUTER, "inner": DG_SHOTS_INNER}[shot_order])
             self.shots = shots
             for src in sources:       # (x, y, z, f0, t0, amp)
                 dg_add_source(self.ctx, *src)

@@ -117,7 +117,8 @@ def test_autograd_function():
     assert np.allclose(rh.grad.numpy(), grho, rtol=1e-10, atol=0)
 
 
-def test_shots_sum_their_gradients():
+@pytest.mark.parametrize("order", ["outer", "inner"])
+def test_shots_sum_their_gradients(order):
     m = I.cube_wavy_mesh(3, 2, 0.03)
     c2, rho = I.random_material(m.K, 11, 1.0, 2.0, 0.8, 1.2)
     recs = [(0.2, 0.7, 0.8), (0.6, 0.4, 0.2), (0.8, 0.8, 0.5)]
@@ -126,7 +127,7 @@ def test_shots_sum_their_gradients():
               checkpoint_every=6)
     rng = np.random.default_rng(2)
     data = torch.as_tensor(rng.standard_normal((15, 2, 3)) * 1e-3, dtype=torch.float64, device="cuda")
-    pb2 = AD.Problem(shot_sources=srcs, shots=2, **kw)
+    pb2 = AD.Problem(shot_sources=srcs, shots=2, shot_order=order, **kw)
     J, g2, gr = AD.misfit_and_gradient(pb2, c2, rho, data)
     Js, g2s, grs = 0.0, 0.0, 0.0
     for s in range(2):

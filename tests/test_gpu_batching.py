@@ -18,14 +18,15 @@ from paper_1607_03399_gb300.dg import Solver  # noqa: E402
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 @pytest.mark.parametrize("meshname", ["wedges", "hybrid"])
-def test_shots_match_single_shot_runs(precision, meshname):
+@pytest.mark.parametrize("order", ["outer", "inner"])
+def test_shots_match_single_shot_runs(precision, meshname, order):
     m = I.cube_wavy_mesh(4, 3, 0.03) if meshname == "wedges" else I.hybrid_mesh(3, 2, 1)
     c2, rho = I.random_material(m.K, 7, 1.0, 2.0, 0.5, 1.5)
     S = 3
     pos = [(0.31, 0.62, 0.4), (0.7, 0.2, 0.55), (0.5, 0.5, 0.2)]
     shot_sources = [(s, *pos[s], 6.0 + s, 0.05, 1.0 + s) for s in range(S)]
     B = Solver(m.VX, m.EToV, m.etype, 3, c2, rho, precision=precision, shots=S, shot_sources=shot_sources,
-               sources=[(0.45, 0.4, 0.5, 5.0, 0.0, 0.3)])
+               sources=[(0.45, 0.4, 0.5, 5.0, 0.0, 0.3)], shot_order=order)
     rng = np.random.default_rng(1)
     q = rng.uniform(-1, 1, size=(S, 4, B.total_nodes)).astype(B.np_dtype)
     B.set_fields(q)

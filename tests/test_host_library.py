@@ -179,6 +179,11 @@ def test_shots_arguments_and_sizes():
         dg.dg_add_shot_source(ctx, 4, 0.5, 0.5, 0.5, 5.0, 0.1, 1.0)
         _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_set_shots(ctx, 4))   # would orphan the shot-4 source
         dg.dg_set_shots(ctx, 6)
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_set_shot_order(ctx, 2))
+        dg.dg_set_shot_order(ctx, dg.DG_SHOTS_INNER)
+        _, fb6 = dg.dg_device_bytes(ctx)
+        dg.dg_set_shot_order(ctx, dg.DG_SHOTS_OUTER)
+        assert dg.dg_device_bytes(ctx)[1] == fb6   # the order changes no buffer size
     finally:
         dg.dg_destroy(ctx)
 
