@@ -380,14 +380,15 @@ def measure_multimesh(args, torch, dev):
             "ratio": s_a / (ms_b / 1e3)}
 
 
-ADJOINT_SIZES = {"full": (48, 24, 8), "small": (24, 12, 2)}
+ADJOINT_SIZES = {"full": (48, 24, 8, 800), "small": (24, 12, 2, 50)}
 
 
 def measure_adjoint(args, torch, dev):
     """Differentiation workload: 2x48x48 footprint x 24 layers = 110592 wedges,
     N=3, FP32 fields, two-layer c^2 with a Gaussian inclusion, 8 shots (Ricker
-    f0 = 8 below the surface) and 256 surface receivers; misfit against traces
-    of the model with a 10% stronger inclusion; checkpoints every 50 steps.
+    f0 = 8 below the surface) and 256 surface receivers, 800 steps; misfit
+    against traces of the model with a 10% stronger inclusion; checkpoints
+    every 50 steps.
     Times the forward pass (with receiver sampling and checkpoints) and the
     adjoint sweep (segment re-runs, per-step stage recomputation, adjoint
     stages, gradient terms), then both again with checkpoints every 25 steps
@@ -396,15 +397,15 @@ def measure_adjoint(args, torch, dev):
     ratios (faster of two passes each), the peak device memory of each and
     whether the two gradients agree bit for bit.  The headline ratio is the
     stage-record one.
-    `--adjoint-size small` (2x24x24 x 12 layers, 2 shots) is the profiling case."""
+    `--adjoint-size small` (2x24x24 x 12 layers, 2 shots, 50 steps) is the
+    profiling case."""
     from paper_1607_03399_gb300 import inputs as I
     from paper_1607_03399_gb300 import adjoint as AD
-    side, layers, nshots = ADJOINT_SIZES[args.adjoint_size]
+    side, layers, nshots, nsteps = ADJOINT_SIZES[args.adjoint_size]
     torch.cuda.empty_cache()  # the earlier workloads' cached blocks
     m = I.bumpy_layered_mesh(side, layers)
     pos = I.surface_shots(nshots, 5)
     recs = I.surface_receivers(16)
-    nsteps = max(50, min(args.steps * 2, 200))
     pb = AD.Problem(m.VX, m.EToV, m.etype, 3, 0.0, nsteps, recs, shots=nshots, checkpoint_every=50,
                     shot_sources=[(s, *pos[s], 8.0, 0.125, 1.0) for s in range(nshots)], device=str(dev))
     c2t, rho = I.inclusion_model(m, amp=0.55)
