@@ -274,8 +274,9 @@ int dg_load_state(dg_ctx* ctx, const void* d_src, double t);
  * W P A P W^{-1} with W the energy mass (Section 4.1) and P = diag(1, -I)
  * (velocity sign flip); in the variable mu = P W^{-1} lambda the adjoint of
  * one LSRK45 step runs the forward stage with the update coefficients
- * reversed, and receiver residuals enter exactly like point sources.  Meshes
- * of wedges only; every shot shares the receivers.
+ * reversed, and receiver residuals enter exactly like point sources.  Wedges
+ * and tets (the gradient terms of a tet use its affine mass J M^tet and face
+ * masses J_f M^tri); every shot shares the receivers.
  *
  * Use: dg_adjoint_bytes -> allocate -> dg_adjoint_bind (zeroes everything)
  * -> for n = nsteps .. 1: dg_adjoint_inject(residuals of step n);
@@ -283,7 +284,7 @@ int dg_load_state(dg_ctx* ctx, const void* d_src, double t);
  * dg_adjoint_step recomputes the forward step from the current state and
  * time (which it leaves unchanged), then applies the five adjoint stages and
  * accumulates the gradient terms.  Errors: DG_ERR_ARG, DG_ERR_STATE,
- * DG_ERR_MESH (tetrahedra), DG_ERR_CUDA. */
+ * DG_ERR_CUDA. */
 int dg_adjoint_bytes(const dg_ctx* ctx, size_t* bytes);
 int dg_adjoint_bind(dg_ctx* ctx, void* d_work);
 int dg_adjoint_reset(dg_ctx* ctx);

@@ -128,7 +128,9 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
     cdf[f] = M.w_code[f * Kp + e];
   }
 #pragma unroll
-  for (int f = 0; f < 5; ++f) zPf[f] = M.w_mat[2 * Kp + (nbf[f] < 0 ? e : nbf[f])];
+  for (int f = 0; f < 5; ++f)
+    zPf[f] = nbf[f] < 0 ? zM
+                        : ((f < 2 && (cdf[f] & kCodeTet)) ? M.t_mat[2 * M.Kt_pad + nbf[f]] : M.w_mat[2 * Kp + nbf[f]]);
   __syncthreads();
   if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0)) && lane == 0) atomicOr(failed, 1);
   __syncthreads();
@@ -286,7 +288,15 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
       const real n0 = GEO(fb ? G_NT0 : G_NB0), n1 = GEO(fb ? G_NT1 : G_NB1), n2 = GEO(fb ? G_NT2 : G_NB2);
       const real Jf = GEO(fb ? G_JFT : G_JFB);
       const real zP = fb ? zPf[1] : zPf[0];
-      const int own0 = fb ? N * Nt : 0, nb0 = ((code >> 4) & 3) ? N * Nt : 0;
+      // the neighbour across a triangle face: a wedge (its bottom or top slice) or,
+      // at the wedge/tet interface, a tet (one of its faces)
+      const bool ntet = nbr >= 0 && (code & kCodeTet) != 0;
+      const int own0 = fb ? N * Nt : 0, nf = (code >> 4) & 3;
+      auto nbt = [&](const real* glob, int k) {
+        const int nk = O.tab.tri_perm[code & 15][k];
+        return ntet ? ld4(glob, tidx<N>(M.tet_off, nbr >> 5, O.tab.tet_face[nf][nk], nbr & 31))
+                    : ld4(glob, widx<N>(nbr >> 5, (nf ? N * Nt : 0) + nk, nbr & 31));
+      };
       real a[Nt], b[Nt], c[Nt], d[Nt];  // [p], [mu_p], [u_n], [mu_un] (boundary: own values)
 #pragma unroll
       for (int k = 0; k < Nt; ++k) {
@@ -297,8 +307,7 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
           c[k] = n0 * qo.u + n1 * qo.v + n2 * qo.w;
           d[k] = n0 * xo.u + n1 * xo.v + n2 * xo.w;
         } else {
-          const int node = nb0 + O.tab.tri_perm[code & 15][k];
-          const Q4 qn = nbv(Q, nbr, node), xn = nbv(X, nbr, node);
+          const Q4 qn = nbt(Q, k), xn = nbt(X, k);
           a[k] = qn.p - qo.p;
           b[k] = xn.p - xo.p;
           c[k] = n0 * (qn.u - qo.u) + n1 * (qn.v - qo.v) + n2 * (qn.w - qo.w);
@@ -337,6 +346,185 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
     gr[e] += dt * (sr + sz * double(zM) / (2.0 * rho));
   }
 #undef GEO
+}
+
+// The same gradient terms on the tets (affine: M^k = J M^tet with the reference
+// tet mass, face mass J_f M^tri): per tet, J mu_p^T M^tet r_p / kappa^2 + dz/dkappa G
+// and J mu_u^T M^tet r_u + dz/drho G, G the penalty derivative summed over the four
+// faces, whose neighbours are tets or, across the interface, wedges.  CTA = a
+// 32-tet block x 4 warps; the block's mu and r slabs in shared memory; warp w
+// takes face w and element-term rows [w C, w C + C); the partial sums are
+// reduced in a fixed order and added, times dt, in double.
+template <int N>
+__host__ __device__ constexpr int tgrad_smem_bytes() {
+  return int(sizeof(real)) * 2 * 4 * npt_of(N) * kB + 8 * 3 * 4 * kB;
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_tet_grad(const DevMesh<real> M, const real* __restrict__ X,
+                                                  const real* __restrict__ Q, const real* __restrict__ R, double dt,
+                                                  int flux, int bc, double* __restrict__ gk, double* __restrict__ gr) {
+  constexpr int Np = npt_of(N), Nt = nt_of(N), C = (Np + 3) / 4;
+  const AllOps<N, real>& O = OPS<N>();
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  real* sX = reinterpret_cast<real*>(smem_raw);              // [Np][32][4]
+  real* sR = sX + 4 * Np * kB;                                // [Np][32][4]
+  double* red = reinterpret_cast<double*>(sR + 4 * Np * kB);  // [warp][3][32]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int blk = blockIdx.x, e = blk * kB + lane;
+  const int Kp = M.Kt_pad;
+  const int64_t base = tidx<N>(M.tet_off, blk, 0, 0);  // the block's [Np][32][4] records
+  for (int i = threadIdx.x; i < Np * kB; i += blockDim.x) {
+    const Q4 x = ld4(X, base + int64_t(i) * 4), r = ld4(R, base + int64_t(i) * 4);
+    sX[i * 4 + 0] = x.p;
+    sX[i * 4 + 1] = x.u;
+    sX[i * 4 + 2] = x.v;
+    sX[i * 4 + 3] = x.w;
+    sR[i * 4 + 0] = r.p;
+    sR[i * 4 + 1] = r.u;
+    sR[i * 4 + 2] = r.v;
+    sR[i * 4 + 3] = r.w;
+  }
+  const real kappa = M.t_mat[0 * Kp + e], irho = M.t_mat[1 * Kp + e], zM = M.t_mat[2 * Kp + e];
+  // affine geometry (bi-unit reference tet): J, and face w's outward normal and J_f
+  real J, n0, n1, n2, Jf;
+  {
+    real Xv[4][3];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Xv[v][d] = M.t_xyz[(int64_t(blk) * 12 + v * 3 + d) * kB + lane];
+    real G[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) G[d][m] = real(0.5) * (Xv[m + 1][d] - Xv[0][d]);
+    J = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) - G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+        G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+    constexpr int fv[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
+    constexpr int fo[4] = {3, 2, 0, 1};
+    const int a0 = w == 0 ? fv[0][0] : w == 1 ? fv[1][0] : w == 2 ? fv[2][0] : fv[3][0];
+    const int a1 = w == 0 ? fv[0][1] : w == 1 ? fv[1][1] : w == 2 ? fv[2][1] : fv[3][1];
+    const int a2 = w == 0 ? fv[0][2] : w == 1 ? fv[1][2] : w == 2 ? fv[2][2] : fv[3][2];
+    const int ao = fo[0] * (w == 0) + fo[1] * (w == 1) + fo[2] * (w == 2) + fo[3] * (w == 3);
+    real P[4][3];  // the face's vertices and the opposite one, selected without dynamic indexing
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      real v0 = 0, v1 = 0, v2 = 0, vo = 0;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        v0 = a0 == v ? Xv[v][d] : v0;
+        v1 = a1 == v ? Xv[v][d] : v1;
+        v2 = a2 == v ? Xv[v][d] : v2;
+        vo = ao == v ? Xv[v][d] : vo;
+      }
+      P[0][d] = v0;
+      P[1][d] = v1;
+      P[2][d] = v2;
+      P[3][d] = vo;
+    }
+    const real ax = P[1][0] - P[0][0], ay = P[1][1] - P[0][1], az = P[1][2] - P[0][2];
+    const real bx = P[2][0] - P[0][0], by = P[2][1] - P[0][1], bz = P[2][2] - P[0][2];
+    const real cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+    const real cc = cx * cx + cy * cy + cz * cz, ic = rsqrt_r(cc);
+    const real ox = P[3][0] - P[0][0], oy = P[3][1] - P[0][1], oz = P[3][2] - P[0][2];
+    const real sgn = (cx * ox + cy * oy + cz * oz > 0) ? real(-1) : real(1);  // away from the opposite vertex
+    n0 = sgn * cx * ic;
+    n1 = sgn * cy * ic;
+    n2 = sgn * cz * ic;
+    Jf = real(0.25) * cc * ic;
+  }
+  __syncthreads();
+
+  // element terms, rows [w C, w C + C): mu_i . (M^tet r)_i
+  real t1k = 0, t1r = 0;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int i = w * C + c;
+    if (i < Np) {
+      real c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+      for (int l = 0; l < Np; ++l) {
+        const real m = M.tet_mass[i * Np + l];
+        const Q4 r = lds4(sR, l, lane);
+        c0 += m * r.p;
+        c1 += m * r.u;
+        c2 += m * r.v;
+        c3 += m * r.w;
+      }
+      const Q4 x = lds4(sX, i, lane);
+      t1k += x.p * c0;
+      t1r += x.u * c1 + x.v * c2 + x.w * c3;
+    }
+  }
+  t1k *= J / (kappa * kappa);
+  t1r *= J;
+
+  // penalty terms of face w
+  real gz = 0;
+  if (flux == 0) {
+    const int f = w;
+    const int nbr = M.t_nbr[f * Kp + e], code = M.t_code[f * Kp + e];
+    const bool bnd = nbr < 0, ntet = !bnd && (code & kCodeTet) != 0;
+    const real zP = bnd ? zM : (ntet ? M.t_mat[2 * Kp + nbr] : M.w_mat[2 * M.Kw_pad + nbr]);
+    const int nfc = (code >> 4) & 3, perm = code & 15;
+    real a[Nt], b[Nt], cq[Nt], d[Nt];  // [p], [mu_p], [u_n], [mu_un] (boundary: own values)
+#pragma unroll
+    for (int k = 0; k < Nt; ++k) {
+      const int own = O.tab.tet_face[f][k];
+      const Q4 qo = ld4(Q, base + (int64_t(own) * kB + lane) * 4), xo = lds4(sX, own, lane);
+      if (bnd) {
+        a[k] = qo.p;
+        b[k] = xo.p;
+        cq[k] = n0 * qo.u + n1 * qo.v + n2 * qo.w;
+        d[k] = n0 * xo.u + n1 * xo.v + n2 * xo.w;
+      } else {
+        const int nk = O.tab.tri_perm[perm][k];
+        const int node = ntet ? O.tab.tet_face[nfc][nk] : (nfc ? N * Nt : 0) + nk;
+        const int64_t g = ntet ? tidx<N>(M.tet_off, nbr >> 5, node, nbr & 31) : widx<N>(nbr >> 5, node, nbr & 31);
+        const Q4 qn = ld4(Q, g), xn = ld4(X, g);
+        a[k] = qn.p - qo.p;
+        b[k] = xn.p - xo.p;
+        cq[k] = n0 * (qn.u - qo.u) + n1 * (qn.v - qo.v) + n2 * (qn.w - qo.w);
+        d[k] = n0 * (xn.u - xo.u) + n1 * (xn.v - xo.v) + n2 * (xn.w - xo.w);
+      }
+    }
+    real Ip = 0, Iu = 0;
+#pragma unroll
+    for (int k = 0; k < Nt; ++k) {
+      real sp = 0, su = 0;
+#pragma unroll
+      for (int kk = 0; kk < Nt; ++kk) {
+        sp += O.w.M[k * Nt + kk] * b[kk];
+        su += O.w.M[k * Nt + kk] * d[kk];
+      }
+      Ip += a[k] * sp;
+      Iu += cq[k] * su;
+    }
+    Ip *= Jf;
+    Iu *= Jf;
+    if (!bnd) {
+      const real tp = real(2) / (zM + zP);
+      gz = real(0.25) * tp * tp * Ip + real(0.25) * Iu;
+    } else {
+      gz = bc == 0 ? Ip / (zM * zM) : Iu;
+    }
+  }
+  // reduce the warps' partial sums in a fixed order
+  red[(w * 3 + 0) * kB + lane] = double(t1k);
+  red[(w * 3 + 1) * kB + lane] = double(t1r);
+  red[(w * 3 + 2) * kB + lane] = double(gz);
+  __syncthreads();
+  if (w == 0 && e < M.Kt) {
+    double sk = 0.0, sr = 0.0, sz = 0.0;
+    for (int ww = 0; ww < 4; ++ww) {
+      sk += red[(ww * 3 + 0) * kB + lane];
+      sr += red[(ww * 3 + 1) * kB + lane];
+      sz += red[(ww * 3 + 2) * kB + lane];
+    }
+    const double rho = 1.0 / double(irho);
+    gk[e] += dt * (sk + sz * double(zM) / (2.0 * double(kappa)));
+    gr[e] += dt * (sr + sz * double(zM) / (2.0 * rho));
+  }
 }
 
 }  // namespace REALNS

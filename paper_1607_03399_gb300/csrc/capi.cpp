@@ -72,6 +72,14 @@ int grad_f64(int N, const DevMesh<double>& m, const double* x, const double* q, 
              double* gk, double* gr, void* s) {
   DGW_SWITCH_N(N, launch_grad_f64, (m, x, q, r, dt, fl, bc, gk, gr, s))
 }
+int tgrad_f32(int N, const DevMesh<float>& m, const float* x, const float* q, const float* r, double dt, int fl, int bc,
+              double* gk, double* gr, void* s) {
+  DGW_SWITCH_N(N, launch_tgrad_f32, (m, x, q, r, dt, fl, bc, gk, gr, s))
+}
+int tgrad_f64(int N, const DevMesh<double>& m, const double* x, const double* q, const double* r, double dt, int fl,
+              int bc, double* gk, double* gr, void* s) {
+  DGW_SWITCH_N(N, launch_tgrad_f64, (m, x, q, r, dt, fl, bc, gk, gr, s))
+}
 }  // namespace
 
 namespace {
@@ -1529,10 +1537,18 @@ int dg_autotune(dg_ctx* c, int nrep, int* variant, double* us) {
 namespace {
 constexpr int kAdjFields = 14;
 enum { kAdjMuq = 0, kAdjX0 = 1, kAdjX1 = 2, kAdjRes = 3, kAdjQs = 4 /*4 buffers*/, kAdjScr = 8, kAdjRs = 9 /*5*/ };
+// FP64 gradient sums per device element: [d/dkappa wedges][d/drho wedges][d/dkappa tets][d/drho tets]
 size_t adj_grad_bytes(const dg_ctx* c) { return align256(size_t(nblk(vKw(c))) * kB * sizeof(double)); }
+size_t adj_tgrad_bytes(const dg_ctx* c) { return align256(size_t(nblk(vKt(c))) * kB * sizeof(double)); }
 void* adj_field(dg_ctx* c, int i) { return c->adj + size_t(i) * c->field_bytes; }
 double* adj_gk(dg_ctx* c) { return reinterpret_cast<double*>(c->adj + kAdjFields * c->field_bytes); }
 double* adj_gr(dg_ctx* c) { return reinterpret_cast<double*>(c->adj + kAdjFields * c->field_bytes + adj_grad_bytes(c)); }
+double* adj_tgk(dg_ctx* c) {
+  return reinterpret_cast<double*>(c->adj + kAdjFields * c->field_bytes + 2 * adj_grad_bytes(c));
+}
+double* adj_tgr(dg_ctx* c) {
+  return reinterpret_cast<double*>(c->adj + kAdjFields * c->field_bytes + 2 * adj_grad_bytes(c) + adj_tgrad_bytes(c));
+}
 }  // namespace
 
 int dg_sample(dg_ctx* c, void* d_out) {
@@ -1579,7 +1595,7 @@ int dg_adjoint_bytes(const dg_ctx* c, size_t* bytes) {
   if (!c) return DG_ERR_ARG;
   if (!bytes) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
-  *bytes = kAdjFields * field_bytes_of(c) + 2 * adj_grad_bytes(c);
+  *bytes = kAdjFields * field_bytes_of(c) + 2 * adj_grad_bytes(c) + 2 * adj_tgrad_bytes(c);
   return DG_OK;
 }
 
@@ -1587,7 +1603,6 @@ int dg_adjoint_bind(dg_ctx* c, void* d_work) {
   if (!c) return DG_ERR_ARG;
   if (!d_work) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_adjoint_bind before dg_bind");
-  if (!c->tets.empty()) return c->fail(DG_ERR_MESH, "the adjoint takes meshes of wedges only");
   c->adj = static_cast<unsigned char*>(d_work);
   return dg_adjoint_reset(c);
 }
@@ -1637,6 +1652,13 @@ int adjoint_reverse_stages(dg_ctx* c, double dt, const void* const* Q, const voi
       lr = grad_f32(c->N, c->m32, static_cast<const float*>(xin), static_cast<const float*>(Q[st]),
                     static_cast<const float*>(R[st]), dt, c->flux, c->bc, adj_gk(c), adj_gr(c), c->stream);
     if (lr) return cuda_fail(c, cudaError_t(lr), "gradient launch");
+    if (c->prec == DG_F64)
+      lr = tgrad_f64(c->N, c->m64, static_cast<const double*>(xin), static_cast<const double*>(Q[st]),
+                     static_cast<const double*>(R[st]), dt, c->flux, c->bc, adj_tgk(c), adj_tgr(c), c->stream);
+    else
+      lr = tgrad_f32(c->N, c->m32, static_cast<const float*>(xin), static_cast<const float*>(Q[st]),
+                     static_cast<const float*>(R[st]), dt, c->flux, c->bc, adj_tgk(c), adj_tgr(c), c->stream);
+    if (lr) return cuda_fail(c, cudaError_t(lr), "tet gradient launch");
     StageExtra x;
     x.g = kLSRK_A[st];
     x.no_sources = true;
@@ -1787,18 +1809,30 @@ int dg_adjoint_gradient(dg_ctx* c, double* g_kappa, double* g_rho) {
   if (!g_kappa || !g_rho) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_gradient before dg_adjoint_bind");
   const int64_t Kw = int64_t(c->wedges.size()), nv = nblk(vKw(c)) * kB;
-  std::vector<double> gk(nv), gr(nv);
+  const int64_t Kt = int64_t(c->tets.size()), nt = nblk(vKt(c)) * kB;
+  std::vector<double> gk(nv), gr(nv), tk(nt), tr(nt);
   cudaError_t e = cudaMemcpyAsync(gk.data(), adj_gk(c), nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(gr.data(), adj_gr(c), nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && nt > 0)
+    e = cudaMemcpyAsync(tk.data(), adj_tgk(c), nt * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && nt > 0)
+    e = cudaMemcpyAsync(tr.data(), adj_tgr(c), nt * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "gradient download");
   for (int64_t k = 0; k < c->K; ++k) g_kappa[k] = g_rho[k] = 0.0;
-  for (int64_t s = 0; s < c->shots; ++s)
+  // sum over shots in shot order, per element of either type
+  for (int64_t s = 0; s < c->shots; ++s) {
     for (int64_t w = 0; w < Kw; ++w) {
       const int64_t v = c->shot_inner ? w * c->shots + s : s * Kw + w;
       g_kappa[c->wedges[w]] += gk[v];
       g_rho[c->wedges[w]] += gr[v];
     }
+    for (int64_t t = 0; t < Kt; ++t) {
+      const int64_t v = c->shot_inner ? t * c->shots + s : s * Kt + t;
+      g_kappa[c->tets[t]] += tk[v];
+      g_rho[c->tets[t]] += tr[v];
+    }
+  }
   return check_device_error(c);
 }
 

@@ -157,7 +157,9 @@ enum : int { kErrTimeout = 1, kErrNonfinite = 2 };
   int launch_inject_##P##n##N(const DevMesh<T>& m, T* muq, T* x, const T* resid, int nshots, T b5,     \
                               void* stream);                                                       \
   int launch_grad_##P##n##N(const DevMesh<T>& m, const T* x, const T* q, const T* r, double dt, int flux, \
-                            int bc, double* gk, double* gr, void* stream);
+                            int bc, double* gk, double* gr, void* stream);                        \
+  int launch_tgrad_##P##n##N(const DevMesh<T>& m, const T* x, const T* q, const T* r, double dt, int flux, \
+                             int bc, double* gk, double* gr, void* stream);
 DGW_DECLARE_LAUNCHERS(f32, float, 1)
 DGW_DECLARE_LAUNCHERS(f32, float, 2)
 DGW_DECLARE_LAUNCHERS(f32, float, 3)

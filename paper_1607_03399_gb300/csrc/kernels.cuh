@@ -1226,6 +1226,8 @@ int prepare_n() {
     err = cudaFuncSetAttribute(k_pack<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, pack_smem_bytes<N>());
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_wedge_grad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, grad_smem_bytes<N>());
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_tet_grad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, tgrad_smem_bytes<N>());
   return int(err);
 }
 
@@ -1306,6 +1308,14 @@ int DGW_CAT(launch_grad_, REALNS)(const DevMesh<REAL>& m, const REAL* x, const R
     constexpr int bytes = REALNS::grad_smem_bytes<NORD>();
     REALNS::k_wedge_grad<NORD><<<m.nblk_w, 32 * (NORD + 1), bytes, cudaStream_t(stream)>>>(m, x, q, r, dt, flux, bc, gk,
                                                                                           gr);
+  }
+  return int(cudaGetLastError());
+}
+int DGW_CAT(launch_tgrad_, REALNS)(const DevMesh<REAL>& m, const REAL* x, const REAL* q, const REAL* r, double dt,
+                                   int flux, int bc, double* gk, double* gr, void* stream) {
+  if (m.nblk_t > 0) {
+    constexpr int bytes = REALNS::tgrad_smem_bytes<NORD>();
+    REALNS::k_tet_grad<NORD><<<m.nblk_t, 128, bytes, cudaStream_t(stream)>>>(m, x, q, r, dt, flux, bc, gk, gr);
   }
   return int(cudaGetLastError());
 }

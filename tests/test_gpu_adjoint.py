@@ -1,4 +1,4 @@
-"""The discrete adjoint on the GPU (wedge meshes): the adjoint step is the
+"""The discrete adjoint on the GPU (wedge and hybrid meshes): the adjoint step is the
 transpose of the forward step in the energy inner product (dot test, FP64),
 and the misfit gradient equals the oracle's reverse-mode gradient, central
 differences of the GPU misfit, and the torch.autograd path."""
@@ -20,10 +20,12 @@ from paper_1607_03399_gb300 import adjoint as AD  # noqa: E402
 from paper_1607_03399_gb300.dg import Solver  # noqa: E402
 
 
-@pytest.mark.parametrize("flux,bc", [("upwind", "rigid"), ("central", "rigid"), ("upwind", "dirichlet")])
-def test_adjoint_step_dot_product(flux, bc):
+@pytest.mark.parametrize("flux,bc,meshname", [("upwind", "rigid", "wedges"), ("central", "rigid", "wedges"),
+                                              ("upwind", "dirichlet", "wedges"), ("upwind", "rigid", "hybrid"),
+                                              ("central", "dirichlet", "hybrid")])
+def test_adjoint_step_dot_product(flux, bc, meshname):
     """<Phi v, W P mu_n> = <v, W P mu_{n-1}> for one step (mu = P W^{-1} lambda)."""
-    m = I.cube_wavy_mesh(3, 2, 0.05)
+    m = I.cube_wavy_mesh(3, 2, 0.05) if meshname == "wedges" else I.hybrid_mesh(2, 2, 1)
     c2, rho = I.random_material(m.K, 2, 1.0, 2.0, 0.7, 1.3)
     S = Solver(m.VX, m.EToV, m.etype, 2, c2, rho, precision="f64", flux=flux, bc=bc)
     O = Oracle(m.VX, m.EToV, m.etype, 2, c2, rho, flux=flux, bc=bc)
@@ -49,8 +51,8 @@ def test_adjoint_step_dot_product(flux, bc):
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
-def _problem(precision, ck=5):
-    m = I.cube_wavy_mesh(2, 1, 0.05)
+def _problem(precision, ck=5, meshname="wedges"):
+    m = I.cube_wavy_mesh(2, 1, 0.05) if meshname == "wedges" else I.hybrid_mesh(2, 1, 1)
     rng = np.random.default_rng(0)
     kap, rho = rng.uniform(1, 2, m.K), rng.uniform(0.8, 1.3, m.K)
     src = (0.4, 0.6, 0.5, 3.0, 0.2, 1.0)
@@ -73,8 +75,9 @@ def _gpu_gradient(pb, kap, rho, data):
 
 
 @pytest.mark.parametrize("precision,tol", [("f64", 1e-9), ("f32", 2e-3)])
-def test_gradient_matches_oracle_reverse_mode(precision, tol):
-    m, st, data, pb, kap, rho = _problem(precision)
+@pytest.mark.parametrize("meshname", ["wedges", "hybrid"])
+def test_gradient_matches_oracle_reverse_mode(precision, tol, meshname):
+    m, st, data, pb, kap, rho = _problem(precision, meshname=meshname)
     J, gk, gr = _gpu_gradient(pb, kap, rho, data)
     ok, orr = OA.gradient_reverse(st, data)
     assert abs(J - OA.misfit(st, data)) <= (1e-12 if precision == "f64" else 1e-4) * abs(J)

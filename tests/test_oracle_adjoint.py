@@ -33,14 +33,17 @@ def test_transpose_is_energy_weighted_velocity_flip(meshname, bc, flux):
     assert np.abs(A.T - A).max() > 1e-2 * np.abs(A).max()
 
 
-def test_oracle_reverse_gradient_matches_finite_differences():
-    m = I.cube_wavy_mesh(2, 1, 0.05)
+@pytest.mark.parametrize("meshname", ["wedges", "hybrid"])
+def test_oracle_reverse_gradient_matches_finite_differences(meshname):
+    m = I.cube_wavy_mesh(2, 1, 0.05) if meshname == "wedges" else I.hybrid_mesh(2, 1, 1)
     rng = np.random.default_rng(0)
     kap, rho = rng.uniform(1, 2, m.K), rng.uniform(0.8, 1.3, m.K)
     st = OA.Setup(m, 1, kap, rho, [(0.4, 0.6, 0.5, 3.0, 0.2, 1.0)], [(0.7, 0.3, 0.6), (0.2, 0.2, 0.3)], 0.02, 12)
     data = OA.traces(st) * 0.9 + 0.01
     gk, gr = OA.gradient_reverse(st, data)
-    fk, fr = OA.gradient_fd(st, data, [0, 3, 7])
-    for k in (0, 3, 7):
+    # wedges and, on the hybrid mesh, tets on both sides of the interface
+    picks = (0, 3, 7) if meshname == "wedges" else (0, 7, 8, 20, m.K - 1)
+    fk, fr = OA.gradient_fd(st, data, list(picks))
+    for k in picks:
         assert abs(gk[k] - fk[k]) <= 1e-6 * abs(fk[k])
         assert abs(gr[k] - fr[k]) <= 1e-6 * abs(fr[k])
