@@ -86,7 +86,9 @@ __host__ __device__ constexpr int grad_tri_warp(int N, int fb) {
   return N >= 4 ? 3 + fb : (N == 3 ? 3 : (N == 2 ? fb : 1));
 }
 
-template <int N>
+// TETS: the mesh has tets, so a triangle face may neighbour one (wedge-only
+// meshes take the instantiation without that branch)
+template <int N, bool TETS>
 __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 4 : 2) : (N <= 3 ? 2 : 1))
     k_wedge_grad(const DevMesh<real> M, const real* __restrict__ X,
                                                              const real* __restrict__ Q, const real* __restrict__ R,
@@ -130,7 +132,8 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
 #pragma unroll
   for (int f = 0; f < 5; ++f)
     zPf[f] = nbf[f] < 0 ? zM
-                        : ((f < 2 && (cdf[f] & kCodeTet)) ? M.t_mat[2 * M.Kt_pad + nbf[f]] : M.w_mat[2 * Kp + nbf[f]]);
+                        : ((TETS && f < 2 && (cdf[f] & kCodeTet)) ? M.t_mat[2 * M.Kt_pad + nbf[f]]
+                                                                   : M.w_mat[2 * Kp + nbf[f]]);
   __syncthreads();
   if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0)) && lane == 0) atomicOr(failed, 1);
   __syncthreads();
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
       const real zP = fb ? zPf[1] : zPf[0];
       // the neighbour across a triangle face: a wedge (its bottom or top slice) or,
       // at the wedge/tet interface, a tet (one of its faces)
-      const bool ntet = nbr >= 0 && (code & kCodeTet) != 0;
+      const bool ntet = TETS && nbr >= 0 && (code & kCodeTet) != 0;
       const int own0 = fb ? N * Nt : 0, nf = (code >> 4) & 3;
       auto nbt = [&](const real* glob, int k) {
         const int nk = O.tab.tri_perm[code & 15][k];

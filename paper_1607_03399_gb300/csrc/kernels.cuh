@@ -1225,7 +1225,9 @@ int prepare_n() {
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_pack<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, pack_smem_bytes<N>());
   if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(k_wedge_grad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, grad_smem_bytes<N>());
+    err = cudaFuncSetAttribute(k_wedge_grad<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, grad_smem_bytes<N>());
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_wedge_grad<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, grad_smem_bytes<N>());
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_tet_grad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, tgrad_smem_bytes<N>());
   return int(err);
@@ -1306,8 +1308,12 @@ int DGW_CAT(launch_grad_, REALNS)(const DevMesh<REAL>& m, const REAL* x, const R
                                   int flux, int bc, double* gk, double* gr, void* stream) {
   if (m.nblk_w > 0) {
     constexpr int bytes = REALNS::grad_smem_bytes<NORD>();
-    REALNS::k_wedge_grad<NORD><<<m.nblk_w, 32 * (NORD + 1), bytes, cudaStream_t(stream)>>>(m, x, q, r, dt, flux, bc, gk,
-                                                                                          gr);
+    if (m.nblk_t > 0)
+      REALNS::k_wedge_grad<NORD, true><<<m.nblk_w, 32 * (NORD + 1), bytes, cudaStream_t(stream)>>>(m, x, q, r, dt, flux,
+                                                                                                  bc, gk, gr);
+    else
+      REALNS::k_wedge_grad<NORD, false><<<m.nblk_w, 32 * (NORD + 1), bytes, cudaStream_t(stream)>>>(m, x, q, r, dt, flux,
+                                                                                                   bc, gk, gr);
   }
   return int(cudaGetLastError());
 }
