@@ -238,6 +238,24 @@ def test_empty_mesh_and_table_limits():
         dg.dg_destroy(ctx)
 
 
+def test_adjoint_workspace_size():
+    """dg_adjoint_bytes: fourteen packed fields plus the FP64 gradient sums of every
+    device element (wedges and tets, padded blocks), computable before dg_bind."""
+    m = I.hybrid_mesh(3, 2, 1)
+    ctx = dg.dg_mesh_create(m.VX, m.EToV, m.etype)
+    try:
+        _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_adjoint_bytes(ctx))
+        dg.dg_set_order(ctx, 2)
+        dg.dg_set_shots(ctx, 3)
+        _, fb = dg.dg_device_bytes(ctx)
+        nw, nt = int((m.etype == 6).sum()) * 3, int((m.etype == 4).sum()) * 3
+        def pad(n):
+            return (n + 31) // 32 * 32 * 8 + 255 & ~255
+        assert dg.dg_adjoint_bytes(ctx) == 14 * fb + 2 * pad(nw) + 2 * pad(nt)
+    finally:
+        dg.dg_destroy(ctx)
+
+
 def test_merge_meshes_keeps_pieces_apart():
     a, b = I.cube_wavy_mesh(2, 2, 0.02), I.hybrid_mesh(2, 1, 1)
     m = I.merge_meshes([a, b])
