@@ -120,9 +120,9 @@ def test_autograd_function():
     assert np.allclose(rh.grad.numpy(), grho, rtol=1e-10, atol=0)
 
 
-@pytest.mark.parametrize("order", ["outer", "inner"])
-def test_shots_sum_their_gradients(order):
-    m = I.cube_wavy_mesh(3, 2, 0.03)
+@pytest.mark.parametrize("order,meshname", [("outer", "wedges"), ("inner", "wedges"), ("inner", "hybrid")])
+def test_shots_sum_their_gradients(order, meshname):
+    m = I.cube_wavy_mesh(3, 2, 0.03) if meshname == "wedges" else I.hybrid_mesh(2, 2, 1)
     c2, rho = I.random_material(m.K, 11, 1.0, 2.0, 0.8, 1.2)
     recs = [(0.2, 0.7, 0.8), (0.6, 0.4, 0.2), (0.8, 0.8, 0.5)]
     srcs = [(0, 0.3, 0.3, 0.4, 4.0, 0.25, 1.0), (1, 0.7, 0.6, 0.6, 5.0, 0.2, -0.5)]
