@@ -76,19 +76,58 @@ def _mesh(ntri=128, nlayers=16, order="column"):
     return m, c2, rho
 
 
-def _alg_bytes_per_stage(K, nverts, total_nodes, real_bytes=4, N=3, mass="stored"):
-    """Minimum HBM bytes one fused stage must move: read q, read res, write
-    res, write q (4 reals per field-DOF); per wedge 12 vertex coordinates,
-    5 neighbour ids and 5 orientation codes (int32) and 3 material reals;
-    in the stored mode the mass factor (Nt (Nt + 1) / 2 reals), otherwise
-    the 6 vertex ids and 3 coordinates per vertex the in-stage
-    factorisation gathers."""
+def _alg_bytes_per_stage(K, total_nodes, real_bytes=4):
+    """The method's minimum HBM bytes for one fused stage: read q, read res,
+    write res, write q (4 reals per field-DOF, 16 B in FP32) plus about 64 B
+    per element of geometry, topology and material (vertex gather ~12 B
+    amortised, 6 vertex ids 24 B, 5 neighbour ids 20 B, 2 material reals 8 B):
+    16.40 B per field-DOF at N = 3, 16.21 B at N = 4 in FP32."""
+    return 4 * real_bytes * (4 * total_nodes) + 64 * K
+
+
+def _kernel_bytes_per_stage(K, nverts, total_nodes, real_bytes=4, N=3, mass="stored"):
+    """What this kernel design reads and writes at least (above the method's
+    minimum: its own choices): the state as above; per wedge 12 vertex
+    coordinates, 5 neighbour ids and 5 orientation codes (int32) and 3
+    material reals; in the stored mode the mass factor (Nt (Nt + 1) / 2
+    reals), otherwise the 6 vertex ids and 3 coordinates per vertex the
+    in-stage factorisation gathers."""
     dof = 4 * total_nodes
     nt = (N + 1) * (N + 2) // 2
     per_wedge = 10 * 4 + (12 + 3) * real_bytes
     if mass == "stored":
         return 4 * real_bytes * dof + K * (per_wedge + nt * (nt + 1) // 2 * real_bytes)
     return 4 * real_bytes * dof + K * (per_wedge + 6 * 4) + nverts * 3 * real_bytes
+
+
+def _flops_per_wedge(N, mass="stored"):
+    """Arithmetic of one wedge in one stage as the stage kernel performs it
+    (an FMA counts 2), per slice j of the N + 1 slices: D_t on 4 fields
+    (8 Nt Nq), the t-part and triangle-lift assembly (28 Nt), M^tri on 4
+    vectors (8 Nt^2), the two triangular solves with 4 right-hand sides
+    (8 Nt (Nt - 1) + 16 Nt), the strong D_r / D_s part (8 Nt^2 + 16 Nt), the
+    three quadrilateral faces (fluxes 18 Nq, edge masses 8 Nq^2 each), the
+    triangle-face fluxes (15 per node, 2 Nt / Nq nodes per slice) and the
+    fused update (24 Nt); plus about 150 flops of geometry per wedge and, with
+    the factor computed in the stage, the Cholesky factorisation
+    (Nt^3 / 3 + 3 Nt^2 per wedge)."""
+    nt, nq = (N + 1) * (N + 2) // 2, N + 1
+    per_slice = (8 * nt * nq + 28 * nt + 8 * nt * nt + 8 * nt * (nt - 1) + 16 * nt + 8 * nt * nt + 16 * nt
+                 + 3 * (18 * nq + 8 * nq * nq) + 15 * 2 * nt / nq + 24 * nt)
+    f = nq * per_slice + 150
+    if mass != "stored":
+        f += nt ** 3 / 3 + 3 * nt * nt
+    return f
+
+
+def _fma_peaks():
+    """Measured FP32 and FP64 CUDA-core FMA throughput (TFLOP/s) of this GPU."""
+    from paper_1607_03399_gb300 import dg as _dg
+    try:
+        return {"fp32_tflops": _dg.dg_fma_peak(_dg.DG_F32), "fp64_tflops": _dg.dg_fma_peak(_dg.DG_F64),
+                "how": "dg_fma_peak: independent FMA chains on every SM, one launch timed by CUDA events"}
+    except Exception as e:  # pragma: no cover - reported, not fatal
+        return {"fp32_tflops": None, "fp64_tflops": None, "error": str(e)}
 
 
 class Clocks:
@@ -137,11 +176,22 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def _blas_threads():
+    """BLAS / OpenMP thread count numpy would use in a fresh process."""
+    try:
+        from threadpoolctl import threadpool_info
+        return sum(d.get("num_threads", 0) for d in threadpool_info()) or None
+    except Exception:
+        return None
+
+
 def _cpu_baseline(kind_steps: int = 2):
-    """Oracle on the host cores, on a bounded sample of the same recipe, in a
-    fresh single-threaded process."""
+    """Oracle on the host cores, on a bounded sample of the same recipe, in
+    fresh processes: once restricted to one thread and once with every core
+    allowed to the BLAS / OpenMP runtimes (the oracle's einsum contractions
+    are numpy loops, so extra cores barely help; the figures show it)."""
     code = f"""
-import sys, time, json
+import sys, time, json, os
 sys.path.insert(0, {ROOT!r})
 import numpy as np
 from oracle.dg import Solver
@@ -155,15 +205,26 @@ q = S.step(q, dt, 1)
 t = time.perf_counter()
 q = S.step(q, dt, {kind_steps})
 el = time.perf_counter() - t
-print(json.dumps({{"dof": 4 * S.conn.total_nodes, "K": S.K, "sec": el, "steps": {kind_steps}}}))
+try:
+    from threadpoolctl import threadpool_info
+    blas = sum(d.get("num_threads", 0) for d in threadpool_info())
+except Exception:
+    blas = None
+print(json.dumps({{"dof": 4 * S.conn.total_nodes, "K": S.K, "sec": el, "steps": {kind_steps}, "blas_threads": blas}}))
 """
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    v = d["dof"] * 5 * d["steps"] / d["sec"] / 1e9
-    return {"value": v, "unit": "GDOF-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{d['steps']} LSRK45 steps (5 stages each) of the FP64 NumPy oracle on {d['K']} wedges "
-                      f"(2x16x16 footprint x 16 bumpy layers, same recipe), N=3"}
+    ncpu = os.cpu_count() or 1
+    runs = {}
+    for label, nth in (("one_core", 1), ("all_cores", ncpu)):
+        env = dict(os.environ, OMP_NUM_THREADS=str(nth), OPENBLAS_NUM_THREADS=str(nth), MKL_NUM_THREADS=str(nth))
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        runs[label] = {"value": d["dof"] * 5 * d["steps"] / d["sec"] / 1e9, "threads": nth,
+                       "blas_threads": d.get("blas_threads"), "sec": d["sec"]}
+    d1 = runs["one_core"]
+    return {"value": d1["value"], "unit": "GDOF-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{kind_steps} LSRK45 steps (5 stages each) of the FP64 NumPy oracle on 8192 wedges "
+                      f"(2x16x16 footprint x 16 bumpy layers, same recipe), N=3",
+            "os_cpu_count": ncpu, "one_core": d1, "all_cores": runs["all_cores"]}
 
 
 def run_reference(args, rank, world):
@@ -247,15 +308,16 @@ def measure_order(N, args, torch, dev, m, c2, rho, mass, barrier=None):
     return res
 
 
-def measure_hybrid(args, torch, dev):
+def measure_hybrid(args, torch, dev, tet_layers=4):
     """Hybrid wedge + tet workload: 2x96x96 footprint, 12 bumpy wedge layers under
-    4 flat layers of prisms split into 3 tets each, N=3, FP32, c^2 from c ~ U[1,3]
+    4 flat layers of prisms split into 3 tets each (221184 tets; tet_layers=6
+    gives the 331776-tet variant), N=3, FP32, c^2 from c ~ U[1,3]
     per element, rho = 1, Gaussian pressure pulse (width 0.05) at the centre,
     rigid walls, upwind.  The whole stage is timed by graph replay of LSRK45 steps,
     each element type's stage kernel separately by dg_stage_times."""
     from paper_1607_03399_gb300 import inputs as I
     from paper_1607_03399_gb300.dg import Solver
-    m = I.hybrid_mesh(96, 12, 4)
+    m = I.hybrid_mesh(96, 12, tet_layers)
     c2, rho = I.random_material(m.K, 3, 1.0, 3.0)
     S = Solver(m.VX, m.EToV, m.etype, 3, c2, rho, precision="f32", device=str(dev))
     q = I.gaussian_pulse(S.node_coords(), (0.5, 0.5, 0.5), 0.05).astype(np.float32)
@@ -279,12 +341,50 @@ def measure_hybrid(args, torch, dev):
     peak, _ = _peaks()
     # tet algorithmic bytes: 16 B per field-DOF, per tet 4 vertex ids, 4 neighbour ids and codes, 3 material reals
     tet_bytes = 16 * dof_t + Kt * (4 * 4 + 8 * 4 + 3 * 4)
-    return {"workload": "hybrid_2x96x96_12wedge_4tet_layers_N3", "wedges": Kw, "tets": Kt,
+    return {"workload": f"hybrid_2x96x96_12wedge_{tet_layers}tet_layers_N3", "wedges": Kw, "tets": Kt,
             "field_dof": dof_w + dof_t, "steps": nsteps, "stage_us": st * 1e6,
             "value": (dof_w + dof_t) / st / 1e9, "unit": "GDOF-updates/s",
             "wedge_stage_us": tw, "wedge_gdofs": dof_w / (tw * 1e-6) / 1e9,
             "tet_stage_us": tt, "tet_gdofs": dof_t / (tt * 1e-6) / 1e9,
             "tet_alg_bytes": tet_bytes, "tet_frac": tet_bytes / (tt * 1e-6) / 1e9 / peak}
+
+
+def measure_config1(args, torch, dev):
+    """The FP64 accuracy case: 128-wedge wavy unit cube (4x4 squares split into
+    32 right triangles, 4 layers, interfaces z_k = k/4 + 0.03 sin 2 pi x
+    sin 2 pi y), N=3, c = rho = 1, rigid walls, upwind, the standing mode
+    p = cos(pi x) cos(pi y) cos(pi z) as initial data, 200 LSRK45 steps at
+    CFL 0.5.  Reports the energy every 20 steps and the final L2 error against
+    the exact solution's nodal interpolant, measured in the scheme's exact mass
+    norm: with c = rho = 1 the discrete energy of the difference state is half
+    its squared L2 norm, so ||e|| = sqrt(2 E(q - q_exact)) through
+    dg_energy_static (full state, and pressure only)."""
+    from paper_1607_03399_gb300 import dg as _dg
+    from paper_1607_03399_gb300 import inputs as I
+    from paper_1607_03399_gb300.dg import Solver
+    m = I.cube_wavy_mesh(4, 4, 0.03)
+    S = Solver(m.VX, m.EToV, m.etype, 3, precision="f64", device=str(dev))
+    xyz = S.node_coords()
+    q0 = I.standing_mode_unit_cube(xyz, 0.0)
+    dt = S.stable_dt(0.5)
+    S.set_fields(q0)
+    hist = [S.energy()]
+    for _ in range(10):
+        S.step(dt, 20)
+        hist.append(S.energy())
+    q = S.get_fields()
+    T = S.time()
+    d = q - I.standing_mode_unit_cube(xyz, T)
+    dd = torch.from_numpy(np.ascontiguousarray(d)).to(dev)
+    dp = dd.clone()
+    dp[1:] = 0
+    torch.cuda.synchronize(dev)
+    err = np.sqrt(2.0 * _dg.dg_energy_static(S.ctx, dd.data_ptr()))
+    err_p = np.sqrt(2.0 * _dg.dg_energy_static(S.ctx, dp.data_ptr()))
+    S.close()
+    return {"workload": "wavy_cube_4x4x4_128wedges_N3_fp64_standing_mode", "steps": 200, "dt": dt, "t_final": T,
+            "l2_error": float(err), "l2_error_p": float(err_p),
+            "energy_every_20_steps": hist, "energy_non_increasing": bool(np.all(np.diff(hist) <= 1e-14 * hist[0]))}
 
 
 def measure_multishot(args, torch, dev):
@@ -565,6 +665,8 @@ def run_ours(args, rank, world):
         r["solver"].close()
         r["solver"] = None
     hybrid = measure_hybrid(args, torch, dev) if (rank == 0 and not args.no_hybrid) else None
+    hybrid6 = measure_hybrid(args, torch, dev, tet_layers=6) if (rank == 0 and not args.no_hybrid) else None
+    config1 = measure_config1(args, torch, dev) if rank == 0 else None
     multishot = measure_multishot(args, torch, dev) if (rank == 0 and not args.no_batched) else None
     multimesh = measure_multimesh(args, torch, dev) if (rank == 0 and not args.no_batched) else None
     adjoint = measure_adjoint(args, torch, dev) if (rank == 0 and not args.no_adjoint) else None
@@ -582,29 +684,44 @@ def run_ours(args, rank, world):
             dist.destroy_process_group()
         return
     peak, peak_kind = _peaks()
+    fma = _fma_peaks()
+    fp32_peak = fma.get("fp32_tflops")
     r3 = out[orders[0]]
     K, nverts = m.K, m.VX.shape[0]
     ms_step = r3["ms_max"] / args.steps
     value = _gdofs(r3["dof"], 5 * args.steps, r3["ms_max"] / 1e3, world)
     stage_s = r3["ms"] / 1e3 / (5 * args.steps)
-    alg = _alg_bytes_per_stage(K, nverts, r3["dof"] // 4, N=orders[0], mass=args.mass)
+    alg = _alg_bytes_per_stage(K, r3["dof"] // 4)
+    kbytes = _kernel_bytes_per_stage(K, nverts, r3["dof"] // 4, N=orders[0], mass=args.mass)
     achieved = alg / stage_s / 1e9
+
+    def flop_rate(N, mode, st):
+        tf = _flops_per_wedge(N, mode) * K / st / 1e12
+        return {"tflops": tf, "fp32_peak_tflops": fp32_peak, "frac_fp32": tf / fp32_peak if fp32_peak else None,
+                "flops_per_field_dof": _flops_per_wedge(N, mode) / (4 * (N + 1) ** 2 * (N + 2) / 2)}
+
     by_order = {}
     for N, r in out.items():
         st = r["ms"] / 1e3 / (5 * args.steps)
-        a = _alg_bytes_per_stage(K, nverts, r["dof"] // 4, N=N, mass=args.mass)
+        a = _alg_bytes_per_stage(K, r["dof"] // 4)
+        kb = _kernel_bytes_per_stage(K, nverts, r["dof"] // 4, N=N, mass=args.mass)
         by_order[str(N)] = {"autotune": r["autotune"],
                             "value": _gdofs(r["dof"], 5 * args.steps, r["ms_max"] / 1e3, world),
                             "ms_per_step": r["ms_max"] / args.steps, "stage_us": st * 1e6,
                             "alg_bytes_per_stage": a, "achieved_gbs": a / st / 1e9,
-                            "frac": a / st / 1e9 / peak, "dof": r["dof"]}
+                            "frac": a / st / 1e9 / peak, "kernel_bytes_per_stage": kb,
+                            "kernel_bytes_frac": kb / st / 1e9 / peak, "dof": r["dof"],
+                            "alu": flop_rate(N, args.mass, st)}
     by_mass = {}
     if alt is not None:
         for mode, r in ((args.mass, r3), (other, alt)):
             st = r["ms"] / 1e3 / (5 * args.steps)
-            a = _alg_bytes_per_stage(K, nverts, r["dof"] // 4, N=orders[0], mass=mode)
+            a = _alg_bytes_per_stage(K, r["dof"] // 4)
+            kb = _kernel_bytes_per_stage(K, nverts, r["dof"] // 4, N=orders[0], mass=mode)
             by_mass[mode] = {"value": _gdofs(r["dof"], 5 * args.steps, r["ms_max"] / 1e3, world), "stage_us": st * 1e6,
-                             "alg_bytes_per_stage": a, "frac": a / st / 1e9 / peak}
+                             "alg_bytes_per_stage": a, "frac": a / st / 1e9 / peak,
+                             "kernel_bytes_per_stage": kb, "kernel_bytes_frac": kb / st / 1e9 / peak,
+                             "alu": flop_rate(orders[0], mode, st)}
     cpu = _cpu_baseline() if (world == 1 and not args.no_cpu) else None
     line = {
         "metric": METRIC, "value": value, "unit": "GDOF-updates/s", "n_gpus": world, "steps": args.steps,
@@ -619,7 +736,16 @@ def run_ours(args, rank, world):
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": _traffic_per_launch(args.mass) if (args.workload == "full" and orders[0] == 3
                                                                    and args.element_order == "column") else None,
-                     "alg_bytes_per_launch": alg},
+                     "alg_bytes_per_launch": alg,
+                     "alg_bytes": "the method's minimum: 16 B per field-DOF (read q and res, write res and q) "
+                                  "+ 64 B per wedge of mesh data",
+                     "kernel_bytes_per_launch": kbytes,
+                     "kernel_bytes": "what this kernel must move: the state as above, 100 B of mesh tables per "
+                                     "wedge and the stored mass factor (overhead above the method's minimum)",
+                     "alu": by_order[str(orders[0])]["alu"]},
+        "fma_peaks": fma,
+        "config1": config1,
+        "hybrid6": hybrid6,
         "by_order": by_order,
         "by_mass": by_mass or None,
         "hybrid": hybrid,

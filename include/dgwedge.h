@@ -100,7 +100,10 @@ int dg_mesh_create(dg_ctx** out, int64_t nverts, const double* VX, int64_t nelem
  * Section 4.2) and the face-node orientation maps. */
 int dg_set_order(dg_ctx* ctx, int N);
 
-/* Per-element c^2 and rho (host arrays of length nelem, copied; both > 0).
+/* Per-element c^2 and rho (host arrays of length nelem, copied; both > 0),
+ * the piecewise-constant coefficients of the acoustic system (Section 2:
+ * kappa = rho c^2 multiplies the pressure equation, 1/rho the velocity
+ * equations, and the upwind penalties use the impedance rho c).
  * Default: c^2 = rho = 1. */
 int dg_set_material(dg_ctx* ctx, const double* c2, const double* rho);
 
@@ -162,6 +165,7 @@ int dg_set_options(dg_ctx* ctx, int bc, int flux, int precision);
  * Before dg_bind.  Errors: DG_ERR_ARG (unknown mode), DG_ERR_STATE. */
 int dg_set_mass_mode(dg_ctx* ctx, int mode);
 
+
 /* Node counts: total wedge nodes and total tet nodes; the canonical layout
  * holds wedge_nodes + tet_nodes nodes. */
 int dg_num_nodes(const dg_ctx* ctx, int64_t* wedge_nodes, int64_t* tet_nodes);
@@ -197,7 +201,9 @@ int dg_device_bytes(const dg_ctx* ctx, size_t* mesh_bytes, size_t* field_bytes);
  * (NULL = legacy default stream), upload the mesh blob and operator tables,
  * and zero the state.  q0/q1 are the two state buffers the Runge-Kutta stages
  * alternate between, res the low-storage residual.  The current device must be
- * the one that owns the buffers. */
+ * the one that owns the buffers; dg_bind records it, and every later call that
+ * issues GPU work makes that device current for its duration and restores the
+ * caller's current device before returning. */
 int dg_bind(dg_ctx* ctx, void* d_mesh, void* d_q0, void* d_q1, void* d_res, void* stream);
 
 /* Set / read the state in the canonical layout ([4][total_nodes] of float or
@@ -219,7 +225,11 @@ int dg_get_fields(dg_ctx* ctx, void* q, int on_device);
 int dg_rhs(dg_ctx* ctx, const void* d_q, void* d_rhs);
 
 /* Advance the bound state by nsteps LSRK45 steps of size dt (dt > 0,
- * nsteps >= 0).  One fused kernel per element type per stage, replayed from
+ * nsteps >= 0): the five-stage, two-register low-storage Runge-Kutta scheme
+ * of Carpenter and Kennedy (1994), the explicit integrator family of the
+ * paper's experiments (Section 6.2; the paper itself runs multirate AB3),
+ * res <- a_s res + dt rhs(q, t_n + c_s dt), q <- q + b_s res per stage.
+ * One fused kernel per element type per stage, replayed from
  * a CUDA graph.  Asynchronous; launch errors are returned, device-side errors
  * (bounded waits) surface at the next synchronising call. */
 int dg_step(dg_ctx* ctx, double dt, int64_t nsteps);
@@ -344,24 +354,40 @@ int dg_energy(dg_ctx* ctx, double* E);
  * in the paper; a service for callers that cannot allocate device memory at
  * the point of the call -- code running while a framework forbids
  * allocations, inside host callbacks, or with a locked memory pool).
- *   d_q  device pointer, canonical layout [4][total_nodes] of the context's
- *        precision (any state, not only the bound one); not modified.
- *   E    host pointer; receives the energy (same definition as dg_energy).
+ *   d_q  device pointer, canonical layout [shots][4][total_nodes] of the
+ *        context's precision (as dg_save_state writes it; any state, not only
+ *        the bound one); not modified.
+ *   E    host pointer; receives the energy (same definition as dg_energy),
+ *        summed over the shots.
  * The per-block partial sums live in a file-scope device array of 65536
  * doubles plus one total (512 KB, resident on every GPU that loads the
- * library until exit), so meshes of at most 65536 * 128 = 8388608 elements
- * are accepted; larger ones return DG_ERR_ARG.  No cudaMalloc, cudaFree or
- * allocating library routine is called.  The first call on a device looks up
- * the array's device address (with that device current); make that first
- * call before any stream capture.  All calls share the array: calls that
- * overlap on the GPU (other streams, other contexts) race; each call fully
- * rewrites the partials it sums.  Synchronises the bound stream.
+ * library until exit), so at most 65536 * 128 = 8388608 elements (wedges
+ * and tets of all shots) are accepted; more return DG_ERR_ARG.  No
+ * cudaMalloc, cudaFree or allocating library routine is called.  The call
+ * runs on the device bound by dg_bind (made current for the call, the
+ * caller's device restored afterwards).  The first call on a device looks up
+ * the array's device address; make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (other
+ * streams, other contexts) race; each call fully rewrites the partials it
+ * sums.  Synchronises the bound stream.
  * Errors: DG_ERR_ARG, DG_ERR_STATE (before dg_bind), DG_ERR_CUDA,
- * DG_ERR_NONFINITE. */
+ * DG_ERR_NONFINITE, and DG_ERR_TIMEOUT if a device-side wait had run out
+ * since the last check (as dg_energy). */
 int dg_energy_static(dg_ctx* ctx, const void* d_q, double* E);
 
 /* Synchronise the bound stream and report pending device-side errors. */
 int dg_sync(dg_ctx* ctx);
+
+/* Failure-path check of the bounded device-side waits (no counterpart in the
+ * paper).  Enqueues on the bound stream one kernel that arms an mbarrier for
+ * bytes no copy will deliver and waits on it with the stages' bounded wait
+ * (a 64-poll budget instead of the stages' ~1 s), so the wait runs out, the
+ * kernel sets the timeout bit of the device error word and returns -- what a
+ * stage does when one of its bulk copies never lands.  Nothing faults or
+ * hangs and the context stays usable: the next synchronising call (dg_sync,
+ * dg_energy, ...) returns DG_ERR_TIMEOUT and clears the word.  Asynchronous.
+ * Errors: DG_ERR_STATE (before dg_bind), DG_ERR_CUDA. */
+int dg_expire_wait(dg_ctx* ctx);
 
 /* Simulation time of the bound state (sum of dt over completed steps). */
 int dg_time(const dg_ctx* ctx, double* t);
@@ -370,6 +396,15 @@ int dg_time(const dg_ctx* ctx, double* t);
  * The paper bounds dt by trace and Markov constants without printing them
  * (Section 6); this is the library's explicit form of that bound. */
 int dg_stable_dt(const dg_ctx* ctx, double cfl, double* dt);
+
+/* Measured CUDA-core fused multiply-add throughput of the current device in
+ * TFLOP/s (2 flops per FMA), precision DG_F32 or DG_F64 (no counterpart in
+ * the paper: the arithmetic roofline that the stage kernels' flop rates are
+ * reported against).  Runs a warm-up and one timed launch of independent FMA
+ * chains on every SM, on `stream` (a cudaStream_t, NULL = legacy default),
+ * timed with CUDA events; synchronous, about 10 ms.  Needs no context.
+ * Errors: DG_ERR_ARG (null output, unknown precision), DG_ERR_CUDA. */
+int dg_fma_peak(int precision, void* stream, double* tflops);
 
 const char* dg_last_error(const dg_ctx* ctx);
 void dg_destroy(dg_ctx* ctx);

@@ -51,6 +51,8 @@ int pack_f64(int N, const DevMesh<double>& m, const double* c, double* p, bool u
 int energy_f32(int N, const DevMesh<float>& m, const float* q, void* s) { DGW_SWITCH_N(N, launch_energy_f32, (m, q, s)) }
 int clock_f32(int N, double* c, double dt, void* s) { DGW_SWITCH_N(N, launch_clock_f32, (c, dt, s)) }
 int clock_f64(int N, double* c, double dt, void* s) { DGW_SWITCH_N(N, launch_clock_f64, (c, dt, s)) }
+int wait_expire_f32(int N, int* e, void* s) { DGW_SWITCH_N(N, launch_wait_expire_f32, (e, s)) }
+int wait_expire_f64(int N, int* e, void* s) { DGW_SWITCH_N(N, launch_wait_expire_f64, (e, s)) }
 int energy_f64(int N, const DevMesh<double>& m, const double* q, void* s) { DGW_SWITCH_N(N, launch_energy_f64, (m, q, s)) }
 int sample_f32(int N, const DevMesh<float>& m, const float* q, float* o, int ns, void* s) {
   DGW_SWITCH_N(N, launch_sample_f32, (m, q, o, ns, s))
@@ -773,6 +775,28 @@ int check_device_error(dg_ctx* c) {
   return DG_OK;
 }
 
+// Makes the bound context's device current for the duration of an entry
+// point and restores the caller's device afterwards, so work, symbol lookups
+// and stream operations always address the device whose memory was bound.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(const dg_ctx* c) {
+    if (!c->bound) return;
+    int cur = -1;
+    err = cudaGetDevice(&cur);
+    if (err == cudaSuccess && cur != c->device) {
+      err = cudaSetDevice(c->device);
+      if (err == cudaSuccess) prev = cur;
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 void drop_graphs(dg_ctx* c) {
   for (int i = 0; i < 2; ++i) {
     if (c->gexec[i]) cudaGraphExecDestroy(c->gexec[i]);
@@ -1331,6 +1355,8 @@ int dg_set_fields(dg_ctx* c, const void* q, int on_device) {
   if (!c) return DG_ERR_ARG;
   if (!q) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_set_fields before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   int rc = ensure_ops(c);
   if (rc) return rc;
   const size_t rs = c->prec == DG_F64 ? 8 : 4;
@@ -1363,6 +1389,8 @@ int dg_get_fields(dg_ctx* c, void* q, int on_device) {
   if (!c) return DG_ERR_ARG;
   if (!q) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_get_fields before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   int rc = ensure_ops(c);  // also opts the pack kernel in to its shared memory
   if (rc) return rc;
   const size_t rs = c->prec == DG_F64 ? 8 : 4;
@@ -1383,6 +1411,8 @@ int dg_rhs(dg_ctx* c, const void* d_q, void* d_rhs) {
   if (!c) return DG_ERR_ARG;
   if (!d_q || !d_rhs) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_rhs before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   int rc = ensure_ops(c);
   if (rc) return rc;
   void* A = c->d_q[1 - c->cur];
@@ -1402,6 +1432,8 @@ int dg_rhs(dg_ctx* c, const void* d_q, void* d_rhs) {
 int dg_step(dg_ctx* c, double dt, int64_t nsteps) {
   if (!c) return DG_ERR_ARG;
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_step before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   if (!(dt > 0) || nsteps < 0) return c->fail(DG_ERR_ARG, "dt must be positive and nsteps >= 0");
   int rc = ensure_ops(c);
   if (rc) return rc;
@@ -1450,6 +1482,8 @@ int dg_stage_times(dg_ctx* c, int nrep, double* us_w, double* us_t) {
   if (!c) return DG_ERR_ARG;
   if (nrep < 1 || !us_w || !us_t) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_stage_times before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   int rc = ensure_ops(c);
   if (rc) return rc;
   *us_w = *us_t = 0.0;
@@ -1496,6 +1530,8 @@ int dg_autotune(dg_ctx* c, int nrep, int* variant, double* us) {
   if (!c) return DG_ERR_ARG;
   if (nrep < 1 || !variant || !us) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_autotune before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   // candidates: (factor recomputed in the stage?, wedge blocks per CTA)
   std::vector<std::pair<bool, int>> cand;
   const int maxb = (c->prec == DG_F32 && c->N == 3) ? 2 : 1;
@@ -1555,6 +1591,8 @@ int dg_sample(dg_ctx* c, void* d_out) {
   if (!c) return DG_ERR_ARG;
   if (!d_out) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_sample before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   int rc = ensure_ops(c);
   if (rc) return rc;
   if (c->prec == DG_F64)
@@ -1571,6 +1609,8 @@ int dg_save_state(dg_ctx* c, void* d_dst) {
   if (!c) return DG_ERR_ARG;
   if (!d_dst) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_save_state before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   cudaError_t e = cudaMemcpyAsync(d_dst, c->d_q[c->cur], c->field_bytes, cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "state save");
   return DG_OK;
@@ -1580,6 +1620,8 @@ int dg_load_state(dg_ctx* c, const void* d_src, double t) {
   if (!c) return DG_ERR_ARG;
   if (!d_src || !std::isfinite(t)) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_load_state before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   cudaError_t e = cudaMemcpyAsync(c->d_q[c->cur], d_src, c->field_bytes, cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "state load");
   c->t = t;
@@ -1603,6 +1645,8 @@ int dg_adjoint_bind(dg_ctx* c, void* d_work) {
   if (!c) return DG_ERR_ARG;
   if (!d_work) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_adjoint_bind before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   c->adj = static_cast<unsigned char*>(d_work);
   return dg_adjoint_reset(c);
 }
@@ -1610,6 +1654,8 @@ int dg_adjoint_bind(dg_ctx* c, void* d_work) {
 int dg_adjoint_reset(dg_ctx* c) {
   if (!c) return DG_ERR_ARG;
   if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_reset before dg_adjoint_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   size_t bytes = 0;
   dg_adjoint_bytes(c, &bytes);
   cudaError_t e = cudaMemsetAsync(c->adj, 0, bytes, c->stream);
@@ -1622,6 +1668,8 @@ int dg_adjoint_inject(dg_ctx* c, const void* d_resid) {
   if (!c) return DG_ERR_ARG;
   if (!d_resid) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_inject before dg_adjoint_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   int rc = ensure_ops(c);
   if (rc) return rc;
   if (c->prec == DG_F64)
@@ -1675,6 +1723,8 @@ int dg_adjoint_step(dg_ctx* c, double dt) {
   if (!c) return DG_ERR_ARG;
   if (!(dt > 0)) return c->fail(DG_ERR_ARG, "dt must be positive");
   if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_step before dg_adjoint_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   int rc = ensure_ops(c);
   if (rc) return rc;
   // the forward step from the current state and time, keeping every stage's
@@ -1708,6 +1758,8 @@ int dg_step_record_chain(dg_ctx* c, double dt, int64_t nsteps, void* const* d_re
     if (!d_recs[i] || reinterpret_cast<uintptr_t>(d_recs[i]) % 256) return c->fail(DG_ERR_ARG, "null or misaligned record");
   if (!(dt > 0)) return c->fail(DG_ERR_ARG, "dt must be positive");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_step_record before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   int rc = ensure_ops(c);
   if (rc || nsteps == 0) return rc;
   const size_t fb = c->field_bytes;
@@ -1747,6 +1799,8 @@ int dg_adjoint_step_recorded(dg_ctx* c, double dt, const void* d_rec) {
   if (!d_rec || reinterpret_cast<uintptr_t>(d_rec) % 256) return c->fail(DG_ERR_ARG, "null or misaligned record");
   if (!(dt > 0)) return c->fail(DG_ERR_ARG, "dt must be positive");
   if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_step_recorded before dg_adjoint_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   int rc = ensure_ops(c);
   if (rc) return rc;
   const unsigned char* rec = static_cast<const unsigned char*>(d_rec);
@@ -1764,6 +1818,8 @@ int dg_adjoint_set(dg_ctx* c, const void* mu_q, const void* x, int on_device) {
   if (!c) return DG_ERR_ARG;
   if (!mu_q || !x) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_set before dg_adjoint_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   int rc = ensure_ops(c);
   if (rc) return rc;
   const size_t rs = c->prec == DG_F64 ? 8 : 4;
@@ -1789,6 +1845,8 @@ int dg_adjoint_get(dg_ctx* c, void* dst, int on_device) {
   if (!c) return DG_ERR_ARG;
   if (!dst) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_get before dg_adjoint_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   int rc = ensure_ops(c);
   if (rc) return rc;
   const size_t rs = c->prec == DG_F64 ? 8 : 4;
@@ -1808,6 +1866,8 @@ int dg_adjoint_gradient(dg_ctx* c, double* g_kappa, double* g_rho) {
   if (!c) return DG_ERR_ARG;
   if (!g_kappa || !g_rho) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->adj) return c->fail(DG_ERR_STATE, "dg_adjoint_gradient before dg_adjoint_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   const int64_t Kw = int64_t(c->wedges.size()), nv = nblk(vKw(c)) * kB;
   const int64_t Kt = int64_t(c->tets.size()), nt = nblk(vKt(c)) * kB;
   std::vector<double> gk(nv), gr(nv), tk(nt), tr(nt);
@@ -1840,6 +1900,8 @@ int dg_energy(dg_ctx* c, double* E) {
   if (!c) return DG_ERR_ARG;
   if (!E) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_energy before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   int rc = ensure_ops(c);
   if (rc) return rc;
   int lr;
@@ -1862,6 +1924,8 @@ int dg_energy_static(dg_ctx* c, const void* d_q, double* E) {
   if (!c) return DG_ERR_ARG;
   if (!d_q || !E) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_energy_static before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   const int64_t K = vKw(c) + vKt(c);
   const int64_t nblocks = (K + 127) / 128;
   if (nblocks > kStaticPartials)
@@ -1882,12 +1946,26 @@ int dg_energy_static(dg_ctx* c, const void* d_q, double* E) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "static energy download");
   if (!std::isfinite(*E)) return c->fail(DG_ERR_NONFINITE, "non-finite energy");
+  // a device-side error raised by earlier work on the stream (bounded waits)
+  return check_device_error(c);
+}
+
+int dg_expire_wait(dg_ctx* c) {
+  if (!c) return DG_ERR_ARG;
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_expire_wait before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
+  int* derr = (c->prec == DG_F64) ? c->m64.err : c->m32.err;
+  const int rc = (c->prec == DG_F64) ? wait_expire_f64(c->N, derr, c->stream) : wait_expire_f32(c->N, derr, c->stream);
+  if (rc) return cuda_fail(c, cudaError_t(rc), "wait-expiry launch");
   return DG_OK;
 }
 
 int dg_sync(dg_ctx* c) {
   if (!c) return DG_ERR_ARG;
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_sync before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
   return check_device_error(c);
@@ -1918,6 +1996,7 @@ const char* dg_last_error(const dg_ctx* c) { return c ? c->err.c_str() : "null c
 
 void dg_destroy(dg_ctx* c) {
   if (!c) return;
+  DeviceGuard device_guard(c);
   drop_graphs(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;

@@ -153,6 +153,7 @@ enum : int { kErrTimeout = 1, kErrNonfinite = 2 };
   int launch_pack_##P##n##N(const DevMesh<T>& m, const T* canon, T* packed, bool unpack, void* s); \
   int launch_energy_##P##n##N(const DevMesh<T>& m, const T* q, void* stream);                      \
   int launch_clock_##P##n##N(double* clock, double dt, void* stream);                              \
+  int launch_wait_expire_##P##n##N(int* err, void* stream);                                        \
   int launch_sample_##P##n##N(const DevMesh<T>& m, const T* q, T* out, int nshots, void* stream);     \
   int launch_inject_##P##n##N(const DevMesh<T>& m, T* muq, T* x, const T* resid, int nshots, T b5,     \
                               void* stream);                                                       \

@@ -6,8 +6,12 @@
 // library, so the entry point can run where the caller must not allocate
 // (inside a framework's allocation-free region, a host callback, or while a
 // memory pool is locked).  The state is read in the canonical layout
-// [4][total_nodes]; geometry and material come from the bound mesh blob.
+// [shots][4][total_nodes] (the virtual element of each shot carries its
+// shot's canonical offset); geometry and material come from the bound mesh
+// blob.  The energy returned is the sum over shots.
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "dg_internal.hpp"
 
@@ -18,8 +22,10 @@ namespace {
 // Per-block partial sums followed by the total: kStaticPartials * 128 elements at most.
 __device__ __align__(256) double g_energy_scratch[kStaticPartials + 1];
 
-// Device address of g_energy_scratch per device (0 until set up).
+// Device address of g_energy_scratch per device (0 until set up); written
+// once per device under the mutex.
 double* g_scratch_ptr[64] = {nullptr};
+std::mutex g_scratch_mu;
 
 template <typename real>
 __device__ double quad_form(const real* q, int64_t stride, int64_t off, const real* Mmat, int n, int f) {
@@ -120,13 +126,21 @@ int launch(const DevMesh<real>& m, const real* q, const real* wops, double* scra
 }  // namespace
 
 // One-time, per-device set-up: the device address of the scratch array (the
-// array's name in host code is only a host-side stand-in).  Must run with the
-// device current; the first dg_energy_static call on a device performs it.
+// array's name in host code is only a host-side stand-in).  The address is
+// looked up with `device` current -- the call refuses to run with another
+// device current, so a wrong device's address can never be cached -- and kept
+// per device; concurrent first calls from several host threads are
+// serialised.  The first dg_energy_static call on a device performs it.
 int energy_static_scratch(int device, double** out) {
   if (device < 0 || device >= 64) return int(cudaErrorInvalidDevice);
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return int(e);
+  if (cur != device) return int(cudaErrorInvalidDevice);
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_ptr[device]) {
     void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_energy_scratch);
+    e = cudaGetSymbolAddress(&p, g_energy_scratch);
     if (e != cudaSuccess) return int(e);
     g_scratch_ptr[device] = static_cast<double*>(p);
   }

@@ -248,10 +248,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
 }
 // About a second of polling at most (each poll suspends for at most ~1 us).
 constexpr long long kWaitLimit = 1ll << 20;
+template <long long Limit = kWaitLimit>
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
-  for (long long it = 0; it < kWaitLimit; ++it)
+  for (long long it = 0; it < Limit; ++it)
     if (mbar_try_wait(bar, phase)) return true;
   return false;
+}
+
+// Failure-path check: one warp arms an mbarrier for bytes that no copy will
+// ever deliver (no copy is issued), so the stages' bounded wait runs out --
+// here after 64 polls instead of the stages' ~1 s budget -- and the kernel
+// reports DG_ERR_TIMEOUT through the device error word, exactly as a stage
+// whose copy never landed does, then returns.  Nothing is in flight when it
+// exits; the GPU and the context stay usable.
+__global__ void k_wait_expire(int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_expect_tx(&bar, 16u);
+  }
+  __syncwarp();
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded<64>(&bar, 0));
+  if (!ok && threadIdx.x == 0) atomicOr(err, kErrTimeout);
 }
 
 // per-element geometric factors kept in shared memory ([item][32])
@@ -1323,6 +1342,10 @@ int DGW_CAT(launch_tgrad_, REALNS)(const DevMesh<REAL>& m, const REAL* x, const 
     constexpr int bytes = REALNS::tgrad_smem_bytes<NORD>();
     REALNS::k_tet_grad<NORD><<<m.nblk_t, 128, bytes, cudaStream_t(stream)>>>(m, x, q, r, dt, flux, bc, gk, gr);
   }
+  return int(cudaGetLastError());
+}
+int DGW_CAT(launch_wait_expire_, REALNS)(int* err, void* stream) {
+  REALNS::k_wait_expire<<<1, 32, 0, cudaStream_t(stream)>>>(err);
   return int(cudaGetLastError());
 }
 int DGW_CAT(launch_clock_, REALNS)(double* clock, double dt, void* stream) {

@@ -30,7 +30,7 @@ DG_SHOTS_OUTER, DG_SHOTS_INNER = 0, 1
 
 EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_shots", "dg_add_shot_source", "dg_set_shot_order", "dg_set_options", "dg_set_mass_mode", "dg_num_nodes",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
-           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_stage_times", "dg_autotune", "dg_add_receiver", "dg_sample", "dg_save_state",
+           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_expire_wait", "dg_fma_peak", "dg_stage_times", "dg_autotune", "dg_add_receiver", "dg_sample", "dg_save_state",
            "dg_load_state", "dg_adjoint_bytes", "dg_adjoint_bind", "dg_adjoint_reset", "dg_adjoint_inject",
            "dg_adjoint_step", "dg_step_record_bytes", "dg_step_record", "dg_step_record_chain", "dg_adjoint_step_recorded", "dg_adjoint_set", "dg_adjoint_get", "dg_adjoint_gradient", "dg_sync", "dg_time",
            "dg_stable_dt", "dg_last_error", "dg_destroy")
@@ -95,6 +95,8 @@ def lib():
         "dg_adjoint_get": (c_int, [P, P, c_int]),
         "dg_adjoint_gradient": (c_int, [P, P, P]),
         "dg_sync": (c_int, [P]),
+        "dg_expire_wait": (c_int, [P]),
+        "dg_fma_peak": (c_int, [c_int, P, POINTER(c_double)]),
         "dg_time": (c_int, [P, POINTER(c_double)]),
         "dg_stable_dt": (c_int, [P, c_double, POINTER(c_double)]),
         "dg_last_error": (c_char_p, [P]),
@@ -326,6 +328,19 @@ def dg_adjoint_gradient(ctx, K: int):
     gk, gr = np.zeros(K), np.zeros(K)
     _check(ctx, lib().dg_adjoint_gradient(ctx, gk.ctypes.data, gr.ctypes.data))
     return gk, gr
+
+
+def dg_expire_wait(ctx):
+    _check(ctx, lib().dg_expire_wait(ctx))
+
+
+def dg_fma_peak(precision: int, stream: int = 0) -> float:
+    """Measured CUDA-core FMA throughput of the current device, TFLOP/s."""
+    t = c_double()
+    rc = lib().dg_fma_peak(precision, c_void_p(stream), ctypes.byref(t))
+    if rc != DG_OK:
+        raise DGError(rc, "dg_fma_peak failed")
+    return t.value
 
 
 def dg_sync(ctx):
