@@ -80,6 +80,7 @@ enum { DG_BC_DIRICHLET = 0, DG_BC_RIGID = 1 };
 enum { DG_FLUX_UPWIND = 0, DG_FLUX_CENTRAL = 1 };
 enum { DG_F32 = 0, DG_F64 = 1 };
 enum { DG_MASS_ONTHEFLY = 0, DG_MASS_STORED = 1 };
+enum { DG_OPS_FP32 = 0, DG_OPS_TF32X3 = 1, DG_OPS_TF32 = 2, DG_OPS_BF16 = 3 };
 enum { DG_SHOTS_OUTER = 0, DG_SHOTS_INNER = 1 };
 
 /* Create a mesh context from vertices and element-to-vertex lists
@@ -165,6 +166,24 @@ int dg_set_options(dg_ctx* ctx, int bc, int flux, int precision);
  * Before dg_bind.  Errors: DG_ERR_ARG (unknown mode), DG_ERR_STATE. */
 int dg_set_mass_mode(dg_ctx* ctx, int mode);
 
+/* How the wedge stage applies the shared reference triangle operators of
+ * Section 4.2 -- M^tri in the weak-form accumulation and D_r, D_s in the
+ * strong part; the Nt x Nt matrices common to every element, applied to a
+ * whole 32-element block slice by slice (the per-element geometric factors
+ * of Lemma 3.1 and the per-element mass inverse stay in FP32 on the CUDA
+ * cores):
+ *   DG_OPS_FP32    FP32 fused multiply-adds on the CUDA cores (default);
+ *   DG_OPS_TF32X3  tensor cores, each operand split into two TF32 numbers
+ *                  (three products, FP32 accumulation): about FP32 accuracy;
+ *   DG_OPS_TF32    tensor cores, TF32 operands, FP32 accumulation;
+ *   DG_OPS_BF16    tensor cores, BF16 operands, FP32 accumulation.
+ * Fields, fluxes, the rest of the stage and the update stay FP32.  Needs the
+ * DG_F32 precision (DG_ERR_ARG otherwise); applies to every stage launch of
+ * the context (steps, dg_rhs, the adjoint).  Call after dg_set_options and
+ * before dg_bind; the tet stage is unaffected.  The paper's kernels use FP32
+ * CUDA cores only (Section 6.3); the variants trade operator accuracy for
+ * tensor-core throughput. */
+int dg_set_op_precision(dg_ctx* ctx, int mode);
 
 /* Node counts: total wedge nodes and total tet nodes; the canonical layout
  * holds wedge_nodes + tet_nodes nodes. */

@@ -135,6 +135,7 @@ struct dg_ctx {
   // options
   int bc = DG_BC_RIGID, flux = DG_FLUX_UPWIND, prec = DG_F32;
   int mass = DG_MASS_STORED;
+  int op = DG_OPS_FP32;  // how the wedge stage applies the shared triangle operators
   // shots: independent copies of the state on the same mesh, advanced together
   int64_t shots = 1;
   bool shot_inner = false;  // DG_SHOTS_INNER: the shots of one element are neighbouring lanes
@@ -741,6 +742,7 @@ int launch_stage(dg_ctx* c, const void* q_in, void* q_out, void* res, double a, 
     A.flux = c->flux;
     A.wedge_bpc = c->tuned_bpc;
     if (c->tuned_onthefly) A.m.w_fac = nullptr;
+    A.op = c->op;
     A.rk_g = float(x.g);
     A.rhs_out = static_cast<float*>(x.rhs_out);
     if (x.no_sources) A.m.nsrc = 0;
@@ -1142,6 +1144,8 @@ int dg_set_options(dg_ctx* c, int bc, int flux, int precision) {
   if ((bc != DG_BC_DIRICHLET && bc != DG_BC_RIGID) || (flux != DG_FLUX_UPWIND && flux != DG_FLUX_CENTRAL) ||
       (precision != DG_F32 && precision != DG_F64))
     return c->fail(DG_ERR_ARG, "option out of range");
+  if (precision != DG_F32 && c->op != DG_OPS_FP32)
+    return c->fail(DG_ERR_ARG, "tensor-core operator applies need DG_F32 fields");
   c->bc = bc;
   c->flux = flux;
   c->prec = precision;
@@ -1153,6 +1157,16 @@ int dg_set_mass_mode(dg_ctx* c, int mode) {
   if (c->bound) return c->fail(DG_ERR_STATE, "dg_set_mass_mode after dg_bind");
   if (mode != DG_MASS_ONTHEFLY && mode != DG_MASS_STORED) return c->fail(DG_ERR_ARG, "mass mode out of range");
   c->mass = mode;
+  return DG_OK;
+}
+
+int dg_set_op_precision(dg_ctx* c, int mode) {
+  if (!c) return DG_ERR_ARG;
+  if (c->bound) return c->fail(DG_ERR_STATE, "dg_set_op_precision after dg_bind");
+  if (mode < DG_OPS_FP32 || mode > DG_OPS_BF16) return c->fail(DG_ERR_ARG, "operator precision out of range");
+  if (mode != DG_OPS_FP32 && c->prec != DG_F32)
+    return c->fail(DG_ERR_ARG, "tensor-core operator applies need DG_F32 fields");
+  c->op = mode;
   return DG_OK;
 }
 

@@ -141,9 +141,20 @@ struct StageArgs {
   double c_stage = 0;           // stage time = *clock + c_stage * dt
   int bc = 1, flux = 0;
   int wedge_bpc = 0;            // wedge blocks per CTA: 0 = the default for the mass mode
+  int op = 0;                   // kOpFFMA, or a tensor-core variant (FP32 fields)
 };
 
 enum : int { kErrTimeout = 1, kErrNonfinite = 2 };
+
+// How the wedge stage applies the shared triangle operators (M^tri, D_r,
+// D_s): FP32 FMA chains on the CUDA cores, or warp-level tensor-core MMA with
+// 3xTF32 (about FP32 accuracy), TF32 or BF16 operands and FP32 accumulation
+// (FP32 fields only).
+enum : int { kOpFFMA = 0, kOpTF32x3 = 1, kOpTF32 = 2, kOpBF16 = 3 };
+// row pitch (floats) of the per-warp operand tiles of the tensor-core applies:
+// 8 mod 32, so the B-operand loads (4 rows x 8 columns) and the 64-bit C
+// stores (half-warps over 4 rows) hit distinct banks
+constexpr int kTP = 4 * 32 + 8;
 
 // Launchers, one set per (precision, order) translation unit k_<p>_n<N>.cu;
 // all return 0 or a cudaError_t value.

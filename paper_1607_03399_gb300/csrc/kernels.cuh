@@ -172,6 +172,114 @@ __device__ __forceinline__ void taus(int flux, real zM, real zP, real& tau_p, re
   tau_u = up ? zavg : real(0);
 }
 
+// ---------------------------------------------------------------------------
+// shared reference operators on the tensor cores (FP32 fields, warp-level
+// mma.sync): Out = Op * In with Op an Nt x Nt triangle operator zero-padded
+// to 16 x 16 (the A operand, in registers) and In an Nt-row tile in shared
+// memory whose columns are (element, field) pairs (the B operand).  TF32 is
+// m16n8k8 (two k-steps cover Nt <= 16), BF16 m16n8k16 (one k-step); both
+// accumulate in FP32.  3xTF32 splits each operand x = hi + lo into two TF32
+// numbers and adds lo*hi + hi*lo + hi*hi (dropping lo*lo), which recovers
+// about FP32 accuracy.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// (lo, hi) -> bf16x2 with lo in the low half (the lower k index of an operand pair)
+__device__ __forceinline__ uint32_t bf16x2_of(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// A operand registers of one operator: [k-step][4] (hi and, for 3xTF32, lo parts)
+template <int OP>
+struct AFrag {
+  uint32_t h[2][4];
+  uint32_t l[OP == kOpTF32x3 ? 2 : 1][4];
+};
+// Fragment of the row-major Nt x Nt operator Op (rows = outputs), zero-padded.
+// m16n8k8 TF32: a0 (g, t), a1 (g + 8, t), a2 (g, t + 4), a3 (g + 8, t + 4) of
+// the 16 x 8 slice of k-step ks; m16n8k16 BF16: pairs of columns (2t, 2t + 1)
+// and (2t + 8, 2t + 9) of rows g and g + 8 (g = lane / 4, t = lane % 4).
+template <int NT, int OP>
+__device__ __forceinline__ void afrag_load(const float* Op, int lane, AFrag<OP>& A) {
+  const int g = lane >> 2, t = lane & 3;
+  auto at = [&](int r, int c) -> float { return (r < NT && c < NT) ? Op[r * NT + c] : 0.f; };
+  if constexpr (OP == kOpBF16) {
+    A.h[0][0] = bf16x2_of(at(g, 2 * t), at(g, 2 * t + 1));
+    A.h[0][1] = bf16x2_of(at(g + 8, 2 * t), at(g + 8, 2 * t + 1));
+    A.h[0][2] = bf16x2_of(at(g, 2 * t + 8), at(g, 2 * t + 9));
+    A.h[0][3] = bf16x2_of(at(g + 8, 2 * t + 8), at(g + 8, 2 * t + 9));
+  } else {
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const float v[4] = {at(g, t + 8 * ks), at(g + 8, t + 8 * ks), at(g, t + 4 + 8 * ks), at(g + 8, t + 4 + 8 * ks)};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        A.h[ks][r] = tf32_of(v[r]);
+        if constexpr (OP == kOpTF32x3) A.l[ks][r] = tf32_of(v[r] - __uint_as_float(A.h[ks][r]));
+      }
+    }
+  }
+}
+// B operand of one n-tile: column `col` of the Nt-row tile B (row pitch P);
+// rows >= Nt are zero (never read).  TF32: [k-step] (k = t, t + 4) per step;
+// BF16: (2t, 2t + 1) and (2t + 8, 2t + 9).
+template <int OP>
+struct BFrag {
+  uint32_t h[2][2];
+  uint32_t l[OP == kOpTF32x3 ? 2 : 1][2];
+};
+template <int NT, int OP>
+__device__ __forceinline__ void bfrag_load(const float* B, int P, int col, int lane, BFrag<OP>& F) {
+  const int t = lane & 3;
+  auto bv = [&](int k) -> float { return k < NT ? B[k * P + col] : 0.f; };
+  if constexpr (OP == kOpBF16) {
+    F.h[0][0] = bf16x2_of(bv(2 * t), bv(2 * t + 1));
+    F.h[0][1] = bf16x2_of(bv(2 * t + 8), bv(2 * t + 9));
+  } else {
+#pragma unroll
+    for (int ks = 0; ks < (NT + 7) / 8; ++ks) {
+      const float x0 = bv(t + 8 * ks), x1 = bv(t + 4 + 8 * ks);
+      F.h[ks][0] = tf32_of(x0);
+      F.h[ks][1] = tf32_of(x1);
+      if constexpr (OP == kOpTF32x3) {
+        F.l[ks][0] = tf32_of(x0 - __uint_as_float(F.h[ks][0]));
+        F.l[ks][1] = tf32_of(x1 - __uint_as_float(F.h[ks][1]));
+      }
+    }
+  }
+}
+// d += Op * B for one 16 x 8 output tile
+template <int NT, int OP>
+__device__ __forceinline__ void op_mma(const AFrag<OP>& A, const BFrag<OP>& F, float (&d)[4]) {
+  if constexpr (OP == kOpBF16) {
+    mma_bf16(d, A.h[0], F.h[0][0], F.h[0][1]);
+  } else {
+#pragma unroll
+    for (int ks = 0; ks < (NT + 7) / 8; ++ks) {
+      if constexpr (OP == kOpTF32x3) {
+        mma_tf32(d, A.l[ks], F.h[ks][0], F.h[ks][1]);
+        mma_tf32(d, A.h[ks], F.l[ks][0], F.l[ks][1]);
+      }
+      mma_tf32(d, A.h[ks], F.h[ks][0], F.h[ks][1]);
+    }
+  }
+}
+
 // Ricker wavelet (1 - 2 a) exp(-a), a = (pi f0 (t - t0))^2 (c13 reading).
 __device__ __forceinline__ double ricker(double f0, double tau) {
   const double a = (3.14159265358979323846 * f0 * tau) * (3.14159265358979323846 * f0 * tau);
@@ -280,28 +388,31 @@ enum WGeo : int {
   G_TX0, G_TX1, G_TY0, G_TY1, G_COUNT
 };
 
-// Residual slab staged in shared memory by the bulk copy (N <= 3).  At N = 4
-// the staged slab measured slower (77 KB of copies per block in flight at two
-// CTAs per SM), so the residual is read from global memory at the update.
-template <int N>
+// Residual slab staged in shared memory by the bulk copy (N <= 3, FP32 FMA
+// applies).  At N = 4 the staged slab measured slower (77 KB of copies per
+// block in flight at two CTAs per SM), and the tensor-core variants spend
+// that shared memory on their operand tiles, so there the residual is read
+// from global memory at the update.
+template <int N, int OP = kOpFFMA>
 __host__ __device__ constexpr bool stage_res() {
-  return N <= 3;
+  return N <= 3 && OP == kOpFFMA;
 }
 
-template <int N>
+template <int N, int OP = kOpFFMA>
 struct WedgeSmem {
   static constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
-  static constexpr int q = 0;                                        // [4][Np][32]
-  static constexpr int r = q + 4 * Np * kB;                          // [4][Np][32] (if staged)
-  static constexpr int L = r + (stage_res<N>() ? 4 * Np * kB : 0);   // [Nt(Nt+1)/2][32]
-  static constexpr int F = L + (Nt * (Nt + 1) / 2) * kB;             // [4][Nt][32]
-  static constexpr int G = F + 4 * Nt * kB;                          // [G_COUNT][32]
-  static constexpr int reals = G + G_COUNT * kB;
+  static constexpr int q = 0;                                            // [4][Np][32]
+  static constexpr int r = q + 4 * Np * kB;                              // [4][Np][32] (if staged)
+  static constexpr int L = r + (stage_res<N, OP>() ? 4 * Np * kB : 0);   // [Nt(Nt+1)/2][32]
+  static constexpr int F = L + (Nt * (Nt + 1) / 2) * kB;                 // [4][Nt][32]
+  static constexpr int G = F + 4 * Nt * kB;                              // [G_COUNT][32]
+  static constexpr int T = G + G_COUNT * kB;                             // per warp [Nt][kTP] (tensor cores)
+  static constexpr int reals = T + (OP == kOpFFMA ? 0 : Nq * Nt * kTP);
 };
 
-template <int N>
+template <int N, int OP = kOpFFMA>
 __host__ __device__ constexpr int wedge_smem_reals() {
-  return WedgeSmem<N>::reals;
+  return WedgeSmem<N, OP>::reals;
 }
 // Element blocks per CTA.  The warps that work on slice j of the CTA's blocks
 // share an SM sub-partition and run the same straight-line code side by side,
@@ -314,9 +425,14 @@ __host__ __device__ constexpr int wedge_bpc_onthefly() {
 }
 // bytes: per block two mbarriers and a status word (32 bytes), then per block
 // the reals (each block's slabs start 16-byte aligned)
-template <int N, int BPC>
+template <int N, int BPC, int OP = kOpFFMA>
 __host__ __device__ constexpr int wedge_smem_bytes() {
-  return BPC * (32 + wedge_smem_reals<N>() * int(sizeof(real)));
+  return BPC * (32 + wedge_smem_reals<N, OP>() * int(sizeof(real)));
+}
+// resident CTAs per SM the stage is compiled for
+template <int N, int BPC, int OP>
+__host__ __device__ constexpr int wedge_min_ctas() {
+  return sizeof(REAL) == 4 ? (OP != kOpFFMA ? (N >= 4 ? 2 : 3) : (N >= 4 ? 2 : 4 / BPC)) : 1;
 }
 
 // Lemma 3.1 for one wedge: everything the stage needs, from the six vertices
@@ -395,11 +511,12 @@ __device__ __forceinline__ void wedge_geometry(real* sG, int lane) {
   for (int i = 0; i < G_COUNT; ++i) sG[i * kB + lane] = G[i];
 }
 
-template <int N, int BPC>
-__global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >= 4 ? 2 : 4 / BPC) : 1)
+template <int N, int BPC, int OP = kOpFFMA>
+__global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>())
     k_wedge_stage(const StageArgs<real> A, bool rk) {
   constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
-  using SM = WedgeSmem<N>;
+  static_assert(OP == kOpFFMA || (sizeof(real) == 4 && BPC == 1 && Nt <= 16), "tensor-core applies: FP32, Nt <= 16");
+  using SM = WedgeSmem<N, OP>;
   const AllOps<N, real>& O = OPS<N>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // block sb of this CTA: warps sb (N+1) .. sb (N+1) + N, one per slice
@@ -415,6 +532,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
   real* sL = base + SM::L;
   real* sF = base + SM::F;
   real* sG = base + SM::G;
+  real* sT = base + SM::T + (OP == kOpFFMA ? 0 : j * Nt * kTP);  // this warp's operand tile (tensor cores)
   const DevMesh<real>& M = A.m;
   const real* __restrict__ qin = A.q_in;
   real* __restrict__ qout = A.q_out;
@@ -425,7 +543,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
   const int e = blk * kB + lane;
   const int Kp = M.Kw_pad;
   constexpr uint32_t slab_bytes = uint32_t(4 * Np * kB * sizeof(real));
-  const bool res_async = rk && stage_res<N>();
+  const bool res_async = rk && stage_res<N, OP>();
 #define GEO(item) sG[(item) * kB + lane]
 
   if (!live) return;  // padding block of the last CTA
@@ -461,6 +579,38 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
       bulk_g2s(sr, resg + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[1]);
     }
   }
+  // face neighbours, their impedances and the source flag, loaded while the
+  // slabs are in flight; so are the traces of quadrilateral-face neighbours
+  // outside this block (global memory, read-only during the stage)
+  const real zM = M.w_mat[2 * Kp + e];
+  int qnbr[3], qcode[3];
+  real zPq[3];
+#pragma unroll
+  for (int ed = 0; ed < 3; ++ed) {
+    qnbr[ed] = M.w_nbr[(2 + ed) * Kp + e];
+    qcode[ed] = M.w_code[(2 + ed) * Kp + e];
+  }
+  Q4 nv[3][Nq];
+#pragma unroll
+  for (int ed = 0; ed < 3; ++ed) {
+    const int nbr = qnbr[ed];
+    if (nbr >= 0 && (nbr >> 5) != blk) {
+      const int ep = qcode[ed] >> 1, rev = qcode[ed] & 1;
+      const real* base = qin + widx<N>(nbr >> 5, 0, nbr & 31);
+#pragma unroll
+      for (int m = 0; m < Nq; ++m) nv[ed][m] = ldg4(base, int64_t(j * Nt + O.tab.edge[ep][rev ? N - m : m]) * (kB * 4));
+    }
+  }
+#pragma unroll
+  for (int ed = 0; ed < 3; ++ed) zPq[ed] = qnbr[ed] < 0 ? zM : M.w_mat[2 * Kp + qnbr[ed]];
+  const int tnbr[2] = {M.w_nbr[0 * Kp + e], M.w_nbr[1 * Kp + e]};
+  const int tcode[2] = {M.w_code[0 * Kp + e], M.w_code[1 * Kp + e]};
+  real zPt[2];
+#pragma unroll
+  for (int fb = 0; fb < 2; ++fb)
+    zPt[fb] = tnbr[fb] < 0 ? zM
+                           : ((tcode[fb] & kCodeTet) ? M.t_mat[2 * M.Kt_pad + tnbr[fb]] : M.w_mat[2 * Kp + tnbr[fb]]);
+  const bool src = M.nsrc > 0 && has_source(M, 6, e);
   // every lane of the geometry warp observes the coordinate copy itself
   bool geo_ok = true;
   __syncwarp();
@@ -495,26 +645,6 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
       sL[(i * (i + 1) / 2 + i) * kB + lane] = rsqrt_r(d);
     }
   }
-  // face neighbours, their impedances and the source flag, loaded while the
-  // slabs are in flight
-  const real zM = M.w_mat[2 * Kp + e];
-  int qnbr[3], qcode[3];
-  real zPq[3];
-#pragma unroll
-  for (int ed = 0; ed < 3; ++ed) {
-    qnbr[ed] = M.w_nbr[(2 + ed) * Kp + e];
-    qcode[ed] = M.w_code[(2 + ed) * Kp + e];
-  }
-#pragma unroll
-  for (int ed = 0; ed < 3; ++ed) zPq[ed] = qnbr[ed] < 0 ? zM : M.w_mat[2 * Kp + qnbr[ed]];
-  const int tnbr[2] = {M.w_nbr[0 * Kp + e], M.w_nbr[1 * Kp + e]};
-  const int tcode[2] = {M.w_code[0 * Kp + e], M.w_code[1 * Kp + e]};
-  real zPt[2];
-#pragma unroll
-  for (int fb = 0; fb < 2; ++fb)
-    zPt[fb] = tnbr[fb] < 0 ? zM
-                           : ((tcode[fb] & kCodeTet) ? M.t_mat[2 * M.Kt_pad + tnbr[fb]] : M.w_mat[2 * Kp + tnbr[fb]]);
-  const bool src = M.nsrc > 0 && has_source(M, 6, e);
   if (leader) *status = (mbar_wait_bounded(&bar[0], 0) && geo_ok) ? 1 : 0;
   block_sync();
   if (*reinterpret_cast<volatile int*>(status) == 0) {
@@ -533,20 +663,19 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
   real Wp[Nt], Wu[3][Nt];
 #pragma unroll
   for (int i = 0; i < Nt; ++i) Wp[i] = Wu[0][i] = Wu[1][i] = Wu[2][i] = real(0);
-  // neighbour traces of all three quadrilateral faces requested at once, one
-  // generic load per node whether the neighbour lies in this block (shared
-  // memory) or not (global memory); a boundary face reads its own trace,
-  // which the ghost state then replaces
-  Q4 nv[3][Nq];
+  // neighbour traces of quadrilateral faces whose neighbour lies in this block
+  // (or, on a boundary face, the element's own trace, which the ghost state
+  // then replaces) from the shared slab; the others were requested above
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
     const int nbr = qnbr[ed];
     const bool bnd = nbr < 0;
-    const int ep = bnd ? ed : qcode[ed] >> 1, rev = bnd ? 0 : qcode[ed] & 1;
-    const bool inblk = bnd || (nbr >> 5) == blk;
-    const real* base = inblk ? sq + ((bnd ? lane : (nbr & 31)) << 2) : qin + widx<N>(nbr >> 5, 0, nbr & 31);
+    if (bnd || (nbr >> 5) == blk) {
+      const int ep = bnd ? ed : qcode[ed] >> 1, rev = bnd ? 0 : qcode[ed] & 1;
+      const real* base = sq + ((bnd ? lane : (nbr & 31)) << 2);
 #pragma unroll
-    for (int m = 0; m < Nq; ++m) nv[ed][m] = ldx4(base + (j * Nt + O.tab.edge[ep][rev ? N - m : m]) * (kB * 4));
+      for (int m = 0; m < Nq; ++m) nv[ed][m] = ldx4(base + (j * Nt + O.tab.edge[ep][rev ? N - m : m]) * (kB * 4));
+    }
   }
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
@@ -631,6 +760,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
     const real Aj = GEO(G_A);
     const real cb = GEO(G_JFB) * O.w.ell0[j];
     const real ct = GEO(G_JFT) * O.w.ellN[j];
+    if constexpr (OP == kOpFFMA) {
     // (a) pressure: G = -(t_xJ D_t u_x + t_yJ D_t u_y + A D_t u_z) + lifts; W = M^tri G
     real dp[Nt];
     {
@@ -674,6 +804,56 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
         Wu[c][i] += acc;
       }
     }
+    } else {
+      // (a, b) on the tensor cores: the four vectors G of every element of
+      // the block go to this warp's tile (columns lane * 4 + field), M^tri G
+      // is formed one 16 x 8 output tile at a time in place, and each lane
+      // reads its element's four results back
+      const real nb0 = GEO(G_NB0) * cb, nb1 = GEO(G_NB1) * cb, nb2 = GEO(G_NB2) * cb;
+      const real nt0 = GEO(G_NT0) * ct, nt1 = GEO(G_NT1) * ct, nt2 = GEO(G_NT2) * ct;
+#pragma unroll
+      for (int i = 0; i < Nt; ++i) {
+        real dpp = 0, dux = 0, duy = 0, duz = 0;
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          const Q4 v = lds4(sq, m * Nt + i, lane);
+          dpp += dtr[m] * v.p;
+          dux += dtr[m] * v.u;
+          duy += dtr[m] * v.v;
+          duz += dtr[m] * v.w;
+        }
+        const real fp = sF[(1 * Nt + i) * kB + lane], fq = sF[(3 * Nt + i) * kB + lane];
+        const float4 gv = make_float4(
+            cb * sF[(0 * Nt + i) * kB + lane] + ct * sF[(2 * Nt + i) * kB + lane] - (txJ * dux + tyJ * duy + Aj * duz),
+            nb0 * fp + nt0 * fq - txJ * dpp, nb1 * fp + nt1 * fq - tyJ * dpp, nb2 * fp + nt2 * fq - Aj * dpp);
+        *reinterpret_cast<float4*>(sT + i * kTP + lane * 4) = gv;
+      }
+      __syncwarp();
+      {
+        AFrag<OP> Am;
+        afrag_load<Nt, OP>(O.w.M, lane, Am);
+        const int g = lane >> 2, t = lane & 3;
+#pragma unroll 2
+        for (int nt = 0; nt < 16; ++nt) {
+          BFrag<OP> Bf;
+          bfrag_load<Nt, OP>(sT, kTP, nt * 8 + g, lane, Bf);
+          float d[4] = {0.f, 0.f, 0.f, 0.f};
+          op_mma<Nt, OP>(Am, Bf, d);
+          if (g < Nt) *reinterpret_cast<float2*>(sT + g * kTP + nt * 8 + 2 * t) = make_float2(d[0], d[1]);
+          if (g + 8 < Nt) *reinterpret_cast<float2*>(sT + (g + 8) * kTP + nt * 8 + 2 * t) = make_float2(d[2], d[3]);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < Nt; ++i) {
+        const float4 w = *reinterpret_cast<const float4*>(sT + i * kTP + lane * 4);
+        Wp[i] += w.x;
+        Wu[0][i] += w.y;
+        Wu[1][i] += w.z;
+        Wu[2][i] += w.w;
+      }
+      __syncwarp();
+    }
   }
   // (d) X = (M^{tri,k})^{-1} W: forward and backward substitution, 4 right-hand sides
 #pragma unroll
@@ -709,7 +889,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
     Wu[2][i] *= d;
   }
   // (e) strong r, s parts of slice j (constant metric terms, Lemma 3.1)
-  {
+  if constexpr (OP == kOpFFMA) {
     const real rx = GEO(G_RX), ry = GEO(G_RY), sx = GEO(G_SX), sy = GEO(G_SY);
     real pv[Nt], av[Nt], bv[Nt];
 #pragma unroll
@@ -733,6 +913,40 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
       Wu[0][i] -= rx * pr + sx * ps;
       Wu[1][i] -= ry * pr + sy * ps;
     }
+  } else {
+    // on the tensor cores: D_r and D_s of slice j of the whole slab (columns
+    // lane * 4 + field); the thread pairs holding an element's (p, u) and
+    // (v, w) columns combine them with the element's metric terms into
+    // (div u, d_x p, d_y p), stored to this warp's tile and subtracted by
+    // the element's lane at the update
+    AFrag<OP> Ar, As;
+    afrag_load<Nt, OP>(O.w.Dr, lane, Ar);
+    afrag_load<Nt, OP>(O.w.Ds, lane, As);
+    const int g = lane >> 2, t = lane & 3;
+    const real* Bj = sq + j * Nt * (kB * 4);
+#pragma unroll 2
+    for (int nt = 0; nt < 16; ++nt) {
+      BFrag<OP> Bf;
+      bfrag_load<Nt, OP>(Bj, kB * 4, nt * 8 + g, lane, Bf);
+      float dr[4] = {0.f, 0.f, 0.f, 0.f}, ds[4] = {0.f, 0.f, 0.f, 0.f};
+      op_mma<Nt, OP>(Ar, Bf, dr);
+      op_mma<Nt, OP>(As, Bf, ds);
+      // columns nt * 8 + 2t, + 1: element E = 2 nt + t / 2, fields (p, u) for even t, (v, w) for odd t
+      const int E = 2 * nt + (t >> 1);
+      const real rx = sG[G_RX * kB + E], ry = sG[G_RY * kB + E], sx = sG[G_SX * kB + E], sy = sG[G_SY * kB + E];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float a = dr[2 * h], b = dr[2 * h + 1], c = ds[2 * h], d = ds[2 * h + 1];
+        // even t: a = D_r p, b = D_r u, c = D_s p, d = D_s u; odd t: the same of v and w
+        const float part = (t & 1) ? ry * a + sy * c : rx * b + sx * d;
+        const float other = __shfl_xor_sync(0xffffffffu, part, 1);
+        const int row = g + 8 * h;
+        if (!(t & 1) && row < Nt)
+          *reinterpret_cast<float4*>(sT + row * kTP + E * 4) =
+              make_float4(part + other, rx * a + sx * c, ry * a + sy * c, 0.f);
+      }
+    }
+    __syncwarp();
   }
   // (f) fused low-storage Runge-Kutta update (or plain right-hand side)
   if (res_async && !mbar_wait_bounded(&bar[1], 0)) {
@@ -746,9 +960,15 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, (sizeof(REAL) == 4) ? (N >
     for (int i = 0; i < Nt; ++i) {
       const int n = j * Nt + i;
       const int64_t g = widx<N>(blk, n, lane);
+      if constexpr (OP != kOpFFMA) {
+        const float4 sv = *reinterpret_cast<const float4*>(sT + i * kTP + lane * 4);
+        Wp[i] -= sv.x;
+        Wu[0][i] -= sv.y;
+        Wu[1][i] -= sv.z;
+      }
       Q4 r{kappa * Wp[i], irho * Wu[0][i], irho * Wu[1][i], irho * Wu[2][i]};
       if (rk) {
-        const Q4 r0 = stage_res<N>() ? lds4(sr, n, lane) : ld4(resg, g);
+        const Q4 r0 = stage_res<N, OP>() ? lds4(sr, n, lane) : ld4(resg, g);
         const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
                     A.rk_a * r0.w + A.dt * r.w};
         const Q4 q0 = lds4(sq, n, lane);
@@ -1231,11 +1451,21 @@ namespace REALNS {
 // launchers
 // ---------------------------------------------------------------------------
 // one-time per device: opt in to the dynamic shared memory the stages use
+template <int N, int OP>
+cudaError_t prepare_op() {
+  return cudaFuncSetAttribute(k_wedge_stage<N, 1, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              wedge_smem_bytes<N, 1, OP>());
+}
 template <int N>
 int prepare_n() {
   constexpr int b2 = wedge_bpc_onthefly<N>();
   cudaError_t err = cudaFuncSetAttribute(k_wedge_stage<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          wedge_smem_bytes<N, 1>());
+  if constexpr (sizeof(real) == 4) {
+    if (err == cudaSuccess) err = prepare_op<N, kOpTF32x3>();
+    if (err == cudaSuccess) err = prepare_op<N, kOpTF32>();
+    if (err == cudaSuccess) err = prepare_op<N, kOpBF16>();
+  }
   if (err == cudaSuccess && b2 != 1)
     err = cudaFuncSetAttribute(k_wedge_stage<N, b2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                wedge_smem_bytes<N, b2>());
@@ -1252,12 +1482,24 @@ int prepare_n() {
   return int(err);
 }
 
+template <int N, int OP>
+void launch_op(const StageArgs<real>& a, bool rk, cudaStream_t s) {
+  k_wedge_stage<N, 1, OP><<<a.m.nblk_w, 32 * (N + 1), wedge_smem_bytes<N, 1, OP>(), s>>>(a, rk);
+}
 template <int N>
 int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s) {
   if (a.m.nblk_w > 0) {
     constexpr int b2 = wedge_bpc_onthefly<N>();
     const int want = a.wedge_bpc > 0 ? a.wedge_bpc : (a.m.w_fac != nullptr ? 1 : b2);
-    if (want == 1 || b2 == 1)
+    bool done = false;
+    if constexpr (sizeof(real) == 4) {
+      done = a.op != kOpFFMA;
+      if (a.op == kOpTF32x3) launch_op<N, kOpTF32x3>(a, rk, s);
+      else if (a.op == kOpTF32) launch_op<N, kOpTF32>(a, rk, s);
+      else if (a.op == kOpBF16) launch_op<N, kOpBF16>(a, rk, s);
+    }
+    if (done) {
+    } else if (want == 1 || b2 == 1)
       k_wedge_stage<N, 1><<<a.m.nblk_w, 32 * (N + 1), wedge_smem_bytes<N, 1>(), s>>>(a, rk);
     else
       k_wedge_stage<N, b2><<<(a.m.nblk_w + b2 - 1) / b2, 32 * (N + 1) * b2, wedge_smem_bytes<N, b2>(), s>>>(a, rk);

@@ -27,8 +27,9 @@ DG_FLUX_UPWIND, DG_FLUX_CENTRAL = 0, 1
 DG_F32, DG_F64 = 0, 1
 DG_MASS_ONTHEFLY, DG_MASS_STORED = 0, 1
 DG_SHOTS_OUTER, DG_SHOTS_INNER = 0, 1
+DG_OPS_FP32, DG_OPS_TF32X3, DG_OPS_TF32, DG_OPS_BF16 = 0, 1, 2, 3
 
-EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_shots", "dg_add_shot_source", "dg_set_shot_order", "dg_set_options", "dg_set_mass_mode", "dg_num_nodes",
+EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_shots", "dg_add_shot_source", "dg_set_shot_order", "dg_set_options", "dg_set_mass_mode", "dg_set_op_precision", "dg_num_nodes",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
            "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_expire_wait", "dg_fma_peak", "dg_stage_times", "dg_autotune", "dg_add_receiver", "dg_sample", "dg_save_state",
            "dg_load_state", "dg_adjoint_bytes", "dg_adjoint_bind", "dg_adjoint_reset", "dg_adjoint_inject",
@@ -64,6 +65,7 @@ def lib():
         "dg_set_shot_order": (c_int, [P, c_int]),
         "dg_set_options": (c_int, [P, c_int, c_int, c_int]),
         "dg_set_mass_mode": (c_int, [P, c_int]),
+        "dg_set_op_precision": (c_int, [P, c_int]),
         "dg_num_nodes": (c_int, [P, POINTER(c_int64), POINTER(c_int64)]),
         "dg_node_coords": (c_int, [P, P]),
         "dg_face_neighbors": (c_int, [P, P, POINTER(c_int64)]),
@@ -172,6 +174,10 @@ def dg_set_options(ctx, bc: int, flux: int, precision: int):
 
 def dg_set_mass_mode(ctx, mode: int):
     _check(ctx, lib().dg_set_mass_mode(ctx, mode))
+
+
+def dg_set_op_precision(ctx, mode: int):
+    _check(ctx, lib().dg_set_op_precision(ctx, mode))
 
 
 def dg_num_nodes(ctx):
@@ -372,6 +378,7 @@ BC = {"dirichlet": DG_BC_DIRICHLET, "rigid": DG_BC_RIGID}
 FLUX = {"upwind": DG_FLUX_UPWIND, "central": DG_FLUX_CENTRAL}
 PREC = {"f32": DG_F32, "f64": DG_F64}
 MASS = {"onthefly": DG_MASS_ONTHEFLY, "stored": DG_MASS_STORED}
+OPS = {"fp32": DG_OPS_FP32, "tf32x3": DG_OPS_TF32X3, "tf32": DG_OPS_TF32, "bf16": DG_OPS_BF16}
 
 
 class Solver:
@@ -385,7 +392,7 @@ class Solver:
 
     def __init__(self, VX, EToV, etype, N: int, c2=None, rho=None, bc: str = "rigid", flux: str = "upwind",
                  precision: str = "f32", device: str = "cuda:0", stream=None, sources=(), mass: str = "stored",
-                 shots: int = 1, shot_sources=(), receivers=(), shot_order: str = "outer"):
+                 shots: int = 1, shot_sources=(), receivers=(), shot_order: str = "outer", ops: str = "fp32"):
         import torch
         self.torch = torch
         self.ctx = dg_mesh_create(VX, EToV, etype)
@@ -396,6 +403,7 @@ class Solver:
                 dg_set_material(self.ctx, np.ones(K) if c2 is None else c2, np.ones(K) if rho is None else rho)
             dg_set_options(self.ctx, BC[bc], FLUX[flux], PREC[precision])
             dg_set_mass_mode(self.ctx, MASS[mass])
+            dg_set_op_precision(self.ctx, OPS[ops])
             dg_set_shots(self.ctx, shots)
             dg_set_shot_order(self.ctx, {"outer": DG_SHOTS_OUTER, "inner": DG_SHOTS_INNER}[shot_order])
             self.shots = shots

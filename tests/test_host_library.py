@@ -303,3 +303,17 @@ def test_column_order_keeps_vertical_traces_in_the_block():
     assert sorted(perm.tolist()) == list(range(lm.K))
     ft, fq = _in_block_fractions(lm)
     assert ft == 0.0
+
+
+def test_op_precision_needs_fp32_fields():
+    m = I.cube_wavy_mesh(2, 2, 0.0)
+    ctx = dg.dg_mesh_create(m.VX, m.EToV, m.etype)
+    try:
+        dg.dg_set_order(ctx, 3)
+        dg.dg_set_options(ctx, dg.DG_BC_RIGID, dg.DG_FLUX_UPWIND, dg.DG_F64)
+        with pytest.raises(dg.DGError) as ei:
+            dg.dg_set_op_precision(ctx, dg.DG_OPS_TF32)
+        assert ei.value.code == dg.DG_ERR_ARG
+        dg.dg_set_op_precision(ctx, dg.DG_OPS_FP32)
+    finally:
+        dg.dg_destroy(ctx)
