@@ -279,7 +279,7 @@ def measure_order(N, args, torch, dev, m, c2, rho, mass, barrier=None):
     (several ranks) a barrier on both sides."""
     from paper_1607_03399_gb300.dg import Solver
     S = Solver(m.VX, m.EToV, m.etype, N, c2, rho, precision="f32", device=str(dev),
-               sources=[(0.5, 0.5, 0.5, 10.0, 0.1, 1.0)], mass=mass)
+               sources=[(0.5, 0.5, 0.5, 10.0, 0.1, 1.0)], mass=mass, ops=args.ops)
     q = np.random.default_rng(1).uniform(-1, 1, size=(4, S.total_nodes)).astype(np.float32)
     S.set_fields(q)
     dt = S.stable_dt(0.5)
@@ -436,6 +436,56 @@ def measure_multishot(args, torch, dev):
             "ratio": ms_a / ms_b, "batched_gdofs": S * 4 * 40 * m.K * 5 * n / (ms_b / 1e3) / 1e9,
             "shot_inner": {"batched_shot_steps_per_s": S * n / (ms_i / 1e3), "ratio": ms_a / ms_i,
                            "batched_gdofs": S * 4 * 40 * m.K * 5 * n / (ms_i / 1e3) / 1e9}}
+
+
+def measure_precision(args, torch, dev):
+    """Operator-precision variants (dg_set_op_precision) on the batched
+    workload: 2x64x64 footprint x 32 bumpy layers = 262144 wedges, N=3, FP32
+    fields, 64 shots with their Ricker sources, one launch per stage.  Every
+    variant starts from the same seeded random state (drawn on the device),
+    takes the warm-up and then the timed steps; reported per variant: field
+    GDOF-updates/s, shot-steps/s and the relative L2 deviation of its final
+    state from the FP32 CUDA-core variant's (GPU against GPU: the variants'
+    errors against the FP64 oracle are measured by the precision tests)."""
+    from paper_1607_03399_gb300 import inputs as I
+    from paper_1607_03399_gb300.dg import Solver
+    S = 64
+    m = I.bumpy_layered_mesh(64, 32)
+    c2, rho = I.layered_wavespeed(m)
+    pos = I.surface_shots(S, 4)
+    n = max(3, min(args.steps // 20, 10))
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gen = torch.Generator(device=dev)
+    ref, ref_norm, out = None, None, {}
+    for ops in ("fp32", "tf32x3", "tf32", "bf16"):
+        B = Solver(m.VX, m.EToV, m.etype, 3, c2, rho, precision="f32", device=str(dev), shots=S,
+                   shot_sources=[(s, *pos[s], 8.0, 0.125, 1.0) for s in range(S)], ops=ops)
+        gen.manual_seed(4)
+        q = torch.rand((S, 4, B.total_nodes), device=dev, dtype=torch.float32, generator=gen).mul_(2.0).sub_(1.0)
+        B.set_fields(q)
+        B.sync()
+        del q
+        dt = B.stable_dt(0.5)
+        B.step(dt, args.warmup)
+        B.sync()
+        start.record(B.stream)
+        B.step(dt, n)
+        end.record(B.stream)
+        end.synchronize()
+        ms = start.elapsed_time(end)
+        qf = B.get_fields(device=True)
+        B.close()
+        if ref is None:
+            ref, ref_norm, dev_rel = qf, float(torch.linalg.vector_norm(qf, dtype=torch.float64)), 0.0
+        else:
+            dev_rel = float(torch.linalg.vector_norm(qf - ref, dtype=torch.float64)) / ref_norm
+            del qf
+        out[ops] = {"gdofs": S * 4 * 40 * m.K * 5 * n / (ms / 1e3) / 1e9, "shot_steps_per_s": S * n / (ms / 1e3),
+                    "stage_us": ms * 1e3 / (5 * n), "rel_dev_from_fp32": dev_rel}
+    del ref
+    torch.cuda.empty_cache()
+    return {"workload": "multishot_2x64x64x32_N3_64shots_random_state", "wedges": m.K, "shots": S,
+            "steps": n + args.warmup, "timed_steps": n, "variants": out}
 
 
 def measure_multimesh(args, torch, dev):
@@ -666,9 +716,10 @@ def run_ours(args, rank, world):
         r["solver"] = None
     hybrid = measure_hybrid(args, torch, dev) if (rank == 0 and not args.no_hybrid) else None
     hybrid6 = measure_hybrid(args, torch, dev, tet_layers=6) if (rank == 0 and not args.no_hybrid) else None
-    config1 = measure_config1(args, torch, dev) if rank == 0 else None
+    config1 = measure_config1(args, torch, dev) if (rank == 0 and not args.no_config1) else None
     multishot = measure_multishot(args, torch, dev) if (rank == 0 and not args.no_batched) else None
     multimesh = measure_multimesh(args, torch, dev) if (rank == 0 and not args.no_batched) else None
+    precision = measure_precision(args, torch, dev) if (rank == 0 and not args.no_batched) else None
     adjoint = measure_adjoint(args, torch, dev) if (rank == 0 and not args.no_adjoint) else None
     adjoint_hybrid = measure_adjoint_hybrid(args, torch, dev) if (rank == 0 and not args.no_adjoint) else None
     # the headline order once more with the other way of applying the mass inverse
@@ -731,7 +782,7 @@ def run_ours(args, rank, world):
                    "wedges": K, "order": orders[0], "field_dof": r3["dof"], "element_order": args.element_order,
                    "l2_flush": "inputs larger than L2 (3 state buffers of %.0f MB)" % (r3["dof"] * 4 / 1e6),
                    "bc": "rigid", "flux": "upwind", "source": "Ricker f0=10 t0=0.1 at (0.5,0.5,0.5)",
-                   "mass": args.mass},
+                   "mass": args.mass, "ops": args.ops},
         "roofline": {"kernel": f"k_wedge_stage<{orders[0]}>", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": _traffic_per_launch(args.mass) if (args.workload == "full" and orders[0] == 3
@@ -751,6 +802,7 @@ def run_ours(args, rank, world):
         "hybrid": hybrid,
         "multishot": multishot,
         "multimesh": multimesh,
+        "precision": precision,
         "adjoint": adjoint,
         "adjoint_hybrid": adjoint_hybrid,
         "e2e": r3.get("e2e"),
@@ -779,11 +831,14 @@ def main():
     ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid wedge + tet workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the multi-shot and multi-mesh workloads")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) workload")
+    ap.add_argument("--no-config1", action="store_true", help="skip the FP64 accuracy case (128 wedges, 200 steps)")
     ap.add_argument("--element-order", default="column", choices=["column", "layer"],
                     help="element order of the layered workload (layer: the comparison for the column order)")
     ap.add_argument("--adjoint-size", default="full", choices=sorted(ADJOINT_SIZES),
                     help="size of the adjoint workload (small: the profiling case)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-variant autotuner after timing")
+    ap.add_argument("--ops", default="fp32", choices=["fp32", "tf32x3", "tf32", "bf16"],
+                    help="how the wedge stage applies the shared triangle operators (CUDA-core FP32 or tensor cores)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -166,12 +166,12 @@ int dg_set_options(dg_ctx* ctx, int bc, int flux, int precision);
  * Before dg_bind.  Errors: DG_ERR_ARG (unknown mode), DG_ERR_STATE. */
 int dg_set_mass_mode(dg_ctx* ctx, int mode);
 
-/* How the wedge stage applies the shared reference triangle operators of
- * Section 4.2 -- M^tri in the weak-form accumulation and D_r, D_s in the
- * strong part; the Nt x Nt matrices common to every element, applied to a
- * whole 32-element block slice by slice (the per-element geometric factors
- * of Lemma 3.1 and the per-element mass inverse stay in FP32 on the CUDA
- * cores):
+/* How the wedge stage applies the shared reference triangle mass matrix of
+ * Section 4.2, M^tri, in the weak-form accumulation (per slice, 4 fields:
+ * W_j = M^tri G_j) -- the Nt x Nt matrix common to every element, applied to
+ * a whole 32-element block slice by slice (the per-element geometric factors
+ * of Lemma 3.1, the per-element mass inverse and the strong D_r, D_s part stay
+ * FP32 on the CUDA cores):
  *   DG_OPS_FP32    FP32 fused multiply-adds on the CUDA cores (default);
  *   DG_OPS_TF32X3  tensor cores, each operand split into two TF32 numbers
  *                  (three products, FP32 accumulation): about FP32 accuracy;

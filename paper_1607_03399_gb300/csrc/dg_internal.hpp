@@ -151,10 +151,13 @@ enum : int { kErrTimeout = 1, kErrNonfinite = 2 };
 // 3xTF32 (about FP32 accuracy), TF32 or BF16 operands and FP32 accumulation
 // (FP32 fields only).
 enum : int { kOpFFMA = 0, kOpTF32x3 = 1, kOpTF32 = 2, kOpBF16 = 3 };
-// row pitch (floats) of the per-warp operand tiles of the tensor-core applies:
-// 8 mod 32, so the B-operand loads (4 rows x 8 columns) and the 64-bit C
-// stores (half-warps over 4 rows) hit distinct banks
-constexpr int kTP = 4 * 32 + 8;
+// Per-warp operand tiles of the tensor-core applies: Nt rows of 128 columns
+// (element lane * 4 + field), column c of row r stored at r * 128 +
+// (c XOR ((r mod 4) * 8)): the lanes' 16-byte row accesses, the B-operand
+// loads (4 rows x 8 columns) and the 64-bit C stores (half-warps over 4 rows)
+// all hit distinct banks.
+constexpr int kTP = 4 * 32;
+__host__ __device__ constexpr int tile_at(int r, int c) { return r * kTP + (c ^ ((r & 3) << 3)); }
 
 // Launchers, one set per (precision, order) translation unit k_<p>_n<N>.cu;
 // all return 0 or a cudaError_t value.

@@ -235,18 +235,18 @@ __device__ __forceinline__ void afrag_load(const float* Op, int lane, AFrag<OP>&
     }
   }
 }
-// B operand of one n-tile: column `col` of the Nt-row tile B (row pitch P);
-// rows >= Nt are zero (never read).  TF32: [k-step] (k = t, t + 4) per step;
-// BF16: (2t, 2t + 1) and (2t + 8, 2t + 9).
+// B operand of one n-tile: column `col` of the Nt-row operand tile B (layout
+// tile_at); rows >= Nt are zero (never read).  TF32: [k-step] (k = t, t + 4)
+// per step; BF16: (2t, 2t + 1) and (2t + 8, 2t + 9).
 template <int OP>
 struct BFrag {
   uint32_t h[2][2];
   uint32_t l[OP == kOpTF32x3 ? 2 : 1][2];
 };
 template <int NT, int OP>
-__device__ __forceinline__ void bfrag_load(const float* B, int P, int col, int lane, BFrag<OP>& F) {
+__device__ __forceinline__ void bfrag_load(const float* B, int col, int lane, BFrag<OP>& F) {
   const int t = lane & 3;
-  auto bv = [&](int k) -> float { return k < NT ? B[k * P + col] : 0.f; };
+  auto bv = [&](int k) -> float { return k < NT ? B[tile_at(k, col)] : 0.f; };
   if constexpr (OP == kOpBF16) {
     F.h[0][0] = bf16x2_of(bv(2 * t), bv(2 * t + 1));
     F.h[0][1] = bf16x2_of(bv(2 * t + 8), bv(2 * t + 9));
@@ -388,14 +388,15 @@ enum WGeo : int {
   G_TX0, G_TX1, G_TY0, G_TY1, G_COUNT
 };
 
-// Residual slab staged in shared memory by the bulk copy (N <= 3, FP32 FMA
-// applies).  At N = 4 the staged slab measured slower (77 KB of copies per
-// block in flight at two CTAs per SM), and the tensor-core variants spend
-// that shared memory on their operand tiles, so there the residual is read
-// from global memory at the update.
+// Residual slab staged in shared memory by the bulk copy (N <= 3).  At N = 4
+// the staged slab measured slower (77 KB of copies per block in flight at two
+// CTAs per SM), so there the residual is read from global memory at the
+// update.  With tensor-core applies the operand tiles (Nq x Nt x 128 reals,
+// the size of the residual slab) share the residual slab's space: the
+// residual is copied in once the weak-form accumulation has released them.
 template <int N, int OP = kOpFFMA>
 __host__ __device__ constexpr bool stage_res() {
-  return N <= 3 && OP == kOpFFMA;
+  return N <= 3;
 }
 
 template <int N, int OP = kOpFFMA>
@@ -406,8 +407,9 @@ struct WedgeSmem {
   static constexpr int L = r + (stage_res<N, OP>() ? 4 * Np * kB : 0);   // [Nt(Nt+1)/2][32]
   static constexpr int F = L + (Nt * (Nt + 1) / 2) * kB;                 // [4][Nt][32]
   static constexpr int G = F + 4 * Nt * kB;                              // [G_COUNT][32]
-  static constexpr int T = G + G_COUNT * kB;                             // per warp [Nt][kTP] (tensor cores)
-  static constexpr int reals = T + (OP == kOpFFMA ? 0 : Nq * Nt * kTP);
+  // per-warp operand tiles [Nt][kTP] (tensor cores): the residual slab's space where it is staged
+  static constexpr int T = stage_res<N, OP>() ? r : G + G_COUNT * kB;
+  static constexpr int reals = G + G_COUNT * kB + ((OP == kOpFFMA || stage_res<N, OP>()) ? 0 : Nq * Nt * kTP);
 };
 
 template <int N, int OP = kOpFFMA>
@@ -432,7 +434,7 @@ __host__ __device__ constexpr int wedge_smem_bytes() {
 // resident CTAs per SM the stage is compiled for
 template <int N, int BPC, int OP>
 __host__ __device__ constexpr int wedge_min_ctas() {
-  return sizeof(REAL) == 4 ? (OP != kOpFFMA ? (N >= 4 ? 2 : 3) : (N >= 4 ? 2 : 4 / BPC)) : 1;
+  return sizeof(REAL) == 4 ? (N >= 4 ? 2 : 4 / BPC) : 1;
 }
 
 // Lemma 3.1 for one wedge: everything the stage needs, from the six vertices
@@ -532,7 +534,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
   real* sL = base + SM::L;
   real* sF = base + SM::F;
   real* sG = base + SM::G;
-  real* sT = base + SM::T + (OP == kOpFFMA ? 0 : j * Nt * kTP);  // this warp's operand tile (tensor cores)
+  real* sT = base + SM::T + j * Nt * kTP;  // this warp's operand tile (tensor cores)
   const DevMesh<real>& M = A.m;
   const real* __restrict__ qin = A.q_in;
   real* __restrict__ qout = A.q_out;
@@ -544,6 +546,9 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
   const int Kp = M.Kw_pad;
   constexpr uint32_t slab_bytes = uint32_t(4 * Np * kB * sizeof(real));
   const bool res_async = rk && stage_res<N, OP>();
+  // the residual copy is issued with the state's (FP32 FMA applies) or after
+  // the weak-form accumulation, once the operand tiles in its space are free
+  const bool res_early = res_async && OP == kOpFFMA;
 #define GEO(item) sG[(item) * kB + lane]
 
   if (!live) return;  // padding block of the last CTA
@@ -574,7 +579,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
     bulk_g2s(sq, qin + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[0]);
     // stored mass factor: straight into the factor table with the state slab
     if (stored) bulk_g2s(sL, M.w_fac + int64_t(blk) * NL * kB, fac_bytes, &bar[0]);
-    if (res_async) {
+    if (res_early) {
       mbar_expect_tx(&bar[1], slab_bytes);
       bulk_g2s(sr, resg + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[1]);
     }
@@ -590,11 +595,14 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
     qnbr[ed] = M.w_nbr[(2 + ed) * Kp + e];
     qcode[ed] = M.w_code[(2 + ed) * Kp + e];
   }
+  // (at N = 4 the traces held across the wait cost spills: there they are
+  // requested after it, with the in-block ones)
+  constexpr bool early = N <= 3;
   Q4 nv[3][Nq];
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
     const int nbr = qnbr[ed];
-    if (nbr >= 0 && (nbr >> 5) != blk) {
+    if (early && nbr >= 0 && (nbr >> 5) != blk) {
       const int ep = qcode[ed] >> 1, rev = qcode[ed] & 1;
       const real* base = qin + widx<N>(nbr >> 5, 0, nbr & 31);
 #pragma unroll
@@ -651,7 +659,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
     // the state slab never arrived: report, let any copy in flight drain, leave
     if (leader) {
       atomicOr(M.err, kErrTimeout);
-      if (res_async) mbar_wait_bounded(&bar[1], 0);
+      if (res_early) mbar_wait_bounded(&bar[1], 0);
       mbar_wait_bounded(&bar[0], 0);
       mbar_wait_bounded(&bar[2], 0);
     }
@@ -665,14 +673,16 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
   for (int i = 0; i < Nt; ++i) Wp[i] = Wu[0][i] = Wu[1][i] = Wu[2][i] = real(0);
   // neighbour traces of quadrilateral faces whose neighbour lies in this block
   // (or, on a boundary face, the element's own trace, which the ghost state
-  // then replaces) from the shared slab; the others were requested above
+  // then replaces) from the shared slab; the others were requested above (or,
+  // at N = 4, now, by one generic load each)
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
     const int nbr = qnbr[ed];
     const bool bnd = nbr < 0;
-    if (bnd || (nbr >> 5) == blk) {
+    const bool inblk = bnd || (nbr >> 5) == blk;
+    if (inblk || !early) {
       const int ep = bnd ? ed : qcode[ed] >> 1, rev = bnd ? 0 : qcode[ed] & 1;
-      const real* base = sq + ((bnd ? lane : (nbr & 31)) << 2);
+      const real* base = inblk ? sq + ((bnd ? lane : (nbr & 31)) << 2) : qin + widx<N>(nbr >> 5, 0, nbr & 31);
 #pragma unroll
       for (int m = 0; m < Nq; ++m) nv[ed][m] = ldx4(base + (j * Nt + O.tab.edge[ep][rev ? N - m : m]) * (kB * 4));
     }
@@ -826,7 +836,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
         const float4 gv = make_float4(
             cb * sF[(0 * Nt + i) * kB + lane] + ct * sF[(2 * Nt + i) * kB + lane] - (txJ * dux + tyJ * duy + Aj * duz),
             nb0 * fp + nt0 * fq - txJ * dpp, nb1 * fp + nt1 * fq - tyJ * dpp, nb2 * fp + nt2 * fq - Aj * dpp);
-        *reinterpret_cast<float4*>(sT + i * kTP + lane * 4) = gv;
+        *reinterpret_cast<float4*>(sT + tile_at(i, lane * 4)) = gv;
       }
       __syncwarp();
       {
@@ -836,23 +846,31 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
 #pragma unroll 2
         for (int nt = 0; nt < 16; ++nt) {
           BFrag<OP> Bf;
-          bfrag_load<Nt, OP>(sT, kTP, nt * 8 + g, lane, Bf);
+          bfrag_load<Nt, OP>(sT, nt * 8 + g, lane, Bf);
           float d[4] = {0.f, 0.f, 0.f, 0.f};
           op_mma<Nt, OP>(Am, Bf, d);
-          if (g < Nt) *reinterpret_cast<float2*>(sT + g * kTP + nt * 8 + 2 * t) = make_float2(d[0], d[1]);
-          if (g + 8 < Nt) *reinterpret_cast<float2*>(sT + (g + 8) * kTP + nt * 8 + 2 * t) = make_float2(d[2], d[3]);
+          if (g < Nt) *reinterpret_cast<float2*>(sT + tile_at(g, nt * 8 + 2 * t)) = make_float2(d[0], d[1]);
+          if (g + 8 < Nt) *reinterpret_cast<float2*>(sT + tile_at(g + 8, nt * 8 + 2 * t)) = make_float2(d[2], d[3]);
         }
       }
       __syncwarp();
 #pragma unroll
       for (int i = 0; i < Nt; ++i) {
-        const float4 w = *reinterpret_cast<const float4*>(sT + i * kTP + lane * 4);
+        const float4 w = *reinterpret_cast<const float4*>(sT + tile_at(i, lane * 4));
         Wp[i] += w.x;
         Wu[0][i] += w.y;
         Wu[1][i] += w.z;
         Wu[2][i] += w.w;
       }
-      __syncwarp();
+      if (res_async) {
+        // every warp is done with its tile: the residual slab may now land in their space
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        block_sync();
+        if (leader) {
+          mbar_expect_tx(&bar[1], slab_bytes);
+          bulk_g2s(sr, resg + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[1]);
+        }
+      }
     }
   }
   // (d) X = (M^{tri,k})^{-1} W: forward and backward substitution, 4 right-hand sides
@@ -888,8 +906,11 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
     Wu[1][i] *= d;
     Wu[2][i] *= d;
   }
-  // (e) strong r, s parts of slice j (constant metric terms, Lemma 3.1)
-  if constexpr (OP == kOpFFMA) {
+  // (e) strong r, s parts of slice j (constant metric terms, Lemma 3.1), on
+  // the CUDA cores for every variant (on the tensor cores the results would
+  // have to pass through shared memory back to the element's lane, which
+  // measured slower than these FMAs with constant operands)
+  {
     const real rx = GEO(G_RX), ry = GEO(G_RY), sx = GEO(G_SX), sy = GEO(G_SY);
     real pv[Nt], av[Nt], bv[Nt];
 #pragma unroll
@@ -913,40 +934,6 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
       Wu[0][i] -= rx * pr + sx * ps;
       Wu[1][i] -= ry * pr + sy * ps;
     }
-  } else {
-    // on the tensor cores: D_r and D_s of slice j of the whole slab (columns
-    // lane * 4 + field); the thread pairs holding an element's (p, u) and
-    // (v, w) columns combine them with the element's metric terms into
-    // (div u, d_x p, d_y p), stored to this warp's tile and subtracted by
-    // the element's lane at the update
-    AFrag<OP> Ar, As;
-    afrag_load<Nt, OP>(O.w.Dr, lane, Ar);
-    afrag_load<Nt, OP>(O.w.Ds, lane, As);
-    const int g = lane >> 2, t = lane & 3;
-    const real* Bj = sq + j * Nt * (kB * 4);
-#pragma unroll 2
-    for (int nt = 0; nt < 16; ++nt) {
-      BFrag<OP> Bf;
-      bfrag_load<Nt, OP>(Bj, kB * 4, nt * 8 + g, lane, Bf);
-      float dr[4] = {0.f, 0.f, 0.f, 0.f}, ds[4] = {0.f, 0.f, 0.f, 0.f};
-      op_mma<Nt, OP>(Ar, Bf, dr);
-      op_mma<Nt, OP>(As, Bf, ds);
-      // columns nt * 8 + 2t, + 1: element E = 2 nt + t / 2, fields (p, u) for even t, (v, w) for odd t
-      const int E = 2 * nt + (t >> 1);
-      const real rx = sG[G_RX * kB + E], ry = sG[G_RY * kB + E], sx = sG[G_SX * kB + E], sy = sG[G_SY * kB + E];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float a = dr[2 * h], b = dr[2 * h + 1], c = ds[2 * h], d = ds[2 * h + 1];
-        // even t: a = D_r p, b = D_r u, c = D_s p, d = D_s u; odd t: the same of v and w
-        const float part = (t & 1) ? ry * a + sy * c : rx * b + sx * d;
-        const float other = __shfl_xor_sync(0xffffffffu, part, 1);
-        const int row = g + 8 * h;
-        if (!(t & 1) && row < Nt)
-          *reinterpret_cast<float4*>(sT + row * kTP + E * 4) =
-              make_float4(part + other, rx * a + sx * c, ry * a + sy * c, 0.f);
-      }
-    }
-    __syncwarp();
   }
   // (f) fused low-storage Runge-Kutta update (or plain right-hand side)
   if (res_async && !mbar_wait_bounded(&bar[1], 0)) {
@@ -960,12 +947,6 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
     for (int i = 0; i < Nt; ++i) {
       const int n = j * Nt + i;
       const int64_t g = widx<N>(blk, n, lane);
-      if constexpr (OP != kOpFFMA) {
-        const float4 sv = *reinterpret_cast<const float4*>(sT + i * kTP + lane * 4);
-        Wp[i] -= sv.x;
-        Wu[0][i] -= sv.y;
-        Wu[1][i] -= sv.z;
-      }
       Q4 r{kappa * Wp[i], irho * Wu[0][i], irho * Wu[1][i], irho * Wu[2][i]};
       if (rk) {
         const Q4 r0 = stage_res<N, OP>() ? lds4(sr, n, lane) : ld4(resg, g);

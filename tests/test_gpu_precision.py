@@ -1,6 +1,7 @@
 """Operator applies on the tensor cores (dg_set_op_precision): the shared
-triangle operators M^tri, D_r, D_s of the wedge stage applied with 3xTF32,
-TF32 or BF16 operands and FP32 accumulation, fields FP32.  Each variant's
+triangle mass matrix M^tri of the wedge stage's weak-form accumulation
+applied with 3xTF32, TF32 or BF16 operands and FP32 accumulation, fields
+FP32.  Each variant's
 error against the FP64 oracle per right-hand side and after 1000 LSRK45
 steps, and the discrete energy over those steps (upwind: non-increasing)."""
 import numpy as np
