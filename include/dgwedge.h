@@ -147,6 +147,17 @@ int dg_add_shot_source(dg_ctx* ctx, int64_t shot, double x, double y, double z, 
  * change.  Before dg_bind.  Errors: DG_ERR_ARG (unknown order), DG_ERR_STATE. */
 int dg_set_shot_order(dg_ctx* ctx, int order);
 
+/* Shots per block group (no counterpart in the paper; the layout choice of
+ * the batched form): shots in groups of G (1 <= G, G divides the shot count;
+ * call after dg_set_shots), virtual element (s / G) K G + i G + s % G, so a
+ * 32-lane block holds 32 / G elements of G shots each (G >= 32: the G shots
+ * of one element span G / 32 blocks).  G = 1 is DG_SHOTS_OUTER, G = shots
+ * is DG_SHOTS_INNER.  Results are identical bit for bit for every G; the
+ * canonical field layout does not change.  Before dg_bind.  dg_autotune_layout
+ * picks G by timing.  Errors: DG_ERR_ARG (G does not divide the shots),
+ * DG_ERR_STATE. */
+int dg_set_shot_group(dg_ctx* ctx, int64_t group);
+
 /* Boundary condition (DG_BC_*), flux (DG_FLUX_*), arithmetic precision
  * (DG_F32: fields and arithmetic in float; DG_F64: double).
  * Default: rigid walls, upwind, DG_F32. */
@@ -273,6 +284,18 @@ int dg_stage_times(dg_ctx* ctx, int nrep, double* us_wedge, double* us_tet);
  * All variants compute the same operator up to rounding.  Synchronous.
  * Errors: DG_ERR_ARG, DG_ERR_STATE (before dg_bind), DG_ERR_CUDA. */
 int dg_autotune(dg_ctx* ctx, int nrep, int* variant, double* us);
+
+/* Layout autotuner of the batched form (not in the paper; the paper tunes
+ * its kernels' elements per block, Section 6.2): re-lays out the bound
+ * context's element tables for every shots-per-group choice G of
+ * dg_set_shot_group (1, 2, 4, ... and the shot count, each dividing it),
+ * times one stage of each element type (nrep launches, as dg_stage_times)
+ * and keeps the G with the shortest total.  *group = that G, *us = its
+ * microseconds per stage.  The state buffers and the simulation time are
+ * reset to zero: call it after dg_bind and before dg_set_fields.  The
+ * operator is the same for every G (bit for bit).  Synchronous.
+ * Errors: DG_ERR_ARG, DG_ERR_STATE (before dg_bind), DG_ERR_CUDA. */
+int dg_autotune_layout(dg_ctx* ctx, int nrep, int64_t* group, double* us);
 
 /* ---------------------------------------------------------------- receivers
  * Pressure receivers (not in the paper; the inversion workloads need them):

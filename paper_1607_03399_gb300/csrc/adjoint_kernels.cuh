@@ -22,7 +22,7 @@ __global__ void k_sample(const DevMesh<real> M, const real* __restrict__ q, real
   if (idx >= nshots * M.nrec) return;
   const int shot = idx / M.nrec, r = idx - shot * M.nrec;
   const RecDev rd = M.rec[r];
-  const int e = M.shot_inner ? rd.elem * M.nshots + shot : shot * (rd.type == 6 ? M.Kw1 : M.Kt1) + rd.elem;
+  const int e = int(shot_vid(shot, rd.elem, rd.type == 6 ? M.Kw1 : M.Kt1, M.shot_group));
   const int np = rd.type == 6 ? npw_of(N) : npt_of(N);
   real acc = 0;
   for (int n = 0; n < np; ++n) acc += M.rec_l[rd.loff + n] * q[pidx<N>(M, rd.type, e, n)];
@@ -40,7 +40,7 @@ __global__ void k_inject(const DevMesh<real> M, real* __restrict__ muq, real* __
   if (idx >= nshots * M.nrgrp) return;
   const int shot = idx / M.nrgrp, gi = idx - shot * M.nrgrp;
   const RecGroup g = M.rgrp[gi];
-  const int e = M.shot_inner ? g.elem * M.nshots + shot : shot * (g.type == 6 ? M.Kw1 : M.Kt1) + g.elem;
+  const int e = int(shot_vid(shot, g.elem, g.type == 6 ? M.Kw1 : M.Kt1, M.shot_group));
   const real kappa = g.type == 6 ? M.w_mat[e] : M.t_mat[e];
   const int np = g.type == 6 ? npw_of(N) : npt_of(N);
   for (int n = 0; n < np; ++n) {

@@ -138,7 +138,10 @@ struct dg_ctx {
   int op = DG_OPS_FP32;  // how the wedge stage applies the shared triangle operators
   // shots: independent copies of the state on the same mesh, advanced together
   int64_t shots = 1;
-  bool shot_inner = false;  // DG_SHOTS_INNER: the shots of one element are neighbouring lanes
+  // shots per group G (dg_set_shot_group; 0 = all shots, DG_SHOTS_INNER): the G
+  // shots of a group are neighbouring lanes for each element
+  int64_t shot_group = 1;
+  int64_t group() const { return shot_group == 0 ? shots : shot_group; }
   double t_stage_host = 0.0;  // staging for clock uploads
   // launch variant chosen by dg_autotune: wedge blocks per CTA (0 = default) and
   // whether the stored mass factor is bypassed (factor recomputed in the stage)
@@ -400,9 +403,9 @@ BlobLayout blob_layout(const dg_ctx* c) {
   for (const auto& sc : c->sources) ng += sc.g.size();
   L.srcg = take((ng > 0 ? ng : 1) * rs);
   L.clock = take(sizeof(double));
-  // stored mass factors: per wedge block [Nt (Nt + 1) / 2][32], the stage's shared-memory layout
-  const int64_t nl = int64_t(nt_of(c->N)) * (nt_of(c->N) + 1) / 2;
-  L.wfac = take(c->mass == DG_MASS_STORED ? size_t(Kwp * nl) * rs : 0);
+  // stored mass factors: per wedge block [NL4][32][4], the stage's shared-memory layout
+  const int64_t nl4 = nl4_of(c->N);
+  L.wfac = take(c->mass == DG_MASS_STORED ? size_t(Kwp * nl4 * 4) * rs : 0);
   // per wedge block [12][32]: x, y of the three bottom vertices, z of the six
   L.wxyz = take(size_t(Kwp) * 12 * rs);
   // per tet block [12][32]: x, y, z of the four vertices
@@ -424,10 +427,15 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
   const int64_t S = c->shots, T = c->wedge_nodes + c->tet_nodes;
   const int64_t VKw = S * Kw, VKt = S * Kt;
   const int64_t Kwp = nblk(VKw) * kB, Ktp = nblk(VKt) * kB;
-  // virtual id of (shot s, input element n): shot-major (s K + i) or shot-inner (i S + s)
-  const bool inner = c->shot_inner;
-  auto vid = [&](int64_t s, int64_t n) {
-    return inner ? c->local[n] * S + s : s * (c->etype[n] == DG_WEDGE ? Kw : Kt) + c->local[n];
+  // virtual id of (shot s, input element n): shots in groups of G, a group's
+  // shots consecutive per element (G = 1 shot-major, G = S shot-inner)
+  const int64_t G = c->group();
+  auto vid = [&](int64_t s, int64_t n) { return shot_vid(s, c->local[n], c->etype[n] == DG_WEDGE ? Kw : Kt, G); };
+  // (shot, type-local element) of a virtual element
+  auto vsplit = [&](int64_t v, int64_t K1, int64_t& sh, int64_t& el) {
+    const int64_t r = v % (K1 * G);
+    el = r / G;
+    sh = (v / (K1 * G)) * G + r % G;
   };
   int* w_vid = reinterpret_cast<int*>(blob.data() + L.w_vid);
   int* w_nbr = reinterpret_cast<int*>(blob.data() + L.w_nbr);
@@ -436,8 +444,9 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
   int64_t* w_canon = reinterpret_cast<int64_t*>(blob.data() + L.w_canon);
   for (int64_t w = 0; w < Kwp; ++w) {
     const bool real_slot = w < VKw;  // padding replicates a valid element with no neighbours
-    const int64_t s = real_slot ? (inner ? w % S : w / Kw) : 0;
-    const int64_t k = c->wedges[real_slot ? (inner ? w / S : w % Kw) : 0];
+    int64_t s = 0, el = 0;
+    if (real_slot) vsplit(w, Kw, s, el);
+    const int64_t k = c->wedges[el];
     for (int v = 0; v < 6; ++v) w_vid[v * Kwp + w] = int(c->EToV[k * 6 + v]);
     for (int f = 0; f < 5; ++f) {
       const int64_t n = real_slot ? c->nbr[k][f] : -1;
@@ -467,8 +476,9 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
   int64_t* t_canon = reinterpret_cast<int64_t*>(blob.data() + L.t_canon);
   for (int64_t t = 0; t < Ktp; ++t) {
     const bool real_slot = t < VKt;
-    const int64_t s = real_slot ? (inner ? t % S : t / Kt) : 0;
-    const int64_t k = c->tets[real_slot ? (inner ? t / S : t % Kt) : 0];
+    int64_t s = 0, el = 0;
+    if (real_slot) vsplit(t, Kt, s, el);
+    const int64_t k = c->tets[el];
     for (int v = 0; v < 4; ++v) t_vid[v * Ktp + t] = int(c->EToV[k * 6 + v]);
     for (int f = 0; f < 4; ++f) {
       const int64_t n = real_slot ? c->nbr[k][f] : -1;
@@ -627,9 +637,13 @@ void fill_blob(const dg_ctx* c, const BlobLayout& L, std::vector<unsigned char>&
         for (int l = 0; l <= i; ++l)
           one[size_t(w) * nl + i * (i + 1) / 2 + l] = real(l < i ? Lk[size_t(i) * nt + l] : 1.0 / Lk[size_t(i) * nt + i]);
     }
+    const int64_t nl4 = nl4_of(c->N);
     for (int64_t w = 0; w < Kwp; ++w) {
-      const int64_t lw = w < VKw ? (inner ? w / S : w % Kw) : 0, b = w / kB, lane = w % kB;
-      for (int q = 0; q < nl; ++q) fac[(b * nl + q) * kB + lane] = one[size_t(lw) * nl + q];
+      int64_t sh = 0, lw = 0;
+      if (w < VKw) vsplit(w, Kw, sh, lw);
+      const int64_t b = w / kB, lane = w % kB;
+      for (int q = 0; q < nl4 * 4; ++q)
+        fac[((b * nl4 + q / 4) * kB + lane) * 4 + q % 4] = q < nl ? one[size_t(lw) * nl + q] : real(0);
     }
   }
 }
@@ -681,7 +695,7 @@ void fill_devmesh(const dg_ctx* c, const BlobLayout& L, DevMesh<real>& m) {
   }
   m.Kw1 = int(c->wedges.size());
   m.Kt1 = int(c->tets.size());
-  m.shot_inner = c->shot_inner ? 1 : 0;
+  m.shot_group = int(c->group());
   m.nshots = int(c->shots);
   m.t_srng = reinterpret_cast<const int*>(b + L.tsrng);
   m.clock = reinterpret_cast<double*>(b + L.clock);
@@ -1126,6 +1140,8 @@ int dg_set_shots(dg_ctx* c, int64_t shots) {
     if (sc.shot >= shots) return c->fail(DG_ERR_ARG, "a source refers to a shot beyond the new count");
   const int64_t K = int64_t(std::max(c->wedges.size(), c->tets.size()));
   if (shots * K >= (int64_t(1) << 30)) return c->fail(DG_ERR_ARG, "shots x elements exceeds 2^30");
+  if (c->shot_group > 1 && shots % c->shot_group != 0)
+    return c->fail(DG_ERR_ARG, "the shot group must divide the number of shots");
   c->shots = shots;
   return DG_OK;
 }
@@ -1134,7 +1150,15 @@ int dg_set_shot_order(dg_ctx* c, int order) {
   if (!c) return DG_ERR_ARG;
   if (c->bound) return c->fail(DG_ERR_STATE, "dg_set_shot_order after dg_bind");
   if (order != DG_SHOTS_OUTER && order != DG_SHOTS_INNER) return c->fail(DG_ERR_ARG, "unknown shot order");
-  c->shot_inner = order == DG_SHOTS_INNER;
+  c->shot_group = order == DG_SHOTS_INNER ? 0 : 1;
+  return DG_OK;
+}
+
+int dg_set_shot_group(dg_ctx* c, int64_t group) {
+  if (!c) return DG_ERR_ARG;
+  if (c->bound) return c->fail(DG_ERR_STATE, "dg_set_shot_group after dg_bind");
+  if (group < 1 || c->shots % group != 0) return c->fail(DG_ERR_ARG, "the shot group must divide the number of shots");
+  c->shot_group = group;
   return DG_OK;
 }
 
@@ -1310,6 +1334,7 @@ int dg_bind(dg_ctx* c, void* d_mesh, void* d_q0, void* d_q1, void* d_res, void* 
   if (!d_mesh || !d_q0 || !d_q1 || !d_res) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->N) return c->fail(DG_ERR_STATE, "dg_bind before dg_set_order");
   if (c->bound) return c->fail(DG_ERR_STATE, "context already bound");
+  if (c->shots % c->group() != 0) return c->fail(DG_ERR_ARG, "the shot group must divide the number of shots");
   for (void* p : {d_mesh, d_q0, d_q1, d_res})
     if (reinterpret_cast<uintptr_t>(p) % 256) return c->fail(DG_ERR_ARG, "device buffers must be 256-byte aligned");
   cudaError_t e = cudaGetDevice(&c->device);
@@ -1511,16 +1536,18 @@ int dg_stage_times(dg_ctx* c, int nrep, double* us_w, double* us_t) {
   }
   const DevMesh<float> m32 = c->m32;
   const DevMesh<double> m64 = c->m64;
+  // element blocks of each type in the context's precision (only that mesh is filled)
+  const int nbw = c->prec == DG_F64 ? m64.nblk_w : m32.nblk_w, nbt = c->prec == DG_F64 ? m64.nblk_t : m32.nblk_t;
   for (int type = 0; type < 2 && rc == DG_OK; ++type) {
     // restrict the stage to one element type (the other's blocks are not launched)
     if (type == 0) {
       c->m32.nblk_t = c->m64.nblk_t = 0;
-      if (m32.nblk_w == 0) continue;
+      if (nbw == 0) continue;
     } else {
       c->m32 = m32;
       c->m64 = m64;
       c->m32.nblk_w = c->m64.nblk_w = 0;
-      if (m32.nblk_t == 0) continue;
+      if (nbt == 0) continue;
     }
     e = cudaEventRecord(ev[0], c->stream);
     for (int r = 0; r < nrep && rc == DG_OK && e == cudaSuccess; ++r)
@@ -1538,6 +1565,71 @@ int dg_stage_times(dg_ctx* c, int nrep, double* us_w, double* us_t) {
   cudaEventDestroy(ev[1]);
   if (rc) return rc;
   return check_device_error(c);
+}
+
+namespace {
+// Rebuild and upload the bound context's mesh tables for its current shot
+// group (the blob's size does not depend on it), zero the state buffers and
+// the simulation time, and drop the captured step graphs.  Synchronous.
+int relayout(dg_ctx* c) {
+  const BlobLayout L = blob_layout(c);
+  if (L.total != c->mesh_bytes) return c->fail(DG_ERR_STATE, "mesh blob size changed");
+  std::vector<unsigned char> blob;
+  if (c->prec == DG_F64) {
+    fill_blob<double>(c, L, blob);
+    fill_devmesh<double>(c, L, c->m64);
+  } else {
+    fill_blob<float>(c, L, blob);
+    fill_devmesh<float>(c, L, c->m32);
+  }
+  drop_graphs(c);
+  cudaError_t e = cudaMemcpyAsync(c->d_mesh, blob.data(), blob.size(), cudaMemcpyHostToDevice, c->stream);
+  for (void* p : {c->d_q[0], c->d_q[1], c->d_res})
+    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, c->field_bytes, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "mesh re-layout");
+  c->cur = 0;
+  c->t = 0.0;
+  return DG_OK;
+}
+}  // namespace
+
+int dg_autotune_layout(dg_ctx* c, int nrep, int64_t* group, double* us) {
+  if (!c) return DG_ERR_ARG;
+  if (nrep < 1 || !group || !us) return c->fail(DG_ERR_ARG, "null or invalid argument");
+  if (!c->bound) return c->fail(DG_ERR_STATE, "dg_autotune_layout before dg_bind");
+  DeviceGuard device_guard(c);
+  if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
+  // candidates: 1, 2, 4, ... and the shot count itself, each dividing it
+  std::vector<int64_t> cand;
+  for (int64_t g = 1; g <= c->shots; g *= 2)
+    if (c->shots % g == 0) cand.push_back(g);
+  if (cand.back() != c->shots) cand.push_back(c->shots);
+  double best = 0.0;
+  int64_t bestg = c->group();
+  bool have = false;
+  for (int64_t g : cand) {
+    c->shot_group = g;
+    int rc = relayout(c);
+    double tw = 0.0, tt = 0.0;
+    if (rc == DG_OK) rc = dg_stage_times(c, nrep, &tw, &tt);
+    if (rc != DG_OK) {
+      c->shot_group = bestg;
+      relayout(c);
+      return rc;
+    }
+    if (!have || tw + tt < best) {
+      best = tw + tt;
+      bestg = g;
+      have = true;
+    }
+  }
+  c->shot_group = bestg;
+  const int rc = relayout(c);
+  if (rc) return rc;
+  *group = bestg;
+  *us = best;
+  return DG_OK;
 }
 
 int dg_autotune(dg_ctx* c, int nrep, int* variant, double* us) {
@@ -1897,12 +1989,12 @@ int dg_adjoint_gradient(dg_ctx* c, double* g_kappa, double* g_rho) {
   // sum over shots in shot order, per element of either type
   for (int64_t s = 0; s < c->shots; ++s) {
     for (int64_t w = 0; w < Kw; ++w) {
-      const int64_t v = c->shot_inner ? w * c->shots + s : s * Kw + w;
+      const int64_t v = shot_vid(s, w, Kw, c->group());
       g_kappa[c->wedges[w]] += gk[v];
       g_rho[c->wedges[w]] += gr[v];
     }
     for (int64_t t = 0; t < Kt; ++t) {
-      const int64_t v = c->shot_inner ? t * c->shots + s : s * Kt + t;
+      const int64_t v = shot_vid(s, t, Kt, c->group());
       g_kappa[c->tets[t]] += tk[v];
       g_rho[c->tets[t]] += tr[v];
     }

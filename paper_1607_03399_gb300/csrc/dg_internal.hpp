@@ -31,6 +31,11 @@ constexpr int kStaticPartials = 1 << 16;
 __host__ __device__ constexpr int nt_of(int N) { return (N + 1) * (N + 2) / 2; }
 __host__ __device__ constexpr int npw_of(int N) { return nt_of(N) * (N + 1); }
 __host__ __device__ constexpr int npt_of(int N) { return (N + 1) * (N + 2) * (N + 3) / 6; }
+// Packed lower triangle of the wedge mass factor, Nt (Nt + 1) / 2 entries
+// (entry (i, l <= i) at i (i + 1) / 2 + l), stored per 32-wedge block in
+// groups of four: entry q of lane l at ((q / 4) * 32 + l) * 4 + q % 4, so a
+// lane reads four consecutive entries with one 16-byte access.
+__host__ __device__ constexpr int nl4_of(int N) { return (nt_of(N) * (nt_of(N) + 1) / 2 + 3) / 4; }
 
 // Operator tables placed in device constant memory, one configuration at a time.
 template <int N, typename real>
@@ -124,7 +129,7 @@ struct DevMesh {
   const real* rec_g = nullptr;
   int nrec = 0, nrgrp = 0;
   int Kw1 = 0, Kt1 = 0;              // wedges / tets of one shot
-  int shot_inner = 0, nshots = 1;    // virtual element of (shot s, element i): i S + s, else s K1 + i
+  int shot_group = 1, nshots = 1;    // virtual element of (shot s, element i): (s / G) K1 G + i G + s % G
   const int* w_srng = nullptr;       // per wedge block [begin, end) of its entries in src
   const int* t_srng = nullptr;       // per tet block likewise
 };
@@ -145,6 +150,13 @@ struct StageArgs {
 };
 
 enum : int { kErrTimeout = 1, kErrNonfinite = 2 };
+
+// Virtual element of (shot s, type-local element i) with K1 elements of the
+// type per shot and shots in groups of G: the G shots of a group are
+// consecutive for each element (G = 1: shot-major, G = shots: shot-inner).
+__host__ __device__ inline int64_t shot_vid(int64_t s, int64_t i, int64_t K1, int64_t G) {
+  return (s / G) * (K1 * G) + i * G + s % G;
+}
 
 // How the wedge stage applies the shared triangle operators (M^tri, D_r,
 // D_s): FP32 FMA chains on the CUDA cores, or warp-level tensor-core MMA with

@@ -382,10 +382,12 @@ __global__ void k_wait_expire(int* err) {
 }
 
 // per-element geometric factors kept in shared memory ([item][32])
+// (the column Jacobians J0..J2 come last: the stage does not use them and
+// keeps only the first G_STAGE items)
 enum WGeo : int {
-  G_RX, G_RY, G_SX, G_SY, G_A, G_J0, G_J1, G_J2, G_NB0, G_NB1, G_NB2, G_NT0, G_NT1, G_NT2, G_JFB, G_JFT,
+  G_RX, G_RY, G_SX, G_SY, G_A, G_NB0, G_NB1, G_NB2, G_NT0, G_NT1, G_NT2, G_JFB, G_JFT,
   G_QNX0, G_QNX1, G_QNX2, G_QNY0, G_QNY1, G_QNY2, G_QCA0, G_QCA1, G_QCA2, G_QCB0, G_QCB1, G_QCB2,
-  G_TX0, G_TX1, G_TY0, G_TY1, G_COUNT
+  G_TX0, G_TX1, G_TY0, G_TY1, G_STAGE, G_J0 = G_STAGE, G_J1, G_J2, G_COUNT
 };
 
 // Residual slab staged in shared memory by the bulk copy (N <= 3).  At N = 4
@@ -404,12 +406,12 @@ struct WedgeSmem {
   static constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
   static constexpr int q = 0;                                            // [4][Np][32]
   static constexpr int r = q + 4 * Np * kB;                              // [4][Np][32] (if staged)
-  static constexpr int L = r + (stage_res<N, OP>() ? 4 * Np * kB : 0);   // [Nt(Nt+1)/2][32]
-  static constexpr int F = L + (Nt * (Nt + 1) / 2) * kB;                 // [4][Nt][32]
-  static constexpr int G = F + 4 * Nt * kB;                              // [G_COUNT][32]
+  static constexpr int L = r + (stage_res<N, OP>() ? 4 * Np * kB : 0);   // [NL4][32][4]
+  static constexpr int F = L + nl4_of(N) * 4 * kB;                        // [4][Nt][32]
+  static constexpr int G = F + 4 * Nt * kB;                              // [G_STAGE][32]
   // per-warp operand tiles [Nt][kTP] (tensor cores): the residual slab's space where it is staged
-  static constexpr int T = stage_res<N, OP>() ? r : G + G_COUNT * kB;
-  static constexpr int reals = G + G_COUNT * kB + ((OP == kOpFFMA || stage_res<N, OP>()) ? 0 : Nq * Nt * kTP);
+  static constexpr int T = stage_res<N, OP>() ? r : G + G_STAGE * kB;
+  static constexpr int reals = G + G_STAGE * kB + ((OP == kOpFFMA || stage_res<N, OP>()) ? 0 : Nq * Nt * kTP);
 };
 
 template <int N, int OP = kOpFFMA>
@@ -501,7 +503,8 @@ __device__ __forceinline__ void wedge_geometry_vals(const real (&X)[12], real (&
 }
 
 // The stage's geometry warp: coordinates arrive in the first 12 items of the
-// shared table (one column per lane) and are replaced by the factors.
+// shared table (one column per lane) and are replaced by the first NG factors.
+template <int NG = G_COUNT>
 __device__ __forceinline__ void wedge_geometry(real* sG, int lane) {
   real X[12];
 #pragma unroll
@@ -510,7 +513,7 @@ __device__ __forceinline__ void wedge_geometry(real* sG, int lane) {
   real G[G_COUNT];
   wedge_geometry_vals(X, G);
 #pragma unroll
-  for (int i = 0; i < G_COUNT; ++i) sG[i * kB + lane] = G[i];
+  for (int i = 0; i < NG; ++i) sG[i * kB + lane] = G[i];
 }
 
 template <int N, int BPC, int OP = kOpFFMA>
@@ -550,6 +553,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
   // the weak-form accumulation, once the operand tiles in its space are free
   const bool res_early = res_async && OP == kOpFFMA;
 #define GEO(item) sG[(item) * kB + lane]
+#define LQ(q) sL[(((q) >> 2) * kB + lane) * 4 + ((q) & 3)]
 
   if (!live) return;  // padding block of the last CTA
   // the warps of one block synchronise among themselves (named barrier 1 + sb)
@@ -562,8 +566,8 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
     else if (BPC > 3) asm volatile("bar.sync 4, %0;" ::"n"(32 * Nq) : "memory");
   };
   // 0. bulk copies of the block's state (and residual) slabs; geometry meanwhile
-  constexpr int NL = Nt * (Nt + 1) / 2;
-  constexpr uint32_t fac_bytes = uint32_t(NL * kB * sizeof(real));
+  constexpr int NL4 = nl4_of(N);
+  constexpr uint32_t fac_bytes = uint32_t(NL4 * 4 * kB * sizeof(real));
   const bool stored = M.w_fac != nullptr;
   constexpr uint32_t xyz_bytes = uint32_t(12 * kB * sizeof(real));
   if (leader) {
@@ -578,7 +582,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
     mbar_expect_tx(&bar[0], slab_bytes + (stored ? fac_bytes : 0u));
     bulk_g2s(sq, qin + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[0]);
     // stored mass factor: straight into the factor table with the state slab
-    if (stored) bulk_g2s(sL, M.w_fac + int64_t(blk) * NL * kB, fac_bytes, &bar[0]);
+    if (stored) bulk_g2s(sL, M.w_fac + int64_t(blk) * NL4 * 4 * kB, fac_bytes, &bar[0]);
     if (res_early) {
       mbar_expect_tx(&bar[1], slab_bytes);
       bulk_g2s(sr, resg + int64_t(blk) * 4 * Np * kB, slab_bytes, &bar[1]);
@@ -595,9 +599,10 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
     qnbr[ed] = M.w_nbr[(2 + ed) * Kp + e];
     qcode[ed] = M.w_code[(2 + ed) * Kp + e];
   }
-  // (at N = 4 the traces held across the wait cost spills: there they are
-  // requested after it, with the in-block ones)
-  constexpr bool early = N <= 3;
+  // (at N = 4 the traces held across the wait cost spills, and with the factor
+  // computed in the stage they slow the factorising warp: there they are
+  // requested after the wait, with the in-block ones)
+  const bool early = N <= 3 && stored;
   Q4 nv[3][Nq];
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
@@ -624,7 +629,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
   __syncwarp();
   if (j == 0) {
     geo_ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[2], 0));
-    if (geo_ok) wedge_geometry(sG, lane);
+    if (geo_ok) wedge_geometry<G_STAGE>(sG, lane);
   }
   if (j == 1 && !stored) {
     // While the slabs are in flight: M^{tri,k} = sum_a J_a M_a with
@@ -642,15 +647,15 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
       for (int l = 0; l < i; ++l) {
         real s = J0 * O.w.Ma[0][i * Nt + l] + J1 * O.w.Ma[1][i * Nt + l] + J2 * O.w.Ma[2][i * Nt + l];
 #pragma unroll
-        for (int k = 0; k < l; ++k) s -= row[k] * sL[(l * (l + 1) / 2 + k) * kB + lane];
-        row[l] = s * sL[(l * (l + 1) / 2 + l) * kB + lane];
+        for (int k = 0; k < l; ++k) s -= row[k] * LQ(l * (l + 1) / 2 + k);
+        row[l] = s * LQ(l * (l + 1) / 2 + l);
       }
       real d = J0 * O.w.Ma[0][i * Nt + i] + J1 * O.w.Ma[1][i * Nt + i] + J2 * O.w.Ma[2][i * Nt + i];
 #pragma unroll
       for (int k = 0; k < i; ++k) d -= row[k] * row[k];
 #pragma unroll
-      for (int l = 0; l < i; ++l) sL[(i * (i + 1) / 2 + l) * kB + lane] = row[l];
-      sL[(i * (i + 1) / 2 + i) * kB + lane] = rsqrt_r(d);
+      for (int l = 0; l < i; ++l) LQ(i * (i + 1) / 2 + l) = row[l];
+      LQ(i * (i + 1) / 2 + i) = rsqrt_r(d);
     }
   }
   if (leader) *status = (mbar_wait_bounded(&bar[0], 0) && geo_ok) ? 1 : 0;
@@ -674,17 +679,21 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
   // neighbour traces of quadrilateral faces whose neighbour lies in this block
   // (or, on a boundary face, the element's own trace, which the ghost state
   // then replaces) from the shared slab; the others were requested above (or,
-  // at N = 4, now, by one generic load each)
+  // at N = 4, now, from global memory)
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
     const int nbr = qnbr[ed];
     const bool bnd = nbr < 0;
     const bool inblk = bnd || (nbr >> 5) == blk;
-    if (inblk || !early) {
-      const int ep = bnd ? ed : qcode[ed] >> 1, rev = bnd ? 0 : qcode[ed] & 1;
-      const real* base = inblk ? sq + ((bnd ? lane : (nbr & 31)) << 2) : qin + widx<N>(nbr >> 5, 0, nbr & 31);
+    const int ep = bnd ? ed : qcode[ed] >> 1, rev = bnd ? 0 : qcode[ed] & 1;
+    if (inblk) {
+      const int nl = bnd ? lane : (nbr & 31);
 #pragma unroll
-      for (int m = 0; m < Nq; ++m) nv[ed][m] = ldx4(base + (j * Nt + O.tab.edge[ep][rev ? N - m : m]) * (kB * 4));
+      for (int m = 0; m < Nq; ++m) nv[ed][m] = lds4(sq, j * Nt + O.tab.edge[ep][rev ? N - m : m], nl);
+    } else if (!early) {
+      const real* base = qin + widx<N>(nbr >> 5, 0, nbr & 31);
+#pragma unroll
+      for (int m = 0; m < Nq; ++m) nv[ed][m] = ldg4(base, int64_t(j * Nt + O.tab.edge[ep][rev ? N - m : m]) * (kB * 4));
     }
   }
 #pragma unroll
@@ -746,9 +755,9 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
     const int nbe = bnd ? e : nbr;
     const int node = ntet ? O.tab.tet_face[nf][nk] : (nf ? N * Nt : 0) + nk;
     const bool inblk = !ntet && (nbe >> 5) == blk;
-    const real* a = inblk ? sq + ((node * kB + (nbe & 31)) << 2)
-                          : qin + (ntet ? tidx<N>(M.tet_off, nbe >> 5, node, nbe & 31) : widx<N>(nbe >> 5, node, nbe & 31));
-    const Q4 nv = ldx4(a);
+    // explicit shared or global loads (a generic load would wait on the long scoreboard either way)
+    const Q4 nv = inblk ? lds4(sq, node, nbe & 31)
+                        : ldg4(qin, ntet ? tidx<N>(M.tet_off, nbe >> 5, node, nbe & 31) : widx<N>(nbe >> 5, node, nbe & 31));
     const real dp = bnd ? bdp : nv.p - o.p;
     const real dun = bnd ? bdun : nn0 * nv.u + nn1 * nv.v + nn2 * nv.w - unM;
     real Fp, Fu;
@@ -873,38 +882,58 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
       }
     }
   }
-  // (d) X = (M^{tri,k})^{-1} W: forward and backward substitution, 4 right-hand sides
+  // (d) X = (M^{tri,k})^{-1} W: forward and backward substitution, 4
+  // right-hand sides, both sweeping the packed factor row by row (the
+  // backward one in column-update form), four entries per shared load
+  {
+    // row i of the factor, entries q = i (i + 1) / 2 + k, k = 0..i
+    auto load_row = [&](int i, real (&Lr)[Nt]) {
+      const int a0 = i * (i + 1) / 2;
 #pragma unroll
-  for (int i = 0; i < Nt; ++i) {
+      for (int c4 = a0 >> 2; c4 <= (a0 + i) >> 2; ++c4) {
+        const Q4 v = ldop4(sL + (c4 * kB + lane) * 4);
+        const real vv[4] = {v.p, v.u, v.v, v.w};
 #pragma unroll
-    for (int k = 0; k < i; ++k) {
-      const real l = sL[(i * (i + 1) / 2 + k) * kB + lane];
-      Wp[i] -= l * Wp[k];
-      Wu[0][i] -= l * Wu[0][k];
-      Wu[1][i] -= l * Wu[1][k];
-      Wu[2][i] -= l * Wu[2][k];
+        for (int q = 0; q < 4; ++q) {
+          const int k = c4 * 4 + q - a0;
+          if (k >= 0 && k <= i) Lr[k] = vv[q];
+        }
+      }
+    };
+#pragma unroll
+    for (int i = 0; i < Nt; ++i) {
+      real Lr[Nt];
+      load_row(i, Lr);
+#pragma unroll
+      for (int k = 0; k < i; ++k) {
+        Wp[i] -= Lr[k] * Wp[k];
+        Wu[0][i] -= Lr[k] * Wu[0][k];
+        Wu[1][i] -= Lr[k] * Wu[1][k];
+        Wu[2][i] -= Lr[k] * Wu[2][k];
+      }
+      const real d = Lr[i];
+      Wp[i] *= d;
+      Wu[0][i] *= d;
+      Wu[1][i] *= d;
+      Wu[2][i] *= d;
     }
-    const real d = sL[(i * (i + 1) / 2 + i) * kB + lane];
-    Wp[i] *= d;
-    Wu[0][i] *= d;
-    Wu[1][i] *= d;
-    Wu[2][i] *= d;
-  }
 #pragma unroll
-  for (int i = Nt - 1; i >= 0; --i) {
+    for (int i = Nt - 1; i >= 0; --i) {
+      real Lr[Nt];
+      load_row(i, Lr);
+      const real d = Lr[i];
+      Wp[i] *= d;
+      Wu[0][i] *= d;
+      Wu[1][i] *= d;
+      Wu[2][i] *= d;
 #pragma unroll
-    for (int k = i + 1; k < Nt; ++k) {
-      const real l = sL[(k * (k + 1) / 2 + i) * kB + lane];
-      Wp[i] -= l * Wp[k];
-      Wu[0][i] -= l * Wu[0][k];
-      Wu[1][i] -= l * Wu[1][k];
-      Wu[2][i] -= l * Wu[2][k];
+      for (int k = 0; k < i; ++k) {
+        Wp[k] -= Lr[k] * Wp[i];
+        Wu[0][k] -= Lr[k] * Wu[0][i];
+        Wu[1][k] -= Lr[k] * Wu[1][i];
+        Wu[2][k] -= Lr[k] * Wu[2][i];
+      }
     }
-    const real d = sL[(i * (i + 1) / 2 + i) * kB + lane];
-    Wp[i] *= d;
-    Wu[0][i] *= d;
-    Wu[1][i] *= d;
-    Wu[2][i] *= d;
   }
   // (e) strong r, s parts of slice j (constant metric terms, Lemma 3.1), on
   // the CUDA cores for every variant (on the tensor cores the results would
@@ -964,6 +993,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
     }
   }
 #undef GEO
+#undef LQ
 }
 
 // ---------------------------------------------------------------------------

@@ -29,9 +29,9 @@ DG_MASS_ONTHEFLY, DG_MASS_STORED = 0, 1
 DG_SHOTS_OUTER, DG_SHOTS_INNER = 0, 1
 DG_OPS_FP32, DG_OPS_TF32X3, DG_OPS_TF32, DG_OPS_BF16 = 0, 1, 2, 3
 
-EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_shots", "dg_add_shot_source", "dg_set_shot_order", "dg_set_options", "dg_set_mass_mode", "dg_set_op_precision", "dg_num_nodes",
+EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_shots", "dg_add_shot_source", "dg_set_shot_order", "dg_set_shot_group", "dg_set_options", "dg_set_mass_mode", "dg_set_op_precision", "dg_num_nodes",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
-           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_expire_wait", "dg_fma_peak", "dg_stage_times", "dg_autotune", "dg_add_receiver", "dg_sample", "dg_save_state",
+           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_expire_wait", "dg_fma_peak", "dg_stage_times", "dg_autotune", "dg_autotune_layout", "dg_add_receiver", "dg_sample", "dg_save_state",
            "dg_load_state", "dg_adjoint_bytes", "dg_adjoint_bind", "dg_adjoint_reset", "dg_adjoint_inject",
            "dg_adjoint_step", "dg_step_record_bytes", "dg_step_record", "dg_step_record_chain", "dg_adjoint_step_recorded", "dg_adjoint_set", "dg_adjoint_get", "dg_adjoint_gradient", "dg_sync", "dg_time",
            "dg_stable_dt", "dg_last_error", "dg_destroy")
@@ -63,6 +63,7 @@ def lib():
         "dg_set_shots": (c_int, [P, c_int64]),
         "dg_add_shot_source": (c_int, [P, c_int64, c_double, c_double, c_double, c_double, c_double, c_double]),
         "dg_set_shot_order": (c_int, [P, c_int]),
+        "dg_set_shot_group": (c_int, [P, c_int64]),
         "dg_set_options": (c_int, [P, c_int, c_int, c_int]),
         "dg_set_mass_mode": (c_int, [P, c_int]),
         "dg_set_op_precision": (c_int, [P, c_int]),
@@ -80,6 +81,7 @@ def lib():
         "dg_energy_static": (c_int, [P, P, POINTER(c_double)]),
         "dg_stage_times": (c_int, [P, c_int, POINTER(c_double), POINTER(c_double)]),
         "dg_autotune": (c_int, [P, c_int, POINTER(c_int), POINTER(c_double)]),
+        "dg_autotune_layout": (c_int, [P, c_int, POINTER(c_int64), POINTER(c_double)]),
         "dg_add_receiver": (c_int, [P, c_double, c_double, c_double]),
         "dg_sample": (c_int, [P, P]),
         "dg_save_state": (c_int, [P, P]),
@@ -166,6 +168,10 @@ def dg_set_shot_order(ctx, order: int):
 
 def dg_add_shot_source(ctx, shot: int, x, y, z, f0, t0, amp):
     _check(ctx, lib().dg_add_shot_source(ctx, shot, x, y, z, f0, t0, amp))
+
+
+def dg_set_shot_group(ctx, group: int):
+    _check(ctx, lib().dg_set_shot_group(ctx, group))
 
 
 def dg_set_options(ctx, bc: int, flux: int, precision: int):
@@ -260,6 +266,12 @@ def dg_autotune(ctx, nrep: int):
     v, us = c_int(), c_double()
     _check(ctx, lib().dg_autotune(ctx, nrep, ctypes.byref(v), ctypes.byref(us)))
     return v.value, us.value
+
+
+def dg_autotune_layout(ctx, nrep: int):
+    g, us = c_int64(), c_double()
+    _check(ctx, lib().dg_autotune_layout(ctx, nrep, ctypes.byref(g), ctypes.byref(us)))
+    return g.value, us.value
 
 
 def dg_add_receiver(ctx, x, y, z) -> int:
@@ -405,7 +417,10 @@ class Solver:
             dg_set_mass_mode(self.ctx, MASS[mass])
             dg_set_op_precision(self.ctx, OPS[ops])
             dg_set_shots(self.ctx, shots)
-            dg_set_shot_order(self.ctx, {"outer": DG_SHOTS_OUTER, "inner": DG_SHOTS_INNER}[shot_order])
+            if isinstance(shot_order, str):
+                dg_set_shot_order(self.ctx, {"outer": DG_SHOTS_OUTER, "inner": DG_SHOTS_INNER}[shot_order])
+            else:  # shots per group
+                dg_set_shot_group(self.ctx, int(shot_order))
             self.shots = shots
             for src in sources:       # (x, y, z, f0, t0, amp)
                 dg_add_source(self.ctx, *src)
@@ -495,6 +510,12 @@ class Solver:
         return v >> 1, bool(v & 1), us
 
     # -- receivers, checkpoints, adjoint ------------------------------------
+    def autotune_layout(self, nrep: int = 10):
+        """Pick the shots-per-group layout by timing (resets the state to zero):
+        returns (shots per group, us per stage)."""
+        self._wait_torch()
+        return dg_autotune_layout(self.ctx, nrep)
+
     def sample(self, out):
         """Pressure at the receivers into the device tensor out[shots][receivers]."""
         self._wait_torch()

@@ -47,7 +47,7 @@ def test_shots_match_single_shot_runs(precision, meshname, order):
 
 
 @pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f32", 1e-5)])
-@pytest.mark.parametrize("order", ["outer", "inner"])
+@pytest.mark.parametrize("order", ["outer", "inner", 2])
 def test_shots_match_the_oracle_per_shot(precision, tol, order):
     """Four shots of a hybrid mesh in one launch per stage, each with its own
     Ricker source and initial state, against the oracle run shot by shot."""
@@ -96,3 +96,47 @@ def test_merged_meshes_match_separate_runs():
         assert np.array_equal(A.get_fields(), qm[:, node0:node0 + n]), i
         A.close()
         node0 += n
+
+
+@pytest.mark.parametrize("group", [2, 4])
+def test_shot_groups_are_bitwise_the_shot_major_run(group):
+    """Eight shots in groups of 2 or 4 (a block holds 16 or 8 elements of 2 or
+    4 shots each): every shot's state after 10 steps equals the shot-major
+    layout's bit for bit."""
+    m = I.cube_wavy_mesh(4, 4, 0.03)
+    c2, rho = I.random_material(m.K, 3, 1.0, 2.0, 0.5, 1.5)
+    S = 8
+    src = [(s, 0.2 + 0.08 * s, 0.5, 0.5, 6.0, 0.05, 1.0) for s in range(S)]
+    q = np.random.default_rng(2).uniform(-1, 1, size=(S, 4, 0))
+    out = {}
+    for order in ("outer", group):
+        B = Solver(m.VX, m.EToV, m.etype, 3, c2, rho, precision="f32", shots=S, shot_sources=src, shot_order=order)
+        if q.shape[2] == 0:
+            q = np.random.default_rng(2).uniform(-1, 1, size=(S, 4, B.total_nodes)).astype(np.float32)
+        B.set_fields(q)
+        dt = B.stable_dt(0.4)
+        B.step(dt, 10)
+        out[order] = B.get_fields()
+        B.close()
+    assert np.array_equal(out["outer"], out[group])
+
+
+def test_layout_autotuner_keeps_the_operator():
+    """dg_autotune_layout picks a shots-per-group layout among 1, 2, 4, 8; the
+    steps taken afterwards match the oracle shot by shot."""
+    m = I.hybrid_mesh(3, 2, 1)
+    c2, rho = I.random_material(m.K, 4, 1.0, 2.0, 0.5, 1.5)
+    S = 8
+    B = Solver(m.VX, m.EToV, m.etype, 3, c2, rho, precision="f64", shots=S)
+    g, us = B.autotune_layout(3)
+    assert g in (1, 2, 4, 8) and us > 0
+    q = np.random.default_rng(9).uniform(-1, 1, size=(S, 4, B.total_nodes))
+    B.set_fields(q)
+    dt = B.stable_dt(0.4)
+    B.step(dt, 4)
+    qb = B.get_fields()
+    B.close()
+    O = Oracle(m.VX, m.EToV, m.etype, 3, c2, rho)
+    for s in (0, 5):
+        ref = O.step(q[s], dt, 4)
+        assert np.linalg.norm(qb[s] - ref) <= 1e-12 * np.linalg.norm(ref)

@@ -239,10 +239,11 @@ def test_point_sources(precision, tol, rhs_tol):
     S.close()
 
 
-def test_stage_times_leave_the_state_alone():
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_stage_times_leave_the_state_alone(precision):
     """dg_stage_times times both element types and changes neither the state
-    nor the next step (hybrid mesh, FP32)."""
-    S, O = _pair(MESHES["hybrid"](), 3, "f32")
+    nor the next step (hybrid mesh, both precisions)."""
+    S, O = _pair(MESHES["hybrid"](), 3, precision)
     q = I.random_fields(S.total_nodes, 4).astype(np.float32)
     S.set_fields(q)
     tw, tt = S.stage_times(3)

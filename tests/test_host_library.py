@@ -155,8 +155,8 @@ def test_call_order_and_argument_errors():
         dg.dg_set_mass_mode(ctx, dg.DG_MASS_STORED)
         mb4, fb4 = dg.dg_device_bytes(ctx)
         assert fb3 == fb4 == fb2 and mb4 == mb2
-        nl = 6 * 7 // 2
-        assert mb4 - mb3 >= 32 * nl * 8 and mb4 - mb3 < 32 * nl * 8 + 256
+        nl4 = (6 * 7 // 2 + 3) // 4  # the packed factor in groups of four entries per lane
+        assert mb4 - mb3 >= 32 * 4 * nl4 * 8 and mb4 - mb3 < 32 * 4 * nl4 * 8 + 256
     finally:
         dg.dg_destroy(ctx)
 
@@ -315,5 +315,24 @@ def test_op_precision_needs_fp32_fields():
             dg.dg_set_op_precision(ctx, dg.DG_OPS_TF32)
         assert ei.value.code == dg.DG_ERR_ARG
         dg.dg_set_op_precision(ctx, dg.DG_OPS_FP32)
+    finally:
+        dg.dg_destroy(ctx)
+
+
+def test_shot_group_must_divide_the_shots():
+    m = I.cube_wavy_mesh(2, 2, 0.0)
+    ctx = dg.dg_mesh_create(m.VX, m.EToV, m.etype)
+    try:
+        dg.dg_set_order(ctx, 2)
+        dg.dg_set_shots(ctx, 6)
+        for bad in (0, 4, 5):
+            with pytest.raises(dg.DGError) as ei:
+                dg.dg_set_shot_group(ctx, bad)
+            assert ei.value.code == dg.DG_ERR_ARG
+        for good in (1, 2, 3, 6):
+            dg.dg_set_shot_group(ctx, good)
+        with pytest.raises(dg.DGError) as ei:
+            dg.dg_set_shots(ctx, 4)  # 6 shots per group no longer divides
+        assert ei.value.code == dg.DG_ERR_ARG
     finally:
         dg.dg_destroy(ctx)
