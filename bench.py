@@ -302,8 +302,8 @@ def measure_order(N, args, torch, dev, m, c2, rho, mass, barrier=None):
     dof = 4 * S.total_nodes
     tune = None
     if not args.no_autotune:
-        bpc, onthefly, us = S.autotune(10)
-        tune = {"blocks_per_cta": bpc, "factor_in_stage": onthefly, "stage_us": us}
+        bpc, onthefly, split, us = S.autotune(10)
+        tune = {"blocks_per_cta": bpc, "factor_in_stage": onthefly, "field_pair_split": split, "stage_us": us}
     res = {"ms": ms, "dof": dof, "clocks": clk.summary(), "solver": S, "dt": dt, "q": q, "autotune": tune}
     return res
 

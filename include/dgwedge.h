@@ -96,7 +96,7 @@ enum { DG_SHOTS_OUTER = 0, DG_SHOTS_INNER = 1 };
 int dg_mesh_create(dg_ctx** out, int64_t nverts, const double* VX, int64_t nelem,
                    const int64_t* EToV, const uint8_t* etype);
 
-/* Polynomial degree N in 1..4 (Section 3).  Builds the reference operators
+/* Polynomial degree N in 1..5 (Section 3; the paper's experiments run 1..5).  Builds the reference operators
  * (GLL line, Warp & Blend triangle/tet, Section 3.1; Kronecker factors of
  * Section 4.2) and the face-node orientation maps. */
 int dg_set_order(dg_ctx* ctx, int N);
@@ -278,12 +278,22 @@ int dg_stage_times(dg_ctx* ctx, int nrep, double* us_wedge, double* us_tet);
  * the wedge stage (as dg_stage_times, nrep launches each) in every launch
  * variant this context can run -- 1 or 2 element blocks of 32 wedges per CTA
  * (2 only for N = 3 in DG_F32), and, when the context stores the mass
- * factors, reading them or recomputing them in the stage -- and keeps the
- * fastest for later dg_step / dg_rhs calls.  *variant = 2 * blocks_per_cta +
- * (1 if the factor is recomputed), *us = its mean microseconds per launch.
+ * factors, reading them or recomputing them in the stage; with the stored
+ * factor, FP32 fields and FP32 operator applies also the stage split over
+ * field pairs (two threads per element and slice, for more resident warps)
+ * -- and keeps the fastest for later dg_step / dg_rhs calls.  *variant =
+ * 2 * blocks_per_cta + (1 if the factor is recomputed) + (8 if split), *us =
+ * its mean microseconds per launch.
  * All variants compute the same operator up to rounding.  Synchronous.
  * Errors: DG_ERR_ARG, DG_ERR_STATE (before dg_bind), DG_ERR_CUDA. */
 int dg_autotune(dg_ctx* ctx, int nrep, int* variant, double* us);
+
+/* Select a launch variant directly (encoded as dg_autotune reports it), e.g.
+ * to reapply a tuned choice without timing.  "Factor recomputed" is ignored
+ * when the context does not store the factor (it recomputes anyway).  The
+ * step graphs are captured again at the next dg_step.  Errors: DG_ERR_ARG
+ * (unknown variant, or one this context cannot run). */
+int dg_set_launch_variant(dg_ctx* ctx, int variant);
 
 /* Layout autotuner of the batched form (not in the paper; the paper tunes
  * its kernels' elements per block, Section 6.2): re-lays out the bound
@@ -336,7 +346,8 @@ int dg_load_state(dg_ctx* ctx, const void* d_src, double t);
  * dg_adjoint_step recomputes the forward step from the current state and
  * time (which it leaves unchanged), then applies the five adjoint stages and
  * accumulates the gradient terms.  Errors: DG_ERR_ARG, DG_ERR_STATE,
- * DG_ERR_CUDA. */
+ * DG_ERR_CUDA; dg_adjoint_bind also DG_ERR_ORDER at N = 5 in DG_F64 (the
+ * gradient kernel's shared memory exceeds a CTA's there). */
 int dg_adjoint_bytes(const dg_ctx* ctx, size_t* bytes);
 int dg_adjoint_bind(dg_ctx* ctx, void* d_work);
 int dg_adjoint_reset(dg_ctx* ctx);

@@ -19,9 +19,9 @@ LIB = os.path.join(HERE, "libdgwedge.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_UNITS = [f"k_{p}_n{n}.cu" for p in ("f32", "f64") for n in (1, 2, 3, 4)] + ["energy_static.cu", "peak.cu"]
+CU_UNITS = [f"k_{p}_n{n}.cu" for p in ("f32", "f64") for n in (1, 2, 3, 4, 5)] + ["energy_static.cu", "peak.cu"]
 CPP_UNITS = ["capi.cpp", "refel.cpp"]
-HEADERS = ["dg_internal.hpp", "kernels.cuh", "adjoint_kernels.cuh", "refel.hpp"]
+HEADERS = ["dg_internal.hpp", "kernels.cuh", "adjoint_kernels.cuh", "stage_split.cuh", "refel.hpp"]
 
 
 def _newer(src_list, target):

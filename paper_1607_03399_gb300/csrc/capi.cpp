@@ -30,6 +30,7 @@ namespace {
     case 2: return P##n2 CALL;    \
     case 3: return P##n3 CALL;    \
     case 4: return P##n4 CALL;    \
+    case 5: return P##n5 CALL;    \
   }                               \
   return int(cudaErrorInvalidValue);
 
@@ -147,6 +148,7 @@ struct dg_ctx {
   // whether the stored mass factor is bypassed (factor recomputed in the stage)
   int tuned_bpc = 0;
   bool tuned_onthefly = false;
+  int tuned_split = 0;  // wedge stage split over field pairs: 1 yes, -1 no, 0 the default for the order
   // adjoint workspace (caller-owned): mu_Q, two stage-input buffers, residual,
   // forward stage states Q_1..Q_4 and a scratch output, stage right-hand sides
   // r_1..r_5, then the kappa and rho gradients (doubles per device wedge)
@@ -204,7 +206,7 @@ template <int NN, typename real>
 void fill_ops(const RefElems& R, std::vector<unsigned char>& out) {
   AllOps<NN, real> o;
   std::memset(&o, 0, sizeof(o));
-  const int Nt = R.Nt, Nq = R.Nq, Npt = R.Npt;
+  const int Nt = R.Nt, Nq = R.Nq;
   for (int i = 0; i < Nt; ++i)
     for (int l = 0; l < Nt; ++l) {
       o.w.Dr[i * Nt + l] = real(R.Dr(i, l));
@@ -222,14 +224,6 @@ void fill_ops(const RefElems& R, std::vector<unsigned char>& out) {
     o.w.ell0[m] = real(R.ell0[m]);
     o.w.ellN[m] = real(R.ellN[m]);
     o.w.gll[m] = real(R.gll[m]);
-  }
-  for (int i = 0; i < Npt; ++i) {
-    for (int l = 0; l < Npt; ++l) {
-      o.t.Dr[i * Npt + l] = real(R.tDr(i, l));
-      o.t.Ds[i * Npt + l] = real(R.tDs(i, l));
-      o.t.Dt[i * Npt + l] = real(R.tDt(i, l));
-    }
-    for (int k = 0; k < 4 * Nt; ++k) o.t.LIFT[i * 4 * Nt + k] = real(R.tLIFT(i, k));
   }
   for (int c = 0; c < 9; ++c)
     for (int k = 0; k < Nt; ++k) o.tab.tri_perm[c][k] = R.tri_perm[c].empty() ? 0 : int8_t(R.tri_perm[c][k]);
@@ -249,6 +243,7 @@ void build_ops(dg_ctx* c) {
     case 2: dbl ? fill_ops<2, double>(R, c->ops_host) : fill_ops<2, float>(R, c->ops_host); break;
     case 3: dbl ? fill_ops<3, double>(R, c->ops_host) : fill_ops<3, float>(R, c->ops_host); break;
     case 4: dbl ? fill_ops<4, double>(R, c->ops_host) : fill_ops<4, float>(R, c->ops_host); break;
+    case 5: dbl ? fill_ops<5, double>(R, c->ops_host) : fill_ops<5, float>(R, c->ops_host); break;
   }
 }
 
@@ -757,6 +752,7 @@ int launch_stage(dg_ctx* c, const void* q_in, void* q_out, void* res, double a, 
     A.wedge_bpc = c->tuned_bpc;
     if (c->tuned_onthefly) A.m.w_fac = nullptr;
     A.op = c->op;
+    A.split = c->tuned_split;
     A.rk_g = float(x.g);
     A.rhs_out = static_cast<float*>(x.rhs_out);
     if (x.no_sources) A.m.nsrc = 0;
@@ -972,7 +968,7 @@ int dg_mesh_create(dg_ctx** out, int64_t nverts, const double* VX, int64_t nelem
 int dg_set_order(dg_ctx* c, int N) {
   if (!c) return DG_ERR_ARG;
   if (c->bound) return c->fail(DG_ERR_STATE, "dg_set_order after dg_bind");
-  if (N < 1 || N > kMaxOrder) return c->fail(DG_ERR_ORDER, "order must be in 1..4");
+  if (N < 1 || N > kMaxOrder) return c->fail(DG_ERR_ORDER, "order must be in 1..5");
   try {
     c->ref.reset(new RefElems(build_reference(N)));
   } catch (const std::exception& ex) {
@@ -1335,6 +1331,8 @@ int dg_bind(dg_ctx* c, void* d_mesh, void* d_q0, void* d_q1, void* d_res, void* 
   if (!c->N) return c->fail(DG_ERR_STATE, "dg_bind before dg_set_order");
   if (c->bound) return c->fail(DG_ERR_STATE, "context already bound");
   if (c->shots % c->group() != 0) return c->fail(DG_ERR_ARG, "the shot group must divide the number of shots");
+  if (c->op != DG_OPS_FP32 && nt_of(c->N) > 16)
+    return c->fail(DG_ERR_ORDER, "tensor-core operator applies need N <= 4 (a slice in one 16-row tile)");
   for (void* p : {d_mesh, d_q0, d_q1, d_res})
     if (reinterpret_cast<uintptr_t>(p) % 256) return c->fail(DG_ERR_ARG, "device buffers must be 256-byte aligned");
   cudaError_t e = cudaGetDevice(&c->device);
@@ -1567,6 +1565,21 @@ int dg_stage_times(dg_ctx* c, int nrep, double* us_w, double* us_t) {
   return check_device_error(c);
 }
 
+int dg_set_launch_variant(dg_ctx* c, int variant) {
+  if (!c) return DG_ERR_ARG;
+  const int bpc = (variant >> 1) & 3;
+  const bool onthefly = (variant & 1) != 0, split = (variant & 8) != 0;
+  if ((variant & ~11) != 0 || bpc < 1 || (bpc == 2 && !(c->prec == DG_F32 && c->N == 3)))
+    return c->fail(DG_ERR_ARG, "unknown launch variant");
+  if (split && (onthefly || bpc != 1 || c->prec != DG_F32 || c->mass != DG_MASS_STORED || c->op != DG_OPS_FP32))
+    return c->fail(DG_ERR_ARG, "the split stage needs FP32 fields and applies, the stored factor, one block per CTA");
+  c->tuned_bpc = bpc;
+  c->tuned_onthefly = onthefly && c->mass == DG_MASS_STORED;
+  c->tuned_split = split ? 1 : -1;
+  drop_graphs(c);
+  return DG_OK;
+}
+
 namespace {
 // Rebuild and upload the bound context's mesh tables for its current shot
 // group (the blob's size does not depend on it), zero the state buffers and
@@ -1638,23 +1651,31 @@ int dg_autotune(dg_ctx* c, int nrep, int* variant, double* us) {
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_autotune before dg_bind");
   DeviceGuard device_guard(c);
   if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
-  // candidates: (factor recomputed in the stage?, wedge blocks per CTA)
-  std::vector<std::pair<bool, int>> cand;
+  // candidates: (factor recomputed in the stage?, wedge blocks per CTA, split over field pairs)
+  struct Cand {
+    bool onthefly;
+    int bpc, split;
+  };
+  std::vector<Cand> cand;
   const int maxb = (c->prec == DG_F32 && c->N == 3) ? 2 : 1;
   for (int onthefly = 0; onthefly < 2; ++onthefly) {
     if (!onthefly && c->mass != DG_MASS_STORED) continue;
-    for (int b = 1; b <= maxb; ++b) cand.push_back({onthefly != 0, b});
+    for (int b = 1; b <= maxb; ++b) cand.push_back({onthefly != 0, b, -1});
   }
+  // the field-pair split kernel: FP32 CUDA-core applies with the stored factor
+  if (c->prec == DG_F32 && c->mass == DG_MASS_STORED && c->op == DG_OPS_FP32) cand.push_back({false, 1, 1});
   double best = 0.0;
   int besti = -1;
   for (size_t i = 0; i < cand.size(); ++i) {
-    c->tuned_onthefly = cand[i].first;
-    c->tuned_bpc = cand[i].second;
+    c->tuned_onthefly = cand[i].onthefly;
+    c->tuned_bpc = cand[i].bpc;
+    c->tuned_split = cand[i].split;
     double tw = 0.0, tt = 0.0;
     const int rc = dg_stage_times(c, nrep, &tw, &tt);
     if (rc) {
       c->tuned_onthefly = false;
       c->tuned_bpc = 0;
+      c->tuned_split = 0;
       return rc;
     }
     if (besti < 0 || tw < best) {
@@ -1662,15 +1683,16 @@ int dg_autotune(dg_ctx* c, int nrep, int* variant, double* us) {
       besti = int(i);
     }
   }
-  c->tuned_onthefly = cand[besti].first;
-  c->tuned_bpc = cand[besti].second;
+  c->tuned_onthefly = cand[besti].onthefly;
+  c->tuned_bpc = cand[besti].bpc;
+  c->tuned_split = cand[besti].split;
   // captured step graphs hold the previous launch shape: capture again on the next step
   for (int p = 0; p < 2; ++p)
     if (c->gexec[p]) {
       cudaGraphExecDestroy(c->gexec[p]);
       c->gexec[p] = nullptr;
     }
-  *variant = (cand[besti].second << 1) | (cand[besti].first ? 1 : 0);
+  *variant = (cand[besti].bpc << 1) | (cand[besti].onthefly ? 1 : 0) | (cand[besti].split > 0 ? 8 : 0);
   *us = best;
   return DG_OK;
 }
@@ -1751,6 +1773,8 @@ int dg_adjoint_bind(dg_ctx* c, void* d_work) {
   if (!c) return DG_ERR_ARG;
   if (!d_work) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->bound) return c->fail(DG_ERR_STATE, "dg_adjoint_bind before dg_bind");
+  if (c->N == 5 && c->prec == DG_F64)
+    return c->fail(DG_ERR_ORDER, "the adjoint at N = 5 needs DG_F32 (the FP64 gradient kernel exceeds shared memory)");
   DeviceGuard device_guard(c);
   if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   c->adj = static_cast<unsigned char*>(d_work);

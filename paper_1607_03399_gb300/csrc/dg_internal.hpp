@@ -23,7 +23,7 @@
 namespace dgw {
 
 constexpr int kB = 32;            // elements per block (one warp lane each)
-constexpr int kMaxOrder = 4;
+constexpr int kMaxOrder = 5;
 constexpr int kCodeTet = 64;
 // energy partial sums held by the allocation-free entry point (128 elements each)
 constexpr int kStaticPartials = 1 << 16;
@@ -45,12 +45,6 @@ struct WedgeOps {
   real Dt[Nq * Nq], ell0[Nq], ellN[Nq], Mea[Nq * Nq], Meb[Nq * Nq], M1[Nq * Nq], gll[Nq];
 };
 
-template <int N, typename real>
-struct TetOps {
-  static constexpr int Np = npt_of(N), Nt = nt_of(N);
-  real Dr[Np * Np], Ds[Np * Np], Dt[Np * Np], LIFT[Np * 4 * Nt];
-};
-
 template <int N>
 struct Tables {
   static constexpr int Nt = nt_of(N), Nq = N + 1;
@@ -59,10 +53,11 @@ struct Tables {
   int8_t tet_face[4][Nt];
 };
 
+// (the tet operators live in global memory, in the tet stage's shared-memory
+// image t_ops, so the constant bank holds wedge operators and tables only)
 template <int N, typename real>
 struct AllOps {
   WedgeOps<N, real> w;
-  TetOps<N, real> t;
   Tables<N> tab;
 };
 
@@ -147,6 +142,7 @@ struct StageArgs {
   int bc = 1, flux = 0;
   int wedge_bpc = 0;            // wedge blocks per CTA: 0 = the default for the mass mode
   int op = 0;                   // kOpFFMA, or a tensor-core variant (FP32 fields)
+  int split = 0;                // wedge stage split over field pairs: 1 yes, otherwise no
 };
 
 enum : int { kErrTimeout = 1, kErrNonfinite = 2 };
@@ -191,10 +187,12 @@ DGW_DECLARE_LAUNCHERS(f32, float, 1)
 DGW_DECLARE_LAUNCHERS(f32, float, 2)
 DGW_DECLARE_LAUNCHERS(f32, float, 3)
 DGW_DECLARE_LAUNCHERS(f32, float, 4)
+DGW_DECLARE_LAUNCHERS(f32, float, 5)
 DGW_DECLARE_LAUNCHERS(f64, double, 1)
 DGW_DECLARE_LAUNCHERS(f64, double, 2)
 DGW_DECLARE_LAUNCHERS(f64, double, 3)
 DGW_DECLARE_LAUNCHERS(f64, double, 4)
+DGW_DECLARE_LAUNCHERS(f64, double, 5)
 
 // allocation-free energy (energy_static.cu)
 int energy_static_scratch(int device, double** out);

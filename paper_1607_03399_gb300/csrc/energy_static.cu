@@ -157,6 +157,7 @@ int launch_energy_static(int N, const DevMesh<real>& m, const real* q, const rea
     case 2: return launch<real, 2>(m, q, wops, scratch, nblocks, s);
     case 3: return launch<real, 3>(m, q, wops, scratch, nblocks, s);
     case 4: return launch<real, 4>(m, q, wops, scratch, nblocks, s);
+    case 5: return launch<real, 5>(m, q, wops, scratch, nblocks, s);
   }
   return int(cudaErrorInvalidValue);
 }

@@ -1015,8 +1015,21 @@ __host__ __device__ constexpr int tet_chunk_pad() {  // lift record length per f
   return (tet_chunk<N>() + 3) / 4 * 4;
 }
 template <int N>
-__host__ __device__ constexpr int tet_ops_reals() {
+__host__ __device__ constexpr int tet_ops_image_reals() {  // the global image t_ops: D records, then the lift
   return 4 * npt_of(N) * npt_of(N) + 4 * (4 * nt_of(N)) * tet_chunk_pad<N>();
+}
+// Whether the lift rows are copied to shared memory with the derivative
+// records: everywhere but FP64 at N = 5, where the whole image would exceed a
+// CTA's shared memory; there the warps read their lift rows (uniform
+// addresses) from global memory.
+template <int N>
+__host__ __device__ constexpr bool tet_lift_smem() {
+  return 128 + (tet_ops_image_reals<N>() + 4 * npt_of(N) * kB + 8 * nt_of(N) * kB + 12 * kB +
+                ((sizeof(real) == 4 && N <= 3) ? 4 * npt_of(N) * kB : 0)) * int(sizeof(real)) <= 227 * 1024;
+}
+template <int N>
+__host__ __device__ constexpr int tet_ops_reals() {  // the part of the image in shared memory
+  return tet_lift_smem<N>() ? tet_ops_image_reals<N>() : 4 * npt_of(N) * npt_of(N);
 }
 // The residual slab is bulk-copied too where it costs no CTA per SM (FP32,
 // N <= 3); elsewhere the update reads it from global memory.
@@ -1213,7 +1226,8 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
   }
   __syncthreads();
   {
-    const real* lw = sL + w * (4 * Nt) * CP;  // this warp's lift records [4 Nt][CP]
+    // this warp's lift records [4 Nt][CP] (shared memory, or the global image)
+    const real* lw = (tet_lift_smem<N>() ? sL : M.t_ops + 4 * Np * Np) + w * (4 * Nt) * CP;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       real lu[C];
@@ -1453,6 +1467,7 @@ __global__ void k_energy_final(const double* __restrict__ partials, int n, doubl
 }  // namespace dgw
 
 #include "adjoint_kernels.cuh"
+#include "stage_split.cuh"
 
 namespace dgw {
 namespace REALNS {
@@ -1473,9 +1488,14 @@ int prepare_n() {
   cudaError_t err = cudaFuncSetAttribute(k_wedge_stage<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          wedge_smem_bytes<N, 1>());
   if constexpr (sizeof(real) == 4) {
-    if (err == cudaSuccess) err = prepare_op<N, kOpTF32x3>();
-    if (err == cudaSuccess) err = prepare_op<N, kOpTF32>();
-    if (err == cudaSuccess) err = prepare_op<N, kOpBF16>();
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(k_wedge_stage_split<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 split_smem_bytes<N>());
+    if constexpr (nt_of(N) <= 16) {  // one 16-row tile holds a slice: tensor-core applies
+      if (err == cudaSuccess) err = prepare_op<N, kOpTF32x3>();
+      if (err == cudaSuccess) err = prepare_op<N, kOpTF32>();
+      if (err == cudaSuccess) err = prepare_op<N, kOpBF16>();
+    }
   }
   if (err == cudaSuccess && b2 != 1)
     err = cudaFuncSetAttribute(k_wedge_stage<N, b2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1484,10 +1504,16 @@ int prepare_n() {
     err = cudaFuncSetAttribute(k_tet_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, tet_smem_bytes<N>());
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_pack<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, pack_smem_bytes<N>());
-  if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(k_wedge_grad<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, grad_smem_bytes<N>());
-  if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(k_wedge_grad<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, grad_smem_bytes<N>());
+  // the gradient kernels where their shared memory fits one CTA (not FP64 at N = 5,
+  // whose adjoint the library refuses)
+  if constexpr (grad_smem_bytes<N>() <= 227 * 1024) {
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(k_wedge_grad<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 grad_smem_bytes<N>());
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(k_wedge_grad<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 grad_smem_bytes<N>());
+  }
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_tet_grad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, tgrad_smem_bytes<N>());
   return int(err);
@@ -1504,7 +1530,16 @@ int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s) {
     const int want = a.wedge_bpc > 0 ? a.wedge_bpc : (a.m.w_fac != nullptr ? 1 : b2);
     bool done = false;
     if constexpr (sizeof(real) == 4) {
-      done = a.op != kOpFFMA;
+      // the field-pair split kernel (FP32 CUDA-core applies, stored mass
+      // factor): when the autotuner or dg_set_launch_variant chose it
+      const bool split = a.op == kOpFFMA && a.m.w_fac != nullptr && a.split > 0;
+      if (split) {
+        k_wedge_stage_split<N><<<a.m.nblk_w, 64 * (N + 1), split_smem_bytes<N>(), s>>>(a, rk);
+        done = true;
+      }
+    }
+    if constexpr (sizeof(real) == 4 && nt_of(N) <= 16) {
+      done = done || a.op != kOpFFMA;
       if (a.op == kOpTF32x3) launch_op<N, kOpTF32x3>(a, rk, s);
       else if (a.op == kOpTF32) launch_op<N, kOpTF32>(a, rk, s);
       else if (a.op == kOpBF16) launch_op<N, kOpBF16>(a, rk, s);
@@ -1580,6 +1615,7 @@ int DGW_CAT(launch_grad_, REALNS)(const DevMesh<REAL>& m, const REAL* x, const R
                                   int flux, int bc, double* gk, double* gr, void* stream) {
   if (m.nblk_w > 0) {
     constexpr int bytes = REALNS::grad_smem_bytes<NORD>();
+    if (bytes > 227 * 1024) return int(cudaErrorInvalidConfiguration);
     if (m.nblk_t > 0)
       REALNS::k_wedge_grad<NORD, true><<<m.nblk_w, 32 * (NORD + 1), bytes, cudaStream_t(stream)>>>(m, x, q, r, dt, flux,
                                                                                                   bc, gk, gr);

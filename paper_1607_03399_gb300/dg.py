@@ -31,7 +31,7 @@ DG_OPS_FP32, DG_OPS_TF32X3, DG_OPS_TF32, DG_OPS_BF16 = 0, 1, 2, 3
 
 EXPORTS = ("dg_mesh_create", "dg_set_order", "dg_set_material", "dg_add_source", "dg_set_shots", "dg_add_shot_source", "dg_set_shot_order", "dg_set_shot_group", "dg_set_options", "dg_set_mass_mode", "dg_set_op_precision", "dg_num_nodes",
            "dg_node_coords", "dg_face_neighbors", "dg_reference_operator", "dg_device_bytes", "dg_bind",
-           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_expire_wait", "dg_fma_peak", "dg_stage_times", "dg_autotune", "dg_autotune_layout", "dg_add_receiver", "dg_sample", "dg_save_state",
+           "dg_set_fields", "dg_get_fields", "dg_rhs", "dg_step", "dg_energy", "dg_energy_static", "dg_expire_wait", "dg_fma_peak", "dg_stage_times", "dg_autotune", "dg_autotune_layout", "dg_set_launch_variant", "dg_add_receiver", "dg_sample", "dg_save_state",
            "dg_load_state", "dg_adjoint_bytes", "dg_adjoint_bind", "dg_adjoint_reset", "dg_adjoint_inject",
            "dg_adjoint_step", "dg_step_record_bytes", "dg_step_record", "dg_step_record_chain", "dg_adjoint_step_recorded", "dg_adjoint_set", "dg_adjoint_get", "dg_adjoint_gradient", "dg_sync", "dg_time",
            "dg_stable_dt", "dg_last_error", "dg_destroy")
@@ -82,6 +82,7 @@ def lib():
         "dg_stage_times": (c_int, [P, c_int, POINTER(c_double), POINTER(c_double)]),
         "dg_autotune": (c_int, [P, c_int, POINTER(c_int), POINTER(c_double)]),
         "dg_autotune_layout": (c_int, [P, c_int, POINTER(c_int64), POINTER(c_double)]),
+        "dg_set_launch_variant": (c_int, [P, c_int]),
         "dg_add_receiver": (c_int, [P, c_double, c_double, c_double]),
         "dg_sample": (c_int, [P, P]),
         "dg_save_state": (c_int, [P, P]),
@@ -266,6 +267,10 @@ def dg_autotune(ctx, nrep: int):
     v, us = c_int(), c_double()
     _check(ctx, lib().dg_autotune(ctx, nrep, ctypes.byref(v), ctypes.byref(us)))
     return v.value, us.value
+
+
+def dg_set_launch_variant(ctx, variant: int):
+    _check(ctx, lib().dg_set_launch_variant(ctx, variant))
 
 
 def dg_autotune_layout(ctx, nrep: int):
@@ -504,10 +509,11 @@ class Solver:
         return dg_stage_times(self.ctx, nrep)
 
     def autotune(self, nrep: int = 10):
-        """Pick the fastest wedge-stage launch variant: returns (blocks per CTA, factor in stage?, us)."""
+        """Pick the fastest wedge-stage launch variant: returns (blocks per CTA,
+        factor in stage?, split over field pairs?, us)."""
         self._wait_torch()
         v, us = dg_autotune(self.ctx, nrep)
-        return v >> 1, bool(v & 1), us
+        return (v >> 1) & 3, bool(v & 1), bool(v & 8), us
 
     # -- receivers, checkpoints, adjoint ------------------------------------
     def autotune_layout(self, nrep: int = 10):

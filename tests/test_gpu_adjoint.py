@@ -248,3 +248,32 @@ def test_stage_records_give_the_same_gradient(precision):
     assert J == J2
     assert np.abs(gk).max() > 0 and np.abs(gr).max() > 0
     assert np.array_equal(gk, gk2) and np.array_equal(gr, gr2)
+
+
+def test_fp32_gradient_against_fp64_on_the_inclusion_workload():
+    """The differentiation workload's recipe at reduced size (2x24x24 footprint
+    x 12 layers, two-layer model with the shallow Gaussian inclusion, 2 shots,
+    256 surface receivers, 200 steps): the FP32 misfit and gradient against
+    the FP64 GPU run (itself pinned to the oracle's reverse mode above)."""
+    m = I.bumpy_layered_mesh(24, 12)
+    pos = I.surface_shots(2, 5)
+    recs = I.surface_receivers(16)
+    out = {}
+    for prec in ("f64", "f32"):
+        pb = AD.Problem(m.VX, m.EToV, m.etype, 3, 0.0, 200, recs, shots=2, checkpoint_every=50,
+                        shot_sources=[(s, *pos[s], 8.0, 0.125, 1.0) for s in range(2)], precision=prec)
+        c2t, rho = I.inclusion_model(m, amp=0.55)
+        c2, _ = I.inclusion_model(m, amp=0.5)
+        S = pb.solver(c2t, rho)
+        pb.dt = S.stable_dt(0.5)
+        data, _ = AD.forward(S, pb)
+        S.close()
+        S = pb.solver(c2, rho)
+        traces, ck = AD.forward(S, pb)
+        J = AD.misfit(traces, data)
+        gk, gr = AD.reverse(S, pb, traces, data, ck)
+        S.close()
+        out[prec] = (J, np.concatenate([gk, gr]))
+    (J64, g64), (J32, g32) = out["f64"], out["f32"]
+    assert abs(J32 - J64) <= 1e-4 * J64
+    assert np.linalg.norm(g32 - g64) <= 2e-4 * np.linalg.norm(g64)

@@ -255,13 +255,14 @@ def test_stage_times_leave_the_state_alone(precision):
     S.close()
 
 
-def test_autotune_keeps_the_operator():
+@pytest.mark.parametrize("N", [3, 4])
+def test_autotune_keeps_the_operator(N):
     """dg_autotune picks a launch variant; steps taken with it still match the oracle."""
-    S, O = _pair(MESHES["bumpy150"](), 3, "f32")
+    S, O = _pair(MESHES["bumpy150"](), N, "f32")
     q = I.random_fields(S.total_nodes, 6).astype(np.float32)
     S.set_fields(q)
-    bpc, onthefly, us = S.autotune(3)
-    assert bpc in (1, 2) and us > 0
+    bpc, onthefly, split, us = S.autotune(3)
+    assert bpc in (1, 2) and us > 0 and not (split and onthefly)
     dt = O.stable_dt(0.4)
     S.step(dt, 3)
     assert _rel(S.get_fields(), O.step(q.astype(np.float64), dt, 3)) <= 1e-5
@@ -372,3 +373,61 @@ def test_hybrid_fp32_1000_steps():
     S.close()
     ref = O.step(q0, dt, 1000)
     assert _rel(q, ref) <= 1e-4
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+@pytest.mark.parametrize("split", [1, -1])
+def test_field_pair_split_stage(N, split):
+    """The wedge stage split over field pairs (two threads per element and
+    slice) and the one-thread form, forced either way: right-hand side and
+    ten LSRK45 steps with sources on a hybrid mesh against the oracle."""
+    from paper_1607_03399_gb300 import dg as _dg
+    m = MESHES["hybrid"]()
+    c2, rho = I.random_material(m.K, 5, 1.0, 3.0, 0.5, 2.0)
+    src = (0.41, 0.37, 0.22, 6.0, 0.05, 1.0)
+    S = Solver(m.VX, m.EToV, m.etype, N, c2, rho, precision="f32", sources=[src])
+    O = Oracle(m.VX, m.EToV, m.etype, N, c2, rho)
+    O.add_source(*src)
+    _dg.dg_set_launch_variant(S.ctx, 2 + (8 if split > 0 else 0))  # one block per CTA, split or not
+    q = I.random_fields(S.total_nodes, 13)
+    r = S.rhs(q.astype(np.float32)).cpu().numpy()
+    assert _rel(r, O.rhs(q)) <= 1e-5
+    dt = O.stable_dt(0.4)
+    S.set_fields(q.astype(np.float32))
+    S.step(dt, 10)
+    assert _rel(S.get_fields(), O.step(q.astype(np.float32).astype(np.float64), dt, 10)) <= 1e-5
+    S.close()
+
+
+@pytest.mark.parametrize("meshname", ["wavy128", "hybrid", "tets"])
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_order_5(meshname, precision, tol):
+    """N = 5 (Nt = 21, Np = 126 per wedge, 56 per tet): one right-hand side and
+    three LSRK45 steps against the oracle (FP64 tets read their lift rows from
+    global memory at this order)."""
+    S, O = _pair(MESHES[meshname](), 5, precision, bc="rigid", flux="upwind", seed=4)
+    q = I.random_fields(S.total_nodes, 21)
+    qs = q.astype(S.np_dtype)
+    err = _rel(S.rhs(qs).cpu().numpy(), O.rhs(qs.astype(np.float64)))
+    assert err <= tol, err
+    dt = O.stable_dt(0.4)
+    S.set_fields(qs)
+    S.step(dt, 3)
+    err = _rel(S.get_fields(), O.step(qs.astype(np.float64), dt, 3))
+    S.close()
+    assert err <= tol, err
+
+
+def test_order_5_refusals():
+    """At N = 5 the tensor-core variants and the FP64 adjoint are refused with
+    DG_ERR_ORDER instead of failing at launch."""
+    from paper_1607_03399_gb300 import dg as _dg
+    m = MESHES["wavy128"]()
+    with pytest.raises(_dg.DGError) as ei:
+        Solver(m.VX, m.EToV, m.etype, 5, precision="f32", ops="tf32")
+    assert ei.value.code == _dg.DG_ERR_ORDER
+    S = Solver(m.VX, m.EToV, m.etype, 5, precision="f64")
+    with pytest.raises(_dg.DGError) as ei:
+        S.adjoint_bind()
+    assert ei.value.code == _dg.DG_ERR_ORDER
+    S.close()

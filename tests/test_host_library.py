@@ -26,7 +26,7 @@ def test_library_exports_every_declared_symbol():
     assert declared == set(dg.EXPORTS)
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
 def test_reference_operators_match_oracle(N):
     m = I.cube_wavy_mesh(1, 1, 0.0)
     H = dg.HostMesh(m.VX, m.EToV, m.etype, N)
@@ -48,7 +48,9 @@ def test_reference_operators_match_oracle(N):
     # reference lift of every tet face: M^-1 E_f M^tri
     Minv = np.linalg.inv(tet.M)
     lift = np.concatenate([Minv[:, tet.faces[f]] @ tri.M for f in range(4)], axis=1)
-    assert np.allclose(H.operator("tet.LIFT"), lift, atol=1e-11)
+    # two independent inversions of the tet mass (condition number 250 at N = 4,
+    # 360 at N = 5): agreement relative to the largest entry
+    assert np.allclose(H.operator("tet.LIFT"), lift, atol=4e-12 * np.abs(lift).max())
 
 
 MESHES = {
@@ -132,7 +134,7 @@ def test_call_order_and_argument_errors():
     try:
         _expect_error(dg.DG_ERR_STATE, lambda: dg.dg_num_nodes(ctx))
         _expect_error(dg.DG_ERR_ORDER, lambda: dg.dg_set_order(ctx, 0))
-        _expect_error(dg.DG_ERR_ORDER, lambda: dg.dg_set_order(ctx, 5))
+        _expect_error(dg.DG_ERR_ORDER, lambda: dg.dg_set_order(ctx, 6))
         dg.dg_set_order(ctx, 2)
         _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_set_options(ctx, 7, 0, 0))
         _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_set_material(ctx, -np.ones(m.K), np.ones(m.K)))
@@ -334,5 +336,18 @@ def test_shot_group_must_divide_the_shots():
         with pytest.raises(dg.DGError) as ei:
             dg.dg_set_shots(ctx, 4)  # 6 shots per group no longer divides
         assert ei.value.code == dg.DG_ERR_ARG
+    finally:
+        dg.dg_destroy(ctx)
+
+
+def test_order_5_limits():
+    """N = 5 is accepted; the tensor-core applies (a slice must fit one
+    16-row tile, Nt = 21 here) are refused at bind time only, so this host
+    check stops at the order."""
+    m = I.cube_wavy_mesh(1, 1, 0.0)
+    ctx = dg.dg_mesh_create(m.VX, m.EToV, m.etype)
+    try:
+        dg.dg_set_order(ctx, 5)
+        assert dg.dg_num_nodes(ctx)[0] == m.K * 6 * 21
     finally:
         dg.dg_destroy(ctx)
