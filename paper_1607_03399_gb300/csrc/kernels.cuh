@@ -1093,6 +1093,21 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
   int nbr = M.t_nbr[w * Kp + e], code = M.t_code[w * Kp + e];  // this warp's face w
   const real zP = nbr < 0 ? zM : ((code & kCodeTet) ? M.t_mat[2 * Kp + nbr] : M.w_mat[2 * M.Kw_pad + nbr]);
   const bool src = M.nsrc > 0 && has_source(M, 4, e);
+  // out-of-block neighbour face nodes of this warp's face, requested before the waits
+  Q4 nvs[Nt];
+  const bool t_bnd = nbr < 0;
+  const bool t_ntet = !t_bnd && (code & kCodeTet) != 0;
+  const int t_nbe = t_bnd ? e : nbr;
+  const bool t_inblk = t_bnd || (t_ntet && (t_nbe >> 5) == blk);
+  if (!t_inblk) {
+    const int nfc = (code >> 4) & 3, perm = code & 15;
+    const real* nb = A.q_in + (t_ntet ? tidx<N>(M.tet_off, t_nbe >> 5, 0, t_nbe & 31) : widx<N>(t_nbe >> 5, 0, t_nbe & 31));
+#pragma unroll
+    for (int k = 0; k < Nt; ++k) {
+      const int nk = O.tab.tri_perm[perm][k];
+      nvs[k] = ldg4(nb, int64_t(t_ntet ? O.tab.tet_face[nfc][nk] : (nfc ? N * Nt : 0) + nk) * (kB * 4));
+    }
+  }
   __syncthreads();  // the mbarriers are initialised
 
   // affine geometry: x = sum_v lambda_v X_v on the bi-unit reference tet
@@ -1171,17 +1186,21 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
     const int nfc = (code >> 4) & 3, perm = code & 15;
     const int nbe = bnd ? e : nbr;
     const bool inblk = bnd || (ntet && (nbe >> 5) == blk);
-    // the neighbour's slab: this block's own, another tet block's or a wedge block's in global memory
-    const real* nb = inblk ? sq + ((nbe & 31) << 2)
-                           : A.q_in + (ntet ? tidx<N>(M.tet_off, nbe >> 5, 0, nbe & 31) : widx<N>(nbe >> 5, 0, nbe & 31));
-#pragma unroll 2
+    // the neighbour's face nodes, all requested at once: this block's own slab
+    // (shared loads), or another tet block's or a wedge block's in global memory
+    if (inblk) {
+#pragma unroll
+      for (int k = 0; k < Nt; ++k) {
+        const int nk = bnd ? k : O.tab.tri_perm[perm][k];
+        nvs[k] = lds4(sq, bnd ? O.tab.tet_face[f][k] : O.tab.tet_face[nfc][nk], nbe & 31);
+      }
+    }
+#pragma unroll
     for (int k = 0; k < Nt; ++k) {
       const int own = O.tab.tet_face[f][k];
       const Q4 o = lds4(sq, own, lane);
       const real unM = n0 * o.u + n1 * o.v + n2 * o.w;
-      const int nk = bnd ? k : O.tab.tri_perm[perm][k];
-      const int node = bnd ? own : (ntet ? O.tab.tet_face[nfc][nk] : (nfc ? N * Nt : 0) + nk);
-      const Q4 nv = ldx4(nb + node * (kB * 4));
+      const Q4 nv = nvs[k];
       real bdp, bdun;
       boundary_jumps(A.bc, o.p, unM, bdp, bdun);
       const real dp = bnd ? bdp : nv.p - o.p;
