@@ -322,7 +322,7 @@ int dg_sample(dg_ctx* ctx, void* d_out);
 
 /* Copy of the current packed state (dg_device_bytes' field_bytes) to / from a
  * caller device buffer, for checkpoints.  dg_load_state also sets the
- * simulation time to t.  dg_save_state is async; dg_load_state synchronises.
+ * simulation time to t.  Both are asynchronous on the bound stream.
  * Errors: DG_ERR_ARG, DG_ERR_STATE. */
 int dg_save_state(dg_ctx* ctx, void* d_dst);
 int dg_load_state(dg_ctx* ctx, const void* d_src, double t);

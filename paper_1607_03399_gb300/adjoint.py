@@ -91,8 +91,15 @@ def misfit(traces, data) -> float:
     return 0.5 * float((r * r).sum())
 
 
-def reverse(S: Solver, pb: Problem, traces, data, ck):
-    """dJ/dkappa, dJ/drho per element after a forward() on the same solver."""
+def reverse(S: Solver, pb: Problem, traces, data, ck, R: Solver | None = None):
+    """dJ/dkappa, dJ/drho per element after a forward() on the same solver.
+
+    With stage records and a second solver R of the same problem (same mesh,
+    material, options and shots, its own state and stream), the segment
+    re-runs run on R, one segment ahead, concurrently with the reverse steps
+    on S: two record buffers alternate, and CUDA events order each buffer's
+    re-run before its reverse steps and its reverse steps before its next
+    re-run.  The gradient is the same bit for bit."""
     torch = S.torch
     resid = (traces - data.to(traces.dtype)).contiguous()
     if getattr(S, "d_adj", None) is None:
@@ -101,6 +108,44 @@ def reverse(S: Solver, pb: Problem, traces, data, ck):
         S.adjoint_reset()
     C = pb.checkpoint_every
     starts = list(range(0, pb.nsteps, C))
+    if pb.stage_records and R is not None:
+        order = list(reversed(starts))
+        own = ck.records if (ck.records is not None and order[0] == ck.records_from) else None
+        first = own if own is not None else []
+        bufs = [first + [S.new_record() for _ in range(min(C, pb.nsteps) - len(first))],
+                [S.new_record() for _ in range(min(C, pb.nsteps))]]
+        free = [None, None]  # per buffer: event after its last reverse step
+
+        def rerun(i):
+            """Re-run segment order[i] on R into buffer i % 2; the event that marks it done."""
+            s0 = order[i]
+            s1 = min(s0 + C, pb.nsteps)
+            b = i % 2
+            if free[b] is not None:
+                R.stream.wait_event(free[b])
+            R.load_state(*ck.states[s0])
+            R.step_record_chain(pb.dt, bufs[b][:s1 - s0])
+            ev = torch.cuda.Event()
+            ev.record(R.stream)
+            return ev
+
+        ready = None if own is not None else rerun(0)
+        for i, s0 in enumerate(order):
+            s1 = min(s0 + C, pb.nsteps)
+            b = i % 2
+            nxt = rerun(i + 1) if i + 1 < len(order) else None
+            if ready is not None:
+                S.stream.wait_event(ready)
+            for n in range(s1, s0, -1):
+                S.adjoint_inject(resid[n - 1])
+                S.adjoint_step_recorded(pb.dt, bufs[b][n - 1 - s0])
+            ev = torch.cuda.Event()
+            ev.record(S.stream)
+            free[b] = ev
+            ready = nxt
+        R.sync()
+        S.sync()
+        return S.adjoint_gradient()
     if pb.stage_records:
         recs = ck.records
         if recs is None or len(recs) < min(C, pb.nsteps):

@@ -52,6 +52,8 @@ int pack_f64(int N, const DevMesh<double>& m, const double* c, double* p, bool u
 int energy_f32(int N, const DevMesh<float>& m, const float* q, void* s) { DGW_SWITCH_N(N, launch_energy_f32, (m, q, s)) }
 int clock_f32(int N, double* c, double dt, void* s) { DGW_SWITCH_N(N, launch_clock_f32, (c, dt, s)) }
 int clock_f64(int N, double* c, double dt, void* s) { DGW_SWITCH_N(N, launch_clock_f64, (c, dt, s)) }
+int set_clock_f32(int N, double* c, double t, void* s) { DGW_SWITCH_N(N, launch_set_clock_f32, (c, t, s)) }
+int set_clock_f64(int N, double* c, double t, void* s) { DGW_SWITCH_N(N, launch_set_clock_f64, (c, t, s)) }
 int wait_expire_f32(int N, int* e, void* s) { DGW_SWITCH_N(N, launch_wait_expire_f32, (e, s)) }
 int wait_expire_f64(int N, int* e, void* s) { DGW_SWITCH_N(N, launch_wait_expire_f64, (e, s)) }
 int energy_f64(int N, const DevMesh<double>& m, const double* q, void* s) { DGW_SWITCH_N(N, launch_energy_f64, (m, q, s)) }
@@ -143,7 +145,6 @@ struct dg_ctx {
   // shots of a group are neighbouring lanes for each element
   int64_t shot_group = 1;
   int64_t group() const { return shot_group == 0 ? shots : shot_group; }
-  double t_stage_host = 0.0;  // staging for clock uploads
   // launch variant chosen by dg_autotune: wedge blocks per CTA (0 = default) and
   // whether the stored mass factor is bypassed (factor recomputed in the stage)
   int tuned_bpc = 0;
@@ -1753,11 +1754,10 @@ int dg_load_state(dg_ctx* c, const void* d_src, double t) {
   cudaError_t e = cudaMemcpyAsync(c->d_q[c->cur], d_src, c->field_bytes, cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "state load");
   c->t = t;
-  c->t_stage_host = t;
-  e = cudaMemcpyAsync(c->prec == DG_F64 ? c->m64.clock : c->m32.clock, &c->t_stage_host, sizeof(double),
-                      cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "state load");
+  // the clock by a one-thread kernel on the stream: the call stays asynchronous
+  const int rc = c->prec == DG_F64 ? set_clock_f64(c->N, c->m64.clock, t, c->stream)
+                                   : set_clock_f32(c->N, c->m32.clock, t, c->stream);
+  if (rc) return cuda_fail(c, cudaError_t(rc), "clock set");
   return DG_OK;
 }
 

@@ -176,6 +176,7 @@ __host__ __device__ constexpr int tile_at(int r, int c) { return r * kTP + (c ^ 
   int launch_energy_##P##n##N(const DevMesh<T>& m, const T* q, void* stream);                      \
   int launch_clock_##P##n##N(double* clock, double dt, void* stream);                              \
   int launch_wait_expire_##P##n##N(int* err, void* stream);                                        \
+  int launch_set_clock_##P##n##N(double* clock, double t, void* stream);                           \
   int launch_sample_##P##n##N(const DevMesh<T>& m, const T* q, T* out, int nshots, void* stream);     \
   int launch_inject_##P##n##N(const DevMesh<T>& m, T* muq, T* x, const T* resid, int nshots, T b5,     \
                               void* stream);                                                       \

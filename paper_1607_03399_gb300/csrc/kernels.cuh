@@ -318,6 +318,10 @@ __device__ __forceinline__ void add_sources(const DevMesh<real>& M, int type, in
 __global__ void k_clock(double* clock, double dt) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *clock += dt;
 }
+// sets the device clock (state loads: no host staging, so no synchronisation)
+__global__ void k_set_clock(double* clock, double t) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *clock = t;
+}
 
 // ---------------------------------------------------------------------------
 // wedge stage
@@ -1223,7 +1227,7 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
 #pragma unroll
     for (int c = 0; c < C; ++c) dr[c] = ds[c] = dt[c] = ap[c] = real(0);
     const real* opI = sOp + I0 * 4;  // records (l, I0 + c) at opI + (l Np + c) 4
-#pragma unroll 2
+#pragma unroll 4
     for (int l = 0; l < Np; ++l) {
       const Q4 v = lds4(sq, l, lane);
       const real wr = Ri[0][0] * v.u + Ri[0][1] * v.v + Ri[0][2] * v.w;
@@ -1252,7 +1256,7 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
       real lu[C];
 #pragma unroll
       for (int c = 0; c < C; ++c) lu[c] = real(0);
-#pragma unroll 2
+#pragma unroll 5
       for (int k = 0; k < Nt; ++k) {
         const real Fp = sF[((f * 2 + 0) * Nt + k) * kB + lane];
         const real Fu = sF[((f * 2 + 1) * Nt + k) * kB + lane];
@@ -1654,6 +1658,10 @@ int DGW_CAT(launch_tgrad_, REALNS)(const DevMesh<REAL>& m, const REAL* x, const 
 }
 int DGW_CAT(launch_wait_expire_, REALNS)(int* err, void* stream) {
   REALNS::k_wait_expire<<<1, 32, 0, cudaStream_t(stream)>>>(err);
+  return int(cudaGetLastError());
+}
+int DGW_CAT(launch_set_clock_, REALNS)(double* clock, double t, void* stream) {
+  REALNS::k_set_clock<<<1, 32, 0, cudaStream_t(stream)>>>(clock, t);
   return int(cudaGetLastError());
 }
 int DGW_CAT(launch_clock_, REALNS)(double* clock, double dt, void* stream) {

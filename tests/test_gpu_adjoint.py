@@ -277,3 +277,22 @@ def test_fp32_gradient_against_fp64_on_the_inclusion_workload():
     (J64, g64), (J32, g32) = out["f64"], out["f32"]
     assert abs(J32 - J64) <= 1e-4 * J64
     assert np.linalg.norm(g32 - g64) <= 2e-4 * np.linalg.norm(g64)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_overlapped_reruns_give_the_same_gradient(precision):
+    """Stage records with the segment re-runs on a second solver, concurrent with
+    the reverse steps (three segments): the gradient equals the one-solver
+    sweep's bit for bit."""
+    m, st, data, pb, kap, rho = _problem(precision, ck=4)
+    pb.stage_records = True
+    S = pb.solver(kap / rho, rho)
+    R = pb.solver(kap / rho, rho)
+    d = torch.as_tensor(data[:, None, :], dtype=S.dtype, device=S.device)
+    traces, ck = AD.forward(S, pb)
+    gk1, gr1 = AD.reverse(S, pb, traces, d, ck)
+    traces, ck = AD.forward(S, pb)
+    gk2, gr2 = AD.reverse(S, pb, traces, d, ck, R=R)
+    S.close()
+    R.close()
+    assert np.array_equal(gk1, gk2) and np.array_equal(gr1, gr2)
