@@ -208,9 +208,18 @@ def _autograd_function():
         def forward(ctx, c2, rho, pb, data):
             S = pb.solver(c2.detach().cpu().numpy(), rho.detach().cpu().numpy())
             traces, ck = forward(S, pb)
+            J = torch.tensor(misfit(traces, data), dtype=torch.float64)
+            if not any(ctx.needs_input_grad[:2]):
+                # no gradient will be asked for: release the solver and its
+                # checkpoints now instead of holding device memory with the graph
+                S.close()
+                ctx.state = None
+                return J
+            # (dropping the graph without backward frees them too: the solver
+            # closes itself when the last reference goes)
             ctx.state = (S, pb, traces, data, ck)
             ctx.save_for_backward(c2, rho)
-            return torch.tensor(misfit(traces, data), dtype=torch.float64)
+            return J
 
         @staticmethod
         def backward(ctx, gJ):

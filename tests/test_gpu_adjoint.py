@@ -296,3 +296,14 @@ def test_overlapped_reruns_give_the_same_gradient(precision):
     S.close()
     R.close()
     assert np.array_equal(gk1, gk2) and np.array_equal(gr1, gr2)
+
+
+def test_autograd_without_gradients_releases_the_solver():
+    """A forward pass whose inputs need no gradient keeps no solver."""
+    m, st, data, pb, kap, rho = _problem("f64")
+    c2 = torch.tensor(kap / rho, dtype=torch.float64)
+    rh = torch.tensor(rho, dtype=torch.float64)
+    d = torch.as_tensor(data[:, None, :], dtype=torch.float64, device="cuda")
+    J = AD.acoustic_misfit(c2, rh, pb, d)
+    J2, _, _ = AD.misfit_and_gradient(pb, kap / rho, rho, d)
+    assert not J.requires_grad and abs(float(J) - J2) <= 1e-12 * J2
