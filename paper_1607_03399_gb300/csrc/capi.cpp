@@ -226,6 +226,17 @@ void fill_ops(const RefElems& R, std::vector<unsigned char>& out) {
     o.w.ellN[m] = real(R.ellN[m]);
     o.w.gll[m] = real(R.gll[m]);
   }
+  // output-pair copies (rows 2h and 2h + 1; zero past the last row)
+  auto pairs = [](const real* X, int rows, int cols, real* XP) {
+    for (int h = 0; h < (rows + 1) / 2; ++h)
+      for (int l = 0; l < cols; ++l)
+        for (int b = 0; b < 2; ++b) XP[(h * cols + l) * 2 + b] = 2 * h + b < rows ? X[(2 * h + b) * cols + l] : real(0);
+  };
+  pairs(o.w.M, Nt, Nt, o.w.MP);
+  pairs(o.w.Dr, Nt, Nt, o.w.DrP);
+  pairs(o.w.Ds, Nt, Nt, o.w.DsP);
+  pairs(o.w.Mea, Nq, Nq, o.w.MeaP);
+  pairs(o.w.Meb, Nq, Nq, o.w.MebP);
   for (int c = 0; c < 9; ++c)
     for (int k = 0; k < Nt; ++k) o.tab.tri_perm[c][k] = R.tri_perm[c].empty() ? 0 : int8_t(R.tri_perm[c][k]);
   for (int e = 0; e < 3; ++e)

@@ -43,6 +43,15 @@ struct WedgeOps {
   static constexpr int Nt = nt_of(N), Nq = N + 1;
   real Dr[Nt * Nt], Ds[Nt * Nt], M[Nt * Nt], Ma[3][Nt * Nt];
   real Dt[Nq * Nq], ell0[Nq], ellN[Nq], Mea[Nq * Nq], Meb[Nq * Nq], M1[Nq * Nq], gll[Nq];
+  // The same matrices by output pairs for packed multiply-adds: entry (h, l)
+  // of XP is {X[2h][l], X[2h + 1][l]} at XP[(h * cols + l) * 2] (a zero row
+  // completes an odd row count), so one 8-byte constant operand feeds two rows.
+  static constexpr int Nh = (Nt + 1) / 2, Nqh = (Nq + 1) / 2;
+  alignas(16) real MP[Nh * Nt * 2];
+  alignas(16) real DrP[Nh * Nt * 2];
+  alignas(16) real DsP[Nh * Nt * 2];
+  alignas(16) real MeaP[Nqh * Nq * 2];
+  alignas(16) real MebP[Nqh * Nq * 2];
 };
 
 template <int N>

@@ -19,6 +19,7 @@
 //   operators are scaled reference operators).
 #pragma once
 #include <cuda_runtime.h>
+#include <type_traits>
 
 #include "dg_internal.hpp"
 
@@ -148,6 +149,51 @@ __device__ __forceinline__ void st4(real* q, int64_t idx, const Q4& v) {
   } else {
     reinterpret_cast<double2*>(q + idx)[0] = make_double2(double(v.p), double(v.u));
     reinterpret_cast<double2*>(q + idx)[1] = make_double2(double(v.v), double(v.w));
+  }
+}
+
+// Packed pairs.  In FP32 one packed FMA instruction (sm_100 family) performs
+// two multiply-adds, each rounded as fmaf: half the issue slots of the scalar
+// form, same results.  In FP64 a pair is two scalar FMAs.
+using real2 = typename std::conditional<sizeof(real) == 4, float2, double2>::type;
+__device__ __forceinline__ float2 fma2(const float2 a, const float2 b, const float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 fma2(const double2 a, const double2 b, const double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ real2 dup2(const real v) {
+  real2 r;
+  r.x = v;
+  r.y = v;
+  return r;
+}
+__device__ __forceinline__ real2 mk2(const real a, const real b) {
+  real2 r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+// entry (h, l) of an output-pair table (constant memory; an 8-byte operand)
+__device__ __forceinline__ real2 cpair(const real* XP, int cols, int h, int l) {
+  return *reinterpret_cast<const real2*>(XP + (h * cols + l) * 2);
+}
+// y += X x for an NR x NC operator given by output pairs XP: every output
+// accumulates its products over l in order, from zero, then adds to y
+template <int NR, int NC>
+__device__ __forceinline__ void apply_pairs_add(const real* XP, const real (&x)[NC], real (&y)[NR]) {
+  constexpr int NH = (NR + 1) / 2;
+  real2 acc[NH];
+#pragma unroll
+  for (int h = 0; h < NH; ++h) acc[h] = dup2(real(0));
+#pragma unroll
+  for (int l = 0; l < NC; ++l) {
+    const real2 xx = dup2(x[l]);
+#pragma unroll
+    for (int h = 0; h < NH; ++h) acc[h] = fma2(cpair(XP, NC, h, l), xx, acc[h]);
+  }
+#pragma unroll
+  for (int h = 0; h < NH; ++h) {
+    y[2 * h] += acc[h].x;
+    if (2 * h + 1 < NR) y[2 * h + 1] += acc[h].y;
   }
 }
 
@@ -717,18 +763,30 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
       penalty_flux(dp, dun, tau_p, tau_u, Fp[m], Fu[m]);
     }
     // W += M~_e F, M~_e = (L_e/4)(h_a Mea + h_b Meb) along the edge, identity in t
+    // (Mea, Meb applied by output pairs: packed multiply-adds)
     const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
+    constexpr int NQH = (Nq + 1) / 2;
+    real2 gpa[NQH], gpb[NQH], gua[NQH], gub[NQH];
+#pragma unroll
+    for (int h = 0; h < NQH; ++h) gpa[h] = gpb[h] = gua[h] = gub[h] = dup2(real(0));
+#pragma unroll
+    for (int n = 0; n < Nq; ++n) {
+      const real2 fp2 = dup2(Fp[n]), fu2 = dup2(Fu[n]);
+#pragma unroll
+      for (int h = 0; h < NQH; ++h) {
+        const real2 ea = cpair(O.w.MeaP, Nq, h, n), eb = cpair(O.w.MebP, Nq, h, n);
+        gpa[h] = fma2(ea, fp2, gpa[h]);
+        gpb[h] = fma2(eb, fp2, gpb[h]);
+        gua[h] = fma2(ea, fu2, gua[h]);
+        gub[h] = fma2(eb, fu2, gub[h]);
+      }
+    }
 #pragma unroll
     for (int m = 0; m < Nq; ++m) {
-      real gpa = 0, gpb = 0, gua = 0, gub = 0;
-#pragma unroll
-      for (int n = 0; n < Nq; ++n) {
-        gpa += O.w.Mea[m * Nq + n] * Fp[n];
-        gpb += O.w.Meb[m * Nq + n] * Fp[n];
-        gua += O.w.Mea[m * Nq + n] * Fu[n];
-        gub += O.w.Meb[m * Nq + n] * Fu[n];
-      }
-      const real gp = ca * gpa + cbq * gpb, gu = ca * gua + cbq * gub;
+      const bool hi = m & 1;
+      const real2 pa = gpa[m >> 1], pb = gpb[m >> 1], ua = gua[m >> 1], ub = gub[m >> 1];
+      const real gp = ca * (hi ? pa.y : pa.x) + cbq * (hi ? pb.y : pb.x);
+      const real gu = ca * (hi ? ua.y : ua.x) + cbq * (hi ? ub.y : ub.x);
       const int i = edge_node(N, ed, m);
       Wp[i] += gp;
       Wu[0][i] += nx * gu;
@@ -790,25 +848,20 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
       real G[Nt];
 #pragma unroll
       for (int i = 0; i < Nt; ++i) {
-        real dpp = 0, dux = 0, duy = 0, duz = 0;
+        // D_t of the four fields as two packed pairs (p, u_x) and (u_y, u_z)
+        real2 dpu = dup2(real(0)), dvw = dup2(real(0));
 #pragma unroll
         for (int m = 0; m < Nq; ++m) {
           const Q4 v = lds4(sq, m * Nt + i, lane);
-          dpp += dtr[m] * v.p;
-          dux += dtr[m] * v.u;
-          duy += dtr[m] * v.v;
-          duz += dtr[m] * v.w;
+          const real2 d2 = dup2(dtr[m]);
+          dpu = fma2(d2, mk2(v.p, v.u), dpu);
+          dvw = fma2(d2, mk2(v.v, v.w), dvw);
         }
-        dp[i] = dpp;
-        G[i] = cb * sF[(0 * Nt + i) * kB + lane] + ct * sF[(2 * Nt + i) * kB + lane] - (txJ * dux + tyJ * duy + Aj * duz);
+        dp[i] = dpu.x;
+        G[i] = cb * sF[(0 * Nt + i) * kB + lane] + ct * sF[(2 * Nt + i) * kB + lane] -
+               (txJ * dpu.y + tyJ * dvw.x + Aj * dvw.y);
       }
-#pragma unroll
-      for (int i = 0; i < Nt; ++i) {
-        real acc = 0;
-#pragma unroll
-        for (int l = 0; l < Nt; ++l) acc += O.w.M[i * Nt + l] * G[l];
-        Wp[i] += acc;
-      }
+      apply_pairs_add<Nt, Nt>(O.w.MP, G, Wp);
     }
     // (b) velocity: G_c = -t_cJ D_t p + n_c lifts; W = M^tri G
 #pragma unroll
@@ -819,13 +872,7 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
 #pragma unroll
       for (int i = 0; i < Nt; ++i)
         G[i] = nbc * sF[(1 * Nt + i) * kB + lane] + ntc * sF[(3 * Nt + i) * kB + lane] - tc * dp[i];
-#pragma unroll
-      for (int i = 0; i < Nt; ++i) {
-        real acc = 0;
-#pragma unroll
-        for (int l = 0; l < Nt; ++l) acc += O.w.M[i * Nt + l] * G[l];
-        Wu[c][i] += acc;
-      }
+      apply_pairs_add<Nt, Nt>(O.w.MP, G, Wu[c]);
     }
     } else {
       // (a, b) on the tensor cores: the four vectors G of every element of
@@ -944,28 +991,33 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
   // have to pass through shared memory back to the element's lane, which
   // measured slower than these FMAs with constant operands)
   {
+    // (D_r, D_s applied by output pairs, node l of the slice at a time)
     const real rx = GEO(G_RX), ry = GEO(G_RY), sx = GEO(G_SX), sy = GEO(G_SY);
-    real pv[Nt], av[Nt], bv[Nt];
+    constexpr int NH = (Nt + 1) / 2;
+    real2 dv[NH], pr[NH], ps[NH];
+#pragma unroll
+    for (int h = 0; h < NH; ++h) dv[h] = pr[h] = ps[h] = dup2(real(0));
 #pragma unroll
     for (int l = 0; l < Nt; ++l) {
       const Q4 v = lds4(sq, j * Nt + l, lane);
-      pv[l] = v.p;
-      av[l] = rx * v.u + ry * v.v;
-      bv[l] = sx * v.u + sy * v.v;
+      const real2 p2 = dup2(v.p), a2 = dup2(rx * v.u + ry * v.v), b2 = dup2(sx * v.u + sy * v.v);
+#pragma unroll
+      for (int h = 0; h < NH; ++h) {
+        const real2 r2 = cpair(O.w.DrP, Nt, h, l), s2 = cpair(O.w.DsP, Nt, h, l);
+        dv[h] = fma2(r2, a2, dv[h]);
+        dv[h] = fma2(s2, b2, dv[h]);
+        pr[h] = fma2(r2, p2, pr[h]);
+        ps[h] = fma2(s2, p2, ps[h]);
+      }
     }
 #pragma unroll
     for (int i = 0; i < Nt; ++i) {
-      real dv = 0, pr = 0, ps = 0;
-#pragma unroll
-      for (int l = 0; l < Nt; ++l) {
-        dv += O.w.Dr[i * Nt + l] * av[l];
-        dv += O.w.Ds[i * Nt + l] * bv[l];
-        pr += O.w.Dr[i * Nt + l] * pv[l];
-        ps += O.w.Ds[i * Nt + l] * pv[l];
-      }
-      Wp[i] -= dv;
-      Wu[0][i] -= rx * pr + sx * ps;
-      Wu[1][i] -= ry * pr + sy * ps;
+      const bool hi = i & 1;
+      const real dvi = hi ? dv[i >> 1].y : dv[i >> 1].x;
+      const real pri = hi ? pr[i >> 1].y : pr[i >> 1].x, psi = hi ? ps[i >> 1].y : ps[i >> 1].x;
+      Wp[i] -= dvi;
+      Wu[0][i] -= rx * pri + sx * psi;
+      Wu[1][i] -= ry * pri + sy * psi;
     }
   }
   // (f) fused low-storage Runge-Kutta update (or plain right-hand side)
