@@ -160,6 +160,10 @@ __device__ __forceinline__ float2 fma2(const float2 a, const float2 b, const flo
 __device__ __forceinline__ double2 fma2(const double2 a, const double2 b, const double2 c) {
   return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
 }
+__device__ __forceinline__ float2 add2(const float2 a, const float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 add2(const double2 a, const double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 mul2(const float2 a, const float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 mul2(const double2 a, const double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
 __device__ __forceinline__ real2 dup2(const real v) {
   real2 r;
   r.x = v;
@@ -176,12 +180,11 @@ __device__ __forceinline__ real2 mk2(const real a, const real b) {
 __device__ __forceinline__ real2 cpair(const real* XP, int cols, int h, int l) {
   return *reinterpret_cast<const real2*>(XP + (h * cols + l) * 2);
 }
-// y += X x for an NR x NC operator given by output pairs XP: every output
-// accumulates its products over l in order, from zero, then adds to y
+// acc = X x for an NR x NC operator given by output pairs XP (acc[h] holds
+// rows 2h, 2h + 1): every output accumulates its products over l in order
 template <int NR, int NC>
-__device__ __forceinline__ void apply_pairs_add(const real* XP, const real (&x)[NC], real (&y)[NR]) {
+__device__ __forceinline__ void apply_pairs(const real* XP, const real (&x)[NC], real2 (&acc)[(NR + 1) / 2]) {
   constexpr int NH = (NR + 1) / 2;
-  real2 acc[NH];
 #pragma unroll
   for (int h = 0; h < NH; ++h) acc[h] = dup2(real(0));
 #pragma unroll
@@ -190,12 +193,9 @@ __device__ __forceinline__ void apply_pairs_add(const real* XP, const real (&x)[
 #pragma unroll
     for (int h = 0; h < NH; ++h) acc[h] = fma2(cpair(XP, NC, h, l), xx, acc[h]);
   }
-#pragma unroll
-  for (int h = 0; h < NH; ++h) {
-    y[2 * h] += acc[h].x;
-    if (2 * h + 1 < NR) y[2 * h + 1] += acc[h].y;
-  }
 }
+// row i of a pair-accumulated result
+__device__ __forceinline__ real pair_row(const real2* acc, int i) { return (i & 1) ? acc[i >> 1].y : acc[i >> 1].x; }
 
 // Penalty fluxes of eq. (1): F_p = 1/2 (tau_p [p] - [u_n]), F_u = 1/2 (tau_u [u_n] - [p]).
 __device__ __forceinline__ void penalty_flux(real dp, real dun, real tau_p, real tau_u, real& Fp, real& Fu) {
@@ -358,6 +358,23 @@ __device__ __forceinline__ void add_sources(const DevMesh<real>& M, int type, in
 #pragma unroll
     for (int c = 0; c < C; ++c)
       if (n0 + c < np) acc[c] += w * g[c];
+  }
+}
+// the same on field-pair accumulators whose x component is the pressure
+template <int C>
+__device__ __forceinline__ void add_sources(const DevMesh<real>& M, int type, int elem, int n0, int np, double t,
+                                            real2 (&acc)[C]) {
+  const int* rng = (type == 6 ? M.w_srng : M.t_srng) + 2 * (elem >> 5);
+  const int sb = rng[0], se = rng[1];
+#pragma unroll 1
+  for (int s = sb; s < se; ++s) {
+    const SourceDev& sd = M.src[s];
+    if (sd.elem != elem) continue;
+    const real w = real(sd.amp * ricker(sd.f0, t - sd.t0));
+    const real* __restrict__ g = M.src_g + sd.goff + n0;
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+      if (n0 + c < np) acc[c].x += w * g[c];
   }
 }
 
@@ -723,9 +740,12 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
 
   // 1. prologue: quadrilateral-face fluxes of slice j applied straight into the
   //    weak-form accumulators (every warp); triangle-face fluxes (warps 0 and N)
-  real Wp[Nt], Wu[3][Nt];
+  // accumulators of node i of the slice by field pairs: W01[i] = (p, u_x),
+  // W23[i] = (u_y, u_z), so that the mass solve and the update run on packed pairs
+  constexpr int NH = (Nt + 1) / 2;
+  real2 W01[Nt], W23[Nt];
 #pragma unroll
-  for (int i = 0; i < Nt; ++i) Wp[i] = Wu[0][i] = Wu[1][i] = Wu[2][i] = real(0);
+  for (int i = 0; i < Nt; ++i) W01[i] = W23[i] = dup2(real(0));
   // neighbour traces of quadrilateral faces whose neighbour lies in this block
   // (or, on a boundary face, the element's own trace, which the ghost state
   // then replaces) from the shared slab; the others were requested above (or,
@@ -788,9 +808,9 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
       const real gp = ca * (hi ? pa.y : pa.x) + cbq * (hi ? pb.y : pb.x);
       const real gu = ca * (hi ? ua.y : ua.x) + cbq * (hi ? ub.y : ub.x);
       const int i = edge_node(N, ed, m);
-      Wp[i] += gp;
-      Wu[0][i] += nx * gu;
-      Wu[1][i] += ny * gu;
+      W01[i].x += gp;
+      W01[i].y += nx * gu;
+      W23[i].x += ny * gu;
     }
   }
   // triangle-face node fluxes (bottom then top), spread round-robin over the warps
@@ -861,7 +881,10 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
         G[i] = cb * sF[(0 * Nt + i) * kB + lane] + ct * sF[(2 * Nt + i) * kB + lane] -
                (txJ * dpu.y + tyJ * dvw.x + Aj * dvw.y);
       }
-      apply_pairs_add<Nt, Nt>(O.w.MP, G, Wp);
+      real2 acc[NH];
+      apply_pairs<Nt, Nt>(O.w.MP, G, acc);
+#pragma unroll
+      for (int i = 0; i < Nt; ++i) W01[i].x += pair_row(acc, i);
     }
     // (b) velocity: G_c = -t_cJ D_t p + n_c lifts; W = M^tri G
 #pragma unroll
@@ -872,7 +895,14 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
 #pragma unroll
       for (int i = 0; i < Nt; ++i)
         G[i] = nbc * sF[(1 * Nt + i) * kB + lane] + ntc * sF[(3 * Nt + i) * kB + lane] - tc * dp[i];
-      apply_pairs_add<Nt, Nt>(O.w.MP, G, Wu[c]);
+      real2 acc[NH];
+      apply_pairs<Nt, Nt>(O.w.MP, G, acc);
+#pragma unroll
+      for (int i = 0; i < Nt; ++i) {
+        if (c == 0) W01[i].y += pair_row(acc, i);
+        else if (c == 1) W23[i].x += pair_row(acc, i);
+        else W23[i].y += pair_row(acc, i);
+      }
     }
     } else {
       // (a, b) on the tensor cores: the four vectors G of every element of
@@ -917,10 +947,8 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
 #pragma unroll
       for (int i = 0; i < Nt; ++i) {
         const float4 w = *reinterpret_cast<const float4*>(sT + tile_at(i, lane * 4));
-        Wp[i] += w.x;
-        Wu[0][i] += w.y;
-        Wu[1][i] += w.z;
-        Wu[2][i] += w.w;
+        W01[i] = add2(W01[i], mk2(w.x, w.y));
+        W23[i] = add2(W23[i], mk2(w.z, w.w));
       }
       if (res_async) {
         // every warp is done with its tile: the residual slab may now land in their space
@@ -957,32 +985,26 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
       load_row(i, Lr);
 #pragma unroll
       for (int k = 0; k < i; ++k) {
-        Wp[i] -= Lr[k] * Wp[k];
-        Wu[0][i] -= Lr[k] * Wu[0][k];
-        Wu[1][i] -= Lr[k] * Wu[1][k];
-        Wu[2][i] -= Lr[k] * Wu[2][k];
+        const real2 nl = dup2(-Lr[k]);
+        W01[i] = fma2(nl, W01[k], W01[i]);
+        W23[i] = fma2(nl, W23[k], W23[i]);
       }
-      const real d = Lr[i];
-      Wp[i] *= d;
-      Wu[0][i] *= d;
-      Wu[1][i] *= d;
-      Wu[2][i] *= d;
+      const real2 d = dup2(Lr[i]);
+      W01[i] = mul2(W01[i], d);
+      W23[i] = mul2(W23[i], d);
     }
 #pragma unroll
     for (int i = Nt - 1; i >= 0; --i) {
       real Lr[Nt];
       load_row(i, Lr);
-      const real d = Lr[i];
-      Wp[i] *= d;
-      Wu[0][i] *= d;
-      Wu[1][i] *= d;
-      Wu[2][i] *= d;
+      const real2 d = dup2(Lr[i]);
+      W01[i] = mul2(W01[i], d);
+      W23[i] = mul2(W23[i], d);
 #pragma unroll
       for (int k = 0; k < i; ++k) {
-        Wp[k] -= Lr[k] * Wp[i];
-        Wu[0][k] -= Lr[k] * Wu[0][i];
-        Wu[1][k] -= Lr[k] * Wu[1][i];
-        Wu[2][k] -= Lr[k] * Wu[2][i];
+        const real2 nl = dup2(-Lr[k]);
+        W01[k] = fma2(nl, W01[i], W01[k]);
+        W23[k] = fma2(nl, W23[i], W23[k]);
       }
     }
   }
@@ -993,7 +1015,6 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
   {
     // (D_r, D_s applied by output pairs, node l of the slice at a time)
     const real rx = GEO(G_RX), ry = GEO(G_RY), sx = GEO(G_SX), sy = GEO(G_SY);
-    constexpr int NH = (Nt + 1) / 2;
     real2 dv[NH], pr[NH], ps[NH];
 #pragma unroll
     for (int h = 0; h < NH; ++h) dv[h] = pr[h] = ps[h] = dup2(real(0));
@@ -1015,9 +1036,9 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
       const bool hi = i & 1;
       const real dvi = hi ? dv[i >> 1].y : dv[i >> 1].x;
       const real pri = hi ? pr[i >> 1].y : pr[i >> 1].x, psi = hi ? ps[i >> 1].y : ps[i >> 1].x;
-      Wp[i] -= dvi;
-      Wu[0][i] -= rx * pri + sx * psi;
-      Wu[1][i] -= ry * pri + sy * psi;
+      W01[i].x -= dvi;
+      W01[i].y -= rx * pri + sx * psi;
+      W23[i].x -= ry * pri + sy * psi;
     }
   }
   // (f) fused low-storage Runge-Kutta update (or plain right-hand side)
@@ -1026,22 +1047,25 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
     mbar_wait_bounded(&bar[1], 0);
     return;
   }
-  if (src) add_sources(M, 6, e, j * Nt, Np, *M.clock + A.c_stage * double(A.dt), Wp);
+  if (src) add_sources(M, 6, e, j * Nt, Np, *M.clock + A.c_stage * double(A.dt), W01);
   if (e < M.Kw) {
 #pragma unroll
     for (int i = 0; i < Nt; ++i) {
       const int n = j * Nt + i;
       const int64_t g = widx<N>(blk, n, lane);
-      Q4 r{kappa * Wp[i], irho * Wu[0][i], irho * Wu[1][i], irho * Wu[2][i]};
+      const real2 r01 = mul2(W01[i], mk2(kappa, irho)), r23 = mul2(W23[i], dup2(irho));
+      const Q4 r{r01.x, r01.y, r23.x, r23.y};
       if (rk) {
+        // res = a res + dt r, q = g q + b res, on packed pairs
         const Q4 r0 = stage_res<N, OP>() ? lds4(sr, n, lane) : ld4(resg, g);
-        const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
-                    A.rk_a * r0.w + A.dt * r.w};
+        const real2 a2 = dup2(A.rk_a), dt2 = dup2(A.dt), g2 = dup2(A.rk_g), b2 = dup2(A.rk_b);
+        const real2 rr01 = fma2(a2, mk2(r0.p, r0.u), mul2(dt2, r01));
+        const real2 rr23 = fma2(a2, mk2(r0.v, r0.w), mul2(dt2, r23));
         const Q4 q0 = lds4(sq, n, lane);
-        st4(resg, g, rr);
-        st4(qout, g,
-            Q4{A.rk_g * q0.p + A.rk_b * rr.p, A.rk_g * q0.u + A.rk_b * rr.u, A.rk_g * q0.v + A.rk_b * rr.v,
-               A.rk_g * q0.w + A.rk_b * rr.w});
+        const real2 q01 = fma2(g2, mk2(q0.p, q0.u), mul2(b2, rr01));
+        const real2 q23 = fma2(g2, mk2(q0.v, q0.w), mul2(b2, rr23));
+        st4(resg, g, Q4{rr01.x, rr01.y, rr23.x, rr23.y});
+        st4(qout, g, Q4{q01.x, q01.y, q23.x, q23.y});
         if (A.rhs_out) st4(A.rhs_out, g, r);
       } else {
         st4(qout, g, r);
@@ -1273,11 +1297,20 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
   // operators only), then, once every warp's face fluxes are in the table,
   // the lift and the update
   const int I0 = w * C;
-  real ap[C], au[3][C];
+  // results of the warp's outputs by output pairs (c, c + 1): ap2 the pressure,
+  // au2[d] the velocity components (packed multiply-adds)
+  constexpr int CH = (C + 1) / 2;
+  real2 ap2[CH], au2[3][CH];
   {
-    real dr[C], ds[C], dt[C];
+    // per output: (D_r p, D_s p) and D_t p; (D_r w_r + D_t w_t, D_s w_s) with
+    // w = the reference-direction velocity components
+    real2 drs[C], sab[C];
+    real dt[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) dr[c] = ds[c] = dt[c] = ap[c] = real(0);
+    for (int c = 0; c < C; ++c) {
+      drs[c] = sab[c] = dup2(real(0));
+      dt[c] = real(0);
+    }
     const real* opI = sOp + I0 * 4;  // records (l, I0 + c) at opI + (l Np + c) 4
 #pragma unroll 4
     for (int l = 0; l < Np; ++l) {
@@ -1285,19 +1318,26 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
       const real wr = Ri[0][0] * v.u + Ri[0][1] * v.v + Ri[0][2] * v.w;
       const real ws = Ri[1][0] * v.u + Ri[1][1] * v.v + Ri[1][2] * v.w;
       const real wt = Ri[2][0] * v.u + Ri[2][1] * v.v + Ri[2][2] * v.w;
+      const real2 pp = dup2(v.p), wrs = mk2(wr, ws);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         const Q4 d = ldop4(opI + (l * Np + c) * 4);  // I0 + c >= Np: unused records, results dropped
-        dr[c] += d.p * v.p;
-        ds[c] += d.u * v.p;
+        const real2 dpu = mk2(d.p, d.u);
+        drs[c] = fma2(dpu, pp, drs[c]);
         dt[c] += d.v * v.p;
-        ap[c] -= d.p * wr + d.u * ws + d.v * wt;
+        sab[c] = fma2(dpu, wrs, sab[c]);
+        sab[c].x += d.v * wt;
       }
     }
 #pragma unroll
-    for (int c = 0; c < C; ++c)
+    for (int h = 0; h < CH; ++h) {
+      const int c0 = 2 * h, c1 = 2 * h + 1 < C ? 2 * h + 1 : 2 * h;
+      ap2[h] = mk2(-(sab[c0].x + sab[c0].y), -(sab[c1].x + sab[c1].y));
 #pragma unroll
-      for (int d = 0; d < 3; ++d) au[d][c] = -(Ri[0][d] * dr[c] + Ri[1][d] * ds[c] + Ri[2][d] * dt[c]);
+      for (int d = 0; d < 3; ++d)
+        au2[d][h] = mk2(-(Ri[0][d] * drs[c0].x + Ri[1][d] * drs[c0].y + Ri[2][d] * dt[c0]),
+                        -(Ri[0][d] * drs[c1].x + Ri[1][d] * drs[c1].y + Ri[2][d] * dt[c1]));
+    }
   }
   __syncthreads();
   {
@@ -1305,32 +1345,39 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
     const real* lw = (tet_lift_smem<N>() ? sL : M.t_ops + 4 * Np * Np) + w * (4 * Nt) * CP;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      real lu[C];
+      real2 lu2[CH];
 #pragma unroll
-      for (int c = 0; c < C; ++c) lu[c] = real(0);
+      for (int h = 0; h < CH; ++h) lu2[h] = dup2(real(0));
 #pragma unroll 5
       for (int k = 0; k < Nt; ++k) {
-        const real Fp = sF[((f * 2 + 0) * Nt + k) * kB + lane];
-        const real Fu = sF[((f * 2 + 1) * Nt + k) * kB + lane];
+        const real2 fp2 = dup2(sF[((f * 2 + 0) * Nt + k) * kB + lane]);
+        const real2 fu2 = dup2(sF[((f * 2 + 1) * Nt + k) * kB + lane]);
 #pragma unroll
         for (int c4 = 0; c4 < CP; c4 += 4) {
           const Q4 L = ldop4(lw + (f * Nt + k) * CP + c4);
-          const real Lc[4] = {L.p, L.u, L.v, L.w};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (c4 + q < C) {
-              ap[c4 + q] += Lc[q] * Fp;
-              lu[c4 + q] += Lc[q] * Fu;
-            }
+          const real2 La = mk2(L.p, L.u), Lb = mk2(L.v, L.w);
+          const int h = c4 / 2;
+          if (h < CH) {
+            ap2[h] = fma2(La, fp2, ap2[h]);
+            lu2[h] = fma2(La, fu2, lu2[h]);
+          }
+          if (h + 1 < CH) {
+            ap2[h + 1] = fma2(Lb, fp2, ap2[h + 1]);
+            lu2[h + 1] = fma2(Lb, fu2, lu2[h + 1]);
           }
         }
       }
 #pragma unroll
-      for (int c = 0; c < C; ++c)
+      for (int d = 0; d < 3; ++d) {
+        const real2 n2 = dup2(nf[f][d]);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) au[d][c] += nf[f][d] * lu[c];
+        for (int h = 0; h < CH; ++h) au2[d][h] = fma2(n2, lu2[h], au2[d][h]);
+      }
     }
   }
+  real ap[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) ap[c] = pair_row(ap2, c);
   if (src) add_sources(M, 4, e, I0, Np, *M.clock + A.c_stage * double(A.dt), ap);
   if (stage_res && rk && !__all_sync(0xffffffffu, mbar_wait_bounded(&bar[3], 0))) {
     // the residual slab never arrived: report, let the copy drain, leave
@@ -1346,16 +1393,20 @@ __global__ void __launch_bounds__(128, (sizeof(REAL) == 4) ? (N >= 4 ? 3 : 5) : 
       if (I0 + c < Np) {
         const int i = I0 + c;
         const int64_t gi = tidx<N>(M.tet_off, blk, i, lane);
-        const Q4 r{kappa * ap[c], irho * au[0][c], irho * au[1][c], irho * au[2][c]};
+        const real2 r01 = mul2(mk2(ap[c], pair_row(au2[0], c)), mk2(kappa, irho));
+        const real2 r23 = mul2(mk2(pair_row(au2[1], c), pair_row(au2[2], c)), dup2(irho));
+        const Q4 r{r01.x, r01.y, r23.x, r23.y};
         if (rk) {
+          // res = a res + dt r, q = g q + b res, on packed pairs
           const Q4 r0 = stage_res ? lds4(sr, i, lane) : ld4(A.res, gi);
-          const Q4 rr{A.rk_a * r0.p + A.dt * r.p, A.rk_a * r0.u + A.dt * r.u, A.rk_a * r0.v + A.dt * r.v,
-                      A.rk_a * r0.w + A.dt * r.w};
+          const real2 a2 = dup2(A.rk_a), dt2 = dup2(A.dt), g2 = dup2(A.rk_g), b2 = dup2(A.rk_b);
+          const real2 rr01 = fma2(a2, mk2(r0.p, r0.u), mul2(dt2, r01));
+          const real2 rr23 = fma2(a2, mk2(r0.v, r0.w), mul2(dt2, r23));
           const Q4 q0 = lds4(sq, i, lane);
-          st4(A.res, gi, rr);
-          st4(A.q_out, gi,
-              Q4{A.rk_g * q0.p + A.rk_b * rr.p, A.rk_g * q0.u + A.rk_b * rr.u, A.rk_g * q0.v + A.rk_b * rr.v,
-                 A.rk_g * q0.w + A.rk_b * rr.w});
+          const real2 q01 = fma2(g2, mk2(q0.p, q0.u), mul2(b2, rr01));
+          const real2 q23 = fma2(g2, mk2(q0.v, q0.w), mul2(b2, rr23));
+          st4(A.res, gi, Q4{rr01.x, rr01.y, rr23.x, rr23.y});
+          st4(A.q_out, gi, Q4{q01.x, q01.y, q23.x, q23.y});
           if (A.rhs_out) st4(A.rhs_out, gi, r);
         } else {
           st4(A.q_out, gi, r);
