@@ -340,6 +340,12 @@ int dg_load_state(dg_ctx* ctx, const void* d_src, double t);
  * and tets (the gradient terms of a tet use its affine mass J M^tet and face
  * masses J_f M^tri); every shot shares the receivers.
  *
+ * Workspace (dg_adjoint_bytes, caller-owned device memory): fourteen packed
+ * fields, then FP64 sums per padded device element: d/dkappa and d/drho of
+ * the wedges, of the tets, and five face sums per wedge (the penalty term of
+ * a face between two wedges is evaluated once, by the lower-numbered wedge,
+ * for both; dg_adjoint_gradient combines the face sums through z = rho c).
+ *
  * Use: dg_adjoint_bytes -> allocate -> dg_adjoint_bind (zeroes everything)
  * -> for n = nsteps .. 1: dg_adjoint_inject(residuals of step n);
  * dg_load_state(q_{n-1}, t_{n-1}); dg_adjoint_step(dt) -> dg_adjoint_gradient.

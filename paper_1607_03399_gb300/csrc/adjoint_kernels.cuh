@@ -66,12 +66,13 @@ __global__ void k_inject(const DevMesh<real> M, real* __restrict__ muq, real* __
 // have no penalty.  M^k = M^{tri,k} (x) M^1D (Section 4.2); the face masses are
 // J_f M^tri (triangles) and M~_e (x) M^1D (quadrilaterals).  A CTA takes a
 // 32-wedge block with N+1 warps (slabs of x and q in shared memory): warp j
-// forms the element terms of slice j and the face terms of the faces it owns
-// (grad_tri_warp and quadrilateral face e on warp e mod (N+1)); the warps'
-// partial sums are reduced in a fixed order and added, times dt, in double.
-// Wedge neighbours only (the adjoint takes wedge meshes).  The right-hand
-// side is read from global memory, one slice per warp (staging it as a third
-// slab measured slower at N = 3: fewer CTAs per SM).
+// forms the element terms of slice j and the face terms of the faces it is
+// given (grad_tri_warp and quadrilateral face e on warp e mod (N+1)); the
+// warps' partial element sums are reduced in a fixed order and added, times
+// dt, in double; the face terms go to per-face sums (dz/dkappa and dz/drho
+// applied when the gradient is read).  The right-hand side is read from
+// global memory, one slice per warp (staging it as a third slab measured
+// slower at N = 3: fewer CTAs per SM).
 // Shared memory: x slab, q slab, geometry, [warp][3][32] partial sums, the
 // copy barrier and the failure flag.
 template <int N>
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
     k_wedge_grad(const DevMesh<real> M, const real* __restrict__ X,
                                                              const real* __restrict__ Q, const real* __restrict__ R,
                                                              double dt, int flux, int bc, double* __restrict__ gk,
-                                                             double* __restrict__ gr) {
+                                                             double* __restrict__ gr, double* __restrict__ gz) {
   constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
   const AllOps<N, real>& O = OPS<N>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
   Q4 rj[Nt];
 #pragma unroll
   for (int i = 0; i < Nt; ++i) rj[i] = ld4(R, widx<N>(blk, j * Nt + i, lane));
-  const real kappa = M.w_mat[0 * Kp + e], irho = M.w_mat[1 * Kp + e], zM = M.w_mat[2 * Kp + e];
+  const real kappa = M.w_mat[0 * Kp + e], zM = M.w_mat[2 * Kp + e];
   int nbf[5], cdf[5];
   real zPf[5];
 #pragma unroll
@@ -153,37 +154,47 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
   // element terms: mu^T (M^tri (x) M^1D) r = sum_j' (sum_j M1[j][j'] mu[j])^T M^tri r[j'];
   // warp j takes the term of r's slice j (its own, loaded once from global
   // memory) and the M1-weighted sum of the mu slices from the shared slab
+  // (packed pairs: the mu sums by field pairs (p, u_x), (u_y, u_z); the
+  // entries of M^{tri,k} two rows at a time from the output-pair tables)
   real t1k = 0, t1r = 0;
   {
-    real bt[4][Nt];
+    real2 b01[Nt], b23[Nt];
 #pragma unroll
-    for (int l = 0; l < Nt; ++l) bt[0][l] = bt[1][l] = bt[2][l] = bt[3][l] = real(0);
+    for (int l = 0; l < Nt; ++l) b01[l] = b23[l] = dup2(real(0));
 #pragma unroll
     for (int jp = 0; jp < Nq; ++jp) {
-      const real m1 = O.w.M1[jp * Nq + j];
+      const real2 m1 = dup2(O.w.M1[jp * Nq + j]);
 #pragma unroll
       for (int l = 0; l < Nt; ++l) {
         const Q4 v = lds4(sX, jp * Nt + l, lane);
-        bt[0][l] += m1 * v.p;
-        bt[1][l] += m1 * v.u;
-        bt[2][l] += m1 * v.v;
-        bt[3][l] += m1 * v.w;
+        b01[l] = fma2(m1, mk2(v.p, v.u), b01[l]);
+        b23[l] = fma2(m1, mk2(v.v, v.w), b23[l]);
       }
     }
+    const real2 J0d = dup2(J0), J1d = dup2(J1), J2d = dup2(J2);
+    constexpr int NH = (Nt + 1) / 2;
 #pragma unroll
-    for (int i = 0; i < Nt; ++i) {
-      real c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    for (int h = 0; h < NH; ++h) {
+      // rows i0 = 2h and i1 = 2h + 1 (an odd last row pairs with a zero row)
+      real2 c01a = dup2(real(0)), c23a = dup2(real(0)), c01b = dup2(real(0)), c23b = dup2(real(0));
 #pragma unroll
       for (int l = 0; l < Nt; ++l) {
-        const real mt = J0 * O.w.Ma[0][i * Nt + l] + J1 * O.w.Ma[1][i * Nt + l] + J2 * O.w.Ma[2][i * Nt + l];
-        c0 += mt * bt[0][l];
-        c1 += mt * bt[1][l];
-        c2 += mt * bt[2][l];
-        c3 += mt * bt[3][l];
+        const real2 mt = fma2(cpair(O.w.MaP[0], Nt, h, l), J0d,
+                              fma2(cpair(O.w.MaP[1], Nt, h, l), J1d, mul2(cpair(O.w.MaP[2], Nt, h, l), J2d)));
+        const real2 ma = dup2(mt.x), mb = dup2(mt.y);
+        c01a = fma2(ma, b01[l], c01a);
+        c23a = fma2(ma, b23[l], c23a);
+        c01b = fma2(mb, b01[l], c01b);
+        c23b = fma2(mb, b23[l], c23b);
       }
-      const Q4 r = rj[i];
-      t1k += r.p * c0;
-      t1r += r.u * c1 + r.v * c2 + r.w * c3;
+      const Q4 ra = rj[2 * h];
+      t1k += ra.p * c01a.x;
+      t1r += ra.u * c01a.y + ra.v * c23a.x + ra.w * c23a.y;
+      if (2 * h + 1 < Nt) {
+        const Q4 rb = rj[2 * h + 1];
+        t1k += rb.p * c01b.x;
+        t1r += rb.u * c01b.y + rb.v * c23b.x + rb.w * c23b.y;
+      }
     }
   }
   t1k /= kappa * kappa;
@@ -191,8 +202,17 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
   // face terms: derivative of the upwind penalty in z.  Each face is one
   // warp's task (quadrilateral face e on warp e mod (N+1), the triangle faces
   // on the last warps): the warp forms the jumps of the whole face and its
-  // face-mass integrals, with no exchange between warps.
-  real gz = 0;
+  // face-mass integrals, with no exchange between warps.  The penalty term of
+  // a face is symmetric in its two elements (tau_p, tau_u and the jump
+  // products do not change with the side), so a face between two wedges is
+  // evaluated once, by the lower-numbered wedge, which adds dt times it to
+  // the face sums gz[face][element] of both; boundary faces and faces towards
+  // a tet belong to the wedge.  Each face sum has one writer per launch.
+  auto add_face = [&](int f, int nbr, int nf, real val) {
+    const double v = dt * double(val);
+    gz[int64_t(f) * Kp + e] += v;
+    if (nbr >= 0) gz[int64_t(nf) * Kp + nbr] += v;
+  };
   if (flux == 0) {
     // a neighbour's node value, from global memory also when the neighbour is
     // in this block (a uniform load stream measured faster than choosing the
@@ -211,6 +231,7 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
       const int nbr = ed == 0 ? nbf[2] : (ed == 1 ? nbf[3] : nbf[4]);
       const int code = ed == 0 ? cdf[2] : (ed == 1 ? cdf[3] : cdf[4]);
       const real zP = ed == 0 ? zPf[2] : (ed == 1 ? zPf[3] : zPf[4]);
+      if (nbr >= 0 && nbr < e) continue;  // the neighbour's task
       const real nx = GEO(G_QNX0 + ed), ny = GEO(G_QNY0 + ed);
       const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
       const int ep = nbr < 0 ? ed : code >> 1, rev = nbr < 0 ? 0 : code & 1;
@@ -281,7 +302,7 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
           Ip += a * Bb[jj][m];
           Iu += c * Bd[jj][m];
         }
-      gz += penalty(nbr, zP, Ip, Iu);
+      add_face(2 + ed, nbr, 2 + ep, penalty(nbr, zP, Ip, Iu));
     }
     // triangle face fb (bottom, top; face mass J_f M^tri)
 #pragma unroll 1
@@ -294,6 +315,7 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
       // the neighbour across a triangle face: a wedge (its bottom or top slice) or,
       // at the wedge/tet interface, a tet (one of its faces)
       const bool ntet = TETS && nbr >= 0 && (code & kCodeTet) != 0;
+      if (nbr >= 0 && !ntet && nbr < e) continue;  // the neighbour's task
       const int own0 = fb ? N * Nt : 0, nf = (code >> 4) & 3;
       auto nbt = [&](const real* glob, int k) {
         const int nk = O.tab.tri_perm[code & 15][k];
@@ -329,24 +351,21 @@ __global__ void __launch_bounds__(32 * (N + 1), (sizeof(real) == 4) ? (N <= 3 ? 
         Ip += a[k] * sp;
         Iu += c[k] * su;
       }
-      gz += penalty(nbr, zP, Ip * Jf, Iu * Jf);
+      add_face(fb, ntet ? -1 : nbr, nf, penalty(nbr, zP, Ip * Jf, Iu * Jf));
     }
   }
   // reduce the warps' partial sums in a fixed order
   red[(j * 3 + 0) * kB + lane] = double(t1k);
   red[(j * 3 + 1) * kB + lane] = double(t1r);
-  red[(j * 3 + 2) * kB + lane] = double(gz);
   __syncthreads();
   if (j == 0 && e < M.Kw) {
-    double sk = 0.0, sr = 0.0, sz = 0.0;
+    double sk = 0.0, sr = 0.0;
     for (int jj = 0; jj < Nq; ++jj) {
       sk += red[(jj * 3 + 0) * kB + lane];
       sr += red[(jj * 3 + 1) * kB + lane];
-      sz += red[(jj * 3 + 2) * kB + lane];
     }
-    const double rho = 1.0 / double(irho);
-    gk[e] += dt * (sk + sz * double(zM) / (2.0 * double(kappa)));
-    gr[e] += dt * (sr + sz * double(zM) / (2.0 * rho));
+    gk[e] += dt * sk;
+    gr[e] += dt * sr;
   }
 #undef GEO
 }

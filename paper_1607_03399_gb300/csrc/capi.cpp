@@ -70,12 +70,12 @@ int inject_f64(int N, const DevMesh<double>& m, double* mu, double* x, const dou
   DGW_SWITCH_N(N, launch_inject_f64, (m, mu, x, r, ns, b5, s))
 }
 int grad_f32(int N, const DevMesh<float>& m, const float* x, const float* q, const float* r, double dt, int fl, int bc,
-             double* gk, double* gr, void* s) {
-  DGW_SWITCH_N(N, launch_grad_f32, (m, x, q, r, dt, fl, bc, gk, gr, s))
+             double* gk, double* gr, double* gz, void* s) {
+  DGW_SWITCH_N(N, launch_grad_f32, (m, x, q, r, dt, fl, bc, gk, gr, gz, s))
 }
 int grad_f64(int N, const DevMesh<double>& m, const double* x, const double* q, const double* r, double dt, int fl, int bc,
-             double* gk, double* gr, void* s) {
-  DGW_SWITCH_N(N, launch_grad_f64, (m, x, q, r, dt, fl, bc, gk, gr, s))
+             double* gk, double* gr, double* gz, void* s) {
+  DGW_SWITCH_N(N, launch_grad_f64, (m, x, q, r, dt, fl, bc, gk, gr, gz, s))
 }
 int tgrad_f32(int N, const DevMesh<float>& m, const float* x, const float* q, const float* r, double dt, int fl, int bc,
               double* gk, double* gr, void* s) {
@@ -237,6 +237,7 @@ void fill_ops(const RefElems& R, std::vector<unsigned char>& out) {
   pairs(o.w.Ds, Nt, Nt, o.w.DsP);
   pairs(o.w.Mea, Nq, Nq, o.w.MeaP);
   pairs(o.w.Meb, Nq, Nq, o.w.MebP);
+  for (int a = 0; a < 3; ++a) pairs(o.w.Ma[a], Nt, Nt, o.w.MaP[a]);
   for (int c = 0; c < 9; ++c)
     for (int k = 0; k < Nt; ++k) o.tab.tri_perm[c][k] = R.tri_perm[c].empty() ? 0 : int8_t(R.tri_perm[c][k]);
   for (int e = 0; e < 3; ++e)
@@ -1725,6 +1726,11 @@ double* adj_tgk(dg_ctx* c) {
 double* adj_tgr(dg_ctx* c) {
   return reinterpret_cast<double*>(c->adj + kAdjFields * c->field_bytes + 2 * adj_grad_bytes(c) + adj_tgrad_bytes(c));
 }
+// FP64 face sums of the wedges, [face 0..4][device wedge]: dt times the penalty
+// derivative of each face, written by the face's owner for both of its elements
+double* adj_gz(dg_ctx* c) {
+  return reinterpret_cast<double*>(c->adj + kAdjFields * c->field_bytes + 2 * adj_grad_bytes(c) + 2 * adj_tgrad_bytes(c));
+}
 }  // namespace
 
 int dg_sample(dg_ctx* c, void* d_out) {
@@ -1776,7 +1782,7 @@ int dg_adjoint_bytes(const dg_ctx* c, size_t* bytes) {
   if (!c) return DG_ERR_ARG;
   if (!bytes) return c->fail(DG_ERR_ARG, "null or invalid argument");
   if (!c->N) return c->fail(DG_ERR_STATE, "call needs dg_set_order first");
-  *bytes = kAdjFields * field_bytes_of(c) + 2 * adj_grad_bytes(c) + 2 * adj_tgrad_bytes(c);
+  *bytes = kAdjFields * field_bytes_of(c) + 7 * adj_grad_bytes(c) + 2 * adj_tgrad_bytes(c);
   return DG_OK;
 }
 
@@ -1836,10 +1842,12 @@ int adjoint_reverse_stages(dg_ctx* c, double dt, const void* const* Q, const voi
     int lr;
     if (c->prec == DG_F64)
       lr = grad_f64(c->N, c->m64, static_cast<const double*>(xin), static_cast<const double*>(Q[st]),
-                    static_cast<const double*>(R[st]), dt, c->flux, c->bc, adj_gk(c), adj_gr(c), c->stream);
+                    static_cast<const double*>(R[st]), dt, c->flux, c->bc, adj_gk(c), adj_gr(c), adj_gz(c),
+                    c->stream);
     else
       lr = grad_f32(c->N, c->m32, static_cast<const float*>(xin), static_cast<const float*>(Q[st]),
-                    static_cast<const float*>(R[st]), dt, c->flux, c->bc, adj_gk(c), adj_gr(c), c->stream);
+                    static_cast<const float*>(R[st]), dt, c->flux, c->bc, adj_gk(c), adj_gr(c), adj_gz(c),
+                    c->stream);
     if (lr) return cuda_fail(c, cudaError_t(lr), "gradient launch");
     if (c->prec == DG_F64)
       lr = tgrad_f64(c->N, c->m64, static_cast<const double*>(xin), static_cast<const double*>(Q[st]),
@@ -2011,9 +2019,11 @@ int dg_adjoint_gradient(dg_ctx* c, double* g_kappa, double* g_rho) {
   if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
   const int64_t Kw = int64_t(c->wedges.size()), nv = nblk(vKw(c)) * kB;
   const int64_t Kt = int64_t(c->tets.size()), nt = nblk(vKt(c)) * kB;
-  std::vector<double> gk(nv), gr(nv), tk(nt), tr(nt);
+  std::vector<double> gk(nv), gr(nv), gz(5 * nv), tk(nt), tr(nt);
   cudaError_t e = cudaMemcpyAsync(gk.data(), adj_gk(c), nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(gr.data(), adj_gr(c), nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(gz.data(), adj_gz(c), 5 * nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && nt > 0)
     e = cudaMemcpyAsync(tk.data(), adj_tgk(c), nt * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && nt > 0)
@@ -2021,12 +2031,18 @@ int dg_adjoint_gradient(dg_ctx* c, double* g_kappa, double* g_rho) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "gradient download");
   for (int64_t k = 0; k < c->K; ++k) g_kappa[k] = g_rho[k] = 0.0;
-  // sum over shots in shot order, per element of either type
+  // sum over shots in shot order, per element of either type; a wedge's face
+  // sums G (dt times dJ/dz through the penalty) enter through z = rho c:
+  // dz/dkappa = 1 / (2 c), dz/drho = c / 2
   for (int64_t s = 0; s < c->shots; ++s) {
     for (int64_t w = 0; w < Kw; ++w) {
       const int64_t v = shot_vid(s, w, Kw, c->group());
-      g_kappa[c->wedges[w]] += gk[v];
-      g_rho[c->wedges[w]] += gr[v];
+      const int64_t k = c->wedges[w];
+      double G = 0.0;
+      for (int f = 0; f < 5; ++f) G += gz[f * nv + v];
+      const double cc = std::sqrt(c->c2[k]);
+      g_kappa[k] += gk[v] + G / (2.0 * cc);
+      g_rho[k] += gr[v] + G * (0.5 * cc);
     }
     for (int64_t t = 0; t < Kt; ++t) {
       const int64_t v = shot_vid(s, t, Kt, c->group());

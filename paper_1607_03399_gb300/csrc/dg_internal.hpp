@@ -52,6 +52,7 @@ struct WedgeOps {
   alignas(16) real DsP[Nh * Nt * 2];
   alignas(16) real MeaP[Nqh * Nq * 2];
   alignas(16) real MebP[Nqh * Nq * 2];
+  alignas(16) real MaP[3][Nh * Nt * 2];
 };
 
 template <int N>
@@ -190,7 +191,7 @@ __host__ __device__ constexpr int tile_at(int r, int c) { return r * kTP + (c ^ 
   int launch_inject_##P##n##N(const DevMesh<T>& m, T* muq, T* x, const T* resid, int nshots, T b5,     \
                               void* stream);                                                       \
   int launch_grad_##P##n##N(const DevMesh<T>& m, const T* x, const T* q, const T* r, double dt, int flux, \
-                            int bc, double* gk, double* gr, void* stream);                        \
+                            int bc, double* gk, double* gr, double* gz, void* stream);            \
   int launch_tgrad_##P##n##N(const DevMesh<T>& m, const T* x, const T* q, const T* r, double dt, int flux, \
                              int bc, double* gk, double* gr, void* stream);
 DGW_DECLARE_LAUNCHERS(f32, float, 1)

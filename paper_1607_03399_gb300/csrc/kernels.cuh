@@ -1738,16 +1738,16 @@ int DGW_CAT(launch_inject_, REALNS)(const DevMesh<REAL>& m, REAL* muq, REAL* x, 
   return int(cudaGetLastError());
 }
 int DGW_CAT(launch_grad_, REALNS)(const DevMesh<REAL>& m, const REAL* x, const REAL* q, const REAL* r, double dt,
-                                  int flux, int bc, double* gk, double* gr, void* stream) {
+                                  int flux, int bc, double* gk, double* gr, double* gz, void* stream) {
   if (m.nblk_w > 0) {
     constexpr int bytes = REALNS::grad_smem_bytes<NORD>();
     if (bytes > 227 * 1024) return int(cudaErrorInvalidConfiguration);
     if (m.nblk_t > 0)
       REALNS::k_wedge_grad<NORD, true><<<m.nblk_w, 32 * (NORD + 1), bytes, cudaStream_t(stream)>>>(m, x, q, r, dt, flux,
-                                                                                                  bc, gk, gr);
+                                                                                                  bc, gk, gr, gz);
     else
       REALNS::k_wedge_grad<NORD, false><<<m.nblk_w, 32 * (NORD + 1), bytes, cudaStream_t(stream)>>>(m, x, q, r, dt, flux,
-                                                                                                   bc, gk, gr);
+                                                                                                   bc, gk, gr, gz);
   }
   return int(cudaGetLastError());
 }

@@ -242,7 +242,8 @@ def test_empty_mesh_and_table_limits():
 
 def test_adjoint_workspace_size():
     """dg_adjoint_bytes: fourteen packed fields plus the FP64 gradient sums of every
-    device element (wedges and tets, padded blocks), computable before dg_bind."""
+    device element (wedges and tets, padded blocks) and five face sums per
+    wedge, computable before dg_bind."""
     m = I.hybrid_mesh(3, 2, 1)
     ctx = dg.dg_mesh_create(m.VX, m.EToV, m.etype)
     try:
@@ -253,7 +254,7 @@ def test_adjoint_workspace_size():
         nw, nt = int((m.etype == 6).sum()) * 3, int((m.etype == 4).sum()) * 3
         def pad(n):
             return (n + 31) // 32 * 32 * 8 + 255 & ~255
-        assert dg.dg_adjoint_bytes(ctx) == 14 * fb + 2 * pad(nw) + 2 * pad(nt)
+        assert dg.dg_adjoint_bytes(ctx) == 14 * fb + 7 * pad(nw) + 2 * pad(nt)
     finally:
         dg.dg_destroy(ctx)
 
