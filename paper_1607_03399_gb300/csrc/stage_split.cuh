@@ -135,9 +135,11 @@ __global__ void __launch_bounds__(64 * (N + 1), 2) k_wedge_stage_split(const Sta
   // 1. prologue: quadrilateral-face fluxes of slice j lifted into this
   //    half's accumulators (a: p or u_y, b: u_x or u_z); the triangle-face
   //    node fluxes spread over all warps
-  real Wa[Nt], Wb[Nt];
+  // accumulators of node i as one packed pair: (p, u_x) for h = 0, (u_y, u_z) for h = 1
+  constexpr int NH = (Nt + 1) / 2;
+  real2 W[Nt];
 #pragma unroll
-  for (int i = 0; i < Nt; ++i) Wa[i] = Wb[i] = real(0);
+  for (int i = 0; i < Nt; ++i) W[i] = dup2(real(0));
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
     const int nbr = qnbr[ed];
@@ -168,28 +170,35 @@ __global__ void __launch_bounds__(64 * (N + 1), 2) k_wedge_stage_split(const Sta
       penalty_flux(dp, dun, tau_p, tau_u, Fp[m], Fu[m]);
     }
     // W += M~_e F, M~_e = (L_e/4)(h_a Mea + h_b Meb) along the edge, identity in t
+    // (Mea, Meb by output pairs)
     const real ca = GEO(G_QCA0 + ed), cbq = GEO(G_QCB0 + ed);
+    constexpr int NQH = (Nq + 1) / 2;
+    real2 gua[NQH], gub[NQH], gpa[NQH], gpb[NQH];
+#pragma unroll
+    for (int hh = 0; hh < NQH; ++hh) gua[hh] = gub[hh] = gpa[hh] = gpb[hh] = dup2(real(0));
+#pragma unroll
+    for (int n = 0; n < Nq; ++n) {
+      const real2 fu2 = dup2(Fu[n]), fp2 = dup2(Fp[n]);
+#pragma unroll
+      for (int hh = 0; hh < NQH; ++hh) {
+        const real2 ea = cpair(O.w.MeaP, Nq, hh, n), eb = cpair(O.w.MebP, Nq, hh, n);
+        gua[hh] = fma2(ea, fu2, gua[hh]);
+        gub[hh] = fma2(eb, fu2, gub[hh]);
+        if (h == 0) {
+          gpa[hh] = fma2(ea, fp2, gpa[hh]);
+          gpb[hh] = fma2(eb, fp2, gpb[hh]);
+        }
+      }
+    }
 #pragma unroll
     for (int m = 0; m < Nq; ++m) {
-      real gua = 0, gub = 0;
-#pragma unroll
-      for (int n = 0; n < Nq; ++n) {
-        gua += O.w.Mea[m * Nq + n] * Fu[n];
-        gub += O.w.Meb[m * Nq + n] * Fu[n];
-      }
-      const real gu = ca * gua + cbq * gub;
+      const real gu = ca * pair_row(gua, m) + cbq * pair_row(gub, m);
       const int i = edge_node(N, ed, m);
       if (h == 0) {
-        real gpa = 0, gpb = 0;
-#pragma unroll
-        for (int n = 0; n < Nq; ++n) {
-          gpa += O.w.Mea[m * Nq + n] * Fp[n];
-          gpb += O.w.Meb[m * Nq + n] * Fp[n];
-        }
-        Wa[i] += ca * gpa + cbq * gpb;
-        Wb[i] += nx * gu;
+        W[i].x += ca * pair_row(gpa, m) + cbq * pair_row(gpb, m);
+        W[i].y += nx * gu;
       } else {
-        Wa[i] += ny * gu;
+        W[i].x += ny * gu;
       }
     }
   }
@@ -242,17 +251,17 @@ __global__ void __launch_bounds__(64 * (N + 1), 2) k_wedge_stage_split(const Sta
       const real nb0 = GEO(G_NB0) * cb, nt0 = GEO(G_NT0) * ct;
 #pragma unroll
       for (int i = 0; i < Nt; ++i) {
-        real dpp = 0, dux = 0, duy = 0, duz = 0;
+        real2 dpu = dup2(real(0)), dvw = dup2(real(0));
 #pragma unroll
         for (int m = 0; m < Nq; ++m) {
           const Q4 v = lds4(sq, m * Nt + i, lane);
-          dpp += dtr[m] * v.p;
-          dux += dtr[m] * v.u;
-          duy += dtr[m] * v.v;
-          duz += dtr[m] * v.w;
+          const real2 d2 = dup2(dtr[m]);
+          dpu = fma2(d2, mk2(v.p, v.u), dpu);
+          dvw = fma2(d2, mk2(v.v, v.w), dvw);
         }
-        Ga[i] = cb * sF[(0 * Nt + i) * kB + lane] + ct * sF[(2 * Nt + i) * kB + lane] - (txJ * dux + tyJ * duy + Aj * duz);
-        Gb[i] = nb0 * sF[(1 * Nt + i) * kB + lane] + nt0 * sF[(3 * Nt + i) * kB + lane] - txJ * dpp;
+        Ga[i] = cb * sF[(0 * Nt + i) * kB + lane] + ct * sF[(2 * Nt + i) * kB + lane] -
+                (txJ * dpu.y + tyJ * dvw.x + Aj * dvw.y);
+        Gb[i] = nb0 * sF[(1 * Nt + i) * kB + lane] + nt0 * sF[(3 * Nt + i) * kB + lane] - txJ * dpu.x;
       }
     } else {
       const real nb1 = GEO(G_NB1) * cb, nt1 = GEO(G_NT1) * ct, nb2 = GEO(G_NB2) * cb, nt2 = GEO(G_NT2) * ct;
@@ -266,17 +275,11 @@ __global__ void __launch_bounds__(64 * (N + 1), 2) k_wedge_stage_split(const Sta
         Gb[i] = nb2 * f1 + nt2 * f3 - Aj * dpp;
       }
     }
+    real2 aa[NH], ab[NH];
+    apply_pairs<Nt, Nt>(O.w.MP, Ga, aa);
+    apply_pairs<Nt, Nt>(O.w.MP, Gb, ab);
 #pragma unroll
-    for (int i = 0; i < Nt; ++i) {
-      real aa = 0, ab = 0;
-#pragma unroll
-      for (int l = 0; l < Nt; ++l) {
-        aa += O.w.M[i * Nt + l] * Ga[l];
-        ab += O.w.M[i * Nt + l] * Gb[l];
-      }
-      Wa[i] += aa;
-      Wb[i] += ab;
-    }
+    for (int i = 0; i < Nt; ++i) W[i] = add2(W[i], mk2(pair_row(aa, i), pair_row(ab, i)));
   }
   // 3. X = (M^{tri,k})^{-1} W for the two right-hand sides: forward and
   //    backward sweeps over the packed factor, row by row
@@ -299,62 +302,60 @@ __global__ void __launch_bounds__(64 * (N + 1), 2) k_wedge_stage_split(const Sta
       real Lr[Nt];
       load_row(i, Lr);
 #pragma unroll
-      for (int k = 0; k < i; ++k) {
-        Wa[i] -= Lr[k] * Wa[k];
-        Wb[i] -= Lr[k] * Wb[k];
-      }
-      Wa[i] *= Lr[i];
-      Wb[i] *= Lr[i];
+      for (int k = 0; k < i; ++k) W[i] = fma2(dup2(-Lr[k]), W[k], W[i]);
+      W[i] = mul2(W[i], dup2(Lr[i]));
     }
 #pragma unroll
     for (int i = Nt - 1; i >= 0; --i) {
       real Lr[Nt];
       load_row(i, Lr);
-      Wa[i] *= Lr[i];
-      Wb[i] *= Lr[i];
+      W[i] = mul2(W[i], dup2(Lr[i]));
 #pragma unroll
-      for (int k = 0; k < i; ++k) {
-        Wa[k] -= Lr[k] * Wa[i];
-        Wb[k] -= Lr[k] * Wb[i];
-      }
+      for (int k = 0; k < i; ++k) W[k] = fma2(dup2(-Lr[k]), W[i], W[k]);
     }
   }
   // 4. strong r, s parts (Lemma 3.1 metric terms): h = 0 div u, h = 1 D_r p,
   //    D_s p, whose d_x p goes to h = 0 through the slice's exchange table
   {
     const real rx = GEO(G_RX), ry = GEO(G_RY), sx = GEO(G_SX), sy = GEO(G_SY);
+    // (D_r, D_s by output pairs, node l of the slice at a time)
     if (h == 0) {
-      real av[Nt], bv[Nt];
+      real2 dv[NH];
+#pragma unroll
+      for (int hh = 0; hh < NH; ++hh) dv[hh] = dup2(real(0));
 #pragma unroll
       for (int l = 0; l < Nt; ++l) {
         const Q4 v = lds4(sq, j * Nt + l, lane);
-        av[l] = rx * v.u + ry * v.v;
-        bv[l] = sx * v.u + sy * v.v;
+        const real2 a2 = dup2(rx * v.u + ry * v.v), b2 = dup2(sx * v.u + sy * v.v);
+#pragma unroll
+        for (int hh = 0; hh < NH; ++hh) {
+          dv[hh] = fma2(cpair(O.w.DrP, Nt, hh, l), a2, dv[hh]);
+          dv[hh] = fma2(cpair(O.w.DsP, Nt, hh, l), b2, dv[hh]);
+        }
       }
 #pragma unroll
-      for (int i = 0; i < Nt; ++i) {
-        real dv = 0;
-#pragma unroll
-        for (int l = 0; l < Nt; ++l) dv += O.w.Dr[i * Nt + l] * av[l] + O.w.Ds[i * Nt + l] * bv[l];
-        Wa[i] -= dv;
-      }
+      for (int i = 0; i < Nt; ++i) W[i].x -= pair_row(dv, i);
       pair_sync();
 #pragma unroll
-      for (int i = 0; i < Nt; ++i) Wb[i] -= sX[((j * Nt) + i) * kB + lane];
+      for (int i = 0; i < Nt; ++i) W[i].y -= sX[((j * Nt) + i) * kB + lane];
     } else {
-      real pv[Nt];
+      real2 pr[NH], ps[NH];
 #pragma unroll
-      for (int l = 0; l < Nt; ++l) pv[l] = sq[(((j * Nt) + l) * kB + lane) * 4];
+      for (int hh = 0; hh < NH; ++hh) pr[hh] = ps[hh] = dup2(real(0));
+#pragma unroll
+      for (int l = 0; l < Nt; ++l) {
+        const real2 p2 = dup2(sq[(((j * Nt) + l) * kB + lane) * 4]);
+#pragma unroll
+        for (int hh = 0; hh < NH; ++hh) {
+          pr[hh] = fma2(cpair(O.w.DrP, Nt, hh, l), p2, pr[hh]);
+          ps[hh] = fma2(cpair(O.w.DsP, Nt, hh, l), p2, ps[hh]);
+        }
+      }
 #pragma unroll
       for (int i = 0; i < Nt; ++i) {
-        real pr = 0, ps = 0;
-#pragma unroll
-        for (int l = 0; l < Nt; ++l) {
-          pr += O.w.Dr[i * Nt + l] * pv[l];
-          ps += O.w.Ds[i * Nt + l] * pv[l];
-        }
-        sX[((j * Nt) + i) * kB + lane] = rx * pr + sx * ps;
-        Wa[i] -= ry * pr + sy * ps;
+        const real pri = pair_row(pr, i), psi = pair_row(ps, i);
+        sX[((j * Nt) + i) * kB + lane] = rx * pri + sx * psi;
+        W[i].x -= ry * pri + sy * psi;
       }
       pair_sync();
     }
@@ -363,41 +364,25 @@ __global__ void __launch_bounds__(64 * (N + 1), 2) k_wedge_stage_split(const Sta
   // 5. point sources (pressure, h = 0) and the fused low-storage Runge-Kutta
   //    update (or the plain right-hand side) of this half's two fields
   const real kappa = M.w_mat[0 * Kp + e], irho = M.w_mat[1 * Kp + e];
-  if (src) add_sources(M, 6, e, j * Nt, Np, *M.clock + A.c_stage * double(A.dt), Wa);
-  const real sa = h == 0 ? kappa : irho;
+  if (src) add_sources(M, 6, e, j * Nt, Np, *M.clock + A.c_stage * double(A.dt), W);
+  const real2 sab = mk2(h == 0 ? kappa : irho, irho);
   if (e < M.Kw) {
 #pragma unroll
     for (int i = 0; i < Nt; ++i) {
       const int n = j * Nt + i;
       const int64_t g = widx<N>(blk, n, lane) + 2 * h;
-      const real ra = sa * Wa[i], rb = irho * Wb[i];
+      const real2 r = mul2(W[i], sab);
       if (rk) {
-        real r0a, r0b, q0a, q0b;
-        if constexpr (sizeof(real) == 4) {
-          const float2 r0 = *reinterpret_cast<const float2*>(resg + g);
-          const float2 q0 = *reinterpret_cast<const float2*>(sq + (n * kB + lane) * 4 + 2 * h);
-          r0a = r0.x, r0b = r0.y, q0a = q0.x, q0b = q0.y;
-        } else {
-          const double2 r0 = *reinterpret_cast<const double2*>(resg + g);
-          const double2 q0 = *reinterpret_cast<const double2*>(sq + (n * kB + lane) * 4 + 2 * h);
-          r0a = r0.x, r0b = r0.y, q0a = q0.x, q0b = q0.y;
-        }
-        const real rra = A.rk_a * r0a + A.dt * ra, rrb = A.rk_a * r0b + A.dt * rb;
-        const real qa = A.rk_g * q0a + A.rk_b * rra, qb = A.rk_g * q0b + A.rk_b * rrb;
-        if constexpr (sizeof(real) == 4) {
-          *reinterpret_cast<float2*>(resg + g) = make_float2(rra, rrb);
-          *reinterpret_cast<float2*>(qout + g) = make_float2(qa, qb);
-          if (A.rhs_out) *reinterpret_cast<float2*>(A.rhs_out + g) = make_float2(ra, rb);
-        } else {
-          *reinterpret_cast<double2*>(resg + g) = make_double2(rra, rrb);
-          *reinterpret_cast<double2*>(qout + g) = make_double2(qa, qb);
-          if (A.rhs_out) *reinterpret_cast<double2*>(A.rhs_out + g) = make_double2(ra, rb);
-        }
+        // res = a res + dt r, q = g q + b res on the packed pair
+        const real2 r0 = *reinterpret_cast<const real2*>(resg + g);
+        const real2 q0 = *reinterpret_cast<const real2*>(sq + (n * kB + lane) * 4 + 2 * h);
+        const real2 rr = fma2(dup2(A.rk_a), r0, mul2(dup2(A.dt), r));
+        const real2 qq = fma2(dup2(A.rk_g), q0, mul2(dup2(A.rk_b), rr));
+        *reinterpret_cast<real2*>(resg + g) = rr;
+        *reinterpret_cast<real2*>(qout + g) = qq;
+        if (A.rhs_out) *reinterpret_cast<real2*>(A.rhs_out + g) = r;
       } else {
-        if constexpr (sizeof(real) == 4)
-          *reinterpret_cast<float2*>(qout + g) = make_float2(ra, rb);
-        else
-          *reinterpret_cast<double2*>(qout + g) = make_double2(ra, rb);
+        *reinterpret_cast<real2*>(qout + g) = r;
       }
     }
   }
