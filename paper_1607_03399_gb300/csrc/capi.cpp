@@ -41,8 +41,12 @@ int upload_ops(int N, bool dbl, const void* p, size_t n, void* s) {
     DGW_SWITCH_N(N, upload_ops_f32, (p, n, s))
   }
 }
-int stage_f32(int N, const StageArgs<float>& a, bool rk, void* s) { DGW_SWITCH_N(N, launch_stage_f32, (a, rk, s)) }
-int stage_f64(int N, const StageArgs<double>& a, bool rk, void* s) { DGW_SWITCH_N(N, launch_stage_f64, (a, rk, s)) }
+int stage_f32(int N, const StageArgs<float>& a, bool rk, void* s, void* st, void* ef, void* ej) {
+  DGW_SWITCH_N(N, launch_stage_f32, (a, rk, s, st, ef, ej))
+}
+int stage_f64(int N, const StageArgs<double>& a, bool rk, void* s, void* st, void* ef, void* ej) {
+  DGW_SWITCH_N(N, launch_stage_f64, (a, rk, s, st, ef, ej))
+}
 int pack_f32(int N, const DevMesh<float>& m, const float* c, float* p, bool u, void* s) {
   DGW_SWITCH_N(N, launch_pack_f32, (m, c, p, u, s))
 }
@@ -150,6 +154,7 @@ struct dg_ctx {
   int tuned_bpc = 0;
   bool tuned_onthefly = false;
   int tuned_split = 0;  // wedge stage split over field pairs: 1 yes, -1 no, 0 the default for the order
+  bool tri_far = false;  // some wedge's triangle-face neighbour is a tet or lies in another 32-block
   // adjoint workspace (caller-owned): mu_Q, two stage-input buffers, residual,
   // forward stage states Q_1..Q_4 and a scratch output, stage right-hand sides
   // r_1..r_5, then the kappa and rho gradients (doubles per device wedge)
@@ -174,6 +179,10 @@ struct dg_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  // meshes with both element types: the tet stage's stream, forked from and
+  // joined back into the launching stream by these events
+  cudaStream_t tet_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   void* d_mesh = nullptr;
   void* d_q[2] = {nullptr, nullptr};
   void* d_res = nullptr;
@@ -198,6 +207,23 @@ namespace {
 
 int cuda_fail(dg_ctx* c, cudaError_t e, const char* what) {
   return c->fail(DG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Whether some device wedge's triangle-face neighbour is a tet or lies in
+// another 32-wedge block (a column that straddles two blocks, the wedge/tet
+// interface, shot-inner layouts): then the wedge stage requests those traces
+// before its quadrilateral faces.  From the neighbour tables of a filled blob
+// (w_nbr and w_code are [face][padded device wedge]).
+bool triangle_neighbours_far(const std::vector<unsigned char>& blob, size_t off_nbr, size_t off_code, int64_t VKw) {
+  const int64_t Kwp = (VKw + kB - 1) / kB * kB;
+  const int* wn = reinterpret_cast<const int*>(blob.data() + off_nbr);
+  const int* wc = reinterpret_cast<const int*>(blob.data() + off_code);
+  for (int f = 0; f < 2; ++f)
+    for (int64_t v = 0; v < VKw; ++v) {
+      const int n = wn[f * Kwp + v];
+      if (n >= 0 && ((wc[f * Kwp + v] & kCodeTet) != 0 || (n / kB) != (v / kB))) return true;
+    }
+  return false;
 }
 
 int64_t nblk(int64_t K) { return (K + kB - 1) / kB; }
@@ -749,7 +775,7 @@ int launch_stage(dg_ctx* c, const void* q_in, void* q_out, void* res, double a, 
     A.rk_g = x.g;
     A.rhs_out = static_cast<double*>(x.rhs_out);
     if (x.no_sources) A.m.nsrc = 0;
-    rc = stage_f64(c->N, A, rk, s);
+    rc = stage_f64(c->N, A, rk, s, c->tet_stream, c->ev_fork, c->ev_join);
   } else {
     StageArgs<float> A;
     A.m = c->m32;
@@ -766,10 +792,11 @@ int launch_stage(dg_ctx* c, const void* q_in, void* q_out, void* res, double a, 
     if (c->tuned_onthefly) A.m.w_fac = nullptr;
     A.op = c->op;
     A.split = c->tuned_split;
+    A.tri_far = c->tri_far ? 1 : 0;
     A.rk_g = float(x.g);
     A.rhs_out = static_cast<float*>(x.rhs_out);
     if (x.no_sources) A.m.nsrc = 0;
-    rc = stage_f32(c->N, A, rk, s);
+    rc = stage_f32(c->N, A, rk, s, c->tet_stream, c->ev_fork, c->ev_join);
   }
   if (rc) return cuda_fail(c, cudaError_t(rc), "stage launch");
   return DG_OK;
@@ -1367,6 +1394,7 @@ int dg_bind(dg_ctx* c, void* d_mesh, void* d_q0, void* d_q1, void* d_res, void* 
   c->mesh_bytes = L.total;
   c->wops_off = L.wops;
   c->field_bytes = field_bytes_of(c);
+  c->tri_far = triangle_neighbours_far(blob, L.w_nbr, L.w_code, vKw(c));
   e = cudaMemcpyAsync(d_mesh, blob.data(), blob.size(), cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "mesh upload");
   for (void* p : {d_q0, d_q1, d_res}) {
@@ -1380,6 +1408,12 @@ int dg_bind(dg_ctx* c, void* d_mesh, void* d_q0, void* d_q1, void* d_res, void* 
   if (rc) return rc;
   e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(c, e, "capture stream");
+  if (vKw(c) > 0 && vKt(c) > 0) {
+    e = cudaStreamCreateWithFlags(&c->tet_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tet stream");
+  }
   c->bound = true;
   c->cur = 0;
   c->t = 0.0;
@@ -1608,6 +1642,7 @@ int relayout(dg_ctx* c) {
     fill_blob<float>(c, L, blob);
     fill_devmesh<float>(c, L, c->m32);
   }
+  c->tri_far = triangle_neighbours_far(blob, L.w_nbr, L.w_code, vKw(c));
   drop_graphs(c);
   cudaError_t e = cudaMemcpyAsync(c->d_mesh, blob.data(), blob.size(), cudaMemcpyHostToDevice, c->stream);
   for (void* p : {c->d_q[0], c->d_q[1], c->d_res})
@@ -2156,6 +2191,9 @@ void dg_destroy(dg_ctx* c) {
   DeviceGuard device_guard(c);
   drop_graphs(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->tet_stream) cudaStreamDestroy(c->tet_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
 }
 

@@ -153,6 +153,7 @@ struct StageArgs {
   int wedge_bpc = 0;            // wedge blocks per CTA: 0 = the default for the mass mode
   int op = 0;                   // kOpFFMA, or a tensor-core variant (FP32 fields)
   int split = 0;                // wedge stage split over field pairs: 1 yes, otherwise no
+  int tri_far = 0;              // some wedge's triangle-face neighbour is a tet or in another block
 };
 
 enum : int { kErrTimeout = 1, kErrNonfinite = 2 };
@@ -181,7 +182,8 @@ __host__ __device__ constexpr int tile_at(int r, int c) { return r * kTP + (c ^ 
 // all return 0 or a cudaError_t value.
 #define DGW_DECLARE_LAUNCHERS(P, T, N)                                                              \
   int upload_ops_##P##n##N(const void* host_ops, size_t bytes, void* stream);                      \
-  int launch_stage_##P##n##N(const StageArgs<T>& a, bool rk, void* stream);                        \
+  int launch_stage_##P##n##N(const StageArgs<T>& a, bool rk, void* stream, void* stream_t, void* ev_fork, \
+                             void* ev_join);                                                       \
   int launch_pack_##P##n##N(const DevMesh<T>& m, const T* canon, T* packed, bool unpack, void* s); \
   int launch_energy_##P##n##N(const DevMesh<T>& m, const T* q, void* stream);                      \
   int launch_clock_##P##n##N(double* clock, double dt, void* stream);                              \

@@ -197,10 +197,15 @@ __device__ __forceinline__ void apply_pairs(const real* XP, const real (&x)[NC],
 // row i of a pair-accumulated result
 __device__ __forceinline__ real pair_row(const real2* acc, int i) { return (i & 1) ? acc[i >> 1].y : acc[i >> 1].x; }
 
+// a * b + c rounded once (an explicit FMA: the same rounding wherever the
+// compiler places the expression, so kernel variants that differ only in when
+// they load the operands give the same bits)
+__device__ __forceinline__ float fmar(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmar(double a, double b, double c) { return fma(a, b, c); }
 // Penalty fluxes of eq. (1): F_p = 1/2 (tau_p [p] - [u_n]), F_u = 1/2 (tau_u [u_n] - [p]).
 __device__ __forceinline__ void penalty_flux(real dp, real dun, real tau_p, real tau_u, real& Fp, real& Fu) {
-  Fp = real(0.5) * (tau_p * dp - dun);
-  Fu = real(0.5) * (tau_u * dun - dp);
+  Fp = real(0.5) * fmar(tau_p, dp, -dun);
+  Fu = real(0.5) * fmar(tau_u, dun, -dp);
 }
 // Boundary ghosts: Dirichlet p+ = -p-, u+ = u-  -> [p] = -2p, [u_n] = 0;
 // rigid p+ = p-, u+ = u- - 2 u_n n             -> [p] = 0, [u_n] = -2 u_n.
@@ -583,7 +588,10 @@ __device__ __forceinline__ void wedge_geometry(real* sG, int lane) {
   for (int i = 0; i < NG; ++i) sG[i * kB + lane] = G[i];
 }
 
-template <int N, int BPC, int OP = kOpFFMA>
+// TF: the neighbour nodes of the triangle-face fluxes are requested before the
+// quadrilateral faces (meshes where some of them are tets or lie in another
+// block: StageArgs::tri_far); otherwise each is read where its flux is formed
+template <int N, int BPC, int OP = kOpFFMA, bool TF = false>
 __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>())
     k_wedge_stage(const StageArgs<real> A, bool rk) {
   constexpr int Nt = nt_of(N), Nq = N + 1, Np = Nt * Nq;
@@ -746,6 +754,35 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
   real2 W01[Nt], W23[Nt];
 #pragma unroll
   for (int i = 0; i < Nt; ++i) W01[i] = W23[i] = dup2(real(0));
+  // the neighbour node of triangle-face flux t of this warp (round-robin over
+  // the warps, bottom then top): a tet's face node, or a wedge's bottom/top
+  // node in this block's slab or in global memory; a boundary face reads its
+  // own node.  With TF all are requested before the quadrilateral faces, whose
+  // work covers the latency of the global ones.
+  constexpr int NTT = (2 * Nt + Nq - 1) / Nq;
+  auto tri_nbr_node = [&](int t) {
+    const int idx = j + t * Nq;
+    const int fb = idx >= Nt ? 1 : 0;
+    const int k = idx - fb * Nt;
+    const int nbr = tnbr[fb];
+    const int code = tcode[fb];
+    const bool bnd = nbr < 0;
+    const bool ntet = !bnd && (code & kCodeTet) != 0;
+    const int nf = bnd ? fb : (code >> 4) & 3;
+    const int nk = bnd ? k : O.tab.tri_perm[code & 15][k];
+    const int nbe = bnd ? e : nbr;
+    const int node = ntet ? O.tab.tet_face[nf][nk] : (nf ? N * Nt : 0) + nk;
+    const bool inblk = !ntet && (nbe >> 5) == blk;
+    // explicit shared or global loads (a generic load would wait on the long scoreboard either way)
+    return inblk ? lds4(sq, node, nbe & 31)
+                 : ldg4(qin, ntet ? tidx<N>(M.tet_off, nbe >> 5, node, nbe & 31) : widx<N>(nbe >> 5, node, nbe & 31));
+  };
+  Q4 tnv[TF ? NTT : 1];
+  if constexpr (TF) {
+#pragma unroll
+    for (int t = 0; t < NTT; ++t)
+      if (j + t * Nq < 2 * Nt) tnv[t] = tri_nbr_node(t);
+  }
   // neighbour traces of quadrilateral faces whose neighbour lies in this block
   // (or, on a boundary face, the element's own trace, which the ghost state
   // then replaces) from the shared slab; the others were requested above (or,
@@ -815,33 +852,25 @@ __global__ void __launch_bounds__(32 * (N + 1) * BPC, wedge_min_ctas<N, BPC, OP>
   }
   // triangle-face node fluxes (bottom then top), spread round-robin over the warps
 #pragma unroll
-  for (int t = 0; t < (2 * Nt + Nq - 1) / Nq; ++t) {
+  for (int t = 0; t < NTT; ++t) {
     const int idx = j + t * Nq;
     if (idx >= 2 * Nt) break;
     const int fb = idx >= Nt ? 1 : 0;
     const int k = idx - fb * Nt;
     const real nn0 = GEO(fb ? G_NT0 : G_NB0), nn1 = GEO(fb ? G_NT1 : G_NB1), nn2 = GEO(fb ? G_NT2 : G_NB2);
     const int nbr = tnbr[fb];
-    const int code = tcode[fb];
     const Q4 o = lds4(sq, (fb ? N * Nt : 0) + k, lane);
-    const real unM = nn0 * o.u + nn1 * o.v + nn2 * o.w;
+    const real unM = fmar(nn2, o.w, fmar(nn1, o.v, nn0 * o.u));
     real tau_p, tau_u, bdp, bdun;
     taus(A.flux, zM, fb ? zPt[1] : zPt[0], tau_p, tau_u);
     boundary_jumps(A.bc, o.p, unM, bdp, bdun);
-    // neighbour node: a tet's face node, or a wedge's bottom/top node (in this
-    // block's slab or in global memory); a boundary face reads its own node
     const bool bnd = nbr < 0;
-    const bool ntet = !bnd && (code & kCodeTet) != 0;
-    const int nf = bnd ? fb : (code >> 4) & 3;
-    const int nk = bnd ? k : O.tab.tri_perm[code & 15][k];
-    const int nbe = bnd ? e : nbr;
-    const int node = ntet ? O.tab.tet_face[nf][nk] : (nf ? N * Nt : 0) + nk;
-    const bool inblk = !ntet && (nbe >> 5) == blk;
-    // explicit shared or global loads (a generic load would wait on the long scoreboard either way)
-    const Q4 nv = inblk ? lds4(sq, node, nbe & 31)
-                        : ldg4(qin, ntet ? tidx<N>(M.tet_off, nbe >> 5, node, nbe & 31) : widx<N>(nbe >> 5, node, nbe & 31));
+    Q4 nv;
+    if constexpr (TF) nv = tnv[t];
+    else nv = tri_nbr_node(t);
+    // (explicit FMAs: both variants of the neighbour load give the same bits)
     const real dp = bnd ? bdp : nv.p - o.p;
-    const real dun = bnd ? bdun : nn0 * nv.u + nn1 * nv.v + nn2 * nv.w - unM;
+    const real dun = bnd ? bdun : fmar(nn2, nv.w, fmar(nn1, nv.v, nn0 * nv.u)) - unM;
     real Fp, Fu;
     penalty_flux(dp, dun, tau_p, tau_u, Fp, Fu);
     sF[((2 * fb + 0) * Nt + k) * kB + lane] = Fp;
@@ -1613,6 +1642,9 @@ int prepare_n() {
   constexpr int b2 = wedge_bpc_onthefly<N>();
   cudaError_t err = cudaFuncSetAttribute(k_wedge_stage<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          wedge_smem_bytes<N, 1>());
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_wedge_stage<N, 1, kOpFFMA, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               wedge_smem_bytes<N, 1>());
   if constexpr (sizeof(real) == 4) {
     if (err == cudaSuccess)
       err = cudaFuncSetAttribute(k_wedge_stage_split<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1650,7 +1682,22 @@ void launch_op(const StageArgs<real>& a, bool rk, cudaStream_t s) {
   k_wedge_stage<N, 1, OP><<<a.m.nblk_w, 32 * (N + 1), wedge_smem_bytes<N, 1, OP>(), s>>>(a, rk);
 }
 template <int N>
-int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s) {
+int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s, cudaStream_t st, cudaEvent_t ev_fork,
+                   cudaEvent_t ev_join) {
+  // wedges and tets of one stage are independent (each reads the stage input,
+  // writes only its own elements): with a second stream the tet stage runs on
+  // it, forked from and joined back into s (also inside a graph capture), so
+  // the two kernels share the GPU instead of running back to back
+  const bool fork = a.m.nblk_w > 0 && a.m.nblk_t > 0 && st != nullptr && ev_fork != nullptr && ev_join != nullptr;
+  if (fork) {
+    cudaError_t err = cudaEventRecord(ev_fork, s);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(st, ev_fork, 0);
+    if (err != cudaSuccess) return int(err);
+    k_tet_stage<N><<<a.m.nblk_t, 128, tet_smem_bytes<N>(), st>>>(a, rk);
+    err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaEventRecord(ev_join, st);
+    if (err != cudaSuccess) return int(err);
+  }
   if (a.m.nblk_w > 0) {
     constexpr int b2 = wedge_bpc_onthefly<N>();
     const int want = a.wedge_bpc > 0 ? a.wedge_bpc : (a.m.w_fac != nullptr ? 1 : b2);
@@ -1671,13 +1718,16 @@ int launch_stage_n(const StageArgs<real>& a, bool rk, cudaStream_t s) {
       else if (a.op == kOpBF16) launch_op<N, kOpBF16>(a, rk, s);
     }
     if (done) {
-    } else if (want == 1 || b2 == 1)
+    } else if ((want == 1 || b2 == 1) && a.tri_far)
+      k_wedge_stage<N, 1, kOpFFMA, true><<<a.m.nblk_w, 32 * (N + 1), wedge_smem_bytes<N, 1>(), s>>>(a, rk);
+    else if (want == 1 || b2 == 1)
       k_wedge_stage<N, 1><<<a.m.nblk_w, 32 * (N + 1), wedge_smem_bytes<N, 1>(), s>>>(a, rk);
     else
       k_wedge_stage<N, b2><<<(a.m.nblk_w + b2 - 1) / b2, 32 * (N + 1) * b2, wedge_smem_bytes<N, b2>(), s>>>(a, rk);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return int(err);
   }
+  if (fork) return int(cudaStreamWaitEvent(s, ev_join, 0));
   if (a.m.nblk_t > 0) {
     k_tet_stage<N><<<a.m.nblk_t, 128, tet_smem_bytes<N>(), s>>>(a, rk);
     cudaError_t err = cudaGetLastError();
@@ -1717,8 +1767,10 @@ int DGW_CAT(upload_ops_, REALNS)(const void* host_ops, size_t bytes, void* strea
   if (rc) return rc;
   return int(cudaMemcpyToSymbolAsync(REALNS::c_ops, host_ops, bytes, 0, cudaMemcpyHostToDevice, cudaStream_t(stream)));
 }
-int DGW_CAT(launch_stage_, REALNS)(const StageArgs<REAL>& a, bool rk, void* stream) {
-  return REALNS::launch_stage_n<NORD>(a, rk, cudaStream_t(stream));
+int DGW_CAT(launch_stage_, REALNS)(const StageArgs<REAL>& a, bool rk, void* stream, void* stream_t, void* ev_fork,
+                                   void* ev_join) {
+  return REALNS::launch_stage_n<NORD>(a, rk, cudaStream_t(stream), cudaStream_t(stream_t), cudaEvent_t(ev_fork),
+                                      cudaEvent_t(ev_join));
 }
 int DGW_CAT(launch_pack_, REALNS)(const DevMesh<REAL>& m, const REAL* canon, REAL* packed, bool unpack, void* stream) {
   return REALNS::launch_pack_n<NORD>(m, canon, packed, unpack, cudaStream_t(stream));
