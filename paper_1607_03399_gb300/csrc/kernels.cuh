@@ -462,15 +462,19 @@ enum WGeo : int {
   G_TX0, G_TX1, G_TY0, G_TY1, G_STAGE, G_J0 = G_STAGE, G_J1, G_J2, G_COUNT
 };
 
-// Residual slab staged in shared memory by the bulk copy (N <= 3).  At N = 4
-// the staged slab measured slower (77 KB of copies per block in flight at two
-// CTAs per SM), so there the residual is read from global memory at the
-// update.  With tensor-core applies the operand tiles (Nq x Nt x 128 reals,
-// the size of the residual slab) share the residual slab's space: the
-// residual is copied in once the weak-form accumulation has released them.
+// Residual slab staged in shared memory by the bulk copy (FP32 up to N = 4,
+// FP64 up to N = 3), so that the update reads it there instead of one
+// dependent global load per node at the end of the kernel.  At N = 4 the
+// stage runs two CTAs per SM (registers), and 103 KB of shared memory per CTA
+// still fits two: with the packed-pair arithmetic the staged slab measured
+// 1075 -> 820 us per stage on 524,288 wedges (before it, with the scalar
+// arithmetic, it had measured slower).  With tensor-core applies the operand
+// tiles (Nq x Nt x 128 reals, the size of the residual slab) share the
+// residual slab's space: the residual is copied in once the weak-form
+// accumulation has released them.
 template <int N, int OP = kOpFFMA>
 __host__ __device__ constexpr bool stage_res() {
-  return N <= 3;
+  return sizeof(real) == 4 ? N <= 4 : N <= 3;
 }
 
 template <int N, int OP = kOpFFMA>
