@@ -1616,7 +1616,8 @@ int dg_set_launch_variant(dg_ctx* c, int variant) {
   if (!c) return DG_ERR_ARG;
   const int bpc = (variant >> 1) & 3;
   const bool onthefly = (variant & 1) != 0, split = (variant & 8) != 0;
-  if ((variant & ~11) != 0 || bpc < 1 || (bpc == 2 && !(c->prec == DG_F32 && c->N == 3)))
+  // bits: 0 factor recomputed, 1-2 blocks per CTA (1 or 2), 3 split stage
+  if ((variant & ~15) != 0 || bpc < 1 || bpc > 2 || (bpc == 2 && !(c->prec == DG_F32 && c->N == 3)))
     return c->fail(DG_ERR_ARG, "unknown launch variant");
   if (split && (onthefly || bpc != 1 || c->prec != DG_F32 || c->mass != DG_MASS_STORED || c->op != DG_OPS_FP32))
     return c->fail(DG_ERR_ARG, "the split stage needs FP32 fields and applies, the stored factor, one block per CTA");

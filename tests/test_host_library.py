@@ -352,3 +352,21 @@ def test_order_5_limits():
         assert dg.dg_num_nodes(ctx)[0] == m.K * 6 * 21
     finally:
         dg.dg_destroy(ctx)
+
+
+def test_launch_variant_encoding():
+    """dg_set_launch_variant takes the encoding dg_autotune reports: bit 0 the
+    factor recomputed, bits 1-2 blocks per CTA (1, or 2 for FP32 at N = 3),
+    bit 3 the field-pair split stage (stored factor, one block per CTA)."""
+    m = I.cube_wavy_mesh(2, 1, 0.0)
+    ctx = dg.dg_mesh_create(m.VX, m.EToV, m.etype)
+    try:
+        dg.dg_set_order(ctx, 3)
+        for v in (2, 3, 4, 5, 10):
+            dg.dg_set_launch_variant(ctx, v)
+        for v in (0, 1, 6, 7, 11, 12, 16, 18):
+            _expect_error(dg.DG_ERR_ARG, lambda v=v: dg.dg_set_launch_variant(ctx, v))
+        dg.dg_set_order(ctx, 4)
+        _expect_error(dg.DG_ERR_ARG, lambda: dg.dg_set_launch_variant(ctx, 4))
+    finally:
+        dg.dg_destroy(ctx)
