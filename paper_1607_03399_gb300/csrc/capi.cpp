@@ -160,6 +160,10 @@ struct dg_ctx {
   // r_1..r_5, then the kappa and rho gradients (doubles per device wedge)
   unsigned char* adj = nullptr;
   int adj_x = 0;
+  // the gradient launches of the reverse sweep run on their own stream beside
+  // the adjoint stage of the same Runge-Kutta stage (fork and join events)
+  cudaStream_t grad_stream = nullptr;
+  cudaEvent_t ev_gfork = nullptr, ev_gjoin = nullptr;
   // point sources (pressure equation)
   struct Source {
     int64_t elem;
@@ -1830,6 +1834,12 @@ int dg_adjoint_bind(dg_ctx* c, void* d_work) {
     return c->fail(DG_ERR_ORDER, "the adjoint at N = 5 needs DG_F32 (the FP64 gradient kernel exceeds shared memory)");
   DeviceGuard device_guard(c);
   if (device_guard.err != cudaSuccess) return cuda_fail(c, device_guard.err, "set device");
+  if (!c->grad_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->grad_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_gfork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_gjoin, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(c, e, "gradient stream");
+  }
   c->adj = static_cast<unsigned char*>(d_work);
   return dg_adjoint_reset(c);
 }
@@ -1875,27 +1885,40 @@ int adjoint_reverse_stages(dg_ctx* c, double dt, const void* const* Q, const voi
   for (int st = 4; st >= 0 && rc == DG_OK; --st) {
     void* xin = adj_field(c, c->adj_x);
     void* xout = adj_field(c, c->adj_x == kAdjX0 ? kAdjX1 : kAdjX0);
+    // the gradient terms of stage st read x (= xin), Q[st] and R[st]; the
+    // adjoint stage reads xin and writes xout and mu_Q: the two run side by
+    // side, the gradient on its own stream, joined before the next stage
+    // overwrites xin
+    cudaStream_t gs = c->grad_stream ? c->grad_stream : c->stream;
+    if (gs != c->stream) {
+      cudaError_t e = cudaEventRecord(c->ev_gfork, c->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(gs, c->ev_gfork, 0);
+      if (e != cudaSuccess) return cuda_fail(c, e, "gradient fork");
+    }
     int lr;
     if (c->prec == DG_F64)
       lr = grad_f64(c->N, c->m64, static_cast<const double*>(xin), static_cast<const double*>(Q[st]),
-                    static_cast<const double*>(R[st]), dt, c->flux, c->bc, adj_gk(c), adj_gr(c), adj_gz(c),
-                    c->stream);
+                    static_cast<const double*>(R[st]), dt, c->flux, c->bc, adj_gk(c), adj_gr(c), adj_gz(c), gs);
     else
       lr = grad_f32(c->N, c->m32, static_cast<const float*>(xin), static_cast<const float*>(Q[st]),
-                    static_cast<const float*>(R[st]), dt, c->flux, c->bc, adj_gk(c), adj_gr(c), adj_gz(c),
-                    c->stream);
+                    static_cast<const float*>(R[st]), dt, c->flux, c->bc, adj_gk(c), adj_gr(c), adj_gz(c), gs);
     if (lr) return cuda_fail(c, cudaError_t(lr), "gradient launch");
     if (c->prec == DG_F64)
       lr = tgrad_f64(c->N, c->m64, static_cast<const double*>(xin), static_cast<const double*>(Q[st]),
-                     static_cast<const double*>(R[st]), dt, c->flux, c->bc, adj_tgk(c), adj_tgr(c), c->stream);
+                     static_cast<const double*>(R[st]), dt, c->flux, c->bc, adj_tgk(c), adj_tgr(c), gs);
     else
       lr = tgrad_f32(c->N, c->m32, static_cast<const float*>(xin), static_cast<const float*>(Q[st]),
-                     static_cast<const float*>(R[st]), dt, c->flux, c->bc, adj_tgk(c), adj_tgr(c), c->stream);
+                     static_cast<const float*>(R[st]), dt, c->flux, c->bc, adj_tgk(c), adj_tgr(c), gs);
     if (lr) return cuda_fail(c, cudaError_t(lr), "tet gradient launch");
     StageExtra x;
     x.g = kLSRK_A[st];
     x.no_sources = true;
     rc = launch_stage(c, xin, xout, adj_field(c, kAdjMuq), 1.0, kLSRK_B[(st + 4) % 5], dt, true, c->stream, 0.0, x);
+    if (gs != c->stream) {
+      cudaError_t e = cudaEventRecord(c->ev_gjoin, gs);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_gjoin, 0);
+      if (e != cudaSuccess && rc == DG_OK) rc = cuda_fail(c, e, "gradient join");
+    }
     c->adj_x = c->adj_x == kAdjX0 ? kAdjX1 : kAdjX0;
   }
   return rc;
@@ -2193,6 +2216,9 @@ void dg_destroy(dg_ctx* c) {
   drop_graphs(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->tet_stream) cudaStreamDestroy(c->tet_stream);
+  if (c->grad_stream) cudaStreamDestroy(c->grad_stream);
+  if (c->ev_gfork) cudaEventDestroy(c->ev_gfork);
+  if (c->ev_gjoin) cudaEventDestroy(c->ev_gjoin);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
