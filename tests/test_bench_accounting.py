@@ -23,8 +23,9 @@ def test_method_minimum_bytes_per_dof(N, per_dof):
     assert kb - a == K * (100 + 4 * nt * (nt + 1) // 2 - 64)
 
 
-def test_flop_count_is_of_the_survey_size():
-    # about 94-105 flop per field-DOF at N = 3 and 133-150 at N = 4 (in-stage factor)
+def test_flop_count_is_of_the_expected_size():
+    # about 94-105 flop per field-DOF at N = 3 and 133-150 at N = 4 (in-stage factor):
+    # D_t, M^tri on four vectors, two triangular sweeps, D_r/D_s, faces and update
     f3 = bench._flops_per_wedge(3, "onthefly") / (4 * 40)
     f4 = bench._flops_per_wedge(4, "onthefly") / (4 * 75)
     assert 90 < f3 < 120 and 125 < f4 < 170
