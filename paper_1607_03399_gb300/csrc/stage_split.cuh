@@ -9,9 +9,10 @@
 // weak-form accumulators of two fields only (2 Nt instead of 4 Nt), so twice
 // the warps can be resident where the one-thread-per-slice kernel is limited
 // by registers (N = 4).  A launch variant of dg_autotune: at N = 4 on the
-// 524,288-wedge workload it measured 1403 us per stage against 1302 us for
-// the one-thread form (96 registers with spills, duplicated face gathers), so
-// it is not the default.  Work split:
+// 524,288-wedge workload, both on packed pairs, it measured 1248 us per stage
+// against 1061 us for the one-thread form (96 registers with spills, duplicated
+// face gathers; the one-thread form has since staged its residual slab too,
+// 810 us), so it is not the default.  Work split:
 //   fluxes: both halves form the quadrilateral-face jumps of their slice
 //     (the same neighbour traces); h = 0 lifts F_p and n_x F_u, h = 1 n_y F_u;
 //     the triangle-face node fluxes are spread over all warps;
