@@ -305,10 +305,6 @@ int ensure_ops(dg_ctx* c) {
 }
 
 // ----------------------------------------------------------------- geometry helpers
-void wedge_face_vertex_list(const dg_ctx* c, int64_t k, int f, int64_t* out) {
-  for (int i = 0; i < (f < 2 ? 3 : 4); ++i) out[i] = c->EToV[k * 6 + kWedgeFaceVerts[f][i]];
-}
-
 int nfaces_of(uint8_t t) { return t == DG_WEDGE ? 5 : 4; }
 
 // vertex list (3 ids) of a triangle face in that element's face vertex order
